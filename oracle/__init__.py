@@ -1,0 +1,392 @@
+"""FP64 CPU oracle for SMC with a ChEES-HMC proposal (arXiv 2504.02627).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The oracle is plain C
+(``oracle/*.c``) compiled to ``liboracle.so`` and wrapped here with ctypes; it
+shares no code with the CUDA library.  Arrays are numpy, particle-major
+``[N, D]`` (particle j's coordinates contiguous).
+
+Each wrapper names the passage of the paper it follows; the pins that fix each
+function independently live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["rng.c", "targets.c", "hmc.c", "weights.c", "chees.c", "smc.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
+TAG_INIT, TAG_MOM, TAG_RESAMPLE, TAG_MH = 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (FP contraction off: identical bits on
+    x86-64 and aarch64).  OpenMP is used when the compiler has it."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        t = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= t for s in srcs):
+            return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"]
+    cs = [os.path.join(_HERE, s) for s in _SOURCES]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp"] + cs + ["-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + cs + ["-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Target(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("D", C.c_int64), ("n", C.c_int64),
+                ("X", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double)), ("P", C.POINTER(C.c_double)),
+                ("c", C.c_double), ("hyper", C.c_double * 4)]
+
+
+class Config(C.Structure):
+    _fields_ = [("n_particles", C.c_int64), ("n_iters", C.c_int64), ("n_warmup", C.c_int64),
+                ("step_size", C.c_double), ("traj_len0", C.c_double),
+                ("max_steps", C.c_int32), ("ess_frac", C.c_double), ("seed", C.c_uint64),
+                ("jitter", C.c_int32), ("accept_reject", C.c_int32), ("adapt", C.c_int32),
+                ("chees_initial_p", C.c_int32), ("adam_lr", C.c_double),
+                ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
+                ("init_scale", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ess", C.c_double), ("ess_pre", C.c_double), ("log_z_inc", C.c_double),
+                ("mean_alpha", C.c_double), ("traj_len", C.c_double),
+                ("grad_evals", C.c_int64), ("steps_min", C.c_int32),
+                ("steps_max", C.c_int32), ("resampled", C.c_int32), ("pad", C.c_int32)]
+
+
+class CheesState(C.Structure):
+    _fields_ = [("log_L", C.c_double), ("m", C.c_double), ("v", C.c_double),
+                ("t", C.c_int32), ("Lbar", C.c_double)]
+
+
+_DP = C.POINTER(C.c_double)
+_I32P = C.POINTER(C.c_int32)
+_U64P = C.POINTER(C.c_uint64)
+
+
+class IterIO(C.Structure):
+    _fields_ = [("theta", _DP), ("grad", _DP), ("logpi", _DP), ("logw", _DP),
+                ("chees", C.POINTER(CheesState)), ("log_z", _DP),
+                ("ancestors", _I32P), ("steps", _I32P), ("p0", _DP), ("p1", _DP),
+                ("dH", _DP), ("alpha", _DP)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.oracle_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_uint32)]
+        L.oracle_u01.argtypes = [C.c_uint32, C.c_uint32]
+        L.oracle_u01.restype = C.c_double
+        L.oracle_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, _DP]
+        L.oracle_resample_r64.argtypes = [C.c_uint64, C.c_uint32]
+        L.oracle_resample_r64.restype = C.c_uint64
+        L.oracle_halton2.argtypes = [C.c_uint32]
+        L.oracle_halton2.restype = C.c_double
+        L.oracle_step_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
+        L.oracle_step_count.restype = C.c_int32
+        L.oracle_logpi.argtypes = [C.POINTER(Target), _DP, _DP]
+        L.oracle_logpi.restype = C.c_double
+        L.oracle_hamiltonian.argtypes = [_DP, C.c_int64, C.c_double]
+        L.oracle_hamiltonian.restype = C.c_double
+        L.oracle_leapfrog.argtypes = [C.POINTER(Target), _DP, _DP, _DP, _DP, C.c_double, C.c_int32]
+        L.oracle_normalise.argtypes = [_DP, C.c_int64, _DP, _DP, _DP]
+        L.oracle_quantise.argtypes = [_DP, C.c_int64, _U64P]
+        L.oracle_quantise.restype = C.c_int32
+        L.oracle_systematic.argtypes = [_U64P, C.c_int64, C.c_uint64, _I32P]
+        L.oracle_systematic.restype = C.c_uint64
+        L.oracle_multinomial.argtypes = [_U64P, C.c_int64, _U64P, _I32P]
+        L.oracle_chees_gradient.argtypes = [_DP, _DP, _DP, _DP, _DP, C.c_int64, C.c_int64, _DP, _DP]
+        L.oracle_chees_gradient.restype = C.c_int
+        L.oracle_chees_adam.argtypes = [C.POINTER(CheesState), C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_int32]
+        L.oracle_smc_init.argtypes = [C.POINTER(Target), C.POINTER(Config), _DP, _DP, _DP, _DP, C.c_int32]
+        L.oracle_smc_init.restype = C.c_double
+        L.oracle_smc_iteration.argtypes = [C.POINTER(Target), C.POINTER(Config), C.c_int64,
+                                           C.POINTER(IterIO), C.POINTER(Stats), C.c_int32]
+        L.oracle_smc_iteration.restype = C.c_int
+        L.oracle_smc_run.argtypes = [C.POINTER(Target), C.POINTER(Config), _DP, _DP, _DP,
+                                     C.POINTER(Stats), C.c_int32]
+        L.oracle_smc_run.restype = C.c_int
+        L.oracle_moments.argtypes = [_DP, _DP, C.c_int64, C.c_int64, _DP, _DP]
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- targets
+class TargetSpec:
+    """Owns the numpy arrays behind an ``oracle_target`` struct (Sec. 2)."""
+
+    def __init__(self, kind, D, n=0, X=None, y=None, mu=None, P=None, c=0.0, hyper=()):
+        self.kind, self.D, self.n = int(kind), int(D), int(n)
+        self.X = None if X is None else _f64(X)
+        self.y = None if y is None else _f64(y)
+        self.mu = None if mu is None else _f64(mu)
+        self.P = None if P is None else _f64(P)
+        h = list(hyper) + [0.0] * (4 - len(hyper))
+        self.struct = Target(self.kind, self.D, self.n, _dp(self.X), _dp(self.y), _dp(self.mu),
+                             _dp(self.P), float(c), (C.c_double * 4)(*h))
+
+    @staticmethod
+    def gauss_dense(mu, P, c=0.0):
+        mu = _f64(mu)
+        return TargetSpec(GAUSS_DENSE, mu.size, mu=mu, P=P, c=c)
+
+    @staticmethod
+    def logistic(X, y, tau=1.0):
+        X = _f64(X)
+        return TargetSpec(LOGISTIC, X.shape[1], X.shape[0], X=X, y=y, hyper=(tau,))
+
+    @staticmethod
+    def linear_gauss(X, y, sigma=1.0, tau=1.0):
+        X = _f64(X)
+        return TargetSpec(LINEAR_GAUSS, X.shape[1], X.shape[0], X=X, y=y, hyper=(sigma, tau))
+
+    @staticmethod
+    def hier_normal(ybar, n_g, ss, sigma=1.0):
+        ybar = _f64(ybar)
+        return TargetSpec(HIER_NORMAL, 2 + ybar.size, ybar.size, y=ybar, mu=n_g, P=ss,
+                          hyper=(sigma,))
+
+    @staticmethod
+    def banana(D, a, b):
+        return TargetSpec(BANANA, D, hyper=(a, b))
+
+
+def logpi(t: TargetSpec, theta):
+    """log pi and its gradient for each row of ``theta`` ([N, D] or [D])."""
+    th = _f64(np.atleast_2d(theta))
+    g = np.empty_like(th)
+    lp = np.empty(th.shape[0])
+    for j in range(th.shape[0]):
+        row = th[j]
+        gr = g[j]
+        lp[j] = lib().oracle_logpi(C.byref(t.struct), _dp(row), _dp(gr))
+    return lp, g
+
+
+def leapfrog(t: TargetSpec, theta, p, eps, steps):
+    """``steps`` leapfrog steps (Algorithm 1) for every row; returns
+    (theta, p, grad, logpi) after the trajectory."""
+    th = _f64(np.atleast_2d(theta)).copy()
+    pp = _f64(np.atleast_2d(p)).copy()
+    lp, g = logpi(t, th)
+    steps = np.broadcast_to(np.asarray(steps, dtype=np.int64), (th.shape[0],))
+    for j in range(th.shape[0]):
+        lpj = C.c_double(lp[j])
+        r_th, r_p, r_g = th[j], pp[j], g[j]
+        lib().oracle_leapfrog(C.byref(t.struct), _dp(r_th), _dp(r_p), _dp(r_g), C.byref(lpj),
+                              float(eps), int(steps[j]))
+        lp[j] = lpj.value
+    return th, pp, g, lp
+
+
+def hamiltonian(p, logpi_value):
+    p = _f64(p)
+    return lib().oracle_hamiltonian(_dp(p), p.size, float(logpi_value))
+
+
+# ---------------------------------------------------------------- rng
+def philox(ctr, seed):
+    """Philox4x32-10 block for a counter (4 x uint32) and 64-bit seed."""
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    out = (C.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, C.c_uint64(int(seed)), out)
+    return np.array(list(out), dtype=np.uint32)
+
+
+def u01(w0, w1):
+    return lib().oracle_u01(int(w0), int(w1))
+
+
+def normals(seed, tag, k, j, D):
+    out = np.empty(D)
+    lib().oracle_normals(C.c_uint64(int(seed)), tag, k, j, D, _dp(out))
+    return out
+
+
+def resample_r64(seed, k):
+    return int(lib().oracle_resample_r64(C.c_uint64(int(seed)), int(k)))
+
+
+def halton2(n):
+    return lib().oracle_halton2(int(n))
+
+
+def step_count(h, L, eps, max_steps):
+    return int(lib().oracle_step_count(float(h), float(L), float(eps), int(max_steps)))
+
+
+# ---------------------------------------------------------------- weights
+def normalise(logw):
+    lw = _f64(logw)
+    lse, ess = C.c_double(), C.c_double()
+    W = np.empty_like(lw)
+    lib().oracle_normalise(_dp(lw), lw.size, C.byref(lse), C.byref(ess), _dp(W))
+    return lse.value, ess.value, W
+
+
+def quantise(W):
+    W = _f64(W)
+    q = np.empty(W.size, dtype=np.uint64)
+    S = lib().oracle_quantise(_dp(W), W.size, q.ctypes.data_as(_U64P))
+    return S, q
+
+
+def systematic(q, r64):
+    q = np.ascontiguousarray(q, dtype=np.uint64)
+    anc = np.empty(q.size, dtype=np.int32)
+    T = lib().oracle_systematic(q.ctypes.data_as(_U64P), q.size, C.c_uint64(int(r64)),
+                                anc.ctypes.data_as(_I32P))
+    return int(T), anc
+
+
+def multinomial(q, u64):
+    q = np.ascontiguousarray(q, dtype=np.uint64)
+    u = np.ascontiguousarray(u64, dtype=np.uint64)
+    anc = np.empty(q.size, dtype=np.int32)
+    lib().oracle_multinomial(q.ctypes.data_as(_U64P), q.size, u.ctypes.data_as(_U64P),
+                             anc.ctypes.data_as(_I32P))
+    return anc
+
+
+def moments(theta, logw):
+    th = _f64(theta)
+    lw = _f64(logw)
+    N, D = th.shape
+    mean, var = np.empty(D), np.empty(D)
+    lib().oracle_moments(_dp(th), _dp(lw), N, D, _dp(mean), _dp(var))
+    return mean, var
+
+
+# ---------------------------------------------------------------- ChEES
+def chees_gradient(theta0, theta1, p, l, alpha):
+    t0, t1, pp = _f64(theta0), _f64(theta1), _f64(p)
+    N, D = t0.shape
+    l, a = _f64(l), _f64(alpha)
+    g = C.c_double()
+    per = np.empty(N)
+    ok = lib().oracle_chees_gradient(_dp(t0), _dp(t1), _dp(pp), _dp(l), _dp(a), N, D,
+                                     C.byref(g), _dp(per))
+    return (g.value if ok else None), per
+
+
+def chees_adam(state: CheesState, ghat, lr, b1, b2, adam_eps, eps, max_steps):
+    lib().oracle_chees_adam(C.byref(state), float(ghat), lr, b1, b2, adam_eps, eps, max_steps)
+    return state
+
+
+# ---------------------------------------------------------------- sampler
+@dataclass
+class SMCConfig:
+    """Sampler settings (Algorithm 3 + Algorithm 2).  Defaults follow the
+    paper where it speaks (ESS threshold J/2, 1-d Halton jitter, no
+    accept-reject); the Adam constants are this project's choice."""
+    n_particles: int = 256
+    n_iters: int = 20
+    n_warmup: int = 10
+    step_size: float = 0.1
+    traj_len0: float = 5.0
+    max_steps: int = 500
+    ess_frac: float = 0.5
+    seed: int = 1000
+    jitter: int = 1
+    accept_reject: int = 0
+    adapt: int = 1
+    chees_initial_p: int = 0
+    adam_lr: float = 0.025
+    adam_b1: float = 0.9
+    adam_b2: float = 0.999
+    adam_eps: float = 1e-8
+    init_scale: float = 1.0
+
+    def struct(self):
+        return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
+                      self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
+                      self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
+                      self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale)
+
+
+def stats_to_dicts(arr):
+    return [{f: getattr(s, f) for f, _ in Stats._fields_ if f != "pad"} for s in arr]
+
+
+def smc_run(t: TargetSpec, cfg: SMCConfig, nthreads: int = 0):
+    """Whole sampler (Algorithm 3).  Returns dict with theta [N, D], logw,
+    log_z, stats (list of per-iteration dicts) and status."""
+    N, D, K = cfg.n_particles, t.D, cfg.n_iters
+    theta = np.empty((N, D))
+    logw = np.empty(N)
+    lz = C.c_double()
+    st = (Stats * K)()
+    c = cfg.struct()
+    status = lib().oracle_smc_run(C.byref(t.struct), C.byref(c), _dp(theta), _dp(logw),
+                                  C.byref(lz), st, int(nthreads))
+    return {"theta": theta, "logw": logw, "log_z": lz.value, "stats": stats_to_dicts(st),
+            "status": status}
+
+
+def smc_init(t: TargetSpec, cfg: SMCConfig, nthreads: int = 0):
+    N, D = cfg.n_particles, t.D
+    theta, grad = np.empty((N, D)), np.empty((N, D))
+    lp, lw = np.empty(N), np.empty(N)
+    c = cfg.struct()
+    lz = lib().oracle_smc_init(C.byref(t.struct), C.byref(c), _dp(theta), _dp(grad), _dp(lp),
+                               _dp(lw), int(nthreads))
+    return {"theta": theta, "grad": grad, "logpi": lp, "logw": lw, "log_z": lz}
+
+
+def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: int = 0):
+    """One iteration (Algorithm 3 body) on a state dict as returned by
+    ``smc_init`` plus ``chees`` (CheesState).  Mutates theta/grad/logpi/logw/
+    log_z/chees in place and returns the per-iteration intermediates."""
+    N, D = cfg.n_particles, t.D
+    for key in ("theta", "grad", "logpi", "logw"):
+        state[key] = _f64(state[key])
+    out = {"ancestors": np.empty(N, np.int32), "steps": np.empty(N, np.int32),
+           "p0": np.empty((N, D)), "p1": np.empty((N, D)), "dH": np.empty(N),
+           "alpha": np.empty(N)}
+    lz = C.c_double(state["log_z"])
+    io = IterIO(_dp(state["theta"]), _dp(state["grad"]), _dp(state["logpi"]),
+                _dp(state["logw"]), C.pointer(state["chees"]), C.pointer(lz),
+                out["ancestors"].ctypes.data_as(_I32P), out["steps"].ctypes.data_as(_I32P),
+                _dp(out["p0"]), _dp(out["p1"]), _dp(out["dH"]), _dp(out["alpha"]))
+    st = Stats()
+    c = cfg.struct()
+    out["status"] = lib().oracle_smc_iteration(C.byref(t.struct), C.byref(c), int(k),
+                                               C.byref(io), C.byref(st), int(nthreads))
+    state["log_z"] = lz.value
+    out["stats"] = stats_to_dicts([st])[0]
+    return out
+
+
+def initial_chees_state(cfg: SMCConfig) -> CheesState:
+    lo, hi = np.log(cfg.step_size), np.log(cfg.max_steps * cfg.step_size)
+    return CheesState(float(np.clip(np.log(cfg.traj_len0), lo, hi)), 0.0, 0.0, 0, 0.0)
