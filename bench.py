@@ -1,0 +1,405 @@
+"""Benchmark of the SMC-ChEES hot path on GB300 (one JSON line on rank 0).
+
+Workload (default): Bayesian logistic regression, n=1000 observations, D=25
+(intercept + 24 N(0,1) features), N=4096 particles, K=50 SMC iterations,
+1-d Halton jitter, eps=1e-3, L0=5, at most 500 leapfrog steps.  One "step"
+is one complete sampler run (initial draw + K iterations: every stage of the
+path), restarted on the device with a new seed (smc_reset) each step.
+
+value      = real particle-gradient evaluations (sum of leapfrog steps over
+             particles and iterations, all ranks) / device time of the timed
+             steps (CUDA events on the library's stream, L2 flushed between
+             steps outside the events, max over ranks).
+e2e        = the same metric through the public C-ABI from host memory:
+             smc_init (host model data copied in) -> smc_run -> particles,
+             log-weights and evidence copied back -> smc_destroy.
+roofline   = the trajectory kernel (dominant): algorithmic FLOPs per launch
+             (4 n D per particle-gradient + 2 n D per particle for the endpoint
+             energy) / its mean event-timed duration.
+cpu_baseline / --impl reference = the FP64 C oracle on the host cores.
+
+N > 1 (torchrun): independent replicas, one per GPU, different seeds
+("replicas only": the method's particle sets do not exchange data).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _workload(name):
+    if name == "logistic":
+        return workloads.logistic()
+    if name == "gauss10":
+        return workloads.gauss10()
+    if name == "hier":
+        return workloads.hier()
+    if name == "logistic_large":
+        return workloads.logistic_large()
+    raise ValueError(name)
+
+
+def _flops_per_grad(w):
+    if w["kind"] in ("logistic", "linear_gauss"):
+        return 4.0 * w["n"] * w["D"], 2.0 * w["n"] * w["D"]
+    if w["kind"] == "gauss_dense":
+        return 2.0 * w["D"] ** 2, 2.0 * w["D"] ** 2
+    return 0.0, 0.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _traffic_for(kernel_file):
+    """Per-launch DRAM bytes of the trajectory kernel from a committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        src = os.path.join(ROOT, "paper_2504_02627_gb300", "csrc", kernel_file)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        e = t.get(kernel_file)
+        if e and e.get("source_sha256_16") == h:
+            return e.get("bytes_per_launch_full")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_oracle_rate(w, run, seconds_target=20.0, iters=2):
+    """The FP64 oracle on the host cores: the first `iters` SMC iterations of
+    the same workload (all particles, full data); returns grad-evals/s."""
+    import oracle
+    if w["kind"] == "logistic":
+        t = oracle.TargetSpec.logistic(w["X"], w["y"], w.get("tau", 1.0))
+    elif w["kind"] == "gauss_dense":
+        t = oracle.TargetSpec.gauss_dense(w["mu"], w["P"])
+    else:
+        t = oracle.TargetSpec.hier_normal(w["ybar"], w["n_g"], w["ss"], w["sigma"])
+    cores = os.cpu_count() or 1
+    cfg = oracle.SMCConfig(seed=999, **dict(run))
+    t0 = time.perf_counter()
+    st = oracle.smc_init(t, cfg, nthreads=cores)
+    st["chees"] = oracle.initial_chees_state(cfg)
+    ge, done = 0, 0
+    for k in range(1, iters + 1):
+        out = oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        ge += out["stats"]["grad_evals"]
+        done += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return ge / dt, cores, dt, done
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, on the host cores, one
+    SMC iteration of the workload per step (bounded sample)."""
+    import oracle
+    w = _workload(args.workload)
+    run = dict(w["run"])
+    if rank != 0:
+        return None
+    t = oracle.TargetSpec.logistic(w["X"], w["y"], w.get("tau", 1.0)) if w["kind"] == "logistic" else \
+        oracle.TargetSpec.gauss_dense(w["mu"], w["P"])
+    cores = os.cpu_count() or 1
+    cfg = oracle.SMCConfig(seed=2024, **run)
+    st = oracle.smc_init(t, cfg, nthreads=cores)
+    st["chees"] = oracle.initial_chees_state(cfg)
+    k = 1
+    for _ in range(args.warmup):
+        oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        k += 1
+    t0 = time.perf_counter()
+    ge, ess = 0, 0.0
+    for _ in range(args.steps):
+        out = oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        ge += out["stats"]["grad_evals"]
+        ess += out["stats"]["ess"]
+        k += 1
+    dt = time.perf_counter() - t0
+    val = ge / dt
+    sample = (f"{args.steps} SMC iterations (k={args.warmup + 1}..{k - 1}) of the {args.workload} workload "
+              f"after {args.warmup} untimed, N={run['n_particles']}, FP64 C oracle, OpenMP")
+    return {"metric": METRIC, "value": val, "unit": "particle-grad-evals/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload]},
+            "cpu_baseline": {"value": val, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "particle-grad-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "ess_per_s": ess / dt}
+
+
+METRIC = "particle-grad-evals/s & ESS/s at fixed log-Z error, chosen vs plain FP32 on 1 GB300"
+WORKLOAD_DESC = {
+    "logistic": "Bayesian logistic regression, synthetic, n=1000, D=25 (intercept + 24 N(0,1) features), "
+                "N=4096 particles, K=50 SMC iterations, ChEES-HMC eps=1e-3 L0=5 max 500 steps, 1-d Halton",
+    "gauss10": "10-d correlated Gaussian, N=256, K=20",
+    "hier": "hierarchical normal, 64 uneven runs",
+    "logistic_large": "logistic regression n=100000 D=100 N=16384 K=30",
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="logistic")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import paper_2504_02627_gb300 as g
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream().cuda_stream
+
+    w = _workload(args.workload)
+    run = dict(w["run"])
+    K = run["n_iters"]
+    md = g.ModelData.from_workload(w)
+    cfg = g.make_config(seed=1000 + 1000 * rank, precision=args.precision, **run)
+    smp = g.Sampler(md, cfg, stream)
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one_run(seed):
+        smp.reset(seed)
+        smp.run(K)
+
+    for i in range(args.warmup):
+        one_run(10_000 + 1000 * rank + i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ge_total, ess_post, lz = 0, 0.0, []
+    smp.profile(True)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        one_run(20_000 + 1000 * rank + i)
+        ev[i][1].record()
+        s = smp.summary()[0]          # synchronises after the step; outside the events
+        ge_total += s["grad_evals"]
+        ess_post += s["ess_sum_post_warmup"]
+        lz.append(s["log_z"])
+    torch.cuda.synchronize()
+    prof = smp.get_profile()
+    smp.profile(False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([dev_ms, float(ge_total), ess_post], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dev_ms = float(tmax[0])
+        ge_all, ess_all = float(t[1]), float(t[2])
+    else:
+        ge_all, ess_all = float(ge_total), ess_post
+    value = ge_all / (dev_ms / 1e3)
+
+    # ---------------- roofline of the trajectory kernel
+    peaks, peak_kind = _peaks()
+    fl_grad, fl_end = _flops_per_grad(w)
+    n_part = run["n_particles"]
+    traj_flops = fl_grad * ge_total + fl_end * n_part * K * args.steps
+    traj_ms = prof["traj_ms"]
+    traj_n = max(1, prof["traj_launches"])
+    achieved = traj_flops / traj_n / (traj_ms / traj_n / 1e3) / 1e12
+    if args.precision == 0:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (max SM clock)"}
+        kfile = "traj_simt.cu"
+    else:
+        pk = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "peak_source": f"bf16 dense, {peak_kind}"}
+        kfile = "traj_tc.cu"
+    tr = _traffic_for(kfile)
+    roof["traffic"] = tr
+    roof["kernel"] = "trajectory (leapfrog) kernel"
+    roof["launches_timed"] = prof["traj_launches"]
+    roof["share_of_step_time"] = traj_ms / dev_ms if dev_ms > 0 else None
+
+    # ---------------- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        lib = g.lib()
+        h2d = 0
+        for a in md.arrays:
+            if a is not None:
+                h2d += a.nbytes
+        D = w["D"]
+        theta_h = np.empty((D, n_part), dtype=np.float32)
+        logw_h = np.empty(n_part)
+        lz_h = np.empty(1)
+        times, ge_e = [], 0
+        for i in range(max(2, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = C.c_void_p()
+            c2 = g.make_config(seed=30_000 + i + 1000 * rank, precision=args.precision, **run)
+            g.check(lib.smc_init(C.byref(h), C.byref(c2), C.byref(md.struct), C.c_void_p(stream)), "smc_init")
+            g.check(lib.smc_run(h, K, None), "smc_run", h)
+            g.check(lib.smc_get_particles(h, theta_h.ctypes.data, logw_h.ctypes.data, 0), "particles", h)
+            g.check(lib.smc_log_evidence(h, lz_h.ctypes.data_as(C.POINTER(C.c_double))), "evidence", h)
+            summ = (g._binding.SmcSummary * 1)()
+            g.check(lib.smc_get_summary(h, summ), "summary", h)
+            lib.smc_destroy(h)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            ge_e += summ[0].grad_evals
+        e2e = {"value": ge_e * world / sum(times), "unit": "particle-grad-evals/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(theta_h.nbytes + logw_h.nbytes + 8),
+               "steps": len(times)}
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # ---------------- CPU baseline (oracle on the host cores), rank 0, N=1 only
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, dt, iters = cpu_oracle_rate(w, run)
+        cpu = {"value": rate, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {iters} SMC iterations of the same workload (N={n_part}, full data), "
+                         f"FP64 C oracle, OpenMP, {dt:.1f} s wall"}
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "particle-grad-evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dev_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == 0 else "bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "step": f"one full sampler run ({K} iterations)",
+                   "precision": ["fp32", "bf16x3", "bf16"][args.precision],
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "ess_per_s": {"value": ess_all / (dev_ms / 1e3), "unit": "ESS/s",
+                      "note": "sum of post-warm-up J_eff over iterations / device time"},
+        "log_z": {"mean": float(np.mean(lz)), "sd": float(np.std(lz, ddof=1)) if len(lz) > 1 else None},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

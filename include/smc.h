@@ -1,0 +1,282 @@
+/*
+ * smc.h -- C ABI of libsmcchees, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of an SMC sampler with a ChEES-HMC proposal
+ * (Millard, Murphy, Frisch, Maskell, "Incorporating the ChEES Criterion into
+ * Sequential Monte Carlo Samplers", arXiv 2504.02627).
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only; sizes are int64_t, floating scalars are double.
+ *  - Every call returns smc_status; no exception or abort crosses the ABI.
+ *  - "stream" is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  The caller owns the stream and keeps it alive while a handle that
+ *    uses it exists.
+ *  - Device arrays on the GPU side are particle-major [D x N]: element (d, j)
+ *    lives at d * ld + j, with ld >= N, so consecutive particles are
+ *    consecutive in memory.
+ *  - The library allocates its own device memory (stream-ordered) in the
+ *    *_create / smc_init calls; the kernel-level smc_k_* calls allocate
+ *    nothing beyond what their comment states and write only their outputs.
+ *  - Model data passed at creation are host FP64 arrays, copied (and cast) by
+ *    the library; the caller may free them when the call returns.
+ *  - Calls on one handle are not thread-safe; separate handles are independent.
+ *  - Results are a deterministic function of (config, model, seed).
+ */
+#ifndef SMC_CHEES_H
+#define SMC_CHEES_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMC_OK = 0,
+    SMC_E_INVAL = -1,       /* bad argument or unsupported configuration          */
+    SMC_E_NOMEM = -2,       /* device allocation failed                           */
+    SMC_E_CUDA = -3,        /* a CUDA call failed; smc_last_error has the text    */
+    SMC_E_DEGENERATE = -4,  /* every weight is zero (all log-weights -inf)        */
+    SMC_E_TIMEOUT = -5,     /* a bounded device wait gave up (scan look-back)     */
+    SMC_E_STATE = -6        /* handle is in a sticky error state                  */
+} smc_status;
+
+/* ------------------------------------------------------------------ models
+ * The target pi(theta) = p(x | theta) q0(theta) (Sec. 2).  Densities are
+ * normalised (except GAUSS_DENSE, which adds the constant c), so that the
+ * evidence estimate is the marginal likelihood.
+ *  GAUSS_DENSE  log pi = c - 1/2 (theta - mu)' P (theta - mu); mu [dim],
+ *               prec P [dim x dim] row-major.
+ *  LOGISTIC     y_i ~ Bernoulli(sigmoid(x_i' theta)), theta ~ N(0, tau^2 I)
+ *               (Sec. 4, German Credit); X [n_obs x dim] row-major, y [n_obs]
+ *               in {0,1}; hyper[0] = tau.
+ *  HIER_NORMAL  theta = (mu, log tau, eta_1..eta_G), dim = G + 2; group
+ *               effect mu + tau eta_g, y_gi ~ N(., sigma^2) given by the
+ *               sufficient statistics group_mean, group_n, group_ss [G];
+ *               priors N(0,1) on mu, log tau, eta; hyper[0] = sigma; n_obs = G.
+ *  BANANA       dim/2 independent pairs (Sec. 4, Rosenbrock):
+ *               x_o ~ N(0, a), x_e ~ N(b (x_o^2 - a), 1); hyper = {a, b}.
+ *  LINEAR_GAUSS y_i ~ N(x_i' theta, sigma^2), theta ~ N(0, tau^2 I);
+ *               X, y as LOGISTIC; hyper = {sigma, tau}.
+ */
+typedef enum {
+    SMC_MODEL_GAUSS_DENSE = 0,
+    SMC_MODEL_LOGISTIC = 1,
+    SMC_MODEL_HIER_NORMAL = 2,
+    SMC_MODEL_BANANA = 3,
+    SMC_MODEL_LINEAR_GAUSS = 4
+} smc_model_kind;
+
+typedef struct {
+    int32_t kind;               /* smc_model_kind                                 */
+    int32_t pad;
+    int64_t dim;                /* D                                              */
+    int64_t n_obs;              /* n (LOGISTIC, LINEAR_GAUSS) or G (HIER_NORMAL)  */
+    const double* X;            /* host, n_obs x dim row-major                    */
+    const double* y;            /* host, n_obs                                    */
+    const double* mu;           /* host, dim                                      */
+    const double* prec;         /* host, dim x dim row-major                      */
+    const double* group_mean;   /* host, G                                        */
+    const double* group_n;      /* host, G                                        */
+    const double* group_ss;     /* host, G                                        */
+    double c;                   /* additive constant (GAUSS_DENSE)                */
+    double hyper[4];
+} smc_model;
+
+/* Likelihood arithmetic for the GEMM-shaped models (LOGISTIC, LINEAR_GAUSS). */
+typedef enum {
+    SMC_PREC_FP32 = 0,      /* FP32 SIMT, FP32 everywhere on the trajectory       */
+    SMC_PREC_BF16X3 = 1,    /* tcgen05 BF16 x3 split products, FP32 accumulation  */
+    SMC_PREC_BF16 = 2       /* tcgen05 BF16 operands, FP32 accumulation           */
+} smc_precision;
+
+/* ------------------------------------------------------------------ config
+ * Algorithm 3 (SMC) with the proposal of Algorithm 2 (ChEES-HMC).
+ * Defaults used by the Python binding: ess_frac 0.5 (J_eff < J/2, Sec. 3),
+ * jitter 1 (1-d Halton, Sec. 3.2), accept_reject 0 (no accept-reject,
+ * Sec. 3.1), adapt 1; the Adam constants are this library's choice.
+ */
+typedef struct {
+    int64_t n_particles;    /* J for this run                                     */
+    int64_t n_iters;        /* K (also the Halton index stride)                   */
+    int64_t n_warmup;       /* M_warmup: ChEES adapts while k < M_warmup          */
+    double step_size;       /* epsilon                                            */
+    double traj_len0;       /* L_0 in time units, clamped to [eps, max_steps*eps] */
+    int32_t max_steps;      /* leapfrog cap (>= 1)                                */
+    int32_t jitter;         /* 0: h = 1; 1: base-2 Halton of n = j*K + k          */
+    double ess_frac;        /* resample when ESS < ess_frac * J                   */
+    uint64_t seed;          /* Philox4x32-10 key                                  */
+    int32_t accept_reject;  /* must be 0 (the paper's SMC-ChEES)                  */
+    int32_t adapt;          /* 1: ChEES adaptation of L during warm-up            */
+    double adam_lr, adam_b1, adam_b2, adam_eps;
+    double init_scale;      /* q_init = N(0, init_scale^2 I)                      */
+    int32_t precision;      /* smc_precision                                      */
+    int32_t pad;
+} smc_config;
+
+typedef struct {
+    double ess;             /* J_eff after this iteration's reweighting (Eq. ESS) */
+    double ess_pre;         /* J_eff tested for resampling                        */
+    double log_z_inc;       /* log sum_j W_j exp(-Delta H_j)                      */
+    double mean_alpha;      /* mean HMC acceptance probability                    */
+    double traj_len;        /* L used for this iteration's jitter                 */
+    int64_t grad_evals;     /* sum_j S_j (gradients evaluated on the trajectory)  */
+    int32_t steps_min, steps_max;
+    int32_t resampled;
+    int32_t pad;
+} smc_stats;
+
+typedef struct smc_handle smc_handle;   /* opaque; owned by the library */
+
+/* Creates a sampler, allocates its device state on `stream`, draws theta_0 ~
+ * q_init and sets w_1 = pi / q_init (Algorithm 3, first two lines; Eqs. for
+ * theta_0 and w_1).  Errors: SMC_E_INVAL (bad config/model), SMC_E_NOMEM,
+ * SMC_E_CUDA.  On error *out is NULL. */
+smc_status smc_init(smc_handle** out, const smc_config* cfg, const smc_model* model,
+                    void* stream);
+
+/* Creates n_runs independent samplers over the same model in one handle; run
+ * r uses cfg[r] (particle counts may differ; K, M_warmup and precision must
+ * agree).  Kernels process all runs in each launch. */
+smc_status smc_init_batch(smc_handle** out, int64_t n_runs, const smc_config* cfg,
+                          const smc_model* model, void* stream);
+
+/* One SMC iteration (the loop body of Algorithm 3): normalise, ESS test,
+ * systematic resampling, jittered ChEES-HMC move of every particle, reweight
+ * by -Delta H, ChEES adaptation.  stats (n_runs entries) may be NULL; when
+ * non-NULL the call synchronises the stream and copies the statistics. */
+smc_status smc_step(smc_handle* h, smc_stats* stats);
+
+/* n_iters calls of smc_step; per_iter (n_iters * n_runs, iteration-major) may
+ * be NULL, in which case nothing synchronises until the caller asks. */
+smc_status smc_run(smc_handle* h, int64_t n_iters, smc_stats* per_iter);
+
+/* log Z estimate per run (n_runs doubles, host).  Synchronises the stream. */
+smc_status smc_log_evidence(const smc_handle* h, double* out);
+
+/* Copies particles out: theta [dim x N_total] FP32 particle-major (ld =
+ * N_total) and log-weights [N_total] FP64.  device_ptrs = 1: the pointers are
+ * device pointers on the handle's device; 0: host pointers.  Either may be
+ * NULL.  Synchronises the stream. */
+smc_status smc_get_particles(const smc_handle* h, float* theta, double* logw,
+                             int32_t device_ptrs);
+
+/* Weighted posterior mean and variance (Eq. for realised estimates) of run 0
+ * (host arrays of dim doubles). */
+smc_status smc_moments(const smc_handle* h, double* mean, double* var);
+
+/* Internal per-particle buffers of the last completed iteration, for
+ * inspection and parity tests.  Copies `bytes` bytes into dst (device_ptrs as
+ * above).  Buffer ids: */
+typedef enum {
+    SMC_BUF_THETA = 0,      /* f32 [dim x ld]   current positions                 */
+    SMC_BUF_GRAD = 1,       /* f32 [dim x ld]   grad log pi at THETA              */
+    SMC_BUF_LOGPI = 2,      /* f64 [N]          log pi at THETA                   */
+    SMC_BUF_LOGW = 3,       /* f64 [N]          log-weights                       */
+    SMC_BUF_W = 4,          /* f64 [N]          normalised weights before resampling */
+    SMC_BUF_ANCESTORS = 5,  /* i32 [N]          ancestors (run-local) if resampled */
+    SMC_BUF_STEPS = 6,      /* i32 [N]          leapfrog steps S_j                */
+    SMC_BUF_P_FINAL = 7,    /* f32 [dim x ld]   final momenta                     */
+    SMC_BUF_DH = 8,         /* f64 [N]          Delta H                           */
+    SMC_BUF_ALPHA = 9,      /* f64 [N]          acceptance probabilities          */
+    SMC_BUF_THETA_PREV = 10,/* f32 [dim x ld]   positions before the move (after resampling) */
+    SMC_BUF_RUNSTATE = 11   /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L_used, ess */
+} smc_buffer;
+smc_status smc_get_buffer(const smc_handle* h, int32_t which, void* dst, int64_t bytes,
+                          int32_t device_ptrs);
+/* Leading dimension ld of the [dim x ld] buffers, total particle count, runs. */
+smc_status smc_get_layout(const smc_handle* h, int64_t* ld, int64_t* n_total, int64_t* n_runs);
+
+/* Restarts every run of the handle from a fresh initial draw (Algorithm 3,
+ * first two lines) with seed + r for run r, reusing the device memory:
+ * nothing is allocated.  Clears the adaptation state, the evidence and the
+ * summary counters; keeps the configuration. */
+smc_status smc_reset(smc_handle* h, uint64_t seed);
+
+/* Cumulative counters per run since smc_init / smc_reset. */
+typedef struct {
+    int64_t iterations;         /* completed SMC iterations                         */
+    int64_t grad_evals;         /* sum over iterations of sum_j S_j                 */
+    double ess_sum;             /* sum over iterations of J_eff after reweighting   */
+    double ess_sum_post_warmup; /* the same over iterations k > M_warmup            */
+    double log_z;               /* current log evidence estimate                    */
+    int64_t resamples;          /* iterations that resampled                        */
+} smc_summary;
+smc_status smc_get_summary(const smc_handle* h, smc_summary* per_run);
+
+/* Trajectory-kernel timing with CUDA events recorded on the handle's stream
+ * around every trajectory launch while enabled (enable = 1 also clears the
+ * totals).  smc_get_profile synchronises and returns the summed device time
+ * of those launches in ms, their count, and the number of kernels the library
+ * launched while profiling was on. */
+smc_status smc_profile(smc_handle* h, int32_t enable);
+smc_status smc_get_profile(smc_handle* h, double* traj_ms, int64_t* traj_launches,
+                           int64_t* kernel_launches);
+
+/* Copies the last error text (NUL-terminated, truncated to len). */
+smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len);
+
+/* Frees the handle and its device memory (stream-ordered). NULL is a no-op. */
+void smc_destroy(smc_handle* h);
+
+/* ------------------------------------------------------------------ kernels
+ * Kernel-level entry points on caller-owned DEVICE buffers.  They run single
+ * stages of the path for parity tests and for callers that drive their own
+ * loop.  None allocates device memory except smc_model_create.
+ */
+typedef struct smc_dev_model smc_dev_model;
+
+/* Uploads model data to the device (the target of Sec. 2). */
+smc_status smc_model_create(smc_dev_model** out, const smc_model* model, void* stream);
+void smc_model_destroy(smc_dev_model* m);
+
+/* Philox4x32-10 (Salmon et al., SC'11) blocks: ctr [n x 4] u32 -> out [n x 4]. */
+smc_status smc_k_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n,
+                        void* stream);
+
+/* Standard normals of particle slots j = 0..N-1 for (tag, k): out [D x ld] f64,
+ * Box-Muller on Philox blocks (i, j, k, tag), i = d / 2.  tag 1: initial draw,
+ * 2: momentum (Sec. 2.1, p ~ N(0, I)). */
+smc_status smc_k_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int64_t D,
+                         double* out, int64_t ld, void* stream);
+
+/* Jittered step counts (Algorithm 2: ceil(h L / eps), clipped to [1, max]):
+ * h_j = radical inverse base 2 of n = j*K + k (jitter = 1) or 1 (jitter = 0);
+ * out_h [N] f64 (may be NULL), out_steps [N] i32. */
+smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps,
+                       int32_t max_steps, int32_t jitter, double* out_h, int32_t* out_steps,
+                       void* stream);
+
+/* log pi and grad log pi (Sec. 2) at theta [D x ld] f32: logpi [N] f64,
+ * grad [D x ld] f32. */
+smc_status smc_k_target(const smc_dev_model* m, const float* theta, int64_t N, int64_t ld,
+                        double* logpi, float* grad, int32_t precision, void* stream);
+
+/* steps[j] leapfrog steps (Eqs. for p_{l+1/2}, theta_{l+1}, p_{l+1};
+ * Algorithm 1) with step size eps, in place on theta, p, grad [D x ld] f32 and
+ * logpi [N] f64 (which must hold grad log pi and log pi at the start).  On
+ * return logpi holds log pi at the end point. */
+smc_status smc_k_leapfrog(const smc_dev_model* m, float* theta, float* p, float* grad,
+                          double* logpi, const int32_t* steps, double eps, int64_t N,
+                          int64_t ld, int32_t precision, void* stream);
+
+/* Normalised weights (Sec. 3): lse, ess (device scalars, f64) and W [N] f64
+ * from logw [N] f64. */
+smc_status smc_k_normalise(const double* logw, int64_t N, double* W, double* lse,
+                           double* ess, void* stream);
+
+/* Fixed-point systematic resampling: q_j = floor(W_j 2^S), S = 62 -
+ * ceil(log2 N); T = sum q (exact, uint64); U = floor(r64 T / 2^64); ancestor
+ * of output i = smallest j with N C_j > i T + U (C = inclusive prefix of q,
+ * by a decoupled look-back scan).  W is read-only; writes q [N] u64,
+ * ancestors [N] i32 and *status_out (device i32: 0 ok, -4 T == 0, -5 the
+ * look-back wait gave up).  Uses `scratch` (device, caller-allocated, at least
+ * smc_k_resample_scratch_bytes(N) bytes, 256-byte aligned) for the tile
+ * descriptors; its contents on entry do not matter.  N <= 2^30. */
+int64_t smc_k_resample_scratch_bytes(int64_t N);
+smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
+                          int32_t* ancestors, int32_t* status_out, void* scratch,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

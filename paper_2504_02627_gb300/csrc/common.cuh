@@ -1,0 +1,153 @@
+// common.cuh -- device building blocks shared by the libsmcchees kernels.
+//
+// Counter-based random numbers (Philox4x32-10, Salmon et al., SC'11), the
+// Box-Muller transform, the base-2 radical inverse used to jitter trajectory
+// lengths (1-d Halton, Sec. 3.2 of arXiv 2504.02627), the step-count rule of
+// Algorithm 2, and warp/block reductions.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smc {
+
+// ---------------------------------------------------------------- run state
+// Per-run parameters (read-only on the device during a step).
+struct RunParams {
+    int64_t off;            // first particle of the run in the global arrays
+    int64_t n;              // particles in the run
+    uint64_t seed;          // Philox key
+    double eps;             // leapfrog step size
+    double ess_frac;        // resampling threshold (fraction of n)
+    double init_scale;      // q_init standard deviation
+    double adam_lr, adam_b1, adam_b2, adam_eps;
+    double log_L_lo, log_L_hi;   // clamp of log L: [log eps, log(max_steps * eps)]
+    int32_t max_steps;
+    int32_t jitter;
+    int32_t adapt;
+    int32_t n_tiles;        // resampling scan tiles of this run
+    int64_t tile0;          // first global scan tile of the run
+    int64_t n_iters, n_warmup;
+};
+
+// Per-run mutable state (device).  Read back by smc_get_buffer(RUNSTATE) as
+// the first 8 doubles.
+struct RunState {
+    double log_z;       // running log evidence
+    double log_L;       // log trajectory length (Adam variable)
+    double adam_m, adam_v;
+    double Lbar;        // moving average of L
+    double adam_t;      // Adam step count (stored as double for the readout)
+    double L_used;      // L used for this iteration's jitter
+    double ess;         // ESS after the last reweighting
+    // ---- below: not part of the 8-double readout
+    double lse;         // log-sum-exp of the log-weights before the move
+    double ess_pre;
+    double log_z_inc;
+    double mean_alpha;
+    uint64_t T, U;      // fixed-point total and offset of the last resampling
+    int64_t k;          // 1-based iteration about to run / just run
+    int64_t grad_evals;
+    int32_t resample;   // this iteration resamples
+    int32_t status;     // 0 ok, -4 degenerate, -5 look-back gave up
+    int32_t steps_min, steps_max;
+    // cumulative counters since the initial draw
+    int64_t iters_total, grad_evals_total, resamples_total;
+    double ess_sum, ess_sum_post;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Round: the 32x32->64 products of counter words 0 and 2 with the round
+// multipliers; new words are (hi(c2*M1) ^ c1 ^ k0, lo(c2*M1), hi(c0*M0) ^ c3 ^ k1,
+// lo(c0*M0)); the key advances by the Weyl increments (golden ratio and
+// sqrt(3) - 1 as 32-bit fractions) after each of the ten rounds.
+struct Philox4 { uint32_t x, y, z, w; };
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(Philox4 c, uint64_t seed) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+        uint64_t a = (uint64_t)0xD2511F53u * c.x, b = (uint64_t)0xCD9E8D57u * c.z;
+        uint32_t hi0 = (uint32_t)(a >> 32), lo0 = (uint32_t)a;
+        uint32_t hi1 = (uint32_t)(b >> 32), lo1 = (uint32_t)b;
+#endif
+        c = Philox4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum : uint32_t { TAG_INIT = 1, TAG_MOM = 2, TAG_RESAMPLE = 3, TAG_MH = 4 };
+
+// Uniform on (0,1): 26 high bits of each word form a 52-bit integer m and the
+// value is (m + 0.5) 2^-52, exact in FP64.
+__device__ __forceinline__ double u01_52(uint32_t a, uint32_t b) {
+    uint64_t m = ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+    return ((double)m + 0.5) * 2.220446049250313080847263336181640625e-16;  // 2^-52
+}
+
+// Two standard normals from one Philox block by Box-Muller in FP64.
+__device__ __forceinline__ void normal_pair(uint64_t seed, uint32_t i, uint32_t j, uint32_t k,
+                                            uint32_t tag, double& z0, double& z1) {
+    Philox4 w = philox4x32_10(Philox4{i, j, k, tag}, seed);
+    double u1 = u01_52(w.x, w.y), u2 = u01_52(w.z, w.w);
+    double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// ---------------------------------------------------------------- jitter
+// Base-2 radical inverse of n: bit reversal of the 32-bit integer, times 2^-32
+// (exact in FP64 for n < 2^32).
+__device__ __forceinline__ double halton2(uint32_t n) {
+    return (double)__brev(n) * 2.3283064365386962890625e-10;  // 2^-32
+}
+
+// Algorithm 2: ceil(h L / eps), at least 1 and at most max_steps.
+__device__ __forceinline__ int32_t step_count(double h, double L, double eps, int32_t max_steps) {
+    double s = ceil(__ddiv_rn(__dmul_rn(h, L), eps));
+    if (!(s >= 1.0)) return 1;
+    if (s >= (double)max_steps) return max_steps;
+    return (int32_t)s;
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction through shared memory; every thread gets the result.
+// `buf` needs blockDim.x / 32 entries.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, T* buf, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) buf[wid] = v;
+    __syncthreads();
+    T r = buf[0];
+    for (int w = 1; w < nw; ++w) r = op(r, buf[w]);
+    return r;
+}
+
+struct OpSum { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
+struct OpMax { template <typename T> __device__ T operator()(T a, T b) const { return a > b ? a : b; } };
+struct OpMin { template <typename T> __device__ T operator()(T a, T b) const { return a < b ? a : b; } };
+
+}  // namespace smc

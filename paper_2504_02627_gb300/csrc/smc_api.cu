@@ -1,0 +1,822 @@
+// smc_api.cu -- host driver behind include/smc.h: device memory, the
+// per-iteration launch sequence of Algorithm 3, statistics, and the
+// kernel-level entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/smc.h"
+#include "common.cuh"
+#include "smc_kernels.cuh"
+#include "traj.cuh"
+
+using namespace smc;
+
+namespace {
+constexpr double LOG_2PI = 1.8378770664093454835606594728112;
+
+struct DevAlloc {
+    std::vector<void*> ptrs;
+    cudaStream_t s = nullptr;
+    cudaError_t err = cudaSuccess;
+    template <typename T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+        if (e != cudaSuccess) {
+            err = e;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    void release() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+        ptrs.clear();
+    }
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct smc_dev_model {
+    DevModel m{};
+    DevAlloc mem;
+};
+
+struct smc_handle {
+    cudaStream_t stream = nullptr;
+    int64_t n_runs = 0, N = 0, ld = 0, D = 0, K = 0;
+    int32_t precision = 0;
+    smc_dev_model model;
+    DevAlloc mem;
+    std::vector<RunParams> h_runs;
+    RunParams* d_runs = nullptr;
+    RunState* d_rstate = nullptr;
+    int32_t* d_run_of = nullptr;
+    int32_t* d_tile_run = nullptr;
+    float* theta[2] = {nullptr, nullptr};
+    float* grad[2] = {nullptr, nullptr};
+    double* logpi[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* p_final = nullptr;
+    double *logw = nullptr, *W = nullptr, *dH = nullptr, *alpha = nullptr;
+    unsigned long long* q = nullptr;
+    int32_t *anc = nullptr, *src = nullptr, *steps = nullptr, *perm = nullptr, *hist = nullptr;
+    unsigned int* counter = nullptr;
+    TileDesc* tiles = nullptr;
+    int64_t n_tiles = 0;
+    int32_t max_steps_all = 0;
+    int64_t iters_done = 0;
+    int sticky = 0;
+    std::string err;
+    std::vector<smc_config> cfg;
+    // profiling: events around trajectory launches, launch counter
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    size_t n_event_pairs = 0;
+    int64_t kernel_launches = 0;
+};
+
+namespace {
+
+smc_status fail(smc_handle* h, smc_status st, const std::string& msg) {
+    if (h) {
+        h->err = msg;
+        if (st == SMC_E_CUDA || st == SMC_E_TIMEOUT || st == SMC_E_DEGENERATE) h->sticky = st;
+    }
+    return st;
+}
+
+smc_status cuda_fail(smc_handle* h, cudaError_t e, const char* where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? SMC_E_NOMEM : SMC_E_CUDA, msg);
+}
+
+std::vector<float> to_f32(const double* x, size_t n) {
+    std::vector<float> v(n);
+    for (size_t i = 0; i < n; ++i) v[i] = (float)x[i];
+    return v;
+}
+
+uint16_t f32_to_bf16_rn(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);   // NaN stays NaN
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_f32(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Validates a model description and uploads it.  Returns an error text or "".
+std::string upload_model(smc_dev_model* dm, const smc_model* md, cudaStream_t s) {
+    if (!md) return "model is NULL";
+    if (md->dim < 1 || md->dim > 1024) return "dim must be in [1, 1024]";
+    DevModel& m = dm->m;
+    m = DevModel{};
+    m.kind = md->kind;
+    m.D = (int32_t)md->dim;
+    m.Dp = (int32_t)round_up(md->dim, 4);
+    m.n = (int32_t)md->n_obs;
+    m.h0 = md->hyper[0];
+    m.h1 = md->hyper[1];
+    dm->mem.s = s;
+    auto up = [&](const std::vector<float>& v) -> float* {
+        float* p = dm->mem.get<float>(v.size());
+        if (p) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+        return p;
+    };
+    const int64_t D = md->dim;
+    switch (md->kind) {
+        case SMC_MODEL_GAUSS_DENSE: {
+            if (!md->mu || !md->prec) return "GAUSS_DENSE needs mu and prec";
+            m.mu = up(to_f32(md->mu, (size_t)D));
+            m.P = up(to_f32(md->prec, (size_t)(D * D)));
+            m.lconst = md->c;
+            break;
+        }
+        case SMC_MODEL_LOGISTIC:
+        case SMC_MODEL_LINEAR_GAUSS: {
+            if (!md->X || !md->y || md->n_obs < 1) return "regression models need X, y and n_obs >= 1";
+            const bool logit = md->kind == SMC_MODEL_LOGISTIC;
+            const double tau = logit ? md->hyper[0] : md->hyper[1];
+            if (!(tau > 0.0)) return "prior scale tau must be > 0";
+            if (!logit && !(md->hyper[0] > 0.0)) return "noise scale sigma must be > 0";
+            const int64_t n = md->n_obs, Dp = m.Dp;
+            std::vector<float> X((size_t)(n * Dp), 0.0f);
+            std::vector<uint16_t> Xh((size_t)(n * Dp), 0), Xl((size_t)(n * Dp), 0);
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t d = 0; d < D; ++d) {
+                    const float x = (float)md->X[i * D + d];
+                    X[(size_t)(i * Dp + d)] = x;
+                    const uint16_t hi = f32_to_bf16_rn(x);
+                    Xh[(size_t)(i * Dp + d)] = hi;
+                    Xl[(size_t)(i * Dp + d)] = f32_to_bf16_rn(x - bf16_to_f32(hi));
+                }
+            m.X = up(X);
+            m.y = up(to_f32(md->y, (size_t)n));
+            uint16_t* xh = dm->mem.get<uint16_t>(Xh.size());
+            uint16_t* xl = dm->mem.get<uint16_t>(Xl.size());
+            if (xh) cudaMemcpyAsync(xh, Xh.data(), Xh.size() * 2, cudaMemcpyHostToDevice, s);
+            if (xl) cudaMemcpyAsync(xl, Xl.data(), Xl.size() * 2, cudaMemcpyHostToDevice, s);
+            m.Xbf = xh;
+            m.Xbf_lo = xl;
+            if (logit) {
+                m.lconst = -0.5 * (double)D * (LOG_2PI + 2.0 * std::log(tau));
+            } else {
+                const double sigma = md->hyper[0];
+                m.lconst = -0.5 * (double)n * (LOG_2PI + 2.0 * std::log(sigma)) -
+                           0.5 * (double)D * (LOG_2PI + 2.0 * std::log(tau));
+            }
+            // the host synchronises before the staging vectors go out of scope
+            cudaStreamSynchronize(s);
+            break;
+        }
+        case SMC_MODEL_HIER_NORMAL: {
+            const int64_t G = md->n_obs;
+            if (G < 1 || D != G + 2) return "HIER_NORMAL needs dim == n_obs + 2";
+            if (!md->group_mean || !md->group_n || !md->group_ss) return "HIER_NORMAL needs group statistics";
+            if (!(md->hyper[0] > 0.0)) return "sigma must be > 0";
+            m.gmean = up(to_f32(md->group_mean, (size_t)G));
+            m.gn = up(to_f32(md->group_n, (size_t)G));
+            m.gss = up(to_f32(md->group_ss, (size_t)G));
+            const double sigma = md->hyper[0];
+            double c = -LOG_2PI;   // priors on mu and log tau
+            for (int64_t g = 0; g < G; ++g)
+                c += -0.5 * md->group_n[g] * (LOG_2PI + 2.0 * std::log(sigma)) - 0.5 * LOG_2PI;
+            m.lconst = c;
+            break;
+        }
+        case SMC_MODEL_BANANA: {
+            if (D % 2 != 0) return "BANANA needs an even dim";
+            if (!(md->hyper[0] > 0.0)) return "BANANA variance a must be > 0";
+            m.lconst = -(double)(D / 2) * (0.5 * (LOG_2PI + std::log(md->hyper[0])) + 0.5 * LOG_2PI);
+            break;
+        }
+        default: return "unknown model kind";
+    }
+    if (dm->mem.err != cudaSuccess) return std::string("device allocation failed: ") + cudaGetErrorString(dm->mem.err);
+    cudaStreamSynchronize(s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return std::string("model upload: ") + cudaGetErrorString(e);
+    return "";
+}
+
+std::string check_config(const smc_config& c) {
+    if (c.n_particles < 1 || c.n_particles > (1ll << 30)) return "n_particles must be in [1, 2^30]";
+    if (c.n_iters < 1) return "n_iters must be >= 1";
+    if (c.n_iters * c.n_particles + c.n_iters >= (1ll << 32)) return "n_particles * n_iters must be < 2^32 (Halton index)";
+    if (!(c.step_size > 0.0) || !std::isfinite(c.step_size)) return "step_size must be > 0";
+    if (!(c.traj_len0 > 0.0)) return "traj_len0 must be > 0";
+    if (c.max_steps < 1 || c.max_steps > 65536) return "max_steps must be in [1, 65536]";
+    if (c.jitter != 0 && c.jitter != 1) return "jitter must be 0 or 1";
+    if (c.accept_reject != 0) return "accept_reject must be 0";
+    if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
+    if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
+    if (c.precision < 0 || c.precision > 2) return "unknown precision";
+    return "";
+}
+
+StepBufs make_bufs(smc_handle* h) {
+    StepBufs b{};
+    b.runs = h->d_runs;
+    b.rstate = h->d_rstate;
+    b.run_of = h->d_run_of;
+    b.tile_run = h->d_tile_run;
+    b.n_runs = h->n_runs;
+    b.N = h->N;
+    b.ld = h->ld;
+    b.D = h->D;
+    b.logw = h->logw;
+    b.W = h->W;
+    b.q = h->q;
+    b.anc = h->anc;
+    b.src = h->src;
+    b.steps = h->steps;
+    b.perm = h->perm;
+    b.hist = h->hist;
+    b.counter = h->counter;
+    b.tiles = h->tiles;
+    b.n_tiles = h->n_tiles;
+    b.max_steps_all = h->max_steps_all;
+    b.theta_prev = h->theta[h->cur];
+    b.theta_new = h->theta[1 - h->cur];
+    b.p_final = h->p_final;
+    b.dH = h->dH;
+    b.alpha = h->alpha;
+    return b;
+}
+
+// Initial draw, target evaluation and initial weights (Algorithm 3, first
+// lines) into buffer 0; the run state must already hold k = 1 and log L_0.
+cudaError_t initial_draw(smc_handle* h) {
+    cudaStream_t s = h->stream;
+    h->cur = 0;
+    StepBufs b = make_bufs(h);
+    cudaError_t ce = launch_init_draw(b, h->theta[0], s);
+    if (ce == cudaSuccess) {
+        TrajArgs a{};
+        a.theta_in = h->theta[0];
+        a.grad_out = h->grad[0];
+        a.logpi_out = h->logpi[0];
+        a.run_of = h->d_run_of;
+        a.runs = h->d_runs;
+        a.rstate = h->d_rstate;
+        a.N = h->N;
+        a.ld = h->ld;
+        a.eval_only = 1;
+        ce = launch_traj(h->model.m, a, h->precision, s);
+    }
+    if (ce == cudaSuccess) ce = launch_init_finish(b, h->logpi[0], s);
+    if (h->profiling) h->kernel_launches += 3;
+    return ce;
+}
+
+RunState initial_state(const RunParams& rp, const smc_config& c) {
+    RunState st{};
+    st.log_L = std::fmin(std::fmax(std::log(c.traj_len0), rp.log_L_lo), rp.log_L_hi);
+    st.k = 1;
+    st.L_used = std::exp(st.log_L);
+    return st;
+}
+
+smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const smc_model* model,
+                  void* stream) {
+    if (!out) return SMC_E_INVAL;
+    *out = nullptr;
+    if (n_runs < 1 || !cfg) return SMC_E_INVAL;
+    smc_handle* h = new smc_handle();
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->mem.s = h->stream;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        std::string e = check_config(cfg[r]);
+        if (!e.empty()) {
+            fprintf(stderr, "smc_init: run %lld: %s\n", (long long)r, e.c_str());
+            delete h;
+            return SMC_E_INVAL;
+        }
+        if (cfg[r].n_iters != cfg[0].n_iters || cfg[r].n_warmup != cfg[0].n_warmup ||
+            cfg[r].precision != cfg[0].precision) {
+            fprintf(stderr, "smc_init_batch: runs must share n_iters, n_warmup and precision\n");
+            delete h;
+            return SMC_E_INVAL;
+        }
+    }
+    std::string e = upload_model(&h->model, model, h->stream);
+    if (!e.empty()) {
+        fprintf(stderr, "smc_init: %s\n", e.c_str());
+        h->model.mem.release();
+        delete h;
+        return SMC_E_INVAL;
+    }
+    h->precision = cfg[0].precision;
+    if (!traj_supported(h->model.m, h->precision)) {
+        fprintf(stderr, "smc_init: no kernel for this model / dimension / precision\n");
+        h->model.mem.release();
+        delete h;
+        return SMC_E_INVAL;
+    }
+    h->n_runs = n_runs;
+    h->D = model->dim;
+    h->K = cfg[0].n_iters;
+    int64_t N = 0, tiles = 0;
+    int32_t smax = 0;
+    h->h_runs.resize((size_t)n_runs);
+    std::vector<RunState> h_state((size_t)n_runs);
+    for (int64_t r = 0; r < n_runs; ++r) {
+        RunParams& rp = h->h_runs[(size_t)r];
+        rp = RunParams{};
+        rp.off = N;
+        rp.n = cfg[r].n_particles;
+        rp.seed = cfg[r].seed;
+        rp.eps = cfg[r].step_size;
+        rp.ess_frac = cfg[r].ess_frac;
+        rp.init_scale = cfg[r].init_scale;
+        rp.adam_lr = cfg[r].adam_lr;
+        rp.adam_b1 = cfg[r].adam_b1;
+        rp.adam_b2 = cfg[r].adam_b2;
+        rp.adam_eps = cfg[r].adam_eps;
+        rp.log_L_lo = std::log(cfg[r].step_size);
+        rp.log_L_hi = std::log((double)cfg[r].max_steps * cfg[r].step_size);
+        rp.max_steps = cfg[r].max_steps;
+        rp.jitter = cfg[r].jitter;
+        rp.adapt = cfg[r].adapt;
+        rp.n_tiles = (int32_t)((rp.n + SCAN_TILE - 1) / SCAN_TILE);
+        rp.tile0 = tiles;
+        rp.n_iters = cfg[r].n_iters;
+        rp.n_warmup = cfg[r].n_warmup;
+        h_state[(size_t)r] = initial_state(rp, cfg[r]);
+        N += rp.n;
+        tiles += rp.n_tiles;
+        smax = std::max(smax, rp.max_steps);
+    }
+    h->N = N;
+    h->ld = round_up(N, 32);
+    h->n_tiles = tiles;
+    h->max_steps_all = smax;
+    std::vector<int32_t> run_of((size_t)N), tile_run((size_t)tiles);
+    for (int64_t r = 0; r < n_runs; ++r) {
+        const RunParams& rp = h->h_runs[(size_t)r];
+        for (int64_t i = 0; i < rp.n; ++i) run_of[(size_t)(rp.off + i)] = (int32_t)r;
+        for (int64_t t = 0; t < rp.n_tiles; ++t) tile_run[(size_t)(rp.tile0 + t)] = (int32_t)r;
+    }
+    DevAlloc& A = h->mem;
+    const size_t nd = (size_t)(h->D * h->ld);
+    h->d_runs = A.get<RunParams>((size_t)n_runs);
+    h->d_rstate = A.get<RunState>((size_t)n_runs);
+    h->d_run_of = A.get<int32_t>((size_t)N);
+    h->d_tile_run = A.get<int32_t>((size_t)tiles);
+    for (int b = 0; b < 2; ++b) {
+        h->theta[b] = A.get<float>(nd);
+        h->grad[b] = A.get<float>(nd);
+        h->logpi[b] = A.get<double>((size_t)h->ld);
+    }
+    h->p_final = A.get<float>(nd);
+    h->logw = A.get<double>((size_t)h->ld);
+    h->W = A.get<double>((size_t)h->ld);
+    h->dH = A.get<double>((size_t)h->ld);
+    h->alpha = A.get<double>((size_t)h->ld);
+    h->q = A.get<unsigned long long>((size_t)h->ld);
+    h->anc = A.get<int32_t>((size_t)h->ld);
+    h->src = A.get<int32_t>((size_t)h->ld);
+    h->steps = A.get<int32_t>((size_t)h->ld);
+    h->perm = A.get<int32_t>((size_t)h->ld);
+    h->hist = A.get<int32_t>((size_t)smax + 1);
+    h->counter = A.get<unsigned int>(4);
+    h->tiles = A.get<TileDesc>((size_t)tiles);
+    if (A.err != cudaSuccess) {
+        smc_status st = cuda_fail(h, A.err, "smc_init allocation");
+        smc_destroy(h);
+        return st;
+    }
+    cudaStream_t s = h->stream;
+    cudaMemcpyAsync(h->d_runs, h->h_runs.data(), sizeof(RunParams) * (size_t)n_runs, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->d_rstate, h_state.data(), sizeof(RunState) * (size_t)n_runs, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->d_run_of, run_of.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->d_tile_run, tile_run.data(), sizeof(int32_t) * (size_t)tiles, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(h->tiles, 0, sizeof(TileDesc) * (size_t)tiles, s);
+    cudaMemsetAsync(h->theta[0], 0, nd * sizeof(float), s);
+    cudaMemsetAsync(h->theta[1], 0, nd * sizeof(float), s);
+    cudaMemsetAsync(h->grad[0], 0, nd * sizeof(float), s);
+    cudaMemsetAsync(h->grad[1], 0, nd * sizeof(float), s);
+    cudaMemsetAsync(h->p_final, 0, nd * sizeof(float), s);
+
+    h->cfg.assign(cfg, cfg + n_runs);
+    cudaError_t ce = initial_draw(h);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        smc_status st = cuda_fail(h, ce, "smc_init");
+        fprintf(stderr, "%s\n", h->err.c_str());
+        smc_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SMC_OK;
+}
+
+smc_status read_stats(smc_handle* h, smc_stats* stats) {
+    std::vector<RunState> st((size_t)h->n_runs);
+    cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_step stats");
+    smc_status ret = SMC_OK;
+    for (int64_t r = 0; r < h->n_runs; ++r) {
+        const RunState& s = st[(size_t)r];
+        if (stats) {
+            smc_stats& o = stats[r];
+            o.ess = s.ess;
+            o.ess_pre = s.ess_pre;
+            o.log_z_inc = s.log_z_inc;
+            o.mean_alpha = s.mean_alpha;
+            o.traj_len = s.L_used;
+            o.grad_evals = s.grad_evals;
+            o.steps_min = s.steps_min;
+            o.steps_max = s.steps_max;
+            o.resampled = s.resample;
+            o.pad = 0;
+        }
+        if (s.status == -4) ret = fail(h, SMC_E_DEGENERATE, "all weights are zero in run " + std::to_string(r));
+        if (s.status == -5) ret = fail(h, SMC_E_TIMEOUT, "resampling look-back gave up in run " + std::to_string(r));
+    }
+    return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+smc_status smc_init(smc_handle** out, const smc_config* cfg, const smc_model* model, void* stream) {
+    return create(out, 1, cfg, model, stream);
+}
+
+smc_status smc_init_batch(smc_handle** out, int64_t n_runs, const smc_config* cfg, const smc_model* model,
+                          void* stream) {
+    return create(out, n_runs, cfg, model, stream);
+}
+
+smc_status smc_step(smc_handle* h, smc_stats* stats) {
+    if (!h) return SMC_E_INVAL;
+    if (h->sticky) return SMC_E_STATE;
+    cudaStream_t s = h->stream;
+    StepBufs b = make_bufs(h);
+    cudaError_t e = launch_normalise(b, s);
+    if (e == cudaSuccess) e = launch_resample_scan(b, s);
+    if (e == cudaSuccess) e = launch_steps_sort(b, s);
+    if (e == cudaSuccess) {
+        TrajArgs a{};
+        a.theta_in = h->theta[h->cur];
+        a.grad_in = h->grad[h->cur];
+        a.logpi_in = h->logpi[h->cur];
+        a.theta_out = h->theta[1 - h->cur];
+        a.grad_out = h->grad[1 - h->cur];
+        a.logpi_out = h->logpi[1 - h->cur];
+        a.p_out = h->p_final;
+        a.dH = h->dH;
+        a.alpha = h->alpha;
+        a.steps = h->steps;
+        a.perm = h->perm;
+        a.src = h->src;
+        a.run_of = h->d_run_of;
+        a.runs = h->d_runs;
+        a.rstate = h->d_rstate;
+        a.N = h->N;
+        a.ld = h->ld;
+        if (h->profiling) {
+            const size_t i = 2 * h->n_event_pairs;
+            while (h->events.size() < i + 2) {
+                cudaEvent_t ev;
+                e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return cuda_fail(h, e, "smc_step profiling");
+                h->events.push_back(ev);
+            }
+            cudaEventRecord(h->events[i], s);
+            e = launch_traj(h->model.m, a, h->precision, s);
+            cudaEventRecord(h->events[i + 1], s);
+            h->n_event_pairs += 1;
+            h->kernel_launches += 7;
+        } else {
+            e = launch_traj(h->model.m, a, h->precision, s);
+        }
+    }
+    if (e == cudaSuccess) e = launch_reweight_chees(b, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_step launch");
+    h->cur = 1 - h->cur;
+    h->iters_done += 1;
+    if (stats) return read_stats(h, stats);
+    return SMC_OK;
+}
+
+smc_status smc_run(smc_handle* h, int64_t n_iters, smc_stats* per_iter) {
+    if (!h || n_iters < 0) return SMC_E_INVAL;
+    for (int64_t k = 0; k < n_iters; ++k) {
+        smc_status st = smc_step(h, per_iter ? per_iter + k * h->n_runs : nullptr);
+        if (st != SMC_OK) return st;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_log_evidence(const smc_handle* hc, double* out) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h || !out) return SMC_E_INVAL;
+    std::vector<RunState> st((size_t)h->n_runs);
+    cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_log_evidence");
+    smc_status ret = SMC_OK;
+    for (int64_t r = 0; r < h->n_runs; ++r) {
+        out[r] = st[(size_t)r].log_z;
+        if (st[(size_t)r].status == -4) ret = fail(h, SMC_E_DEGENERATE, "all weights are zero");
+        if (st[(size_t)r].status == -5) ret = fail(h, SMC_E_TIMEOUT, "resampling look-back gave up");
+    }
+    return ret;
+}
+
+smc_status smc_get_layout(const smc_handle* h, int64_t* ld, int64_t* n_total, int64_t* n_runs) {
+    if (!h) return SMC_E_INVAL;
+    if (ld) *ld = h->ld;
+    if (n_total) *n_total = h->N;
+    if (n_runs) *n_runs = h->n_runs;
+    return SMC_OK;
+}
+
+smc_status smc_get_buffer(const smc_handle* hc, int32_t which, void* dst, int64_t bytes, int32_t device_ptrs) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h || !dst || bytes < 0) return SMC_E_INVAL;
+    const void* srcp = nullptr;
+    int64_t avail = 0;
+    const int64_t nd = h->D * h->ld;
+    std::vector<double> runstate;
+    switch (which) {
+        case SMC_BUF_THETA: srcp = h->theta[h->cur]; avail = nd * 4; break;
+        case SMC_BUF_GRAD: srcp = h->grad[h->cur]; avail = nd * 4; break;
+        case SMC_BUF_LOGPI: srcp = h->logpi[h->cur]; avail = h->N * 8; break;
+        case SMC_BUF_LOGW: srcp = h->logw; avail = h->N * 8; break;
+        case SMC_BUF_W: srcp = h->W; avail = h->N * 8; break;
+        case SMC_BUF_ANCESTORS: srcp = h->anc; avail = h->N * 4; break;
+        case SMC_BUF_STEPS: srcp = h->steps; avail = h->N * 4; break;
+        case SMC_BUF_P_FINAL: srcp = h->p_final; avail = nd * 4; break;
+        case SMC_BUF_DH: srcp = h->dH; avail = h->N * 8; break;
+        case SMC_BUF_ALPHA: srcp = h->alpha; avail = h->N * 8; break;
+        case SMC_BUF_THETA_PREV: srcp = h->theta[1 - h->cur]; avail = nd * 4; break;
+        case SMC_BUF_RUNSTATE: {
+            std::vector<RunState> st((size_t)h->n_runs);
+            cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,
+                                            cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "smc_get_buffer");
+            runstate.resize((size_t)(8 * h->n_runs));
+            for (int64_t r = 0; r < h->n_runs; ++r) std::memcpy(&runstate[(size_t)(8 * r)], &st[(size_t)r], 64);
+            if (bytes > (int64_t)(runstate.size() * 8)) return SMC_E_INVAL;
+            if (device_ptrs) {
+                e = cudaMemcpyAsync(dst, runstate.data(), (size_t)bytes, cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+                return e == cudaSuccess ? SMC_OK : cuda_fail(h, e, "smc_get_buffer");
+            }
+            std::memcpy(dst, runstate.data(), (size_t)bytes);
+            return SMC_OK;
+        }
+        default: return SMC_E_INVAL;
+    }
+    if (bytes > avail) return SMC_E_INVAL;
+    cudaError_t e = cudaMemcpyAsync(dst, srcp, (size_t)bytes,
+                                    device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? SMC_OK : cuda_fail(h, e, "smc_get_buffer");
+}
+
+smc_status smc_get_particles(const smc_handle* hc, float* theta, double* logw, int32_t device_ptrs) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h) return SMC_E_INVAL;
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (theta)
+        e = cudaMemcpy2DAsync(theta, (size_t)h->N * sizeof(float), h->theta[h->cur], (size_t)h->ld * sizeof(float),
+                              (size_t)h->N * sizeof(float), (size_t)h->D, kind, h->stream);
+    if (e == cudaSuccess && logw) e = cudaMemcpyAsync(logw, h->logw, (size_t)h->N * 8, kind, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? SMC_OK : cuda_fail(h, e, "smc_get_particles");
+}
+
+smc_status smc_moments(const smc_handle* hc, double* mean, double* var) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h || !mean) return SMC_E_INVAL;
+    const int64_t n = h->h_runs[0].n, D = h->D;
+    std::vector<float> th((size_t)(D * h->N));
+    std::vector<double> lw((size_t)h->N);
+    smc_status st = smc_get_particles(h, th.data(), lw.data(), 0);
+    if (st != SMC_OK) return st;
+    double m = -INFINITY;
+    for (int64_t j = 0; j < n; ++j) m = std::fmax(m, lw[(size_t)j]);
+    if (!(m > -INFINITY)) return fail(h, SMC_E_DEGENERATE, "all weights are zero");
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += std::exp(lw[(size_t)j] - m);
+    for (int64_t d = 0; d < D; ++d) {
+        double mu = 0.0;
+        for (int64_t j = 0; j < n; ++j) mu += std::exp(lw[(size_t)j] - m) / s * th[(size_t)(d * h->N + j)];
+        double v = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            const double e = th[(size_t)(d * h->N + j)] - mu;
+            v += std::exp(lw[(size_t)j] - m) / s * e * e;
+        }
+        mean[d] = mu;
+        if (var) var[d] = v;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_reset(smc_handle* h, uint64_t seed) {
+    if (!h) return SMC_E_INVAL;
+    if (h->sticky == SMC_E_CUDA) return SMC_E_STATE;
+    std::vector<RunState> st((size_t)h->n_runs);
+    for (int64_t r = 0; r < h->n_runs; ++r) {
+        h->h_runs[(size_t)r].seed = seed + (uint64_t)r;
+        st[(size_t)r] = initial_state(h->h_runs[(size_t)r], h->cfg[(size_t)r]);
+    }
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaMemcpyAsync(h->d_runs, h->h_runs.data(), sizeof(RunParams) * (size_t)h->n_runs,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_rstate, st.data(), sizeof(RunState) * (size_t)h->n_runs, cudaMemcpyHostToDevice, s);
+    // the staging vectors are pageable: the copies have consumed them on return
+    if (e == cudaSuccess) e = initial_draw(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_reset");
+    h->sticky = 0;
+    h->err.clear();
+    h->iters_done = 0;
+    return SMC_OK;
+}
+
+smc_status smc_get_summary(const smc_handle* hc, smc_summary* out) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h || !out) return SMC_E_INVAL;
+    std::vector<RunState> st((size_t)h->n_runs);
+    cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_get_summary");
+    for (int64_t r = 0; r < h->n_runs; ++r) {
+        const RunState& x = st[(size_t)r];
+        out[r].iterations = x.iters_total;
+        out[r].grad_evals = x.grad_evals_total;
+        out[r].ess_sum = x.ess_sum;
+        out[r].ess_sum_post_warmup = x.ess_sum_post;
+        out[r].log_z = x.log_z;
+        out[r].resamples = x.resamples_total;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_profile(smc_handle* h, int32_t enable) {
+    if (!h) return SMC_E_INVAL;
+    h->profiling = enable != 0;
+    if (enable) {
+        h->n_event_pairs = 0;
+        h->kernel_launches = 0;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_get_profile(smc_handle* h, double* traj_ms, int64_t* traj_launches, int64_t* kernel_launches) {
+    if (!h) return SMC_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_get_profile");
+    double total = 0.0;
+    for (size_t i = 0; i < h->n_event_pairs; ++i) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "smc_get_profile");
+        total += ms;
+    }
+    if (traj_ms) *traj_ms = total;
+    if (traj_launches) *traj_launches = (int64_t)h->n_event_pairs;
+    if (kernel_launches) *kernel_launches = h->kernel_launches;
+    return SMC_OK;
+}
+
+smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len) {
+    if (!h || !buf || len < 1) return SMC_E_INVAL;
+    std::snprintf(buf, (size_t)len, "%s", h->err.c_str());
+    return SMC_OK;
+}
+
+void smc_destroy(smc_handle* h) {
+    if (!h) return;
+    for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+    h->mem.release();
+    h->model.mem.release();
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+// ------------------------------------------------------------------ kernel-level
+smc_status smc_model_create(smc_dev_model** out, const smc_model* model, void* stream) {
+    if (!out) return SMC_E_INVAL;
+    *out = nullptr;
+    smc_dev_model* m = new smc_dev_model();
+    std::string e = upload_model(m, model, static_cast<cudaStream_t>(stream));
+    if (!e.empty()) {
+        fprintf(stderr, "smc_model_create: %s\n", e.c_str());
+        m->mem.release();
+        delete m;
+        return SMC_E_INVAL;
+    }
+    *out = m;
+    return SMC_OK;
+}
+
+void smc_model_destroy(smc_dev_model* m) {
+    if (!m) return;
+    cudaStream_t s = m->mem.s;
+    m->mem.release();
+    cudaStreamSynchronize(s);
+    delete m;
+}
+
+static smc_status kstatus(cudaError_t e) {
+    if (e == cudaSuccess) return SMC_OK;
+    fprintf(stderr, "libsmcchees: %s\n", cudaGetErrorString(e));
+    return e == cudaErrorInvalidValue ? SMC_E_INVAL : SMC_E_CUDA;
+}
+
+smc_status smc_k_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return SMC_E_INVAL;
+    return kstatus(launch_philox(seed, ctr, out, n, static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int64_t D, double* out, int64_t ld,
+                         void* stream) {
+    if (N < 0 || D < 1 || ld < N || (N > 0 && !out)) return SMC_E_INVAL;
+    return kstatus(launch_normals(seed, tag, k, N, D, out, ld, static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps, int32_t max_steps, int32_t jitter,
+                       double* out_h, int32_t* out_steps, void* stream) {
+    if (N < 0 || K < 1 || k < 0 || !(eps > 0.0) || max_steps < 1 || (N > 0 && !out_steps)) return SMC_E_INVAL;
+    if (N * K + k >= (1ll << 32)) return SMC_E_INVAL;
+    return kstatus(launch_steps_only(N, K, k, L, eps, max_steps, jitter, out_h, out_steps,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_target(const smc_dev_model* m, const float* theta, int64_t N, int64_t ld, double* logpi,
+                        float* grad, int32_t precision, void* stream) {
+    if (!m || N < 0 || ld < N || (N > 0 && (!theta || !logpi || !grad))) return SMC_E_INVAL;
+    if (!traj_supported(m->m, precision)) return SMC_E_INVAL;
+    TrajArgs a{};
+    a.theta_in = theta;
+    a.grad_out = grad;
+    a.logpi_out = logpi;
+    a.N = N;
+    a.ld = ld;
+    a.eval_only = 1;
+    return kstatus(launch_traj(m->m, a, precision, static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_leapfrog(const smc_dev_model* m, float* theta, float* p, float* grad, double* logpi,
+                          const int32_t* steps, double eps, int64_t N, int64_t ld, int32_t precision, void* stream) {
+    if (!m || N < 0 || ld < N || !(eps > 0.0)) return SMC_E_INVAL;
+    if (N > 0 && (!theta || !p || !grad || !logpi || !steps)) return SMC_E_INVAL;
+    if (!traj_supported(m->m, precision)) return SMC_E_INVAL;
+    TrajArgs a{};
+    a.theta_in = theta;
+    a.grad_in = grad;
+    a.logpi_in = logpi;
+    a.theta_out = theta;
+    a.grad_out = grad;
+    a.logpi_out = logpi;
+    a.p_in = p;
+    a.p_out = p;
+    a.steps = steps;
+    a.eps_fixed = eps;
+    a.N = N;
+    a.ld = ld;
+    return kstatus(launch_traj(m->m, a, precision, static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_normalise(const double* logw, int64_t N, double* W, double* lse, double* ess, void* stream) {
+    if (N < 1 || !logw || !W || !lse || !ess) return SMC_E_INVAL;
+    return kstatus(launch_normalise_flat(logw, N, W, lse, ess, static_cast<cudaStream_t>(stream)));
+}
+
+int64_t smc_k_resample_scratch_bytes(int64_t N) { return N < 1 ? 0 : resample_scratch_bytes(N); }
+
+smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q, int32_t* ancestors,
+                          int32_t* status_out, void* scratch, void* stream) {
+    if (N < 1 || N > (1ll << 30) || !W || !q || !ancestors || !status_out || !scratch) return SMC_E_INVAL;
+    return kstatus(launch_resample_flat(W, N, r64, reinterpret_cast<unsigned long long*>(q), ancestors, status_out,
+                                        scratch, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// smc_kernels.cuh -- launchers of the per-iteration SMC kernels (smc_kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace smc {
+
+// Decoupled look-back descriptor of one scan tile: aggregate and inclusive
+// prefix (uint64), published with an epoch-tagged flag.
+struct TileDesc {
+    unsigned long long agg;
+    unsigned long long incl;
+    unsigned int flag;      // (epoch << 2) | {0: not ready, 1: aggregate, 2: prefix}
+    unsigned int pad;
+};
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Per-iteration buffers shared by the stage kernels.
+struct StepBufs {
+    const RunParams* runs;
+    RunState* rstate;
+    const int32_t* run_of;      // particle -> run
+    const int32_t* tile_run;    // scan tile -> run
+    int64_t n_runs, N, ld, D;
+    double* logw;               // [N]
+    double* W;                  // [N]
+    unsigned long long* q;      // [N]
+    int32_t* anc;               // [N] run-local ancestor of each output slot
+    int32_t* src;               // [N] global source index of each particle
+    int32_t* steps;             // [N]
+    int32_t* perm;              // [N] slot -> particle (sorted by steps, descending)
+    int32_t* hist;              // [max_steps + 1]
+    unsigned int* counter;      // dynamic tile counter + sort scratch
+    TileDesc* tiles;
+    int64_t n_tiles;
+    int32_t max_steps_all;
+    int32_t pad;
+    // trajectory results
+    const float* theta_prev;    // positions before the move (source buffer)
+    const float* theta_new;     // proposals
+    const float* p_final;
+    const double* dH;
+    const double* alpha;
+};
+
+cudaError_t launch_init_draw(const StepBufs& b, float* theta, cudaStream_t s);
+cudaError_t launch_init_finish(const StepBufs& b, const double* logpi, cudaStream_t s);
+cudaError_t launch_normalise(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_resample_scan(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_steps_sort(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_reweight_chees(const StepBufs& b, cudaStream_t s);
+
+// Kernel-level entry points (stand-alone buffers).
+cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n, cudaStream_t s);
+cudaError_t launch_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int64_t D, double* out,
+                           int64_t ld, cudaStream_t s);
+cudaError_t launch_steps_only(int64_t N, int64_t K, int64_t k, double L, double eps, int32_t max_steps,
+                              int32_t jitter, double* out_h, int32_t* out_steps, cudaStream_t s);
+cudaError_t launch_normalise_flat(const double* logw, int64_t N, double* W, double* lse, double* ess,
+                                  cudaStream_t s);
+// Stand-alone resampling: scratch layout = [RunParams][RunState][TileDesc x tiles][counter].
+int64_t resample_scratch_bytes(int64_t N);
+cudaError_t launch_resample_flat(const double* W, int64_t N, uint64_t r64, unsigned long long* q,
+                                 int32_t* anc, int32_t* status, void* scratch, cudaStream_t s);
+
+}  // namespace smc

@@ -1,0 +1,57 @@
+// traj.cuh -- interfaces between the host driver and the trajectory kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace smc {
+
+enum ModelKind : int32_t { GAUSS_DENSE = 0, LOGISTIC = 1, HIER_NORMAL = 2, BANANA = 3, LINEAR_GAUSS = 4 };
+
+// Device-resident target (Sec. 2 of the paper).  FP32 copies of the data;
+// X is row-major [n x Dp] with Dp = D rounded up to a multiple of 4 and
+// zero padding.  lconst holds the additive FP64 constant of log pi that does
+// not depend on theta (normalisers), computed once on the host.
+struct DevModel {
+    int32_t kind, D, Dp, n;
+    const float* X;       // [n x Dp]
+    const float* y;       // [n]
+    const float* mu;      // [D]         GAUSS_DENSE
+    const float* P;       // [D x D]     GAUSS_DENSE
+    const float* gmean;   // [n]         HIER_NORMAL group means
+    const float* gn;      // [n]         group sizes
+    const float* gss;     // [n]         within-group sums of squares
+    const uint16_t* Xbf;  // [n x Dp] bf16 (high part), tensor-core paths
+    const uint16_t* Xbf_lo; // [n x Dp] bf16 residual x - bf16(x)
+    double h0, h1;        // LOGISTIC: tau; LINEAR: sigma, tau; HIER: sigma; BANANA: a, b
+    double lconst;        // theta-independent part of log pi
+};
+
+// What a trajectory launch reads and writes.  Slot t of the launch handles
+// particle j = perm ? perm[t] : t; it starts from source index src[j] (the
+// resampled ancestor) or j; outputs go to index j.
+struct TrajArgs {
+    const float* theta_in; const float* grad_in; const double* logpi_in;
+    float* theta_out; float* grad_out; double* logpi_out;
+    const float* p_in;      // momenta given by the caller (nullptr: draw from Philox)
+    float* p_out;           // final momenta (may be nullptr)
+    double* dH;             // Delta H (may be nullptr)
+    double* alpha;          // min(1, exp(-Delta H)) (may be nullptr)
+    const int32_t* steps;   // S_j
+    const int32_t* perm;    // slot -> particle (may be nullptr)
+    const int32_t* src;     // particle -> source index (may be nullptr)
+    const int32_t* run_of;  // particle -> run (may be nullptr: run 0)
+    const RunParams* runs;  // per-run parameters (may be nullptr if eps_fixed used)
+    const RunState* rstate; // per-run state: k for the momentum counter
+    double eps_fixed;       // step size when runs == nullptr
+    int64_t N, ld;
+    int32_t eval_only;      // 1: compute log pi and grad at theta_in, no move
+    int32_t pad;
+};
+
+// Launchers (kernels in traj_simt.cu / traj_tc.cu).  Return cudaError_t of
+// the launch; `supported` reports whether the model/shape has a kernel.
+bool traj_supported(const DevModel& m, int32_t precision);
+cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s);
+
+}  // namespace smc

@@ -1,0 +1,608 @@
+// traj_simt.cu -- FP32 SIMT leapfrog trajectory kernels (Sec. 2.1, Algorithm 1)
+// with the fused momentum draw (Sec. 2.1: p ~ N(0, I)), the endpoint energy
+// error Delta H and the acceptance probability min(1, exp(-Delta H)).
+//
+// Two kernel families:
+//  * traj_thread_kernel: one thread per particle, theta/p/grad in registers;
+//    for targets whose gradient is cheap per particle (dense Gaussian with
+//    D <= 32, banana, hierarchical normal).
+//  * traj_glm_kernel: one CTA per group of G particles for the GEMM-shaped
+//    likelihoods (logistic and linear-Gaussian regression): the design matrix
+//    X stays in shared memory for the whole trajectory, the 512 threads split
+//    the observations (lanes of a half-warp share one broadcast row of X) and
+//    the per-particle gradient X'r is reduced across slices through shared
+//    memory once per leapfrog step.
+#include <cstdio>
+#include <math_constants.h>
+#include "traj.cuh"
+
+namespace smc {
+
+// ============================================================ thread models
+template <int DM>
+struct GaussDenseM {
+    static size_t smem_bytes(const DevModel& m) { return (size_t)(m.D * m.D + m.D) * sizeof(float); }
+    __device__ static void load(const DevModel& m, float* sm) {
+        for (int i = threadIdx.x; i < m.D * m.D; i += blockDim.x) sm[i] = m.P[i];
+        for (int i = threadIdx.x; i < m.D; i += blockDim.x) sm[m.D * m.D + i] = m.mu[i];
+    }
+    // grad log pi = -P (theta - mu)
+    __device__ static void grad(const DevModel& m, const float* sm, const float (&th)[DM], float (&g)[DM]) {
+        const int D = m.D;
+        const float* P = sm;
+        const float* mu = sm + D * D;
+        float dl[DM];
+#pragma unroll
+        for (int d = 0; d < DM; ++d) dl[d] = d < D ? th[d] - mu[d] : 0.0f;
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+            float acc = 0.0f;
+            if (a < D) {
+#pragma unroll
+                for (int b = 0; b < DM; ++b)
+                    if (b < D) acc = fmaf(P[a * D + b], dl[b], acc);
+            }
+            g[a] = -acc;
+        }
+    }
+    // log pi = c - 1/2 (theta - mu)' P (theta - mu), in FP64
+    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM]) {
+        const int D = m.D;
+        const float* P = sm;
+        const float* mu = sm + D * D;
+        double q = 0.0;
+        for (int a = 0; a < D; ++a) {
+            double row = 0.0;
+            for (int b = 0; b < D; ++b) row += (double)P[a * D + b] * ((double)th[b] - (double)mu[b]);
+            q += ((double)th[a] - (double)mu[a]) * row;
+        }
+        return m.lconst - 0.5 * q;
+    }
+};
+
+// Banana pairs (Sec. 4, Rosenbrock): x_o ~ N(0, a), x_e ~ N(b (x_o^2 - a), 1).
+template <int DM>
+struct BananaM {
+    static size_t smem_bytes(const DevModel&) { return 0; }
+    __device__ static void load(const DevModel&, float*) {}
+    __device__ static void grad(const DevModel& m, const float*, const float (&th)[DM], float (&g)[DM]) {
+        const float a = (float)m.h0, b = (float)m.h1, inva = (float)(1.0 / m.h0);
+#pragma unroll
+        for (int i = 0; i + 1 < DM; i += 2) {
+            if (i + 1 < m.D) {
+                float xo = th[i], xe = th[i + 1];
+                float u = xe - b * (xo * xo - a);
+                g[i] = -xo * inva + 2.0f * b * u * xo;
+                g[i + 1] = -u;
+            } else {
+                g[i] = 0.0f;
+                g[i + 1] = 0.0f;
+            }
+        }
+        if (DM & 1) g[DM - 1] = 0.0f;
+    }
+    __device__ static double logpi(const DevModel& m, const float*, const float (&th)[DM]) {
+        double s = 0.0;
+        for (int i = 0; i + 1 < m.D; i += 2) {
+            double xo = th[i], xe = th[i + 1];
+            double u = xe - m.h1 * (xo * xo - m.h0);
+            s += -0.5 * xo * xo / m.h0 - 0.5 * u * u;
+        }
+        return s + m.lconst;
+    }
+};
+
+// Non-centred hierarchical normal with group sufficient statistics:
+// theta = (mu, log tau, eta_1..eta_G), b_g = mu + tau eta_g.
+template <int DM>
+struct HierM {
+    static size_t smem_bytes(const DevModel& m) { return (size_t)3 * m.n * sizeof(float); }
+    __device__ static void load(const DevModel& m, float* sm) {
+        for (int i = threadIdx.x; i < m.n; i += blockDim.x) {
+            sm[i] = m.gmean[i];
+            sm[m.n + i] = m.gn[i];
+            sm[2 * m.n + i] = m.gss[i];
+        }
+    }
+    __device__ static void grad(const DevModel& m, const float* sm, const float (&th)[DM], float (&g)[DM]) {
+        const float inv_s2 = (float)(1.0 / (m.h0 * m.h0));
+        const float mu = th[0], logtau = th[1], tau = expf(logtau);
+        float dmu = 0.0f, dlt = 0.0f;
+#pragma unroll
+        for (int d = 2; d < DM; ++d) {
+            float gd = 0.0f;
+            if (d < m.D) {
+                const int k = d - 2;
+                float eta = th[d];
+                float r = sm[m.n + k] * (sm[k] - fmaf(tau, eta, mu)) * inv_s2;
+                dmu += r;
+                dlt = fmaf(r * tau, eta, dlt);
+                gd = fmaf(r, tau, -eta);
+            }
+            g[d] = gd;
+        }
+        g[0] = dmu - mu;
+        g[1] = dlt - logtau;
+    }
+    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM]) {
+        const double s2 = m.h0 * m.h0;
+        const double mu = th[0], logtau = th[1], tau = exp(logtau);
+        double s = -0.5 * mu * mu - 0.5 * logtau * logtau;
+        for (int k = 0; k < m.n; ++k) {
+            double eta = th[2 + k];
+            double dev = (double)sm[k] - (mu + tau * eta);
+            s += -0.5 * ((double)sm[2 * m.n + k] + (double)sm[m.n + k] * dev * dev) / s2 - 0.5 * eta * eta;
+        }
+        return s + m.lconst;
+    }
+};
+
+__device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& r, double& eps,
+                                             uint64_t& seed, uint32_t& kk, uint32_t& jl) {
+    r = a.run_of ? a.run_of[j] : 0;
+    if (a.runs) {
+        eps = a.runs[r].eps;
+        seed = a.runs[r].seed;
+        jl = (uint32_t)(j - a.runs[r].off);
+    } else {
+        eps = a.eps_fixed;
+        seed = 0;
+        jl = (uint32_t)j;
+    }
+    kk = a.rstate ? (uint32_t)a.rstate[r].k : 0u;
+}
+
+template <template <int> class MT, int DM>
+__global__ void __launch_bounds__(128) traj_thread_kernel(DevModel m, TrajArgs a) {
+    using M = MT<DM>;
+    extern __shared__ __align__(16) float sm[];
+    M::load(m, sm);
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.N) return;
+    const int64_t j = a.perm ? a.perm[t] : t;
+    const int64_t src = a.src ? a.src[j] : j;
+    const int D = m.D;
+    int r;
+    double eps;
+    uint64_t seed;
+    uint32_t kk, jl;
+    particle_run(a, j, r, eps, seed, kk, jl);
+
+    float th[DM], g[DM], p[DM];
+#pragma unroll
+    for (int d = 0; d < DM; ++d) th[d] = d < D ? a.theta_in[(int64_t)d * a.ld + src] : 0.0f;
+
+    if (a.eval_only) {
+        M::grad(m, sm, th, g);
+        double lp = M::logpi(m, sm, th);
+#pragma unroll
+        for (int d = 0; d < DM; ++d)
+            if (d < D) a.grad_out[(int64_t)d * a.ld + j] = g[d];
+        a.logpi_out[j] = lp;
+        return;
+    }
+
+#pragma unroll
+    for (int d = 0; d < DM; ++d) g[d] = d < D ? a.grad_in[(int64_t)d * a.ld + src] : 0.0f;
+    const double lp0 = a.logpi_in[src];
+    if (a.p_in) {
+#pragma unroll
+        for (int d = 0; d < DM; ++d) p[d] = d < D ? a.p_in[(int64_t)d * a.ld + j] : 0.0f;
+    } else {
+#pragma unroll
+        for (int d = 0; d < DM; d += 2) {
+            double z0 = 0.0, z1 = 0.0;
+            if (d < D) normal_pair(seed, (uint32_t)(d >> 1), jl, kk, TAG_MOM, z0, z1);
+            p[d] = d < D ? (float)z0 : 0.0f;
+            if (d + 1 < DM) p[d + 1] = d + 1 < D ? (float)z1 : 0.0f;
+        }
+    }
+    double kin0 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DM; ++d) kin0 += (double)p[d] * (double)p[d];
+    const double H0 = 0.5 * kin0 - lp0;
+
+    const int S = a.steps[j];
+    const float ef = (float)eps, he = (float)(0.5 * eps);
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int d = 0; d < DM; ++d) p[d] = fmaf(he, g[d], p[d]);
+#pragma unroll
+        for (int d = 0; d < DM; ++d) th[d] = fmaf(ef, p[d], th[d]);
+        M::grad(m, sm, th, g);
+#pragma unroll
+        for (int d = 0; d < DM; ++d) p[d] = fmaf(he, g[d], p[d]);
+    }
+    const double lp1 = M::logpi(m, sm, th);
+    double kin1 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DM; ++d) kin1 += (double)p[d] * (double)p[d];
+    double dH = (0.5 * kin1 - lp1) - H0;
+    if (!isfinite(dH)) dH = CUDART_INF;
+#pragma unroll
+    for (int d = 0; d < DM; ++d) {
+        if (d < D) {
+            a.theta_out[(int64_t)d * a.ld + j] = th[d];
+            a.grad_out[(int64_t)d * a.ld + j] = g[d];
+            if (a.p_out) a.p_out[(int64_t)d * a.ld + j] = p[d];
+        }
+    }
+    a.logpi_out[j] = lp1;
+    if (a.dH) a.dH[j] = dH;
+    if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
+}
+
+// ============================================================ GLM kernel
+// G particles per CTA, 512 threads: thread -> (particle pl = tid % G, slice
+// sl = tid / G); slice sl owns observations i = sl, sl + SL, ... (SL = 512/G).
+constexpr int GLM_THREADS = 512;
+
+template <int DP, int G>
+struct GlmSmem {
+    static constexpr int NW = GLM_THREADS / 32;
+    static size_t bytes(int n) {
+        size_t npad = (size_t)((n + 3) & ~3);
+        return sizeof(float) * ((size_t)n * DP + npad + 3 * DP * G + (size_t)NW * DP * G) +
+               sizeof(double) * (2 * G + NW * G) + sizeof(int) * (G + 4);
+    }
+};
+
+template <bool LOGIT>
+__device__ __forceinline__ float glm_resid(float y, float eta, float inv_s2) {
+    if (LOGIT) return y - __fdividef(1.0f, 1.0f + __expf(-eta));
+    return (y - eta) * inv_s2;
+}
+
+template <bool LOGIT>
+__device__ __forceinline__ float glm_loglik_term(float y, float eta, float inv_s) {
+    if (LOGIT) {
+        float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
+        return y * eta - sp;
+    }
+    float z = (y - eta) * inv_s;
+    return -0.5f * z * z;
+}
+
+template <int DP, int G, bool LOGIT>
+__global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, TrajArgs a) {
+    constexpr int NT = GLM_THREADS, NW = NT / 32, SL = NT / G;
+    static_assert(G <= 32 && (32 % G) == 0, "G must divide 32");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = m.n, D = m.D;
+    const int npad = (n + 3) & ~3;
+    float* Xs = reinterpret_cast<float*>(smem_raw);
+    float* ys = Xs + (size_t)n * DP;
+    float* th_s = ys + npad;
+    float* p_s = th_s + DP * G;
+    float* g_s = p_s + DP * G;
+    float* red = g_s + DP * G;
+    double* H0_s = reinterpret_cast<double*>(red + NW * DP * G);
+    double* lp_s = H0_s + G;
+    double* red64 = lp_s + G;
+    int* S_s = reinterpret_cast<int*>(red64 + NW * G);
+    int* smax_s = S_s + G;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int pl = tid % G, sl = tid / G;
+
+    // ---- model data into shared memory (whole trajectory reuses it)
+    {
+        const float4* Xg = reinterpret_cast<const float4*>(m.X);
+        float4* Xs4 = reinterpret_cast<float4*>(Xs);
+        const int nv = n * (DP / 4);
+        for (int i = tid; i < nv; i += NT) Xs4[i] = Xg[i];
+        for (int i = tid; i < n; i += NT) ys[i] = m.y[i];
+    }
+    const float inv_tau2 = LOGIT ? (float)(1.0 / (m.h0 * m.h0)) : (float)(1.0 / (m.h1 * m.h1));
+    const double inv_tau2_d = LOGIT ? 1.0 / (m.h0 * m.h0) : 1.0 / (m.h1 * m.h1);
+    const float inv_s2 = LOGIT ? 0.0f : (float)(1.0 / (m.h0 * m.h0));
+    const float inv_s = LOGIT ? 0.0f : (float)(1.0 / m.h0);
+
+    // ---- particle state of this CTA
+    const int64_t slot0 = (int64_t)blockIdx.x * G;
+    __shared__ int64_t j_s[G], src_s[G];
+    __shared__ float eps_s[G];
+    __shared__ uint64_t seed_s[G];
+    __shared__ uint32_t k_s[G], jl_s[G];
+    if (tid < G) {
+        const int64_t t = slot0 + tid;
+        int64_t j = -1, src = -1;
+        int S = 0;
+        float ef = 0.0f;
+        if (t < a.N) {
+            j = a.perm ? a.perm[t] : t;
+            src = a.src ? a.src[j] : j;
+            S = a.eval_only ? 0 : a.steps[j];
+            int r;
+            double eps;
+            uint64_t seed;
+            uint32_t kk, jl;
+            particle_run(a, j, r, eps, seed, kk, jl);
+            ef = (float)eps;
+            seed_s[tid] = seed;
+            k_s[tid] = kk;
+            jl_s[tid] = jl;
+        }
+        j_s[tid] = j;
+        src_s[tid] = src;
+        S_s[tid] = S;
+        eps_s[tid] = ef;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int mx = 0;
+        for (int i = 0; i < G; ++i) mx = max(mx, S_s[i]);
+        *smax_s = mx;
+    }
+    for (int e = tid; e < DP * G; e += NT) {
+        const int d = e / G, q = e % G;
+        const int64_t src = src_s[q];
+        float tv = 0.0f, gv = 0.0f, pv = 0.0f;
+        if (src >= 0 && d < D) {
+            tv = a.theta_in[(int64_t)d * a.ld + src];
+            if (!a.eval_only) gv = a.grad_in[(int64_t)d * a.ld + src];
+            if (a.p_in && !a.eval_only) pv = a.p_in[(int64_t)d * a.ld + j_s[q]];
+        }
+        th_s[d * G + q] = tv;
+        g_s[d * G + q] = gv;
+        p_s[d * G + q] = pv;
+    }
+    __syncthreads();
+    if (!a.p_in && !a.eval_only) {
+        // momentum p ~ N(0, I) from the (seed, i, j, k, MOM) Philox stream
+        const int npairs = (D + 1) / 2;
+        for (int e = tid; e < npairs * G; e += NT) {
+            const int i = e / G, q = e % G;
+            if (j_s[q] < 0) continue;
+            double z0, z1;
+            normal_pair(seed_s[q], (uint32_t)i, jl_s[q], k_s[q], TAG_MOM, z0, z1);
+            p_s[(2 * i) * G + q] = (float)z0;
+            if (2 * i + 1 < D) p_s[(2 * i + 1) * G + q] = (float)z1;
+        }
+        __syncthreads();
+    }
+    if (tid < G && !a.eval_only) {
+        double kin = 0.0;
+        for (int d = 0; d < D; ++d) {
+            double v = p_s[d * G + tid];
+            kin += v * v;
+        }
+        H0_s[tid] = j_s[tid] >= 0 ? 0.5 * kin - a.logpi_in[src_s[tid]] : 0.0;
+    }
+    const int smax = *smax_s;
+
+    // ---- first half kick and drift of step 1
+    for (int e = tid; e < DP * G; e += NT) {
+        const int d = e / G, q = e % G;
+        if (d < D && S_s[q] >= 1) {
+            const float ef = eps_s[q], he = 0.5f * ef;
+            float pv = fmaf(he, g_s[e], p_s[e]);
+            p_s[e] = pv;
+            th_s[e] = fmaf(ef, pv, th_s[e]);
+        }
+    }
+    __syncthreads();
+
+    const int nsteps = a.eval_only ? 1 : smax;
+    for (int s = 1; s <= nsteps; ++s) {
+        // ---- gradient X'(y - sigmoid(X theta)) for the G particles (phase B)
+        float th[DP], acc[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            th[d] = th_s[d * G + pl];
+            acc[d] = 0.0f;
+        }
+        for (int i = sl; i < n; i += SL) {
+            const float4* xr = reinterpret_cast<const float4*>(Xs + (size_t)i * DP);
+            float4 xv[DP / 4];
+#pragma unroll
+            for (int q = 0; q < DP / 4; ++q) xv[q] = xr[q];
+            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < DP / 4; ++q) {
+                e0 = fmaf(xv[q].x, th[4 * q + 0], e0);
+                e1 = fmaf(xv[q].y, th[4 * q + 1], e1);
+                e2 = fmaf(xv[q].z, th[4 * q + 2], e2);
+                e3 = fmaf(xv[q].w, th[4 * q + 3], e3);
+            }
+            const float r = glm_resid<LOGIT>(ys[i], (e0 + e1) + (e2 + e3), inv_s2);
+#pragma unroll
+            for (int q = 0; q < DP / 4; ++q) {
+                acc[4 * q + 0] = fmaf(r, xv[q].x, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(r, xv[q].y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(r, xv[q].z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(r, xv[q].w, acc[4 * q + 3]);
+            }
+        }
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+#pragma unroll
+            for (int d = 0; d < DP; ++d) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+        }
+        if (lane < G) {
+#pragma unroll
+            for (int d = 0; d < DP; ++d) red[(wid * DP + d) * G + pl] = acc[d];
+        }
+        __syncthreads();
+        // ---- reduce, closing half kick of step s, opening kick + drift of s+1 (phase C)
+        for (int e = tid; e < DP * G; e += NT) {
+            const int d = e / G, q = e % G;
+            if (d >= D) continue;
+            float gs = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) gs += red[(w * DP + d) * G + q];
+            gs -= th_s[e] * inv_tau2;
+            if (a.eval_only) {
+                g_s[e] = gs;
+            } else if (s <= S_s[q]) {
+                const float ef = eps_s[q], he = 0.5f * ef;
+                g_s[e] = gs;
+                float pv = fmaf(he, gs, p_s[e]);
+                if (s + 1 <= S_s[q]) {
+                    pv = fmaf(he, gs, pv);
+                    th_s[e] = fmaf(ef, pv, th_s[e]);
+                }
+                p_s[e] = pv;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- endpoint log pi in FP64 accumulation (energy error, Eq. for alpha)
+    {
+        float th[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) th[d] = th_s[d * G + pl];
+        double ll = 0.0;
+        for (int i = sl; i < n; i += SL) {
+            const float4* xr = reinterpret_cast<const float4*>(Xs + (size_t)i * DP);
+            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < DP / 4; ++q) {
+                float4 x = xr[q];
+                e0 = fmaf(x.x, th[4 * q + 0], e0);
+                e1 = fmaf(x.y, th[4 * q + 1], e1);
+                e2 = fmaf(x.z, th[4 * q + 2], e2);
+                e3 = fmaf(x.w, th[4 * q + 3], e3);
+            }
+            ll += (double)glm_loglik_term<LOGIT>(ys[i], (e0 + e1) + (e2 + e3), inv_s);
+        }
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if (lane < G) red64[wid * G + pl] = ll;
+        __syncthreads();
+        if (tid < G) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += red64[w * G + tid];
+            double sq = 0.0;
+            for (int d = 0; d < D; ++d) {
+                double v = th_s[d * G + tid];
+                sq += v * v;
+            }
+            lp_s[tid] = s - 0.5 * sq * inv_tau2_d + m.lconst;
+        }
+        __syncthreads();
+    }
+
+    // ---- outputs
+    for (int e = tid; e < DP * G; e += NT) {
+        const int d = e / G, q = e % G;
+        const int64_t j = j_s[q];
+        if (j < 0 || d >= D) continue;
+        if (!a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th_s[e];
+        a.grad_out[(int64_t)d * a.ld + j] = g_s[e];
+        if (a.p_out && !a.eval_only) a.p_out[(int64_t)d * a.ld + j] = p_s[e];
+    }
+    if (tid < G && j_s[tid] >= 0) {
+        const int64_t j = j_s[tid];
+        const double lp1 = lp_s[tid];
+        a.logpi_out[j] = lp1;
+        if (!a.eval_only) {
+            double kin = 0.0;
+            for (int d = 0; d < D; ++d) {
+                double v = p_s[d * G + tid];
+                kin += v * v;
+            }
+            double dH = (0.5 * kin - lp1) - H0_s[tid];
+            if (!isfinite(dH)) dH = CUDART_INF;
+            if (a.dH) a.dH[j] = dH;
+            if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
+        }
+    }
+}
+
+// ============================================================ dispatch
+namespace {
+
+template <template <int> class MT, int DM>
+cudaError_t launch_thread(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const int bs = 128;
+    const size_t sm = MT<DM>::smem_bytes(m);
+    auto kern = traj_thread_kernel<MT, DM>;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t grid = (a.N + bs - 1) / bs;
+    if (grid == 0) return cudaSuccess;
+    kern<<<(unsigned)grid, bs, sm, s>>>(m, a);
+    return cudaGetLastError();
+}
+
+template <template <int> class MT>
+cudaError_t dispatch_thread(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const int D = m.D;
+    if (D <= 2) return launch_thread<MT, 2>(m, a, s);
+    if (D <= 4) return launch_thread<MT, 4>(m, a, s);
+    if (D <= 8) return launch_thread<MT, 8>(m, a, s);
+    if (D <= 12) return launch_thread<MT, 12>(m, a, s);
+    if (D <= 16) return launch_thread<MT, 16>(m, a, s);
+    if (D <= 32) return launch_thread<MT, 32>(m, a, s);
+    return cudaErrorInvalidValue;
+}
+
+template <template <int> class MT>
+cudaError_t dispatch_thread_wide(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const int D = m.D;
+    if (D <= 32) return dispatch_thread<MT>(m, a, s);
+    if (D <= 52) return launch_thread<MT, 52>(m, a, s);
+    if (D <= 64) return launch_thread<MT, 64>(m, a, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int DP, int G, bool LOGIT>
+cudaError_t launch_glm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const size_t sm = GlmSmem<DP, G>::bytes(m.n);
+    auto kern = traj_glm_kernel<DP, G, LOGIT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (a.N + G - 1) / G;
+    if (grid == 0) return cudaSuccess;
+    kern<<<(unsigned)grid, GLM_THREADS, sm, s>>>(m, a);
+    return cudaGetLastError();
+}
+
+template <bool LOGIT>
+cudaError_t dispatch_glm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    switch (m.Dp) {
+        case 4: return launch_glm<4, 16, LOGIT>(m, a, s);
+        case 8: return launch_glm<8, 16, LOGIT>(m, a, s);
+        case 16: return launch_glm<16, 16, LOGIT>(m, a, s);
+        case 28: return launch_glm<28, 16, LOGIT>(m, a, s);
+        case 32: return launch_glm<32, 16, LOGIT>(m, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool glm_shape_ok(const DevModel& m) {
+    if (m.Dp != 4 && m.Dp != 8 && m.Dp != 16 && m.Dp != 28 && m.Dp != 32) return false;
+    return GlmSmem<32, 16>::bytes(m.n) <= 220 * 1024;
+}
+
+}  // namespace
+
+bool traj_supported(const DevModel& m, int32_t precision) {
+    switch (m.kind) {
+        case GAUSS_DENSE: return precision == 0 && m.D <= 32;
+        case BANANA: return precision == 0 && m.D <= 64;
+        case HIER_NORMAL: return precision == 0 && m.D <= 64;
+        case LOGISTIC:
+        case LINEAR_GAUSS: return precision == 0 && glm_shape_ok(m);
+        default: return false;
+    }
+}
+
+cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s) {
+    if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
+    switch (m.kind) {
+        case GAUSS_DENSE: return dispatch_thread<GaussDenseM>(m, a, s);
+        case BANANA: return dispatch_thread_wide<BananaM>(m, a, s);
+        case HIER_NORMAL: return dispatch_thread_wide<HierM>(m, a, s);
+        case LOGISTIC: return dispatch_glm<true>(m, a, s);
+        case LINEAR_GAUSS: return dispatch_glm<false>(m, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace smc
