@@ -406,6 +406,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     cudaMemcpyAsync(h->d_run_of, run_of.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(h->d_tile_run, tile_run.data(), sizeof(int32_t) * (size_t)tiles, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->tiles, 0, sizeof(TileDesc) * (size_t)tiles, s);
+    cudaMemsetAsync(h->counter, 0, sizeof(unsigned int) * 4, s);
     cudaMemsetAsync(h->theta[0], 0, nd * sizeof(float), s);
     cudaMemsetAsync(h->theta[1], 0, nd * sizeof(float), s);
     cudaMemsetAsync(h->grad[0], 0, nd * sizeof(float), s);

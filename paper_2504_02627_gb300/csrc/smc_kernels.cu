@@ -70,7 +70,10 @@ __global__ void __launch_bounds__(RUN_THREADS) k_normalise(StepBufs b) {
     const int r = blockIdx.x;
     const RunParams rp = b.runs[r];
     RunState& st = b.rstate[r];
-    if (r == 0 && threadIdx.x == 0) b.counter[0] = 0u;    // dynamic scan-tile counter
+    if (r == 0 && threadIdx.x == 0) {
+        b.counter[0] = 0u;          // dynamic scan-tile counter
+        b.counter[1] += 1u;         // look-back epoch: never repeats within a handle
+    }
     if (st.status != 0) {
         if (threadIdx.x == 0) st.resample = 0;
         return;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
     const RunParams rp = b.runs[r];
     RunState& st = b.rstate[r];
     if (!st.resample) return;
-    const unsigned int epoch = (unsigned int)st.k;
+    const unsigned int epoch = b.counter[1] & 0x3fffffffu;
     const int64_t t_in_run = g - rp.tile0;
     const int64_t base = t_in_run * SCAN_TILE;
     const unsigned long long N = (unsigned long long)rp.n, T = st.T, U = st.U;
@@ -620,6 +623,7 @@ __global__ void __launch_bounds__(RUN_THREADS) k_quantise_flat(const double* W, 
         st.status = T != 0ull ? 0 : -4;
         fs->st = st;
         fs->counter[0] = 0u;
+        fs->counter[1] = 1u;        // tiles are zeroed before every call
     }
 }
 

@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, Tr
         }
         H0_s[tid] = j_s[tid] >= 0 ? 0.5 * kin - a.logpi_in[src_s[tid]] : 0.0;
     }
+    __syncthreads();   // H0 reads p_s before the first half kick below rewrites it
     const int smax = *smax_s;
 
     // ---- first half kick and drift of step 1
