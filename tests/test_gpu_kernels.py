@@ -107,15 +107,16 @@ def _summand_scale(w, th):
     N, D = th.shape
     if w["kind"] in ("logistic", "linear_gauss"):
         eta = th @ w["X"].T
+        eta_abs = np.abs(th) @ np.abs(w["X"]).T          # operands of the inner products
         if w["kind"] == "logistic":
-            r = w["y"][None, :] - 1.0 / (1.0 + np.exp(-eta))
-            terms = np.abs(w["y"][None, :] * eta) + np.logaddexp(0, eta)
+            r = np.abs(w["y"][None, :] - 1.0 / (1.0 + np.exp(-eta))) + 0.25 * eta_abs
+            terms = np.abs(w["y"][None, :] * eta) + np.logaddexp(0, eta) + eta_abs
             tau2 = w.get("tau", 1.0) ** 2
         else:
-            r = (w["y"][None, :] - eta) / w["sigma"] ** 2
-            terms = 0.5 * ((w["y"][None, :] - eta) / w["sigma"]) ** 2
+            r = (np.abs(w["y"][None, :]) + eta_abs) / w["sigma"] ** 2
+            terms = 0.5 * ((np.abs(w["y"][None, :]) + eta_abs) / w["sigma"]) ** 2
             tau2 = w["tau"] ** 2
-        gs = np.abs(r) @ np.abs(w["X"]) + np.abs(th) / tau2
+        gs = r @ np.abs(w["X"]) + np.abs(th) / tau2
         return gs, terms.sum(axis=1) + 0.5 * (th**2).sum(axis=1) / tau2 + 1.0
     if w["kind"] == "gauss_dense":
         gs = np.abs(th - w["mu"]) @ np.abs(w["P"]).T
@@ -123,12 +124,14 @@ def _summand_scale(w, th):
     if w["kind"] == "hier_normal":
         mu, logtau, eta = th[:, :1], th[:, 1:2], th[:, 2:]
         tau = np.exp(logtau)
-        dev_ = w["ybar"][None, :] - (mu + tau * eta)
-        r = np.abs(w["n_g"][None, :] * dev_) / w["sigma"] ** 2
+        # the residual ybar - (mu + tau eta) cancels near the posterior: bound
+        # its FP32 error by the magnitudes of its operands
+        dev_ops = np.abs(w["ybar"][None, :]) + np.abs(mu) + 3.0 * np.abs(tau * eta)
+        r = w["n_g"][None, :] * dev_ops / w["sigma"] ** 2
         gs = np.concatenate([r.sum(1, keepdims=True) + np.abs(mu),
                              (r * tau * np.abs(eta)).sum(1, keepdims=True) + np.abs(logtau),
                              r * tau + np.abs(eta)], axis=1)
-        ls = ((w["ss"][None, :] + w["n_g"][None, :] * dev_**2) / (2 * w["sigma"] ** 2)).sum(1)
+        ls = ((w["ss"][None, :] + w["n_g"][None, :] * dev_ops**2) / (2 * w["sigma"] ** 2)).sum(1)
         return gs, ls + 0.5 * (th**2).sum(1) + 100.0
     # banana pairs
     a, b = w["a"], w["b"]
