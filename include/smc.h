@@ -276,6 +276,25 @@ smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
                           int32_t* ancestors, int32_t* status_out, void* scratch,
                           void* stream);
 
+/* Systematic resampling exactly as smc_k_resample, for callers that cannot
+ * allocate device memory where they resample (a host framework that owns the
+ * whole device memory budget, or a latency-critical loop that cannot afford
+ * the device synchronisation implied by cudaMalloc / cudaFree).  The paper has
+ * no counterpart: it is an interface convenience of this library.
+ * Allocates nothing: the scan descriptors live in a fixed 64 KiB device array
+ * inside the library (present on every device that loads it, until the
+ * process exits), so N is limited to SMC_NOALLOC_MAX_N; larger N returns
+ * SMC_E_INVAL with a message on stderr.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture.
+ * Every call shares the one array, and each call clears the part it uses
+ * before reading it; calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Arguments, outputs and status codes are those of smc_k_resample. */
+#define SMC_NOALLOC_MAX_N 4194304
+smc_status smc_k_resample_noalloc(const double* W, int64_t N, uint64_t r64, uint64_t* q,
+                                  int32_t* ancestors, int32_t* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

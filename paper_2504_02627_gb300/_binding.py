@@ -87,7 +87,10 @@ EXPORTS = {
     "smc_k_resample_scratch_bytes": (C.c_int64, [C.c_int64]),
     "smc_k_resample": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
+    "smc_k_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]),
 }
+NOALLOC_MAX_N = 4194304     # SMC_NOALLOC_MAX_N in include/smc.h
 
 _lib = None
 
