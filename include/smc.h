@@ -178,7 +178,7 @@ typedef enum {
     SMC_BUF_DH = 8,         /* f64 [N]          Delta H                           */
     SMC_BUF_ALPHA = 9,      /* f64 [N]          acceptance probabilities          */
     SMC_BUF_THETA_PREV = 10,/* f32 [dim x ld]   positions before the move (after resampling) */
-    SMC_BUF_RUNSTATE = 11   /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L_used, ess */
+    SMC_BUF_RUNSTATE = 11   /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS */
 } smc_buffer;
 smc_status smc_get_buffer(const smc_handle* h, int32_t which, void* dst, int64_t bytes,
                           int32_t device_ptrs);

@@ -263,7 +263,7 @@ class Sampler:
 
     def runstate(self):
         rs = self.buffer(BUF_RUNSTATE)
-        keys = ["log_z", "log_L", "adam_m", "adam_v", "Lbar", "adam_t", "L_used", "ess"]
+        keys = ["log_z", "log_L", "adam_m", "adam_v", "Lbar", "adam_t", "L_last", "ess"]
         return [dict(zip(keys, row)) for row in rs]
 
     def close(self):

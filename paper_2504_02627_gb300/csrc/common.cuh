@@ -27,30 +27,37 @@ struct RunParams {
     int32_t n_tiles;        // resampling scan tiles of this run
     int64_t tile0;          // first global scan tile of the run
     int64_t n_iters, n_warmup;
+    int32_t slice0;         // first particle slice (SLICE particles) of the run
+    int32_t n_slices;
 };
 
-// Per-run mutable state (device).  Read back by smc_get_buffer(RUNSTATE) as
-// the first 8 doubles.
+constexpr int SLICE = 256;  // particles per CTA in the weight / statistics kernels
+
+// Per-run mutable state (device).  The first 8 doubles are what
+// smc_get_buffer(RUNSTATE) returns.
 struct RunState {
     double log_z;       // running log evidence
     double log_L;       // log trajectory length (Adam variable)
     double adam_m, adam_v;
     double Lbar;        // moving average of L
     double adam_t;      // Adam step count (stored as double for the readout)
-    double L_used;      // L used for this iteration's jitter
+    double L_last;      // L used by the last completed iteration
     double ess;         // ESS after the last reweighting
-    // ---- below: not part of the 8-double readout
-    double lse;         // log-sum-exp of the log-weights before the move
-    double ess_pre;
-    double log_z_inc;
-    double mean_alpha;
-    uint64_t T, U;      // fixed-point total and offset of the last resampling
-    int64_t k;          // 1-based iteration about to run / just run
-    int64_t grad_evals;
+    // ---- decision for the iteration about to run (written by the previous
+    //      iteration's finisher or by the initial weighting)
+    double lse;         // log-sum-exp of the current log-weights
+    double ess_pre;     // their ESS
+    double L_used;      // L for this iteration's jitter
+    unsigned long long T;   // sum of the fixed-point weights (atomic, exact)
+    unsigned long long r64; // systematic-resampling uniform of this iteration
+    int64_t k;          // 1-based iteration about to run
     int32_t resample;   // this iteration resamples
     int32_t status;     // 0 ok, -4 degenerate, -5 look-back gave up
-    int32_t steps_min, steps_max;
-    // cumulative counters since the initial draw
+    // ---- statistics of the last completed iteration
+    double stat_ess_pre, log_z_inc, mean_alpha;
+    int64_t grad_evals;
+    int32_t stat_resampled, steps_min, steps_max, pad;
+    // ---- cumulative counters since the initial draw
     int64_t iters_total, grad_evals_total, resamples_total;
     double ess_sum, ess_sum_post;
 };

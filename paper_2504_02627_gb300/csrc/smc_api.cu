@@ -71,6 +71,11 @@ struct smc_handle {
     int32_t *anc = nullptr, *src = nullptr, *steps = nullptr, *perm = nullptr, *hist = nullptr;
     unsigned int* counter = nullptr;
     TileDesc* tiles = nullptr;
+    int32_t *slice_run = nullptr, *slice_start = nullptr;
+    int64_t n_slices = 0;
+    SlicePart* parts = nullptr;
+    double* colsum = nullptr;
+    unsigned int* done = nullptr;
     int64_t n_tiles = 0;
     int32_t max_steps_all = 0;
     int64_t iters_done = 0;
@@ -250,6 +255,12 @@ StepBufs make_bufs(smc_handle* h) {
     b.tiles = h->tiles;
     b.n_tiles = h->n_tiles;
     b.max_steps_all = h->max_steps_all;
+    b.slice_run = h->slice_run;
+    b.slice_start = h->slice_start;
+    b.n_slices = h->n_slices;
+    b.parts = h->parts;
+    b.colsum = h->colsum;
+    b.done = h->done;
     b.theta_prev = h->theta[h->cur];
     b.theta_new = h->theta[1 - h->cur];
     b.p_final = h->p_final;
@@ -327,10 +338,16 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         delete h;
         return SMC_E_INVAL;
     }
+    if (model->dim > MAX_CHEES_DIM) {
+        fprintf(stderr, "smc_init: dim must be <= %d\n", MAX_CHEES_DIM);
+        h->model.mem.release();
+        delete h;
+        return SMC_E_INVAL;
+    }
     h->n_runs = n_runs;
     h->D = model->dim;
     h->K = cfg[0].n_iters;
-    int64_t N = 0, tiles = 0;
+    int64_t N = 0, tiles = 0, slices = 0;
     int32_t smax = 0;
     h->h_runs.resize((size_t)n_runs);
     std::vector<RunState> h_state((size_t)n_runs);
@@ -356,6 +373,9 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.tile0 = tiles;
         rp.n_iters = cfg[r].n_iters;
         rp.n_warmup = cfg[r].n_warmup;
+        rp.slice0 = (int32_t)slices;
+        rp.n_slices = (int32_t)((rp.n + SLICE - 1) / SLICE);
+        slices += rp.n_slices;
         h_state[(size_t)r] = initial_state(rp, cfg[r]);
         N += rp.n;
         tiles += rp.n_tiles;
@@ -365,11 +385,17 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->ld = round_up(N, 32);
     h->n_tiles = tiles;
     h->max_steps_all = smax;
-    std::vector<int32_t> run_of((size_t)N), tile_run((size_t)tiles);
+    h->n_slices = slices;
+    std::vector<int32_t> run_of((size_t)N), tile_run((size_t)tiles), slice_run((size_t)slices),
+        slice_start((size_t)slices);
     for (int64_t r = 0; r < n_runs; ++r) {
         const RunParams& rp = h->h_runs[(size_t)r];
         for (int64_t i = 0; i < rp.n; ++i) run_of[(size_t)(rp.off + i)] = (int32_t)r;
         for (int64_t t = 0; t < rp.n_tiles; ++t) tile_run[(size_t)(rp.tile0 + t)] = (int32_t)r;
+        for (int64_t q = 0; q < rp.n_slices; ++q) {
+            slice_run[(size_t)(rp.slice0 + q)] = (int32_t)r;
+            slice_start[(size_t)(rp.slice0 + q)] = (int32_t)(q * SLICE);
+        }
     }
     DevAlloc& A = h->mem;
     const size_t nd = (size_t)(h->D * h->ld);
@@ -395,6 +421,11 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->hist = A.get<int32_t>((size_t)smax + 1);
     h->counter = A.get<unsigned int>(4);
     h->tiles = A.get<TileDesc>((size_t)tiles);
+    h->slice_run = A.get<int32_t>((size_t)slices);
+    h->slice_start = A.get<int32_t>((size_t)slices);
+    h->parts = A.get<SlicePart>((size_t)slices);
+    h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
+    h->done = A.get<unsigned int>((size_t)n_runs);
     if (A.err != cudaSuccess) {
         smc_status st = cuda_fail(h, A.err, "smc_init allocation");
         smc_destroy(h);
@@ -407,6 +438,9 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     cudaMemcpyAsync(h->d_tile_run, tile_run.data(), sizeof(int32_t) * (size_t)tiles, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->tiles, 0, sizeof(TileDesc) * (size_t)tiles, s);
     cudaMemsetAsync(h->counter, 0, sizeof(unsigned int) * 4, s);
+    cudaMemsetAsync(h->done, 0, sizeof(unsigned int) * (size_t)n_runs, s);
+    cudaMemcpyAsync(h->slice_run, slice_run.data(), sizeof(int32_t) * (size_t)slices, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->slice_start, slice_start.data(), sizeof(int32_t) * (size_t)slices, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->theta[0], 0, nd * sizeof(float), s);
     cudaMemsetAsync(h->theta[1], 0, nd * sizeof(float), s);
     cudaMemsetAsync(h->grad[0], 0, nd * sizeof(float), s);
@@ -438,14 +472,14 @@ smc_status read_stats(smc_handle* h, smc_stats* stats) {
         if (stats) {
             smc_stats& o = stats[r];
             o.ess = s.ess;
-            o.ess_pre = s.ess_pre;
+            o.ess_pre = s.stat_ess_pre;
             o.log_z_inc = s.log_z_inc;
             o.mean_alpha = s.mean_alpha;
-            o.traj_len = s.L_used;
+            o.traj_len = s.L_last;
             o.grad_evals = s.grad_evals;
             o.steps_min = s.steps_min;
             o.steps_max = s.steps_max;
-            o.resampled = s.resample;
+            o.resampled = s.stat_resampled;
             o.pad = 0;
         }
         if (s.status == -4) ret = fail(h, SMC_E_DEGENERATE, "all weights are zero in run " + std::to_string(r));
@@ -472,9 +506,9 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
     if (h->sticky) return SMC_E_STATE;
     cudaStream_t s = h->stream;
     StepBufs b = make_bufs(h);
-    cudaError_t e = launch_normalise(b, s);
+    cudaError_t e = launch_weights_steps(b, s);
     if (e == cudaSuccess) e = launch_resample_scan(b, s);
-    if (e == cudaSuccess) e = launch_steps_sort(b, s);
+    if (e == cudaSuccess) e = launch_sort(b, s);
     if (e == cudaSuccess) {
         TrajArgs a{};
         a.theta_in = h->theta[h->cur];
@@ -506,12 +540,12 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
             e = launch_traj(h->model.m, a, h->precision, s);
             cudaEventRecord(h->events[i + 1], s);
             h->n_event_pairs += 1;
-            h->kernel_launches += 7;
+            h->kernel_launches += KERNELS_PER_ITERATION;
         } else {
             e = launch_traj(h->model.m, a, h->precision, s);
         }
     }
-    if (e == cudaSuccess) e = launch_reweight_chees(b, s);
+    if (e == cudaSuccess) e = launch_move_stats(b, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "smc_step launch");
     h->cur = 1 - h->cur;
     h->iters_done += 1;

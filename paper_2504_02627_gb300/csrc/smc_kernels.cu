@@ -34,7 +34,31 @@ __global__ void k_init_draw(StepBufs b, float* theta) {
     b.logw[j] = -0.5 * zz - 0.5 * (double)b.D * (LOG_2PI + 2.0 * log(rp.init_scale));
 }
 
-// w_1 = pi(theta_0) / q_init(theta_0) (Eq. for w_1); log Z_0 = LSE(log w) - log J.
+// Resampling uniform of iteration k: Philox block (0, 0, k, RESAMPLE).
+__device__ __forceinline__ unsigned long long resample_r64(uint64_t seed, int64_t k) {
+    const Philox4 w = philox4x32_10(Philox4{0u, 0u, (uint32_t)k, TAG_RESAMPLE}, seed);
+    return ((unsigned long long)w.x << 32) | w.y;
+}
+
+// Decision for the next iteration from the current log-weights: LSE, ESS
+// (Eqs. for W and J_eff) and the resampling test J_eff < frac J (Sec. 3).
+__device__ __forceinline__ void set_decision(RunState& st, const RunParams& rp, double m, double e1, double e2) {
+    if (!(m > -CUDART_INF)) {
+        st.status = -4;
+        st.resample = 0;
+        return;
+    }
+    const double ess = e1 * e1 / e2;
+    st.lse = m + log(e1);
+    st.ess_pre = ess;
+    st.resample = ess < rp.ess_frac * (double)rp.n;
+    st.L_used = exp(st.log_L);
+    st.T = 0ull;
+    st.r64 = resample_r64(rp.seed, st.k);
+}
+
+// w_1 = pi(theta_0) / q_init(theta_0) (Eq. for w_1); log Z_0 = LSE(log w) - log J;
+// and the weight decision of iteration 1.
 __global__ void __launch_bounds__(RUN_THREADS) k_init_finish(StepBufs b, const double* logpi) {
     __shared__ double buf[32];
     const int r = blockIdx.x;
@@ -48,88 +72,67 @@ __global__ void __launch_bounds__(RUN_THREADS) k_init_finish(StepBufs b, const d
         m = fmax(m, lw);
     }
     m = block_reduce(m, buf, OpMax());
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;
     if (m > -CUDART_INF)
-        for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) s += exp(b.logw[rp.off + i] - m);
+        for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) {
+            const double e = exp(b.logw[rp.off + i] - m);
+            s += e;
+            s2 += e * e;
+        }
     s = block_reduce(s, buf, OpSum());
+    s2 = block_reduce(s2, buf, OpSum());
     if (threadIdx.x == 0) {
         RunState& st = b.rstate[r];
         st.log_z = (m > -CUDART_INF) ? m + log(s) - log((double)rp.n) : -CUDART_INF;
-        st.status = (m > -CUDART_INF) ? 0 : -4;
+        st.status = 0;
+        set_decision(st, rp, m, s, s2);
+        b.done[r] = 0u;
     }
 }
 
-// ============================================================ normalise + ESS
-// Normalised weights W = w / sum w (Eq. for the normalised weights), J_eff =
-// 1 / sum W^2 (Eq. for J_eff), the resampling test J_eff < frac J, and, when
-// resampling, the fixed-point weights q_j = floor(W_j 2^S), their exact total
-// T and the systematic offset U = floor(r64 T / 2^64).
-__global__ void __launch_bounds__(RUN_THREADS) k_normalise(StepBufs b) {
-    __shared__ double buf[32];
+// ============================================================ weights + steps
+// Per particle slice: normalised weight W_j = exp(log w_j - LSE), the
+// fixed-point weight q_j = floor(W_j 2^S) with S = 62 - ceil(log2 N) when the
+// run resamples (its slice total is added to T with an exact integer atomic),
+// the 1-d Halton jitter h_j of n = j K + k (Sec. 3.2), the step count
+// S_j = ceil(h_j L / eps) clipped to [1, max] (Algorithm 2), and the
+// histogram of S_j for the counting sort.
+__global__ void __launch_bounds__(SLICE) k_weights_steps(StepBufs b) {
     __shared__ unsigned long long ubuf[32];
-    const int r = blockIdx.x;
-    const RunParams rp = b.runs[r];
+    const int c = blockIdx.x;
+    const int r = b.slice_run[c];
+    const RunParams& rp = b.runs[r];
     RunState& st = b.rstate[r];
-    if (r == 0 && threadIdx.x == 0) {
-        b.counter[0] = 0u;          // dynamic scan-tile counter
-        b.counter[1] += 1u;         // look-back epoch: never repeats within a handle
+    if (c == 0 && threadIdx.x == 0) {
+        b.counter[0] = 0u;      // dynamic scan-tile counter of the next launch
+        b.counter[1] += 1u;     // look-back epoch: never repeats within a handle
     }
-    if (st.status != 0) {
-        if (threadIdx.x == 0) st.resample = 0;
-        return;
-    }
-    const double* lw = b.logw + rp.off;
-    double m = -CUDART_INF;
-    for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) m = fmax(m, lw[i]);
-    m = block_reduce(m, buf, OpMax());
-    if (!(m > -CUDART_INF)) {
-        if (threadIdx.x == 0) {
-            st.status = -4;
-            st.resample = 0;
-        }
-        return;
-    }
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) s += exp(lw[i] - m);
-    s = block_reduce(s, buf, OpSum());
-    const double lse = m + log(s);
-    double s2 = 0.0;
-    for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) {
-        const double w = exp(lw[i] - lse);
-        b.W[rp.off + i] = w;
-        s2 += w * w;
-    }
-    s2 = block_reduce(s2, buf, OpSum());
-    const double ess = 1.0 / s2;
-    const int resample = ess < rp.ess_frac * (double)rp.n;
-    unsigned long long T = 0ull;
-    if (resample) {
-        int c = 0;
-        while (((int64_t)1 << c) < rp.n) ++c;
-        const double scale = ldexp(1.0, 62 - c);
-        for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) {
-            const double v = b.W[rp.off + i] * scale;
-            const unsigned long long qi = v > 0.0 ? __double2ull_rz(v) : 0ull;
-            b.q[rp.off + i] = qi;
-            T += qi;
-        }
-        T = block_reduce(T, ubuf, OpSum());
-    }
-    if (threadIdx.x == 0) {
-        st.lse = lse;
-        st.ess_pre = ess;
-        st.resample = resample;
-        st.L_used = exp(st.log_L);
-        if (resample) {
-            const Philox4 w = philox4x32_10(Philox4{0u, 0u, (uint32_t)st.k, TAG_RESAMPLE}, rp.seed);
-            const unsigned long long r64 = ((unsigned long long)w.x << 32) | w.y;
-            st.T = T;
-            st.U = __umul64hi(r64, T);
-            if (T == 0ull) {
-                st.status = -4;
-                st.resample = 0;
+    const int64_t i = b.slice_start[c] + threadIdx.x;
+    const bool valid = i < rp.n;
+    const int64_t j = rp.off + i;
+    const bool ok = st.status == 0;
+    unsigned long long qi = 0ull;
+    if (valid) {
+        int32_t S = 0;
+        if (ok) {
+            const double w = exp(b.logw[j] - st.lse);
+            b.W[j] = w;
+            if (st.resample) {
+                int sh = 0;
+                while (((int64_t)1 << sh) < rp.n) ++sh;
+                const double v = w * ldexp(1.0, 62 - sh);
+                qi = v > 0.0 ? __double2ull_rz(v) : 0ull;
+                b.q[j] = qi;
             }
+            const double h = rp.jitter ? halton2((uint32_t)(i * rp.n_iters + st.k)) : 1.0;
+            S = step_count(h, st.L_used, rp.eps, rp.max_steps);
         }
+        b.steps[j] = S;
+        atomicAdd(&b.hist[b.max_steps_all - S], 1);
+    }
+    if (ok && st.resample) {
+        qi = block_reduce(qi, ubuf, OpSum());
+        if (threadIdx.x == 0 && qi) atomicAdd(&st.T, qi);
     }
 }
 
@@ -139,7 +142,8 @@ __global__ void __launch_bounds__(RUN_THREADS) k_normalise(StepBufs b) {
 // atomic counter, so every predecessor tile has already started).  Each
 // particle j then owns the output slots i with N C_{j-1} <= i T + U < N C_j,
 // i.e. [cnt(C_{j-1}), cnt(C_j)) with cnt(C) = ceil((N C - U) / T) clipped to
-// [0, N], and writes its own index there (systematic resampling).
+// [0, N], and writes its own index there (systematic resampling).  Runs that
+// do not resample write the identity source index.
 constexpr long long LOOKBACK_SPIN_LIMIT = 1ll << 22;
 
 __device__ __forceinline__ unsigned long long systematic_count(unsigned long long C, unsigned long long N,
@@ -162,11 +166,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
     const int r = b.tile_run ? b.tile_run[g] : 0;
     const RunParams rp = b.runs[r];
     RunState& st = b.rstate[r];
-    if (!st.resample) return;
-    const unsigned int epoch = b.counter[1] & 0x3fffffffu;
     const int64_t t_in_run = g - rp.tile0;
     const int64_t base = t_in_run * SCAN_TILE;
-    const unsigned long long N = (unsigned long long)rp.n, T = st.T, U = st.U;
+    if (!st.resample || st.status != 0) {
+        if (b.src)
+            for (int k = 0; k < SCAN_ITEMS; ++k) {
+                const int64_t i = base + (int64_t)k * SCAN_THREADS + tid;
+                if (i < rp.n) b.src[rp.off + i] = (int32_t)(rp.off + i);
+            }
+        return;
+    }
+    const unsigned int epoch = b.counter[1] & 0x3fffffffu;
+    const unsigned long long N = (unsigned long long)rp.n, T = st.T;
+    if (T == 0ull) {                 // no mass at all: degenerate
+        if (tid == 0) st.status = -4;
+        return;
+    }
+    const unsigned long long U = __umul64hi(st.r64, T);
 
     // thread-local inclusive prefix of SCAN_ITEMS consecutive elements
     unsigned long long v[SCAN_ITEMS];
@@ -250,29 +266,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
         const unsigned long long Ci = off + v[k];
         const unsigned long long Cp = Ci - b.q[rp.off + i];
         const unsigned long long lo = systematic_count(Cp, N, T, U), hi = systematic_count(Ci, N, T, U);
-        for (unsigned long long o = lo; o < hi; ++o) b.anc[rp.off + (int64_t)o] = (int32_t)i;
+        for (unsigned long long o = lo; o < hi; ++o) {
+            b.anc[rp.off + (int64_t)o] = (int32_t)i;
+            if (b.src) b.src[rp.off + (int64_t)o] = (int32_t)(rp.off + i);
+        }
     }
 }
 
-// ============================================================ jitter + sort
-// h_j = radical inverse base 2 of n = j K + k (1-d Halton, Sec. 3.2), S_j =
-// ceil(h_j L / eps) (Algorithm 2), the source index of each particle after
-// resampling, and a histogram of S_j for the counting sort.
-__global__ void k_steps(StepBufs b) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= b.N) return;
-    const int r = b.run_of[j];
-    const RunParams& rp = b.runs[r];
-    const RunState& st = b.rstate[r];
-    const int64_t jl = j - rp.off;
-    b.src[j] = st.resample ? (int32_t)(rp.off + b.anc[j]) : (int32_t)j;
-    const double h = rp.jitter ? halton2((uint32_t)(jl * rp.n_iters + st.k)) : 1.0;
-    const int32_t S = st.status == 0 ? step_count(h, st.L_used, rp.eps, rp.max_steps) : 0;
-    b.steps[j] = S;
-    atomicAdd(&b.hist[b.max_steps_all - S], 1);
-}
-
-// Exclusive scan of the histogram (one CTA), in place.
+// ============================================================ sort by steps
+// Exclusive scan of the step histogram (one CTA), in place.
 __global__ void __launch_bounds__(1024) k_hist_scan(StepBufs b) {
     __shared__ int wsum[32];
     const int nb = b.max_steps_all + 1;
@@ -316,149 +318,219 @@ __global__ void k_sort_scatter(StepBufs b) {
     b.perm[slot] = (int32_t)j;
 }
 
-// ============================================================ reweight + ChEES
-// Incremental weight with the momentum change-of-variable L-kernel: the
-// Jacobians cancel and log w += -Delta H (Sec. 3.1); the evidence factor is
-// sum_j W_j exp(-Delta H_j).  During warm-up the ChEES gradient
-// g_j = l_j (|t1_j - mean t1|^2 - |t0_j - mean t0|^2) (t1_j - mean t1)' p_j
-// (Algorithm 2) is averaged with weights alpha_j and fed to Adam on log L;
-// Lbar <- 0.9 Lbar + 0.1 L; at k = M_warmup, L <- Lbar.
-__global__ void __launch_bounds__(RUN_THREADS) k_reweight_chees(StepBufs b) {
+// ============================================================ move statistics
+// Per particle slice (first pass): with the momentum change-of-variable
+// L-kernel the Jacobians cancel and log w += -Delta H (Sec. 3.1); pieces of
+// log sum_j W_j exp(-Delta H_j) (evidence factor), of the new ESS, sum alpha,
+// sum S_j, and the ChEES column sums of the pre-move and proposed states.
+struct SliceIdx {
+    int r;
+    int64_t i, j;
+    bool valid;
+};
+__device__ __forceinline__ SliceIdx slice_idx(const StepBufs& b) {
+    SliceIdx x;
+    const int c = blockIdx.x;
+    x.r = b.slice_run[c];
+    x.i = b.slice_start[c] + threadIdx.x;
+    x.valid = x.i < b.runs[x.r].n;
+    x.j = b.runs[x.r].off + x.i;
+    return x;
+}
+
+// (max, sum exp) pair of a block; returns (M, S) with S = sum exp(a - M).
+__device__ __forceinline__ void block_lse(double a, double* buf, double& M, double& S) {
+    M = block_reduce(a, buf, OpMax());
+    S = block_reduce(M > -CUDART_INF ? exp(a - M) : 0.0, buf, OpSum());
+}
+
+__global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
     __shared__ double buf[32];
+    __shared__ long long lbuf[32];
     __shared__ int ibuf[32];
-    __shared__ double mean0[1024], mean1[1024];
-    const int r = blockIdx.x;
-    const RunParams rp = b.runs[r];
-    RunState& st = b.rstate[r];
+    __shared__ double wcol[SLICE / 32][2 * MAX_CHEES_DIM];
+    const SliceIdx x = slice_idx(b);
+    const RunParams& rp = b.runs[x.r];
+    const RunState& st = b.rstate[x.r];
     if (st.status != 0) return;
-    const int64_t n = rp.n, off = rp.off;
-    const int resample = st.resample;
-    const double lse = st.lse, logn = log((double)n);
-
-    // (f) evidence factor and new log-weights
-    double m = -CUDART_INF;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t j = off + i;
-        const double lw = (resample ? -logn : b.logw[j] - lse) - b.dH[j];
-        m = fmax(m, lw);
-    }
-    m = block_reduce(m, buf, OpMax());
-    double s = 0.0, sa = 0.0;
-    long long ge = 0;
+    const int c = blockIdx.x;
+    const double logn = log((double)rp.n);
+    double za = -CUDART_INF, lw = -CUDART_INF, al = 0.0;
+    long long S = 0;
     int smin = 0x7fffffff, smax = 0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t j = off + i;
-        const double lw = (resample ? -logn : b.logw[j] - lse) - b.dH[j];
-        if (m > -CUDART_INF) s += exp(lw - m);
-        sa += b.alpha[j];
-        const int Sj = b.steps[j];
-        ge += Sj;
-        smin = min(smin, Sj);
-        smax = max(smax, Sj);
+    if (x.valid) {
+        const double dH = b.dH[x.j];
+        const double old = b.logw[x.j];
+        za = (st.resample ? -logn : old - st.lse) - dH;
+        lw = (st.resample ? -logn : old) - dH;
+        b.logw[x.j] = lw;
+        al = b.alpha[x.j];
+        S = b.steps[x.j];
+        smin = smax = (int)S;
     }
-    s = block_reduce(s, buf, OpSum());
-    sa = block_reduce(sa, buf, OpSum());
-    ge = block_reduce(ge, reinterpret_cast<long long*>(buf), OpSum());
-    smin = block_reduce(smin, ibuf, OpMin());
-    smax = block_reduce(smax, ibuf, OpMax());
-    const double log_z_inc = (m > -CUDART_INF) ? m + log(s) : -CUDART_INF;
-    // new unnormalised log-weights, then their ESS
-    double m2 = -CUDART_INF;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t j = off + i;
-        const double lw = (resample ? -logn : b.logw[j]) - b.dH[j];
-        b.logw[j] = lw;
-        m2 = fmax(m2, lw);
-    }
-    m2 = block_reduce(m2, buf, OpMax());
-    double e1 = 0.0, e2 = 0.0;
-    if (m2 > -CUDART_INF)
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const double w = exp(b.logw[off + i] - m2);
-            e1 += w;
-            e2 += w * w;
+    SlicePart part;
+    block_lse(za, buf, part.za_m, part.za_s);
+    part.w_m = block_reduce(lw, buf, OpMax());
+    const double e = (x.valid && part.w_m > -CUDART_INF) ? exp(lw - part.w_m) : 0.0;
+    part.w_e1 = block_reduce(e, buf, OpSum());
+    part.w_e2 = block_reduce(e * e, buf, OpSum());
+    part.alpha_sum = block_reduce(al, buf, OpSum());
+    part.steps_sum = block_reduce(S, lbuf, OpSum());
+    part.smin = block_reduce(smin, ibuf, OpMin());
+    part.smax = block_reduce(smax, ibuf, OpMax());
+    part.g_num = 0.0;
+    part.g_den = 0.0;
+    if (threadIdx.x == 0) b.parts[c] = part;
+    if (rp.adapt && st.k < rp.n_warmup) {
+        // ChEES column sums: pre-move states (after resampling) and proposals
+        const int D = (int)b.D, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int64_t src = x.valid ? b.src[x.j] : 0;
+        for (int d = 0; d < D; ++d) {
+            double v0 = x.valid ? (double)b.theta_prev[(int64_t)d * b.ld + src] : 0.0;
+            double v1 = x.valid ? (double)b.theta_new[(int64_t)d * b.ld + x.j] : 0.0;
+            v0 = warp_sum(v0);
+            v1 = warp_sum(v1);
+            if (lane == 0) {
+                wcol[wid][d] = v0;
+                wcol[wid][D + d] = v1;
+            }
         }
-    e1 = block_reduce(e1, buf, OpSum());
-    e2 = block_reduce(e2, buf, OpSum());
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * D; t += blockDim.x) {
+            double s = 0.0;
+            for (int w = 0; w < SLICE / 32; ++w) s += wcol[w][t];
+            b.colsum[(int64_t)c * 2 * D + t] = s;
+        }
+    }
+}
 
-    // (g) ChEES adaptation during warm-up
-    const int64_t k = st.k;
-    if (rp.adapt && k < rp.n_warmup) {
-        const int64_t D = b.D;
-        for (int64_t d = threadIdx.x; d < D; d += blockDim.x) {
-            mean0[d] = 0.0;
-            mean1[d] = 0.0;
-        }
-        __syncthreads();
-        for (int64_t d = 0; d < D; ++d) {
-            double a0 = 0.0, a1 = 0.0;
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-                const int64_t j = off + i;
-                a0 += (double)b.theta_prev[d * b.ld + b.src[j]];
-                a1 += (double)b.theta_new[d * b.ld + j];
-            }
-            a0 = warp_sum(a0);
-            a1 = warp_sum(a1);
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&mean0[d], a0);
-                atomicAdd(&mean1[d], a1);
-            }
-        }
-        __syncthreads();
-        for (int64_t d = threadIdx.x; d < D; d += blockDim.x) {
-            mean0[d] /= (double)n;
-            mean1[d] /= (double)n;
+// Second pass: ChEES gradient estimates g_j = l_j (|t1_j - mean t1|^2 -
+// |t0_j - mean t0|^2) (t1_j - mean t1)' p_j weighted by alpha_j (Algorithm 2),
+// then the last slice of each run combines every slice in a fixed order:
+// evidence, log-weights' ESS, Adam ascent on log L, Lbar, the freeze at
+// M_warmup, statistics, and the weight decision of the next iteration.
+__global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
+    __shared__ double buf[32];
+    __shared__ double mean_s[2 * MAX_CHEES_DIM];
+    __shared__ bool last_s;
+    const SliceIdx x = slice_idx(b);
+    const RunParams& rp = b.runs[x.r];
+    RunState& st = b.rstate[x.r];
+    if (st.status != 0) return;
+    const int c = blockIdx.x;
+    const int D = (int)b.D;
+    const bool adapting = rp.adapt && st.k < rp.n_warmup;
+    if (adapting) {
+        for (int t = threadIdx.x; t < 2 * D; t += blockDim.x) {
+            double s = 0.0;
+            for (int q = 0; q < rp.n_slices; ++q) s += b.colsum[(int64_t)(rp.slice0 + q) * 2 * D + t];
+            mean_s[t] = s / (double)rp.n;
         }
         __syncthreads();
         double num = 0.0, den = 0.0;
-        const double L = st.L_used;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const int64_t j = off + i;
+        if (x.valid) {
+            const int64_t src = b.src[x.j];
             double sq0 = 0.0, sq1 = 0.0, proj = 0.0;
-            for (int64_t d = 0; d < D; ++d) {
-                const double e0 = (double)b.theta_prev[d * b.ld + b.src[j]] - mean0[d];
-                const double e1v = (double)b.theta_new[d * b.ld + j] - mean1[d];
+            for (int d = 0; d < D; ++d) {
+                const double e0 = (double)b.theta_prev[(int64_t)d * b.ld + src] - mean_s[d];
+                const double e1 = (double)b.theta_new[(int64_t)d * b.ld + x.j] - mean_s[D + d];
                 sq0 += e0 * e0;
-                sq1 += e1v * e1v;
-                proj += e1v * (double)b.p_final[d * b.ld + j];
+                sq1 += e1 * e1;
+                proj += e1 * (double)b.p_final[(int64_t)d * b.ld + x.j];
             }
-            const double h = rp.jitter ? halton2((uint32_t)(i * rp.n_iters + k)) : 1.0;
-            const double gj = (h * L) * (sq1 - sq0) * proj;
-            num += b.alpha[j] * gj;
-            den += b.alpha[j];
+            const double h = rp.jitter ? halton2((uint32_t)(x.i * rp.n_iters + st.k)) : 1.0;
+            const double a = b.alpha[x.j];
+            num = a * ((h * st.L_used) * (sq1 - sq0) * proj);
+            den = a;
         }
         num = block_reduce(num, buf, OpSum());
         den = block_reduce(den, buf, OpSum());
         if (threadIdx.x == 0) {
-            if (den > 0.0 && isfinite(num / den)) {
-                const double gh = num / den;
-                st.adam_t += 1.0;
-                st.adam_m = rp.adam_b1 * st.adam_m + (1.0 - rp.adam_b1) * gh;
-                st.adam_v = rp.adam_b2 * st.adam_v + (1.0 - rp.adam_b2) * gh * gh;
-                const double mh = st.adam_m / (1.0 - pow(rp.adam_b1, st.adam_t));
-                const double vh = st.adam_v / (1.0 - pow(rp.adam_b2, st.adam_t));
-                st.log_L += rp.adam_lr * mh / (sqrt(vh) + rp.adam_eps);
-                st.log_L = fmin(fmax(st.log_L, rp.log_L_lo), rp.log_L_hi);
-            }
-            st.Lbar = 0.9 * st.Lbar + 0.1 * exp(st.log_L);
+            b.parts[c].g_num = num;
+            b.parts[c].g_den = den;
         }
     }
+    // ticket: the last slice of the run to get here finishes the iteration
     if (threadIdx.x == 0) {
-        if (rp.adapt && k == rp.n_warmup && st.Lbar > 0.0) st.log_L = log(st.Lbar);
-        st.log_z += log_z_inc;
-        st.log_z_inc = log_z_inc;
-        st.mean_alpha = sa / (double)n;
-        st.ess = (m2 > -CUDART_INF) ? e1 * e1 / e2 : 0.0;
-        st.grad_evals = ge;
-        st.iters_total += 1;
-        st.grad_evals_total += ge;
-        st.resamples_total += resample;
-        st.ess_sum += st.ess;
-        if (k > rp.n_warmup) st.ess_sum_post += st.ess;
-        st.steps_min = smin;
-        st.steps_max = smax;
-        st.k = k + 1;
+        __threadfence();
+        const unsigned int t = atomicAdd(&b.done[x.r], 1u);
+        last_s = (t == (unsigned int)rp.n_slices - 1u);
     }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    // fixed-order combination of the run's slices: thread t takes slices
+    // t, t + SLICE, ... and the block reduces in a fixed tree
+    double za_m = -CUDART_INF, w_m = -CUDART_INF;
+    for (int q = threadIdx.x; q < rp.n_slices; q += blockDim.x) {
+        const volatile SlicePart* p = b.parts + rp.slice0 + q;
+        za_m = fmax(za_m, p->za_m);
+        w_m = fmax(w_m, p->w_m);
+    }
+    za_m = block_reduce(za_m, buf, OpMax());
+    w_m = block_reduce(w_m, buf, OpMax());
+    double za_s = 0.0, w_e1 = 0.0, w_e2 = 0.0, asum = 0.0, gnum = 0.0, gden = 0.0;
+    long long ssum = 0;
+    int smin = 0x7fffffff, smax = 0;
+    for (int q = threadIdx.x; q < rp.n_slices; q += blockDim.x) {
+        const volatile SlicePart* p = b.parts + rp.slice0 + q;
+        if (p->za_m > -CUDART_INF) za_s += p->za_s * exp(p->za_m - za_m);
+        if (p->w_m > -CUDART_INF) {
+            const double f = exp(p->w_m - w_m);
+            w_e1 += p->w_e1 * f;
+            w_e2 += p->w_e2 * f * f;
+        }
+        asum += p->alpha_sum;
+        gnum += p->g_num;
+        gden += p->g_den;
+        ssum += p->steps_sum;
+        smin = min(smin, p->smin);
+        smax = max(smax, p->smax);
+    }
+    za_s = block_reduce(za_s, buf, OpSum());
+    w_e1 = block_reduce(w_e1, buf, OpSum());
+    w_e2 = block_reduce(w_e2, buf, OpSum());
+    asum = block_reduce(asum, buf, OpSum());
+    gnum = block_reduce(gnum, buf, OpSum());
+    gden = block_reduce(gden, buf, OpSum());
+    ssum = block_reduce(ssum, reinterpret_cast<long long*>(buf), OpSum());
+    smin = block_reduce(smin, reinterpret_cast<int*>(buf), OpMin());
+    smax = block_reduce(smax, reinterpret_cast<int*>(buf), OpMax());
+    if (threadIdx.x != 0) return;
+    const int64_t k = st.k;
+    if (adapting) {
+        if (gden > 0.0 && isfinite(gnum / gden)) {
+            const double gh = gnum / gden;
+            st.adam_t += 1.0;
+            st.adam_m = rp.adam_b1 * st.adam_m + (1.0 - rp.adam_b1) * gh;
+            st.adam_v = rp.adam_b2 * st.adam_v + (1.0 - rp.adam_b2) * gh * gh;
+            const double mh = st.adam_m / (1.0 - pow(rp.adam_b1, st.adam_t));
+            const double vh = st.adam_v / (1.0 - pow(rp.adam_b2, st.adam_t));
+            st.log_L += rp.adam_lr * mh / (sqrt(vh) + rp.adam_eps);
+            st.log_L = fmin(fmax(st.log_L, rp.log_L_lo), rp.log_L_hi);
+        }
+        st.Lbar = 0.9 * st.Lbar + 0.1 * exp(st.log_L);
+    }
+    if (rp.adapt && k == rp.n_warmup && st.Lbar > 0.0) st.log_L = log(st.Lbar);
+    const double inc = za_m > -CUDART_INF ? za_m + log(za_s) : -CUDART_INF;
+    st.log_z += inc;
+    st.log_z_inc = inc;
+    st.mean_alpha = asum / (double)rp.n;
+    st.ess = w_m > -CUDART_INF ? w_e1 * w_e1 / w_e2 : 0.0;
+    st.stat_ess_pre = st.ess_pre;
+    st.stat_resampled = st.resample;
+    st.L_last = st.L_used;
+    st.grad_evals = ssum;
+    st.steps_min = smin;
+    st.steps_max = smax;
+    st.iters_total += 1;
+    st.grad_evals_total += ssum;
+    st.resamples_total += st.resample;
+    st.ess_sum += st.ess;
+    if (k > rp.n_warmup) st.ess_sum_post += st.ess;
+    st.k = k + 1;
+    set_decision(st, rp, w_m, w_e1, w_e2);
+    b.done[x.r] = 0u;
 }
 
 // ============================================================ launchers
@@ -471,27 +543,26 @@ cudaError_t launch_init_finish(const StepBufs& b, const double* logpi, cudaStrea
     k_init_finish<<<(unsigned)b.n_runs, RUN_THREADS, 0, s>>>(b, logpi);
     return cudaGetLastError();
 }
-cudaError_t launch_normalise(const StepBufs& b, cudaStream_t s) {
-    k_normalise<<<(unsigned)b.n_runs, RUN_THREADS, 0, s>>>(b);
+cudaError_t launch_weights_steps(const StepBufs& b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (size_t)(b.max_steps_all + 1), s);
+    if (e != cudaSuccess) return e;
+    k_weights_steps<<<(unsigned)b.n_slices, SLICE, 0, s>>>(b);
     return cudaGetLastError();
 }
 cudaError_t launch_resample_scan(const StepBufs& b, cudaStream_t s) {
     k_resample_scan<<<(unsigned)b.n_tiles, SCAN_THREADS, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_steps_sort(const StepBufs& b, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (size_t)(b.max_steps_all + 1), s);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_sort(const StepBufs& b, cudaStream_t s) {
     const int bs = 256;
-    const unsigned grid = (unsigned)((b.N + bs - 1) / bs);
-    k_steps<<<grid, bs, 0, s>>>(b);
     k_hist_scan<<<1, 1024, 0, s>>>(b);
-    k_sort_scatter<<<grid, bs, 0, s>>>(b);
+    k_sort_scatter<<<(unsigned)((b.N + bs - 1) / bs), bs, 0, s>>>(b);
     return cudaGetLastError();
 }
-cudaError_t launch_reweight_chees(const StepBufs& b, cudaStream_t s) {
-    if (b.D > 1024) return cudaErrorInvalidValue;
-    k_reweight_chees<<<(unsigned)b.n_runs, RUN_THREADS, 0, s>>>(b);
+cudaError_t launch_move_stats(const StepBufs& b, cudaStream_t s) {
+    if (b.D > MAX_CHEES_DIM) return cudaErrorInvalidValue;
+    k_move_stats<<<(unsigned)b.n_slices, SLICE, 0, s>>>(b);
+    k_chees_finish<<<(unsigned)b.n_slices, SLICE, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -618,7 +689,7 @@ __global__ void __launch_bounds__(RUN_THREADS) k_quantise_flat(const double* W, 
         RunState st = {};
         st.k = 1;
         st.T = T;
-        st.U = __umul64hi((unsigned long long)r64, T);
+        st.r64 = (unsigned long long)r64;
         st.resample = T != 0ull;
         st.status = T != 0ull ? 0 : -4;
         fs->st = st;

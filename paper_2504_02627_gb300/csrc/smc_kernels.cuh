@@ -18,6 +18,16 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
+// Partial results of one particle slice, combined in a fixed order.
+struct SlicePart {
+    double za_m, za_s;      // log-sum-exp pieces of log W_j - Delta H_j
+    double w_m, w_e1, w_e2; // max, sum exp, sum exp^2 of the new log-weights
+    double alpha_sum;
+    double g_num, g_den;    // ChEES: sum alpha_j g_j, sum alpha_j
+    long long steps_sum;
+    int smin, smax;
+};
+
 // Per-iteration buffers shared by the stage kernels.
 struct StepBufs {
     const RunParams* runs;
@@ -38,6 +48,13 @@ struct StepBufs {
     int64_t n_tiles;
     int32_t max_steps_all;
     int32_t pad;
+    // particle slices of the weight / statistics kernels
+    const int32_t* slice_run;   // slice -> run
+    const int32_t* slice_start; // slice -> first run-local particle
+    int64_t n_slices;
+    SlicePart* parts;           // [n_slices]
+    double* colsum;             // [n_slices x 2D] ChEES column sums
+    unsigned int* done;         // [n_runs] slice tickets
     // trajectory results
     const float* theta_prev;    // positions before the move (source buffer)
     const float* theta_new;     // proposals
@@ -46,12 +63,16 @@ struct StepBufs {
     const double* alpha;
 };
 
+// One iteration = weights_steps, resample_scan, sort, trajectory kernel,
+// move_stats (each launch covers every run).
 cudaError_t launch_init_draw(const StepBufs& b, float* theta, cudaStream_t s);
 cudaError_t launch_init_finish(const StepBufs& b, const double* logpi, cudaStream_t s);
-cudaError_t launch_normalise(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_weights_steps(const StepBufs& b, cudaStream_t s);
 cudaError_t launch_resample_scan(const StepBufs& b, cudaStream_t s);
-cudaError_t launch_steps_sort(const StepBufs& b, cudaStream_t s);
-cudaError_t launch_reweight_chees(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_sort(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_move_stats(const StepBufs& b, cudaStream_t s);
+constexpr int KERNELS_PER_ITERATION = 7;   // kernels launched by one smc_step
+constexpr int MAX_CHEES_DIM = 256;         // D handled by the fused ChEES statistics
 
 // Kernel-level entry points (stand-alone buffers).
 cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n, cudaStream_t s);

@@ -87,7 +87,7 @@ def test_iterations_match_oracle_stage_by_stage(name):
             src = np.arange(N)
         th_start = pre["theta"][src]
         # (c) Halton jitter and step counts, bit-exact from the GPU's L
-        L = smp.runstate()[0]["L_used"]
+        L = smp.runstate()[0]["L_last"]
         assert abs(L - np.exp(pre["rs"]["log_L"])) <= 1e-15 * L
         h = np.array([oracle.halton2(j * K + k) for j in range(N)])
         S_o = np.array([oracle.step_count(x, L, run["step_size"], run["max_steps"]) for x in h])
