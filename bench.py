@@ -220,7 +220,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="logistic")
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0: FP32 SIMT, 1: tcgen05 BF16x3, 2: tcgen05 BF16 (the timed main line)")
+    ap.add_argument("--variants", default="0,1,2",
+                    help="precisions also measured (fewer steps) and reported under 'variants'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -299,6 +302,34 @@ def main():
     else:
         ge_all, ess_all = float(ge_total), ess_post
     value = ge_all / (dev_ms / 1e3)
+
+    # ---------------- other precisions of the same workload (plain FP32 vs tensor-core forms)
+    variants = {}
+    for pv in [int(x) for x in args.variants.split(",") if x.strip() != ""]:
+        if pv == args.precision:
+            continue
+        cv = g.make_config(seed=1000 + 1000 * rank, precision=pv, **run)
+        sv = g.Sampler(md, cv, stream)
+        sv.reset(5_000 + rank)
+        sv.run(K)
+        torch.cuda.synchronize()
+        nv = max(1, args.steps // 2)
+        ms_v, ge_v, ess_v = 0.0, 0, 0.0
+        for i in range(nv):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sv.reset(40_000 + 1000 * rank + i)
+            sv.run(K)
+            e1.record()
+            sm_ = sv.summary()[0]
+            ms_v += e0.elapsed_time(e1)
+            ge_v += sm_["grad_evals"]
+            ess_v += sm_["ess_sum_post_warmup"]
+        sv.close()
+        variants[["fp32", "bf16x3", "bf16"][pv]] = {
+            "value": ge_v / (ms_v / 1e3), "unit": "particle-grad-evals/s", "ms_per_step": ms_v / nv,
+            "ess_per_s": ess_v / (ms_v / 1e3), "steps": nv}
 
     # ---------------- roofline of the trajectory kernel
     peaks, peak_kind = _peaks()
@@ -393,6 +424,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "variants": variants,
         "gpu_launches": prof["kernel_launches"],
         "clocks": clk,
     }

@@ -76,6 +76,7 @@ struct smc_handle {
     SlicePart* parts = nullptr;
     double* colsum = nullptr;
     unsigned int* done = nullptr;
+    int* dev_err = nullptr;     // set by a bounded device wait that gave up
     int64_t n_tiles = 0;
     int32_t max_steps_all = 0;
     int64_t iters_done = 0;
@@ -287,6 +288,7 @@ cudaError_t initial_draw(smc_handle* h) {
         a.N = h->N;
         a.ld = h->ld;
         a.eval_only = 1;
+        a.dev_err = h->dev_err;
         ce = launch_traj(h->model.m, a, h->precision, s);
     }
     if (ce == cudaSuccess) ce = launch_init_finish(b, h->logpi[0], s);
@@ -426,6 +428,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->parts = A.get<SlicePart>((size_t)slices);
     h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
     h->done = A.get<unsigned int>((size_t)n_runs);
+    h->dev_err = A.get<int>(1);
     if (A.err != cudaSuccess) {
         smc_status st = cuda_fail(h, A.err, "smc_init allocation");
         smc_destroy(h);
@@ -439,6 +442,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     cudaMemsetAsync(h->tiles, 0, sizeof(TileDesc) * (size_t)tiles, s);
     cudaMemsetAsync(h->counter, 0, sizeof(unsigned int) * 4, s);
     cudaMemsetAsync(h->done, 0, sizeof(unsigned int) * (size_t)n_runs, s);
+    cudaMemsetAsync(h->dev_err, 0, sizeof(int), s);
     cudaMemcpyAsync(h->slice_run, slice_run.data(), sizeof(int32_t) * (size_t)slices, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(h->slice_start, slice_start.data(), sizeof(int32_t) * (size_t)slices, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(h->theta[0], 0, nd * sizeof(float), s);
@@ -467,6 +471,9 @@ smc_status read_stats(smc_handle* h, smc_stats* stats) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "smc_step stats");
     smc_status ret = SMC_OK;
+    int derr = 0;
+    if (cudaMemcpy(&derr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && derr)
+        ret = fail(h, SMC_E_TIMEOUT, "a bounded device wait in the trajectory kernel gave up");
     for (int64_t r = 0; r < h->n_runs; ++r) {
         const RunState& s = st[(size_t)r];
         if (stats) {
@@ -528,6 +535,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
         a.rstate = h->d_rstate;
         a.N = h->N;
         a.ld = h->ld;
+        a.dev_err = h->dev_err;
         if (h->profiling) {
             const size_t i = 2 * h->n_event_pairs;
             while (h->events.size() < i + 2) {

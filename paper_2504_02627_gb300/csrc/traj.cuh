@@ -47,11 +47,31 @@ struct TrajArgs {
     int64_t N, ld;
     int32_t eval_only;      // 1: compute log pi and grad at theta_in, no move
     int32_t pad;
+    int* dev_err;           // set to 1 when a bounded device wait gives up (may be nullptr)
 };
+
+// Run of particle j: step size, Philox key, iteration and run-local index.
+__device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& r, double& eps,
+                                             uint64_t& seed, uint32_t& kk, uint32_t& jl) {
+    r = a.run_of ? a.run_of[j] : 0;
+    if (a.runs) {
+        eps = a.runs[r].eps;
+        seed = a.runs[r].seed;
+        jl = (uint32_t)(j - a.runs[r].off);
+    } else {
+        eps = a.eps_fixed;
+        seed = 0;
+        jl = (uint32_t)j;
+    }
+    kk = a.rstate ? (uint32_t)a.rstate[r].k : 0u;
+}
 
 // Launchers (kernels in traj_simt.cu / traj_tc.cu).  Return cudaError_t of
 // the launch; `supported` reports whether the model/shape has a kernel.
 bool traj_supported(const DevModel& m, int32_t precision);
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s);
+// tensor-core path (traj_tc.cu): logistic / linear regression, BF16 or BF16x3
+bool traj_tc_supported(const DevModel& m);
+cudaError_t launch_traj_tc(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
 
 }  // namespace smc

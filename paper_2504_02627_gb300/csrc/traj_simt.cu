@@ -137,21 +137,6 @@ struct HierM {
     }
 };
 
-__device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& r, double& eps,
-                                             uint64_t& seed, uint32_t& kk, uint32_t& jl) {
-    r = a.run_of ? a.run_of[j] : 0;
-    if (a.runs) {
-        eps = a.runs[r].eps;
-        seed = a.runs[r].seed;
-        jl = (uint32_t)(j - a.runs[r].off);
-    } else {
-        eps = a.eps_fixed;
-        seed = 0;
-        jl = (uint32_t)j;
-    }
-    kk = a.rstate ? (uint32_t)a.rstate[r].k : 0u;
-}
-
 template <template <int> class MT, int DM>
 __global__ void __launch_bounds__(128) traj_thread_kernel(DevModel m, TrajArgs a) {
     using M = MT<DM>;
@@ -584,6 +569,7 @@ bool glm_shape_ok(const DevModel& m) {
 }  // namespace
 
 bool traj_supported(const DevModel& m, int32_t precision) {
+    if (precision == 1 || precision == 2) return traj_tc_supported(m);
     switch (m.kind) {
         case GAUSS_DENSE: return precision == 0 && m.D <= 32;
         case BANANA: return precision == 0 && m.D <= 64;
@@ -596,6 +582,7 @@ bool traj_supported(const DevModel& m, int32_t precision) {
 
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s) {
     if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
+    if (precision == 1 || precision == 2) return launch_traj_tc(m, a, precision == 1, s);
     switch (m.kind) {
         case GAUSS_DENSE: return dispatch_thread<GaussDenseM>(m, a, s);
         case BANANA: return dispatch_thread_wide<BananaM>(m, a, s);

@@ -273,3 +273,70 @@ def test_resampling_one_hot_and_degenerate():
     assert st == 0 and np.all(anc == 4321)
     q, anc, st = _resample_gpu(np.zeros(100), 1)
     assert st == -4
+
+
+# ------------------------------------------------------------- tensor-core path
+# Gradient error bounds of the split-BF16 products (derived in the design doc):
+# x3 (hi*hi + lo*hi + hi*lo, lo*lo dropped): a few 2^-16 of the summand scale;
+# plain BF16: a few 2^-8.  The end-point log pi is FP32 in every mode.
+TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("name", ["logistic_small", "logistic", "linear"])
+@pytest.mark.parametrize("N", [1, 45, 300])
+def test_tc_target_value_and_gradient(name, N, precision):
+    w = rounded_workload(_workloads()[name])
+    t = oracle_target(w)
+    dm = _model(w)
+    th = _theta(w, N)
+    ld = ((N + 31) // 32) * 32
+    D = th.shape[1]
+    t_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    t_d[:, :N] = torch.as_tensor(th.T.astype(np.float32)).cuda()
+    g_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    lp_d = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    g.check(g.lib().smc_k_target(dm.h, ptr(t_d), N, ld, ptr(lp_d), ptr(g_d), precision, stream()), "target")
+    lp_g, gr_g = lp_d.cpu().numpy()[:N], g_d.cpu().numpy()[:, :N].T
+    lp_o, gr_o = oracle.logpi(t, th)
+    gs, ls = _summand_scale(w, th)
+    tol = TC_GRAD_TOL[precision]
+    assert np.all(np.abs(gr_g - gr_o) <= tol * gs + 1e-6), np.max(np.abs(gr_g - gr_o) / gs)
+    assert np.all(np.abs(lp_g - lp_o) <= 1e-5 * ls), np.max(np.abs(lp_g - lp_o) / ls)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("name,eps", [("logistic", 1e-3), ("logistic_small", 0.01), ("linear", 0.005)])
+def test_tc_one_leapfrog_step(name, eps, precision):
+    """One step: theta_1 = theta_0 + eps (p_0 + eps/2 g_0), p_1 = p_0 + eps/2 (g_0 + g_1);
+    a gradient error dg moves p by at most eps*dg and theta by eps^2/2 dg."""
+    w = rounded_workload(_workloads()[name])
+    t = oracle_target(w)
+    dm = _model(w)
+    N = 257
+    th = _theta(w, N)
+    p = f32r(np.random.default_rng(9).standard_normal((N, w["D"])))
+    ld = ((N + 31) // 32) * 32
+    D = w["D"]
+    t_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    t_d[:, :N] = torch.as_tensor(th.T.astype(np.float32)).cuda()
+    p_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    p_d[:, :N] = torch.as_tensor(p.T.astype(np.float32)).cuda()
+    g_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    lp_d = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    g.check(g.lib().smc_k_target(dm.h, ptr(t_d), N, ld, ptr(lp_d), ptr(g_d), precision, stream()), "target")
+    s_d = dev(np.ones(N, dtype=np.int32))
+    g.check(g.lib().smc_k_leapfrog(dm.h, ptr(t_d), ptr(p_d), ptr(g_d), ptr(lp_d), ptr(s_d), eps, N, ld,
+                                   precision, stream()), "leapfrog")
+    th_g = t_d.cpu().numpy()[:, :N].T.astype(np.float64)
+    p_g = p_d.cpu().numpy()[:, :N].T.astype(np.float64)
+    lp_g = lp_d.cpu().numpy()[:N]
+    th_o, p_o, _, lp_o = oracle.leapfrog(t, th, p, eps, 1)
+    gs0, _ = _summand_scale(w, th)
+    gs1, ls1 = _summand_scale(w, th_o)
+    dg = TC_GRAD_TOL[precision] * np.maximum(gs0, gs1) + 1e-6
+    np.testing.assert_array_less(np.abs(p_g - p_o), eps * dg + 1e-5 * (np.abs(p_o) + _rms(p_o)))
+    np.testing.assert_array_less(np.abs(th_g - th_o), 0.5 * eps**2 * dg + 1e-5 * (np.abs(th_o) + _rms(th_o)))
+    # the end-point energy is exact to FP32 accuracy at the GPU's own end point
+    lp_at_g, _ = oracle.logpi(t, th_g)
+    assert np.all(np.abs(lp_g - lp_at_g) <= 1e-5 * ls1)

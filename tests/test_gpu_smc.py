@@ -200,3 +200,47 @@ def test_degenerate_target_reports_status():
     # sticky: later calls report the handle state
     assert g.lib().smc_step(smp.h, None) == -6
     smp.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_tensor_core_iterations_keep_exact_weights(precision):
+    """Tensor-core trajectories (BF16x3 / BF16 gradients): resampling and step
+    counts are still bit-exact, and the weights use the exact energy at the
+    GPU's own end points -- Delta H from the oracle's FP64 log pi at the GPU
+    positions and momenta matches to FP32 accuracy, so the sampler stays exact
+    whatever the gradient precision."""
+    w = rounded_workload(_cases()["logistic"])
+    run = w["run"]
+    t = oracle_target(w)
+    seed = 77
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, precision=precision, **run), stream())
+    N, D, K = run["n_particles"], w["D"], run["n_iters"]
+    for k in range(1, K + 1):
+        pre = {"theta": smp.buffer(B.BUF_THETA).T.astype(np.float64), "logw": smp.buffer(B.BUF_LOGW)}
+        lp_pre, _ = oracle.logpi(t, pre["theta"])
+        np.testing.assert_allclose(smp.buffer(B.BUF_LOGPI), lp_pre, rtol=1e-6, atol=1e-6 * np.abs(lp_pre).max())
+        st = smp.step()[0]
+        _, ess, _ = oracle.normalise(pre["logw"])
+        assert st["resampled"] == int(ess < 0.5 * N)
+        src = np.arange(N)
+        if st["resampled"]:
+            _, q = oracle.quantise(smp.buffer(B.BUF_W))
+            _, src = oracle.systematic(q, oracle.resample_r64(seed, k))
+            np.testing.assert_array_equal(smp.buffer(B.BUF_ANCESTORS), src)
+        L = smp.runstate()[0]["L_last"]
+        S_o = np.array([oracle.step_count(oracle.halton2(j * K + k), L, run["step_size"], run["max_steps"])
+                        for j in range(N)])
+        np.testing.assert_array_equal(smp.buffer(B.BUF_STEPS), S_o)
+        p0 = f32r(np.stack([oracle.normals(seed, oracle.TAG_MOM, k, j, D) for j in range(N)]))
+        th1 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        p1 = smp.buffer(B.BUF_P_FINAL).T.astype(np.float64)
+        lp1, _ = oracle.logpi(t, th1)
+        dH_o = (0.5 * (p1**2).sum(1) - lp1) - (0.5 * (p0**2).sum(1) - lp_pre[src])
+        dH = smp.buffer(B.BUF_DH)
+        tol = 1e-5 * (np.abs(lp1) + np.abs(lp_pre[src]) + (p1**2).sum(1) + 1.0)
+        assert np.all(np.abs(dH - dH_o) <= tol), np.max(np.abs(dH - dH_o) / tol)
+        # the trajectories themselves stay close to the exact-gradient ones
+        th1_o, _, _, _ = oracle.leapfrog(t, pre["theta"][src], p0, run["step_size"], S_o)
+        rel = np.abs(th1 - th1_o) / (np.abs(th1_o) + np.sqrt(np.mean(th1_o**2)))
+        assert np.median(rel) < (1e-3 if precision == 1 else 5e-2)
+    smp.close()
