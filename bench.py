@@ -70,6 +70,10 @@ def _flops_per_grad(w):
         return 4.0 * w["n"] * w["D"], 2.0 * w["n"] * w["D"]
     if w["kind"] == "gauss_dense":
         return 2.0 * w["D"] ** 2, 2.0 * w["D"] ** 2
+    if w["kind"] == "hier_normal":
+        # per group: b = mu + tau eta (2), ybar - b (1), n (.)/s^2 (2), sum (1),
+        # tau eta r into d/dlog tau (3), r tau - eta (2)
+        return 11.0 * w["n"] + 4.0, 14.0 * w["n"]
     return 0.0, 0.0
 
 
@@ -208,7 +212,8 @@ WORKLOAD_DESC = {
     "logistic": "Bayesian logistic regression, synthetic, n=1000, D=25 (intercept + 24 N(0,1) features), "
                 "N=4096 particles, K=50 SMC iterations, ChEES-HMC eps=1e-3 L0=5 max 500 steps, 1-d Halton",
     "gauss10": "10-d correlated Gaussian, N=256, K=20",
-    "hier": "hierarchical normal, 64 uneven runs",
+    "hier": "batched hierarchical normal (non-centred, 50 groups x 20 obs, D=52), 64 independent runs with "
+            "particle counts uniform on 512..8192 (seeded, 278k particles) in every launch, K=50, eps=0.01, L0=1, FP32",
     "logistic_large": "logistic regression n=100000 D=100 N=16384 K=30",
 }
 
@@ -254,8 +259,17 @@ def main():
     run = dict(w["run"])
     K = run["n_iters"]
     md = g.ModelData.from_workload(w)
-    cfg = g.make_config(seed=1000 + 1000 * rank, precision=args.precision, **run)
-    smp = g.Sampler(md, cfg, stream)
+    batched = "run_sizes" in w
+
+    def make_configs(seed0, precision):
+        if not batched:
+            return g.make_config(seed=seed0, precision=precision, **run)
+        # uneven independent runs in one handle (particle counts from the workload)
+        return [g.make_config(seed=seed0 + r, precision=precision, **dict(run, n_particles=int(nr)))
+                for r, nr in enumerate(w["run_sizes"])]
+
+    smp = g.Sampler(md, make_configs(1000 + 1000 * rank, args.precision), stream)
+    n_runs = smp.n_runs
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
@@ -275,22 +289,27 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ge_total, ess_post, lz = 0, 0.0, []
-    smp.profile(True)
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record()
-        one_run(20_000 + 1000 * rank + i)
+        one_run(20_000 + 1000 * rank + i)      # smc_run replays CUDA graphs
         ev[i][1].record()
-        s = smp.summary()[0]          # synchronises after the step; outside the events
-        ge_total += s["grad_evals"]
-        ess_post += s["ess_sum_post_warmup"]
-        lz.append(s["log_z"])
+        summ = smp.summary()                    # synchronises after the step; outside the events
+        ge_total += sum(x["grad_evals"] for x in summ)
+        ess_post += sum(x["ess_sum_post_warmup"] for x in summ)
+        lz.append(summ[0]["log_z"])
     torch.cuda.synchronize()
-    prof = smp.get_profile()
-    smp.profile(False)
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
+    # trajectory-kernel timing and launch count: one more run with in-library
+    # events around every trajectory launch (no graphs), outside the timed region
+    smp.profile(True)
+    flush.zero_()
+    one_run(30_000 + rank)
+    prof_ge = sum(x["grad_evals"] for x in smp.summary())
+    prof = smp.get_profile()
+    smp.profile(False)
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     t = torch.tensor([dev_ms, float(ge_total), ess_post], dtype=torch.float64, device="cuda")
     if dist:
@@ -308,8 +327,10 @@ def main():
     for pv in [int(x) for x in args.variants.split(",") if x.strip() != ""]:
         if pv == args.precision:
             continue
-        cv = g.make_config(seed=1000 + 1000 * rank, precision=pv, **run)
-        sv = g.Sampler(md, cv, stream)
+        try:
+            sv = g.Sampler(md, make_configs(1000 + 1000 * rank, pv), stream)
+        except RuntimeError:
+            continue    # no kernel for this model at that precision
         sv.reset(5_000 + rank)
         sv.run(K)
         torch.cuda.synchronize()
@@ -322,10 +343,10 @@ def main():
             sv.reset(40_000 + 1000 * rank + i)
             sv.run(K)
             e1.record()
-            sm_ = sv.summary()[0]
+            sm_ = sv.summary()
             ms_v += e0.elapsed_time(e1)
-            ge_v += sm_["grad_evals"]
-            ess_v += sm_["ess_sum_post_warmup"]
+            ge_v += sum(x["grad_evals"] for x in sm_)
+            ess_v += sum(x["ess_sum_post_warmup"] for x in sm_)
         sv.close()
         variants[["fp32", "bf16x3", "bf16"][pv]] = {
             "value": ge_v / (ms_v / 1e3), "unit": "particle-grad-evals/s", "ms_per_step": ms_v / nv,
@@ -334,8 +355,8 @@ def main():
     # ---------------- roofline of the trajectory kernel
     peaks, peak_kind = _peaks()
     fl_grad, fl_end = _flops_per_grad(w)
-    n_part = run["n_particles"]
-    traj_flops = fl_grad * ge_total + fl_end * n_part * K * args.steps
+    n_part = smp.n_total
+    traj_flops = fl_grad * prof_ge + fl_end * n_part * K
     traj_ms = prof["traj_ms"]
     traj_n = max(1, prof["traj_launches"])
     achieved = traj_flops / traj_n / (traj_ms / traj_n / 1e3) / 1e12
@@ -352,8 +373,9 @@ def main():
     tr = _traffic_for(kfile)
     roof["traffic"] = tr
     roof["kernel"] = "trajectory (leapfrog) kernel"
-    roof["launches_timed"] = prof["traj_launches"]
-    roof["share_of_step_time"] = traj_ms / dev_ms if dev_ms > 0 else None
+    roof["launches_profiled"] = prof["traj_launches"]
+    roof["mean_launch_ms"] = traj_ms / traj_n
+    roof["share_of_step_time"] = traj_ms / (dev_ms / args.steps) if dev_ms > 0 else None
 
     # ---------------- end to end through the C-ABI with host buffers
     e2e = None
@@ -366,25 +388,30 @@ def main():
         D = w["D"]
         theta_h = np.empty((D, n_part), dtype=np.float32)
         logw_h = np.empty(n_part)
-        lz_h = np.empty(1)
+        lz_h = np.empty(n_runs)
         times, ge_e = [], 0
         for i in range(max(2, args.steps // 2)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = C.c_void_p()
-            c2 = g.make_config(seed=30_000 + i + 1000 * rank, precision=args.precision, **run)
-            g.check(lib.smc_init(C.byref(h), C.byref(c2), C.byref(md.struct), C.c_void_p(stream)), "smc_init")
+            c2 = make_configs(30_000 + 100 * i + 1000 * rank, args.precision)
+            if batched:
+                arr = (g._binding.SmcConfig * len(c2))(*c2)
+                g.check(lib.smc_init_batch(C.byref(h), len(c2), arr, C.byref(md.struct), C.c_void_p(stream)),
+                        "smc_init_batch")
+            else:
+                g.check(lib.smc_init(C.byref(h), C.byref(c2), C.byref(md.struct), C.c_void_p(stream)), "smc_init")
             g.check(lib.smc_run(h, K, None), "smc_run", h)
             g.check(lib.smc_get_particles(h, theta_h.ctypes.data, logw_h.ctypes.data, 0), "particles", h)
             g.check(lib.smc_log_evidence(h, lz_h.ctypes.data_as(C.POINTER(C.c_double))), "evidence", h)
-            summ = (g._binding.SmcSummary * 1)()
+            summ = (g._binding.SmcSummary * n_runs)()
             g.check(lib.smc_get_summary(h, summ), "summary", h)
             lib.smc_destroy(h)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-            ge_e += summ[0].grad_evals
+            ge_e += sum(x.grad_evals for x in summ)
         e2e = {"value": ge_e * world / sum(times), "unit": "particle-grad-evals/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(theta_h.nbytes + logw_h.nbytes + 8),
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(theta_h.nbytes + logw_h.nbytes + lz_h.nbytes),
                "steps": len(times)}
 
     if dist:
@@ -395,7 +422,7 @@ def main():
 
     # ---------------- CPU baseline (oracle on the host cores), rank 0, N=1 only
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not batched:
         rate, cores, dt, iters = cpu_oracle_rate(w, run)
         cpu = {"value": rate, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
                "sample": f"first {iters} SMC iterations of the same workload (N={n_part}, full data), "
@@ -425,7 +452,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "variants": variants,
-        "gpu_launches": prof["kernel_launches"],
+        "gpu_launches": prof["kernel_launches"] * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

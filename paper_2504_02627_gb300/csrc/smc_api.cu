@@ -85,6 +85,10 @@ struct smc_handle {
     std::vector<smc_config> cfg;
     // profiling: events around trajectory launches, launch counter
     bool profiling = false;
+    // CUDA graph of two consecutive iterations (buffer parity 0 -> 1 -> 0)
+    cudaGraphExec_t graph2 = nullptr;
+    cudaStream_t graph_stream = nullptr;   // private stream the graph is captured and replayed on
+    cudaEvent_t fork = nullptr, join = nullptr;
     std::vector<cudaEvent_t> events;
     size_t n_event_pairs = 0;
     int64_t kernel_launches = 0;
@@ -561,9 +565,73 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
     return SMC_OK;
 }
 
+// Captures two consecutive iterations (starting from buffer parity 0) into a
+// CUDA graph, so that a run replays one graph launch per two iterations
+// instead of 2 x 7 kernel launches.
+// The capture happens on the handle's private stream (the caller's stream may
+// be the legacy default stream, which cannot be captured).
+static smc_status capture_two_steps(smc_handle* h) {
+    cudaStream_t s = h->graph_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_run capture");
+    cudaStream_t user = h->stream;
+    h->stream = s;
+    smc_status st = smc_step(h, nullptr);
+    if (st == SMC_OK) st = smc_step(h, nullptr);
+    h->stream = user;
+    e = cudaStreamEndCapture(s, &graph);
+    h->iters_done -= 2;   // captured, not executed
+    if (st != SMC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_run capture");
+    e = cudaGraphInstantiate(&h->graph2, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph2 = nullptr;
+        return cuda_fail(h, e, "smc_run graph instantiate");
+    }
+    return SMC_OK;
+}
+
 smc_status smc_run(smc_handle* h, int64_t n_iters, smc_stats* per_iter) {
     if (!h || n_iters < 0) return SMC_E_INVAL;
-    for (int64_t k = 0; k < n_iters; ++k) {
+    if (h->sticky) return SMC_E_STATE;
+    // Graph replay when nothing has to be read back between iterations.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(h->stream, &cap);
+    const bool graphs = !per_iter && !h->profiling && n_iters >= 2 && cap == cudaStreamCaptureStatusNone;
+    int64_t k = 0;
+    if (graphs) {
+        if (h->cur != 0) {   // align to the captured buffer parity
+            smc_status st = smc_step(h, nullptr);
+            if (st != SMC_OK) return st;
+            ++k;
+        }
+        if (!h->graph_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(h, e, "smc_run graph stream");
+        }
+        if (!h->graph2) {
+            smc_status st = capture_two_steps(h);
+            if (st != SMC_OK) return st;
+        }
+        // caller's stream -> private stream -> caller's stream
+        cudaError_t e = cudaEventRecord(h->fork, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->graph_stream, h->fork, 0);
+        for (; e == cudaSuccess && k + 2 <= n_iters; k += 2) {
+            e = cudaGraphLaunch(h->graph2, h->graph_stream);
+            h->iters_done += 2;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->join, h->graph_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->join, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "smc_run graph launch");
+    }
+    for (; k < n_iters; ++k) {
         smc_status st = smc_step(h, per_iter ? per_iter + k * h->n_runs : nullptr);
         if (st != SMC_OK) return st;
     }
@@ -758,6 +826,13 @@ smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len) {
 void smc_destroy(smc_handle* h) {
     if (!h) return;
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+    if (h->graph2) cudaGraphExecDestroy(h->graph2);
+    if (h->graph_stream) {
+        cudaStreamSynchronize(h->graph_stream);
+        cudaStreamDestroy(h->graph_stream);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     h->mem.release();
     h->model.mem.release();
     cudaStreamSynchronize(h->stream);

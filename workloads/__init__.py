@@ -107,7 +107,7 @@ def hier(groups: int = 50, obs: int = 20, sigma: float = 1.0, seed: int = DATA_S
     return {"kind": "hier_normal", "D": groups + 2, "n": groups, "ybar": ybar, "n_g": n_g,
             "ss": ss, "sigma": sigma, "y_raw": y, "run_sizes": sizes,
             "run": dict(n_particles=int(sizes.sum()), n_iters=50, n_warmup=25,
-                        step_size=0.05, traj_len0=5.0, max_steps=500, init_scale=1.0)}
+                        step_size=0.01, traj_len0=1.0, max_steps=500, init_scale=1.0)}
 
 
 def gauss100_cond(cond: float = 1e4) -> dict:
