@@ -104,7 +104,10 @@ typedef struct {
     int32_t jitter;         /* 0: h = 1; 1: base-2 Halton of n = j*K + k          */
     double ess_frac;        /* resample when ESS < ess_frac * J                   */
     uint64_t seed;          /* Philox4x32-10 key                                  */
-    int32_t accept_reject;  /* must be 0 (the paper's SMC-ChEES)                  */
+    int32_t accept_reject;  /* 0: the paper's SMC-ChEES (every particle moves, log w
+                               += -Delta H); 1: Metropolis select u < alpha after
+                               the move (Eqs. for alpha and the select rule), weight
+                               unchanged; ChEES statistics use the proposals     */
     int32_t adapt;          /* 1: ChEES adaptation of L during warm-up            */
     double adam_lr, adam_b1, adam_b2, adam_eps;
     double init_scale;      /* q_init = N(0, init_scale^2 I)                      */

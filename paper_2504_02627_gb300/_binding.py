@@ -162,9 +162,10 @@ class ModelData:
 
 def make_config(n_particles, n_iters, n_warmup, step_size, traj_len0=5.0, max_steps=500, jitter=1,
                 ess_frac=0.5, seed=1000, adapt=1, adam_lr=0.025, adam_b1=0.9, adam_b2=0.999,
-                adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32) -> SmcConfig:
+                adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32, accept_reject=0) -> SmcConfig:
     return SmcConfig(int(n_particles), int(n_iters), int(n_warmup), float(step_size), float(traj_len0),
-                     int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), 0, int(adapt),
+                     int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), int(accept_reject),
+                     int(adapt),
                      float(adam_lr), float(adam_b1), float(adam_b2), float(adam_eps), float(init_scale),
                      int(precision), 0)
 

@@ -29,6 +29,8 @@ struct RunParams {
     int64_t n_iters, n_warmup;
     int32_t slice0;         // first particle slice (SLICE particles) of the run
     int32_t n_slices;
+    int32_t accept_reject;  // 1: Metropolis select after the move, weight unchanged
+    int32_t pad;
 };
 
 constexpr int SLICE = 256;  // particles per CTA in the weight / statistics kernels

@@ -231,7 +231,7 @@ std::string check_config(const smc_config& c) {
     if (!(c.traj_len0 > 0.0)) return "traj_len0 must be > 0";
     if (c.max_steps < 1 || c.max_steps > 65536) return "max_steps must be in [1, 65536]";
     if (c.jitter != 0 && c.jitter != 1) return "jitter must be 0 or 1";
-    if (c.accept_reject != 0) return "accept_reject must be 0";
+    if (c.accept_reject != 0 && c.accept_reject != 1) return "accept_reject must be 0 or 1";
     if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
     if (c.precision < 0 || c.precision > 2) return "unknown precision";
@@ -268,6 +268,10 @@ StepBufs make_bufs(smc_handle* h) {
     b.done = h->done;
     b.theta_prev = h->theta[h->cur];
     b.theta_new = h->theta[1 - h->cur];
+    b.grad_prev = h->grad[h->cur];
+    b.grad_new = h->grad[1 - h->cur];
+    b.logpi_prev = h->logpi[h->cur];
+    b.logpi_new = h->logpi[1 - h->cur];
     b.p_final = h->p_final;
     b.dH = h->dH;
     b.alpha = h->alpha;
@@ -379,6 +383,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.tile0 = tiles;
         rp.n_iters = cfg[r].n_iters;
         rp.n_warmup = cfg[r].n_warmup;
+        rp.accept_reject = cfg[r].accept_reject;
         rp.slice0 = (int32_t)slices;
         rp.n_slices = (int32_t)((rp.n + SLICE - 1) / SLICE);
         slices += rp.n_slices;

@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
     long long S = 0;
     int smin = 0x7fffffff, smax = 0;
     if (x.valid) {
-        const double dH = b.dH[x.j];
+        // with the Metropolis select the incremental weight is one
+        const double dH = rp.accept_reject ? 0.0 : b.dH[x.j];
         const double old = b.logw[x.j];
         za = (st.resample ? -logn : old - st.lse) - dH;
         lw = (st.resample ? -logn : old) - dH;
@@ -448,6 +449,20 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
         if (threadIdx.x == 0) {
             b.parts[c].g_num = num;
             b.parts[c].g_den = den;
+        }
+    }
+    // Metropolis variant (Eqs. for alpha and the select rule): keep the
+    // proposal when u < alpha, otherwise restore the start state; the ChEES
+    // statistics above used the proposals, as in Algorithm 2.
+    if (rp.accept_reject && x.valid) {
+        const Philox4 w = philox4x32_10(Philox4{0u, (uint32_t)x.i, (uint32_t)st.k, TAG_MH}, rp.seed);
+        if (!(u01_52(w.x, w.y) < b.alpha[x.j])) {
+            const int64_t src = b.src[x.j];
+            for (int d = 0; d < D; ++d) {
+                b.theta_new[(int64_t)d * b.ld + x.j] = b.theta_prev[(int64_t)d * b.ld + src];
+                b.grad_new[(int64_t)d * b.ld + x.j] = b.grad_prev[(int64_t)d * b.ld + src];
+            }
+            b.logpi_new[x.j] = b.logpi_prev[src];
         }
     }
     // ticket: the last slice of the run to get here finishes the iteration

@@ -57,7 +57,11 @@ struct StepBufs {
     unsigned int* done;         // [n_runs] slice tickets
     // trajectory results
     const float* theta_prev;    // positions before the move (source buffer)
-    const float* theta_new;     // proposals
+    float* theta_new;           // proposals (replaced by the start state when rejected)
+    const float* grad_prev;
+    float* grad_new;
+    const double* logpi_prev;
+    double* logpi_new;
     const float* p_final;
     const double* dH;
     const double* alpha;

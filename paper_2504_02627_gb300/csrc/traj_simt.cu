@@ -498,6 +498,208 @@ __global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, Tr
     }
 }
 
+// ============================================================ dense Gaussian, D > 32
+// 32 particles per CTA, 256 threads.  The precision P (transposed, so that a
+// thread's four rows are contiguous) and mu stay in shared memory; theta, p and
+// grad live in shared memory as [DP][32].  grad = -P (theta - mu) is a
+// register-tiled product: thread t owns rows 4*(t/8)..+3 and particles
+// 4*(t%8)..+3 (16 accumulators, two 16-byte shared loads per 16 FMAs).
+constexpr int DENSE_G = 32;
+constexpr int DENSE_THREADS = 256;
+
+template <int DP>
+struct DenseSmem {
+    static size_t bytes() { return sizeof(float) * ((size_t)DP * DP + DP + 3 * DP * DENSE_G) + sizeof(double) * 2 * DENSE_G; }
+};
+
+template <int DP>
+__global__ void __launch_bounds__(DENSE_THREADS, 1) traj_dense_kernel(DevModel m, TrajArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Pt = reinterpret_cast<float*>(smem_raw);        // [DP][DP], Pt[k][d] = P[d][k]
+    float* mu = Pt + DP * DP;                               // [DP]
+    float* th_s = mu + DP;                                  // [DP][32]
+    float* p_s = th_s + DP * DENSE_G;
+    float* g_s = p_s + DP * DENSE_G;
+    double* H0_s = reinterpret_cast<double*>(g_s + DP * DENSE_G);
+    double* lp_s = H0_s + DENSE_G;
+    __shared__ int64_t j_s[DENSE_G], src_s[DENSE_G];
+    __shared__ int S_s[DENSE_G];
+    __shared__ float eps_s[DENSE_G];
+    __shared__ uint64_t seed_s[DENSE_G];
+    __shared__ uint32_t k_s[DENSE_G], jl_s[DENSE_G];
+    __shared__ int smax_s;
+    const int tid = threadIdx.x, D = m.D;
+    for (int e = tid; e < DP * DP; e += DENSE_THREADS) {
+        const int k = e / DP, d = e % DP;
+        Pt[e] = (k < D && d < D) ? m.P[d * D + k] : 0.0f;
+    }
+    for (int e = tid; e < DP; e += DENSE_THREADS) mu[e] = e < D ? m.mu[e] : 0.0f;
+    const int64_t slot0 = (int64_t)blockIdx.x * DENSE_G;
+    if (tid < DENSE_G) {
+        const int64_t t = slot0 + tid;
+        int64_t j = -1, src = -1;
+        int S = 0;
+        float ef = 0.0f;
+        if (t < a.N) {
+            j = a.perm ? a.perm[t] : t;
+            src = a.src ? a.src[j] : j;
+            S = a.eval_only ? 0 : a.steps[j];
+            int r;
+            double eps;
+            uint64_t seed;
+            uint32_t kk, jl;
+            particle_run(a, j, r, eps, seed, kk, jl);
+            ef = (float)eps;
+            seed_s[tid] = seed;
+            k_s[tid] = kk;
+            jl_s[tid] = jl;
+        }
+        j_s[tid] = j;
+        src_s[tid] = src;
+        S_s[tid] = S;
+        eps_s[tid] = ef;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int mx = 0;
+        for (int i = 0; i < DENSE_G; ++i) mx = max(mx, S_s[i]);
+        smax_s = mx;
+    }
+    for (int e = tid; e < DP * DENSE_G; e += DENSE_THREADS) {
+        const int d = e / DENSE_G, q = e % DENSE_G;
+        const int64_t src = src_s[q];
+        float tv = 0.0f, gv = 0.0f, pv = 0.0f;
+        if (src >= 0 && d < D) {
+            tv = a.theta_in[(int64_t)d * a.ld + src];
+            if (!a.eval_only) gv = a.grad_in[(int64_t)d * a.ld + src];
+            if (a.p_in && !a.eval_only) pv = a.p_in[(int64_t)d * a.ld + j_s[q]];
+        }
+        th_s[e] = tv;
+        g_s[e] = gv;
+        p_s[e] = pv;
+    }
+    __syncthreads();
+    if (!a.p_in && !a.eval_only) {
+        const int npairs = (D + 1) / 2;
+        for (int e = tid; e < npairs * DENSE_G; e += DENSE_THREADS) {
+            const int i = e / DENSE_G, q = e % DENSE_G;
+            if (j_s[q] < 0) continue;
+            double z0, z1;
+            normal_pair(seed_s[q], (uint32_t)i, jl_s[q], k_s[q], TAG_MOM, z0, z1);
+            p_s[(2 * i) * DENSE_G + q] = (float)z0;
+            if (2 * i + 1 < D) p_s[(2 * i + 1) * DENSE_G + q] = (float)z1;
+        }
+        __syncthreads();
+    }
+    if (tid < DENSE_G && !a.eval_only) {
+        double kin = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double v = p_s[d * DENSE_G + tid];
+            kin += v * v;
+        }
+        H0_s[tid] = j_s[tid] >= 0 ? 0.5 * kin - a.logpi_in[src_s[tid]] : 0.0;
+    }
+    __syncthreads();   // H0 reads p_s before the first half kick rewrites it
+    const int smax = smax_s;
+    for (int e = tid; e < DP * DENSE_G; e += DENSE_THREADS) {
+        const int d = e / DENSE_G, q = e % DENSE_G;
+        if (d < D && S_s[q] >= 1) {
+            const float ef = eps_s[q], he = 0.5f * ef;
+            const float pv = fmaf(he, g_s[e], p_s[e]);
+            p_s[e] = pv;
+            th_s[e] = fmaf(ef, pv, th_s[e]);
+        }
+    }
+    __syncthreads();
+    const int nsteps = a.eval_only ? 1 : smax;
+    for (int s = 1; s <= nsteps; ++s) {
+        // gradient at the drifted positions into a staging copy (g_s keeps the
+        // frozen gradient of particles whose trajectory has ended)
+        __syncthreads();
+        {
+            const int db = tid >> 3, pb = tid & 7;
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = 0.0f;
+            if (4 * db < DP) {
+                for (int k = 0; k < D; ++k) {
+                    const float4 av4 = *reinterpret_cast<const float4*>(Pt + k * DP + 4 * db);
+                    const float4 t4 = *reinterpret_cast<const float4*>(th_s + k * DENSE_G + 4 * pb);
+                    const float mk = mu[k];
+                    const float b0 = t4.x - mk, b1 = t4.y - mk, b2 = t4.z - mk, b3 = t4.w - mk;
+                    const float av[4] = {av4.x, av4.y, av4.z, av4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[i][0] = fmaf(av[i], b0, acc[i][0]);
+                        acc[i][1] = fmaf(av[i], b1, acc[i][1]);
+                        acc[i][2] = fmaf(av[i], b2, acc[i][2]);
+                        acc[i][3] = fmaf(av[i], b3, acc[i][3]);
+                    }
+                }
+            }
+            __syncthreads();   // every thread has read th_s before anyone moves it
+            if (4 * db < DP) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int d = 4 * db + i;
+                    if (d >= D) continue;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const int q = 4 * pb + qq, e = d * DENSE_G + q;
+                        const float gsv = -acc[i][qq];
+                        if (a.eval_only) {
+                            g_s[e] = gsv;
+                        } else if (s <= S_s[q]) {
+                            const float ef = eps_s[q], he = 0.5f * ef;
+                            g_s[e] = gsv;
+                            float pv = fmaf(he, gsv, p_s[e]);
+                            if (s + 1 <= S_s[q]) {
+                                pv = fmaf(he, gsv, pv);
+                                th_s[e] = fmaf(ef, pv, th_s[e]);
+                            }
+                            p_s[e] = pv;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // end point: log pi = c - 1/2 (theta - mu)' P (theta - mu) = c + 1/2 (theta - mu)' grad,
+    // FP64 accumulation of the FP32 gradient of the final position
+    if (tid < DENSE_G) {
+        double q2 = 0.0, kin = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double dl = (double)th_s[d * DENSE_G + tid] - (double)mu[d];
+            q2 += dl * (double)g_s[d * DENSE_G + tid];
+            const double v = p_s[d * DENSE_G + tid];
+            kin += v * v;
+        }
+        lp_s[tid] = m.lconst + 0.5 * q2;
+        if (j_s[tid] >= 0) {
+            const int64_t j = j_s[tid];
+            const double lp1 = lp_s[tid];
+            a.logpi_out[j] = lp1;
+            if (!a.eval_only) {
+                double dH = (0.5 * kin - lp1) - H0_s[tid];
+                if (!isfinite(dH)) dH = CUDART_INF;
+                if (a.dH) a.dH[j] = dH;
+                if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
+            }
+        }
+    }
+    for (int e = tid; e < DP * DENSE_G; e += DENSE_THREADS) {
+        const int d = e / DENSE_G, q = e % DENSE_G;
+        const int64_t j = j_s[q];
+        if (j < 0 || d >= D) continue;
+        if (!a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th_s[e];
+        a.grad_out[(int64_t)d * a.ld + j] = g_s[e];
+        if (a.p_out && !a.eval_only) a.p_out[(int64_t)d * a.ld + j] = p_s[e];
+    }
+}
+
 // ============================================================ dispatch
 namespace {
 
@@ -561,6 +763,26 @@ cudaError_t dispatch_glm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     }
 }
 
+template <int DP>
+cudaError_t launch_dense(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const size_t sm = DenseSmem<DP>::bytes();
+    auto kern = traj_dense_kernel<DP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (a.N + DENSE_G - 1) / DENSE_G;
+    if (grid == 0) return cudaSuccess;
+    kern<<<(unsigned)grid, DENSE_THREADS, sm, s>>>(m, a);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_dense(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    if (m.D <= 48) return launch_dense<48>(m, a, s);
+    if (m.D <= 64) return launch_dense<64>(m, a, s);
+    if (m.D <= 100) return launch_dense<100>(m, a, s);
+    if (m.D <= 128) return launch_dense<128>(m, a, s);
+    return cudaErrorInvalidValue;
+}
+
 bool glm_shape_ok(const DevModel& m) {
     if (m.Dp != 4 && m.Dp != 8 && m.Dp != 16 && m.Dp != 28 && m.Dp != 32) return false;
     return GlmSmem<32, 16>::bytes(m.n) <= 220 * 1024;
@@ -571,7 +793,7 @@ bool glm_shape_ok(const DevModel& m) {
 bool traj_supported(const DevModel& m, int32_t precision) {
     if (precision == 1 || precision == 2) return traj_tc_supported(m);
     switch (m.kind) {
-        case GAUSS_DENSE: return precision == 0 && m.D <= 32;
+        case GAUSS_DENSE: return precision == 0 && m.D <= 128;
         case BANANA: return precision == 0 && m.D <= 64;
         case HIER_NORMAL: return precision == 0 && m.D <= 64;
         case LOGISTIC:
@@ -584,7 +806,7 @@ cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision,
     if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
     if (precision == 1 || precision == 2) return launch_traj_tc(m, a, precision == 1, s);
     switch (m.kind) {
-        case GAUSS_DENSE: return dispatch_thread<GaussDenseM>(m, a, s);
+        case GAUSS_DENSE: return m.D <= 32 ? dispatch_thread<GaussDenseM>(m, a, s) : dispatch_dense(m, a, s);
         case BANANA: return dispatch_thread_wide<BananaM>(m, a, s);
         case HIER_NORMAL: return dispatch_thread_wide<HierM>(m, a, s);
         case LOGISTIC: return dispatch_glm<true>(m, a, s);

@@ -71,6 +71,8 @@ def _workloads():
         "hier": workloads.hier(),                                      # 50 groups, D=52
         "banana50": workloads.banana50(),
         "banana2": workloads.paper_banana2(),
+        "gauss100": workloads.gauss100_cond(),       # dense precision, D=100 (CTA kernel)
+        "illcond100": workloads.paper_illcond100(),  # Sec. 4 ill-conditioned Gaussian
     }
 
 
@@ -144,7 +146,7 @@ def _summand_scale(w, th):
 
 
 @pytest.mark.parametrize("name", ["gauss10", "logistic", "logistic_small", "linear", "hier", "banana50",
-                                  "banana2"])
+                                  "banana2", "gauss100", "illcond100"])
 @pytest.mark.parametrize("N", [1, 45, 300])
 def test_target_value_and_gradient(name, N):
     w = rounded_workload(_workloads()[name])
@@ -182,7 +184,7 @@ def _rms(a):
 
 @pytest.mark.parametrize("name,eps", [("gauss10", 0.1), ("logistic", 1e-3), ("logistic_small", 0.01),
                                       ("linear", 0.005), ("hier", 0.05), ("banana50", 0.01),
-                                      ("banana2", 0.01)])
+                                      ("banana2", 0.01), ("gauss100", 0.01), ("illcond100", 1e-3)])
 def test_one_leapfrog_step_within_1e5(name, eps):
     w = rounded_workload(_workloads()[name])
     t = oracle_target(w)
@@ -197,7 +199,7 @@ def test_one_leapfrog_step_within_1e5(name, eps):
 
 
 @pytest.mark.parametrize("name,eps", [("gauss10", 0.1), ("logistic", 1e-3), ("hier", 0.01),
-                                      ("banana50", 0.01)])
+                                      ("banana50", 0.01), ("gauss100", 0.005)])
 def test_ragged_trajectories(name, eps):
     """Different step counts per particle (1..40), across several CTAs and a
     ragged tail; tolerance grows linearly with the step count."""

@@ -38,14 +38,19 @@ def _cases():
     ban = workloads.banana50()
     ban["run"] = dict(n_particles=500, n_iters=6, n_warmup=3, step_size=0.02, traj_len0=0.4,
                       max_steps=30, init_scale=1.0)
-    return {"gauss10": workloads.gauss10(), "logistic": lg, "hier": hi, "banana50": ban}
+    g100 = workloads.gauss100_cond()
+    # start close to the mode: from N(0, I) every energy error of this 1e4-
+    # conditioned target is far above 50 and the comparison is meaningless
+    g100["run"] = dict(n_particles=300, n_iters=6, n_warmup=3, step_size=0.002, traj_len0=0.04,
+                       max_steps=40, init_scale=0.02)
+    return {"gauss10": workloads.gauss10(), "logistic": lg, "hier": hi, "banana50": ban, "gauss100": g100}
 
 
 def _cfg(run, seed):
     return g.make_config(seed=seed, **run)
 
 
-@pytest.mark.parametrize("name", ["gauss10", "logistic", "hier", "banana50"])
+@pytest.mark.parametrize("name", ["gauss10", "logistic", "hier", "banana50", "gauss100"])
 def test_iterations_match_oracle_stage_by_stage(name):
     w = rounded_workload(_cases()[name])
     run = w["run"]
@@ -243,4 +248,41 @@ def test_tensor_core_iterations_keep_exact_weights(precision):
         th1_o, _, _, _ = oracle.leapfrog(t, pre["theta"][src], p0, run["step_size"], S_o)
         rel = np.abs(th1 - th1_o) / (np.abs(th1_o) + np.sqrt(np.mean(th1_o**2)))
         assert np.median(rel) < (1e-3 if precision == 1 else 5e-2)
+    smp.close()
+
+
+def test_metropolis_variant_matches_oracle():
+    """accept_reject = 1: Metropolis select u < alpha (Philox block (0, j, k, MH))
+    after the move, weights unchanged, ChEES on the proposals (Algorithm 2)."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(w["run"], n_iters=6, n_warmup=3, step_size=0.3)
+    t = oracle_target(w)
+    seed = 31
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, accept_reject=1, **run), stream())
+    N, D, K = run["n_particles"], w["D"], run["n_iters"]
+    n_rej = 0
+    for k in range(1, K + 1):
+        th_pre = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        lw_pre = smp.buffer(B.BUF_LOGW)
+        st = smp.step()[0]
+        assert st["log_z_inc"] == 0.0
+        src = np.arange(N)
+        if st["resampled"]:
+            _, q = oracle.quantise(smp.buffer(B.BUF_W))
+            _, src = oracle.systematic(q, oracle.resample_r64(seed, k))
+            np.testing.assert_allclose(smp.buffer(B.BUF_LOGW), np.full(N, -np.log(N)))
+        else:
+            np.testing.assert_array_equal(smp.buffer(B.BUF_LOGW), lw_pre)
+        alpha = smp.buffer(B.BUF_ALPHA)
+        u = np.array([oracle.u01(*oracle.philox((0, j, k, oracle.TAG_MH), seed)[:2]) for j in range(N)])
+        acc = u < alpha
+        n_rej += int((~acc).sum())
+        th1 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        np.testing.assert_array_equal(th1[~acc], th_pre[src][~acc])
+        S = smp.buffer(B.BUF_STEPS)
+        p0 = f32r(np.stack([oracle.normals(seed, oracle.TAG_MOM, k, j, D) for j in range(N)]))
+        th1_o, _, _, _ = oracle.leapfrog(t, th_pre[src], p0, run["step_size"], S)
+        err = np.abs(th1 - th1_o)[acc] / (np.abs(th1_o[acc]) + np.sqrt(np.mean(th1_o**2)))
+        assert np.all(err <= 1e-5 * S[acc, None])
+    assert n_rej > 0            # the step size makes some proposals fail
     smp.close()
