@@ -19,7 +19,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["rng.c", "targets.c", "hmc.c", "weights.c", "chees.c", "smc.c"]
+_SOURCES = ["rng.c", "targets.c", "hmc.c", "weights.c", "chees.c", "smc.c", "flow.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
@@ -60,7 +60,8 @@ class Config(C.Structure):
                 ("jitter", C.c_int32), ("accept_reject", C.c_int32), ("adapt", C.c_int32),
                 ("chees_initial_p", C.c_int32), ("adam_lr", C.c_double),
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
-                ("init_scale", C.c_double)]
+                ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
+                ("flow_lr", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -84,7 +85,12 @@ class IterIO(C.Structure):
     _fields_ = [("theta", _DP), ("grad", _DP), ("logpi", _DP), ("logw", _DP),
                 ("chees", C.POINTER(CheesState)), ("log_z", _DP),
                 ("ancestors", _I32P), ("steps", _I32P), ("p0", _DP), ("p1", _DP),
-                ("dH", _DP), ("alpha", _DP)]
+                ("dH", _DP), ("alpha", _DP), ("flow_params", _DP), ("flow_m", _DP), ("flow_v", _DP),
+                ("flow_t", C.POINTER(C.c_int32)), ("flow_H", C.c_int64), ("flow_L", C.c_int64)]
+
+
+class Flow(C.Structure):
+    _fields_ = [("D", C.c_int64), ("H", C.c_int64), ("L", C.c_int64), ("params", _DP)]
 
 
 _lib = None
@@ -129,6 +135,16 @@ def lib():
                                      C.POINTER(Stats), C.c_int32]
         L.oracle_smc_run.restype = C.c_int
         L.oracle_moments.argtypes = [_DP, _DP, C.c_int64, C.c_int64, _DP, _DP]
+        L.oracle_flow_num_params.argtypes = [C.c_int64, C.c_int64, C.c_int64]
+        L.oracle_flow_num_params.restype = C.c_int64
+        L.oracle_flow_forward.argtypes = [C.POINTER(Flow), _DP, _DP, _DP]
+        L.oracle_flow_inverse.argtypes = [C.POINTER(Flow), _DP, _DP, _DP]
+        L.oracle_flow_logpi_z.argtypes = [C.POINTER(Flow), C.POINTER(Target), _DP, _DP, _DP, _DP, _DP]
+        L.oracle_flow_logpi_z.restype = C.c_double
+        L.oracle_flow_loss_grad.argtypes = [C.POINTER(Flow), _DP, _DP, C.c_int64, _DP]
+        L.oracle_flow_loss_grad.restype = C.c_double
+        L.oracle_flow_adam.argtypes = [_DP, _DP, _DP, _DP, C.c_int64, C.c_int32, C.c_double, C.c_double,
+                                       C.c_double, C.c_double]
     return _lib
 
 
@@ -326,12 +342,16 @@ class SMCConfig:
     adam_b2: float = 0.999
     adam_eps: float = 1e-8
     init_scale: float = 1.0
+    flow_train_every: int = 2
+    flow_epochs: int = 10
+    flow_lr: float = 1e-3
 
     def struct(self):
         return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
                       self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
                       self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
-                      self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale)
+                      self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
+                      self.flow_train_every, self.flow_epochs, self.flow_lr)
 
 
 def stats_to_dicts(arr):
@@ -363,10 +383,73 @@ def smc_init(t: TargetSpec, cfg: SMCConfig, nthreads: int = 0):
     return {"theta": theta, "grad": grad, "logpi": lp, "logw": lw, "log_z": lz}
 
 
+class FlowSpec:
+    """Affine-coupling flow parameters (FP64 array, layout of oracle/flow.c)."""
+
+    def __init__(self, D, H, L, params):
+        self.D, self.H, self.L = int(D), int(H), int(L)
+        self.params = np.ascontiguousarray(params, dtype=np.float64)
+        assert self.params.size == num_flow_params(D, H, L)
+        self.struct = Flow(self.D, self.H, self.L, _dp(self.params))
+
+
+def num_flow_params(D, H, L):
+    return int(lib().oracle_flow_num_params(D, H, L))
+
+
+def flow_forward(f: FlowSpec, z):
+    z = _f64(np.atleast_2d(z))
+    x = np.empty_like(z)
+    ld = np.empty(z.shape[0])
+    for j in range(z.shape[0]):
+        v = C.c_double()
+        lib().oracle_flow_forward(C.byref(f.struct), _dp(z[j]), _dp(x[j]), C.byref(v))
+        ld[j] = v.value
+    return x, ld
+
+
+def flow_inverse(f: FlowSpec, x):
+    x = _f64(np.atleast_2d(x))
+    z = np.empty_like(x)
+    ld = np.empty(x.shape[0])
+    for j in range(x.shape[0]):
+        v = C.c_double()
+        lib().oracle_flow_inverse(C.byref(f.struct), _dp(x[j]), _dp(z[j]), C.byref(v))
+        ld[j] = v.value
+    return z, ld
+
+
+def flow_logpi_z(f: FlowSpec, t: TargetSpec, z):
+    """log pi_z(z) = log pi(T(z)) + log|det dT/dz|, its z-gradient, and x = T(z)."""
+    z = _f64(np.atleast_2d(z))
+    N, D = z.shape
+    lpz, gz, x, gx, lpx = np.empty(N), np.empty((N, D)), np.empty((N, D)), np.empty((N, D)), np.empty(N)
+    for j in range(N):
+        v = C.c_double()
+        lpz[j] = lib().oracle_flow_logpi_z(C.byref(f.struct), C.byref(t.struct), _dp(z[j]), _dp(gz[j]),
+                                           _dp(x[j]), _dp(gx[j]), C.byref(v))
+        lpx[j] = v.value
+    return lpz, gz, x, gx, lpx
+
+
+def flow_loss_grad(f: FlowSpec, theta, W):
+    th = _f64(theta)
+    W = _f64(W)
+    grad = np.empty(f.params.size)
+    loss = lib().oracle_flow_loss_grad(C.byref(f.struct), _dp(th), _dp(W), th.shape[0], _dp(grad))
+    return loss, grad
+
+
+def flow_adam(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    lib().oracle_flow_adam(_dp(params), _dp(_f64(grad)), _dp(m), _dp(v), params.size, int(t), lr, b1, b2, eps)
+
+
 def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: int = 0):
     """One iteration (Algorithm 3 body) on a state dict as returned by
-    ``smc_init`` plus ``chees`` (CheesState).  Mutates theta/grad/logpi/logw/
-    log_z/chees in place and returns the per-iteration intermediates."""
+    ``smc_init`` plus ``chees`` (CheesState), and optionally ``flow`` (dict
+    with params, m, v, t (c_int32), H, L) for the learned preconditioner.
+    Mutates theta/grad/logpi/logw/log_z/chees/flow in place and returns the
+    per-iteration intermediates."""
     N, D = cfg.n_particles, t.D
     for key in ("theta", "grad", "logpi", "logw"):
         state[key] = _f64(state[key])
@@ -374,10 +457,14 @@ def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: 
            "p0": np.empty((N, D)), "p1": np.empty((N, D)), "dH": np.empty(N),
            "alpha": np.empty(N)}
     lz = C.c_double(state["log_z"])
+    fl = state.get("flow")
     io = IterIO(_dp(state["theta"]), _dp(state["grad"]), _dp(state["logpi"]),
                 _dp(state["logw"]), C.pointer(state["chees"]), C.pointer(lz),
                 out["ancestors"].ctypes.data_as(_I32P), out["steps"].ctypes.data_as(_I32P),
-                _dp(out["p0"]), _dp(out["p1"]), _dp(out["dH"]), _dp(out["alpha"]))
+                _dp(out["p0"]), _dp(out["p1"]), _dp(out["dH"]), _dp(out["alpha"]),
+                _dp(fl["params"]) if fl else None, _dp(fl["m"]) if fl else None,
+                _dp(fl["v"]) if fl else None, C.pointer(fl["t"]) if fl else None,
+                int(fl["H"]) if fl else 0, int(fl["L"]) if fl else 0)
     st = Stats()
     c = cfg.struct()
     out["status"] = lib().oracle_smc_iteration(C.byref(t.struct), C.byref(c), int(k),
@@ -385,6 +472,28 @@ def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: 
     state["log_z"] = lz.value
     out["stats"] = stats_to_dicts([st])[0]
     return out
+
+
+def new_flow_state(params, H, L):
+    p = np.array(params, dtype=np.float64, copy=True)
+    return {"params": p, "m": np.zeros_like(p), "v": np.zeros_like(p), "t": C.c_int32(0),
+            "H": int(H), "L": int(L)}
+
+
+def smc_run_flow(t: TargetSpec, cfg: SMCConfig, flow_params, H, L, nthreads: int = 0):
+    """The sampler with the learned preconditioner (iteration by iteration)."""
+    st = smc_init(t, cfg, nthreads)
+    st["chees"] = initial_chees_state(cfg)
+    st["flow"] = new_flow_state(flow_params, H, L)
+    stats, status = [], 0
+    for k in range(1, cfg.n_iters + 1):
+        out = smc_iteration(t, cfg, k, st, nthreads)
+        stats.append(out["stats"])
+        status = out["status"]
+        if status != 0:
+            break
+    return {"theta": st["theta"], "logw": st["logw"], "log_z": st["log_z"], "stats": stats,
+            "status": status, "flow": st["flow"]}
 
 
 def initial_chees_state(cfg: SMCConfig) -> CheesState:

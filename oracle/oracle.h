@@ -160,6 +160,9 @@ typedef struct {
     int32_t chees_initial_p;/* 0: final momentum in g_j (default); 1: initial */
     double adam_lr, adam_b1, adam_b2, adam_eps;
     double init_scale;      /* q_init = N(0, init_scale^2 I)                 */
+    int32_t flow_train_every; /* train the flow at warm-up iterations k with (k-1) % every == 0 */
+    int32_t flow_epochs;    /* full-batch Adam steps per training event      */
+    double flow_lr;
 } oracle_config;
 
 typedef struct {
@@ -187,6 +190,8 @@ typedef struct {
     double* theta; double* grad; double* logpi; double* logw;
     oracle_chees_state* chees; double* log_z;
     int32_t* ancestors; int32_t* steps; double* p0; double* p1; double* dH; double* alpha;
+    /* learned preconditioner (NULL: HMC in theta space) and its Adam state */
+    double* flow_params; double* flow_m; double* flow_v; int32_t* flow_t; int64_t flow_H, flow_L;
 } oracle_iter_io;
 int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t k,
                          oracle_iter_io* io, oracle_stats* st, int32_t nthreads);
@@ -195,6 +200,25 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
  * logpi, logw (all N entries) and returns log Z_0 = LSE(logw) - log N. */
 double oracle_smc_init(const oracle_target* t, const oracle_config* c, double* theta,
                        double* grad, double* logpi, double* logw, int32_t nthreads);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner: affine-coupling flow theta = T(z) (flow.c).  HMC
+ * runs on log pi_z(z) = log pi(T(z)) + log|det dT/dz|; the move is exact for
+ * any fixed T, and the weight takes -Delta H in z-space.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t D, H, L;        /* dimension (even), hidden width, coupling layers */
+    const double* params;   /* oracle_flow_num_params(D, H, L) doubles         */
+} oracle_flow;
+int64_t oracle_flow_num_params(int64_t D, int64_t H, int64_t L);
+void oracle_flow_forward(const oracle_flow* f, const double* z, double* x, double* logdet);
+void oracle_flow_inverse(const oracle_flow* f, const double* x, double* z, double* logdet_inv);
+double oracle_flow_logpi_z(const oracle_flow* f, const oracle_target* t, const double* z, double* gz,
+                           double* x_out, double* gx_out, double* logpi_x_out);
+double oracle_flow_loss_grad(const oracle_flow* f, const double* theta, const double* W, int64_t N,
+                             double* grad);
+void oracle_flow_adam(double* params, const double* grad, double* m, double* v, int64_t n, int32_t t,
+                      double lr, double b1, double b2, double eps);
 
 /* Weighted moments (Eq. for realised estimates): mean and variance per dim. */
 void oracle_moments(const double* theta, const double* logw, int64_t N, int64_t D,

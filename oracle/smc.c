@@ -62,6 +62,7 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
                          oracle_iter_io* io, oracle_stats* st, int32_t nthreads) {
     const int64_t N = c->n_particles, D = t->D, K = c->n_iters;
     int status = 0;
+    double* z0 = 0;
     double* W = (double*)malloc((size_t)N * sizeof(double));
     int32_t* anc = io->ancestors ? io->ancestors : (int32_t*)malloc((size_t)N * sizeof(int32_t));
     int32_t* S = io->steps ? io->steps : (int32_t*)malloc((size_t)N * sizeof(int32_t));
@@ -107,6 +108,23 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
         for (int64_t i = 0; i < N; ++i) anc[i] = (int32_t)i;
     }
 
+    /* learned preconditioner: trained on the current weighted particles at
+     * warm-up iterations (k - 1) % every == 0, frozen afterwards */
+    oracle_flow flow = {D, io->flow_H, io->flow_L, io->flow_params};
+    const int use_flow = io->flow_params != 0;
+    if (use_flow && k < c->n_warmup && c->flow_train_every > 0 && (k - 1) % c->flow_train_every == 0) {
+        const int64_t np = oracle_flow_num_params(D, io->flow_H, io->flow_L);
+        double* gradp = (double*)malloc((size_t)np * sizeof(double));
+        for (int32_t e = 0; e < c->flow_epochs; ++e) {
+            oracle_flow_loss_grad(&flow, io->theta, W, N, gradp);
+            *io->flow_t += 1;
+            oracle_flow_adam(io->flow_params, gradp, io->flow_m, io->flow_v, np, *io->flow_t, c->flow_lr, 0.9,
+                             0.999, 1e-8);
+        }
+        free(gradp);
+    }
+    z0 = use_flow ? (double*)malloc((size_t)(N * D) * sizeof(double)) : 0;
+
     /* (c) jittered trajectory lengths l_j = h_j L and step counts. */
     const double L = exp(io->chees->log_L);
     for (int64_t j = 0; j < N; ++j) {
@@ -124,9 +142,37 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
         memcpy(th1 + j * D, io->theta + j * D, (size_t)D * sizeof(double));
         memcpy(g1 + j * D, io->grad + j * D, (size_t)D * sizeof(double));
         lp1[j] = io->logpi[j];
-        double H0 = oracle_hamiltonian(pj, D, lp1[j]);
-        oracle_leapfrog(t, th1 + j * D, pj, g1 + j * D, lp1 + j, c->step_size, S[j]);
-        double H1 = oracle_hamiltonian(pj, D, lp1[j]);
+        double H0, H1;
+        if (!use_flow) {
+            H0 = oracle_hamiltonian(pj, D, lp1[j]);
+            oracle_leapfrog(t, th1 + j * D, pj, g1 + j * D, lp1 + j, c->step_size, S[j]);
+            H1 = oracle_hamiltonian(pj, D, lp1[j]);
+        } else {
+            /* HMC in z = T^-1(theta) on log pi_z (Algorithm 1 in latent space) */
+            double* z = z0 + j * D;
+            double ldi;
+            oracle_flow_inverse(&flow, io->theta + j * D, z, &ldi);
+            double* zz = (double*)malloc((size_t)(3 * D) * sizeof(double));
+            double *gz = zz + D, *x = gz + D;
+            memcpy(zz, z, (size_t)D * sizeof(double));
+            double lpz = oracle_flow_logpi_z(&flow, t, zz, gz, 0, 0, 0);
+            H0 = oracle_hamiltonian(pj, D, lpz);
+            double lpx = lp1[j];
+            for (int32_t l = 0; l < S[j]; ++l) {
+                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * c->step_size * gz[d];
+                for (int64_t d = 0; d < D; ++d) zz[d] += c->step_size * pj[d];
+                lpz = oracle_flow_logpi_z(&flow, t, zz, gz, x, g1 + j * D, &lpx);
+                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * c->step_size * gz[d];
+            }
+            if (S[j] > 0) {
+                memcpy(th1 + j * D, x, (size_t)D * sizeof(double));
+                lp1[j] = lpx;
+            }
+            H1 = oracle_hamiltonian(pj, D, lpz);
+            /* keep the latent start for the ChEES statistics; the end in th1 is
+             * re-mapped below */
+            free(zz);
+        }
         double d = H1 - H0;
         if (!isfinite(d)) d = INFINITY;
         dH[j] = d;
@@ -144,11 +190,23 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
         for (int64_t j = 0; j < N; ++j) io->logw[j] -= dH[j];
     }
 
-    /* (g) ChEES adaptation during warm-up, uses the pre-move states. */
+    /* (g) ChEES adaptation during warm-up, uses the pre-move states (in the
+     * latent space when the flow is on: the momenta live there). */
     if (c->adapt && k < c->n_warmup) {
         double ghat;
         const double* pm = c->chees_initial_p ? p0 : p1;
-        if (oracle_chees_gradient(io->theta, th1, pm, l, alpha, N, D, &ghat, 0))
+        const double* s0 = io->theta;
+        const double* s1 = th1;
+        double* z1 = 0;
+        if (use_flow) {
+            z1 = (double*)malloc((size_t)(N * D) * sizeof(double));
+            for (int64_t j = 0; j < N; ++j) oracle_flow_inverse(&flow, th1 + j * D, z1 + j * D, 0);
+            s0 = z0;
+            s1 = z1;
+        }
+        int okg = oracle_chees_gradient(s0, s1, pm, l, alpha, N, D, &ghat, 0);
+        free(z1);
+        if (okg)
             oracle_chees_adam(io->chees, ghat, c->adam_lr, c->adam_b1, c->adam_b2,
                               c->adam_eps, c->step_size, c->max_steps);
         io->chees->Lbar = 0.9 * io->chees->Lbar + 0.1 * exp(io->chees->log_L);
@@ -195,6 +253,7 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     }
 
 done:
+    free(z0);
     free(W);
     if (!io->ancestors) free(anc);
     if (!io->steps) free(S);
@@ -223,7 +282,7 @@ int oracle_smc_run(const oracle_target* t, const oracle_config* c, double* theta
     if (ch.log_L > hi) ch.log_L = hi;
     int status = 0;
     for (int64_t k = 1; k <= c->n_iters && status == 0; ++k) {
-        oracle_iter_io io = {theta, grad, logpi, logw, &ch, &lz, 0, 0, 0, 0, 0, 0};
+        oracle_iter_io io = {theta, grad, logpi, logw, &ch, &lz, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         status = oracle_smc_iteration(t, c, k, &io, stats ? stats + (k - 1) : 0, nthreads);
     }
     if (theta_out) memcpy(theta_out, theta, (size_t)(N * D) * sizeof(double));
