@@ -7,7 +7,11 @@
  * T = layer_{L-1} o ... o layer_0.  Layer l splits z into halves A_l and B_l
  * (even l: A = first half, B = second; odd l: swapped) and maps
  *   b -> b * exp(s(a)) + t(a),   a unchanged,
- * with (s_raw, t) = W3 relu(W2 relu(W1 a + b1) + b2) + b3, s = 2 tanh(s_raw).
+ * with (s_raw, t) = W3 tanh(W2 tanh(W1 a + b1) + b2) + b3, s = 2 tanh(s_raw).
+ * The hidden activation is smooth (tanh, not a ReLU): HMC in the latent space
+ * follows grad log pi_z, which contains the derivative of the conditioner,
+ * and a ReLU would make that gradient field discontinuous at every kink,
+ * breaking the O(eps^2) energy error of Algorithm 1 there.
  * log|det dT/dz| = sum over layers of sum_k s_k.
  * Parameters, per layer, row-major (out x in):
  *   W1 [H x Dh], b1 [H], W2 [H x H], b2 [H], W3 [D x H], b3 [D]   (Dh = D/2;
@@ -58,12 +62,12 @@ static void conditioner(const oracle_flow* f, int64_t l, const double* z, double
     for (int64_t h = 0; h < H; ++h) {
         double acc = v.b1[h];
         for (int64_t k = 0; k < Dh; ++k) acc += v.W1[h * Dh + k] * z[idx_a(l, k, Dh)];
-        h1[h] = acc > 0.0 ? acc : 0.0;
+        h1[h] = tanh(acc);
     }
     for (int64_t h = 0; h < H; ++h) {
         double acc = v.b2[h];
         for (int64_t k = 0; k < H; ++k) acc += v.W2[h * H + k] * h1[k];
-        h2[h] = acc > 0.0 ? acc : 0.0;
+        h2[h] = tanh(acc);
     }
     for (int64_t r = 0; r < D; ++r) {
         double acc = v.b3[r];
@@ -155,12 +159,12 @@ double oracle_flow_logpi_z(const oracle_flow* f, const oracle_target* t, const d
             for (int64_t h = 0; h < H; ++h) {
                 double acc = 0.0;
                 for (int64_t r = 0; r < D; ++r) acc += v.W3[r * H + h] * co[r];
-                ch2[h] = h2[h] > 0.0 ? acc : 0.0;
+                ch2[h] = acc * (1.0 - h2[h] * h2[h]);
             }
             for (int64_t h = 0; h < H; ++h) {
                 double acc = 0.0;
                 for (int64_t r = 0; r < H; ++r) acc += v.W2[r * H + h] * ch2[r];
-                ch1[h] = h1[h] > 0.0 ? acc : 0.0;
+                ch1[h] = acc * (1.0 - h1[h] * h1[h]);
             }
             for (int64_t k = 0; k < Dh; ++k) {
                 double acc = 0.0;
@@ -235,7 +239,7 @@ double oracle_flow_loss_grad(const oracle_flow* f, const double* theta, const do
             for (int64_t h = 0; h < H; ++h) {
                 double acc = 0.0;
                 for (int64_t r = 0; r < D; ++r) acc += v.W3[r * H + h] * co[r];
-                ch2[h] = h2[h] > 0.0 ? acc : 0.0;
+                ch2[h] = acc * (1.0 - h2[h] * h2[h]);
             }
             for (int64_t r = 0; r < H; ++r) {
                 gb2[r] += ch2[r];
@@ -244,7 +248,7 @@ double oracle_flow_loss_grad(const oracle_flow* f, const double* theta, const do
             for (int64_t h = 0; h < H; ++h) {
                 double acc = 0.0;
                 for (int64_t r = 0; r < H; ++r) acc += v.W2[r * H + h] * ch2[r];
-                ch1[h] = h1[h] > 0.0 ? acc : 0.0;
+                ch1[h] = acc * (1.0 - h1[h] * h1[h]);
             }
             for (int64_t h = 0; h < H; ++h) {
                 gb1[h] += ch1[h];

@@ -154,14 +154,15 @@ def paper_banana2() -> dict:
 def flow_init(D: int, H: int = 128, L: int = 4, seed: int = 99) -> np.ndarray:
     """Initial parameters of the affine-coupling flow (layout of the library and
     the oracle: per layer W1 [H x D/2], b1, W2 [H x H], b2, W3 [D x H], b3).
-    Hidden weights are He-normal draws; the last layer is zero, so the map
-    starts as the identity.  A seeded draw shared by both sides."""
+    Hidden weights are normal draws with variance 1 / fan-in (suited to the
+    tanh hidden units); the last layer is zero, so the map starts as the
+    identity.  A seeded draw shared by both sides."""
     rng = np.random.default_rng(seed)
     Dh = D // 2
     parts = []
     for _ in range(L):
-        parts += [rng.standard_normal(H * Dh) * np.sqrt(2.0 / Dh), np.zeros(H),
-                  rng.standard_normal(H * H) * np.sqrt(2.0 / H), np.zeros(H),
+        parts += [rng.standard_normal(H * Dh) * np.sqrt(1.0 / Dh), np.zeros(H),
+                  rng.standard_normal(H * H) * np.sqrt(1.0 / H), np.zeros(H),
                   np.zeros(D * H), np.zeros(D)]
     return np.concatenate(parts)
 
