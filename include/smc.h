@@ -181,7 +181,9 @@ typedef enum {
     SMC_BUF_DH = 8,         /* f64 [N]          Delta H                           */
     SMC_BUF_ALPHA = 9,      /* f64 [N]          acceptance probabilities          */
     SMC_BUF_THETA_PREV = 10,/* f32 [dim x ld]   positions before the move (after resampling) */
-    SMC_BUF_RUNSTATE = 11   /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS */
+    SMC_BUF_RUNSTATE = 11,  /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS */
+    SMC_BUF_Z0 = 12,        /* f32 [dim x ld]   latent start points z0 = T^-1(theta) of the last move (transport map on) */
+    SMC_BUF_Z1 = 13         /* f32 [dim x ld]   latent end points z' of the last move (transport map on) */
 } smc_buffer;
 smc_status smc_get_buffer(const smc_handle* h, int32_t which, void* dst, int64_t bytes,
                           int32_t device_ptrs);
@@ -220,10 +222,63 @@ smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len);
 /* Frees the handle and its device memory (stream-ordered). NULL is a no-op. */
 void smc_destroy(smc_handle* h);
 
+/* ------------------------------------------------------------------ transport map
+ * A learned preconditioner: an affine-coupling flow theta = T(z) used as a
+ * transport map under HMC.  The move of Algorithm 2 runs in the latent space:
+ * z0 = T^-1(theta), Algorithm 1 on log pi_z(z) = log pi(T(z)) + log|det dT/dz|
+ * with the momentum of Algorithm 2 drawn in z, theta' = T(z').  The energy
+ * error Delta H is taken in z and includes the log-determinant, so -Delta H
+ * remains the exact incremental log-weight of Sec. 3.1.  ChEES statistics
+ * (Algorithm 2) use z0 and z'.  The paper has no learned map; it is this
+ * library's preconditioner, and a zero last layer (T = identity) gives back
+ * the paper's identity-metric sampler.
+ *
+ * T = layer_{L-1} o ... o layer_0.  Layer l keeps half A (even l: coordinates
+ * 0 .. D/2-1; odd l: D/2 .. D-1) and maps the other half b -> b exp(s) + t,
+ * (s_raw, t) = W3 tanh(W2 tanh(W1 a + b1) + b2) + b3, s = 2 tanh(s_raw)
+ * (smooth, so that grad log pi_z is continuous).
+ * Parameters, per layer, row-major (out x in): W1 [H x D/2], b1 [H],
+ * W2 [H x H], b2 [H], W3 [D x H] (rows < D/2 give s_raw, the rest t), b3 [D];
+ * smc_flow_num_params values in all.  FP32 on the device.
+ *
+ * Training: at warm-up iterations k < M_warmup with (k - 1) % train_every ==
+ * 0, after resampling and before the move, `epochs` Adam steps (beta1 0.9,
+ * beta2 0.999, eps 1e-8, step lr) descend the weighted negative
+ * log-likelihood of the particles under the flow density (without the
+ * constant D/2 log 2 pi)
+ *     sum_j W_j ( 1/2 |T^-1(theta_j)|^2 - log|det dT^-1/dtheta (theta_j)| ),
+ * W_j = 1/J after resampling.  The map is frozen from k = M_warmup on.
+ */
+typedef struct {
+    int32_t hidden;         /* H: multiple of 4 in [4, 128]                       */
+    int32_t layers;         /* L: [1, 8]                                          */
+    int32_t train_every;    /* train at k - 1 = 0, train_every, ... (0: never)     */
+    int32_t epochs;         /* Adam steps per training iteration (0: never train) */
+    double lr;              /* Adam step size (> 0)                               */
+} smc_flow_config;
+
+/* Number of parameters of the flow (0 for an invalid shape). */
+int64_t smc_flow_num_params(int64_t dim, int32_t hidden, int32_t layers);
+
+/* Turns the transport map on for a single-run FP32 handle before its first
+ * iteration (also restored, with zero Adam moments, by smc_reset).  params:
+ * host FP64, smc_flow_num_params(dim, hidden, layers) values, copied and cast
+ * to FP32.  Models: GAUSS_DENSE and BANANA with even dim <= 128.
+ * Allocates the parameters, Adam moments, gradient, work copies, per-CTA
+ * gradient partials and the two latent buffers on the handle's stream.
+ * Errors: SMC_E_INVAL (unsupported model / shape / handle state / non-finite
+ * parameter; message in smc_last_error), SMC_E_CUDA. */
+smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const double* params);
+
+/* Current (possibly trained) parameters into params (host FP64, n values =
+ * smc_flow_num_params).  Synchronises the stream. */
+smc_status smc_flow_get_params(const smc_handle* h, double* params, int64_t n);
+
 /* ------------------------------------------------------------------ kernels
  * Kernel-level entry points on caller-owned DEVICE buffers.  They run single
  * stages of the path for parity tests and for callers that drive their own
- * loop.  None allocates device memory except smc_model_create.
+ * loop.  None allocates device memory except smc_model_create and the two
+ * smc_k_flow_* calls (stream-ordered temporaries, freed before returning).
  */
 typedef struct smc_dev_model smc_dev_model;
 
@@ -260,6 +315,29 @@ smc_status smc_k_target(const smc_dev_model* m, const float* theta, int64_t N, i
 smc_status smc_k_leapfrog(const smc_dev_model* m, float* theta, float* p, float* grad,
                           double* logpi, const int32_t* steps, double eps, int64_t N,
                           int64_t ld, int32_t precision, void* stream);
+
+/* The preconditioned move of smc_flow_enable for N particles with given
+ * latent momenta: params device FP32 (smc_flow_num_params values); theta,
+ * grad (= grad log pi at theta), p (latent momenta) f32 [dim x ld] and logpi
+ * f64 [N] are updated in place (theta' = T(z'), its gradient and log pi, the
+ * final latent momenta); steps i32 [N] (>= 1); z0, z1 (f32 [dim x ld], may be
+ * NULL) receive T^-1(theta) and z'; dH (f64 [N], may be NULL) the energy
+ * error in z.  Allocates (stream-ordered) and frees the padded work copies of
+ * the weights. */
+smc_status smc_k_flow_leapfrog(const smc_dev_model* m, int32_t hidden, int32_t layers,
+                               const float* params, float* theta, float* p, float* grad,
+                               double* logpi, const int32_t* steps, double eps, int64_t N,
+                               int64_t ld, float* z0, float* z1, double* dH, void* stream);
+
+/* Gradient of the weighted training loss of smc_flow_enable with respect to
+ * every parameter: grad (device f32, smc_flow_num_params values) from params
+ * (device f32), theta f32 [dim x ld] and W f64 [N] (used as given, not
+ * normalised).  Per-CTA partial gradients are summed in a fixed order, so the
+ * result is deterministic.  Allocates (stream-ordered) and frees the work
+ * copies and the partials (ceil(N / 32) x n_params floats). */
+smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, const float* params,
+                                const float* theta, const double* W, int64_t N, int64_t ld,
+                                float* grad, void* stream);
 
 /* Normalised weights (Sec. 3): lse, ess (device scalars, f64) and W [N] f64
  * from logw [N] f64. */

@@ -19,7 +19,7 @@ SMC_OK, SMC_E_INVAL, SMC_E_NOMEM, SMC_E_CUDA, SMC_E_DEGENERATE, SMC_E_TIMEOUT, S
 GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
 (BUF_THETA, BUF_GRAD, BUF_LOGPI, BUF_LOGW, BUF_W, BUF_ANCESTORS, BUF_STEPS, BUF_P_FINAL,
- BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE) = range(12)
+ BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1) = range(14)
 
 _DP = C.POINTER(C.c_double)
 
@@ -37,6 +37,11 @@ class SmcConfig(C.Structure):
                 ("accept_reject", C.c_int32), ("adapt", C.c_int32), ("adam_lr", C.c_double),
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("precision", C.c_int32), ("pad", C.c_int32)]
+
+
+class SmcFlowConfig(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("layers", C.c_int32), ("train_every", C.c_int32),
+                ("epochs", C.c_int32), ("lr", C.c_double)]
 
 
 class SmcStats(C.Structure):
@@ -89,6 +94,14 @@ EXPORTS = {
                                  C.c_void_p, C.c_void_p]),
     "smc_k_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
+    "smc_flow_num_params": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32]),
+    "smc_flow_enable": (C.c_int, [C.c_void_p, C.POINTER(SmcFlowConfig), _DP]),
+    "smc_flow_get_params": (C.c_int, [C.c_void_p, _DP, C.c_int64]),
+    "smc_k_flow_leapfrog": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_int64,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_k_flow_loss_grad": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 NOALLOC_MAX_N = 4194304     # SMC_NOALLOC_MAX_N in include/smc.h
 
@@ -253,13 +266,31 @@ class Sampler:
                   BUF_LOGPI: ((N,), np.float64), BUF_LOGW: ((N,), np.float64),
                   BUF_W: ((N,), np.float64), BUF_DH: ((N,), np.float64),
                   BUF_ALPHA: ((N,), np.float64), BUF_ANCESTORS: ((N,), np.int32),
-                  BUF_STEPS: ((N,), np.int32), BUF_RUNSTATE: ((self.n_runs, 8), np.float64)}
+                  BUF_STEPS: ((N,), np.int32), BUF_RUNSTATE: ((self.n_runs, 8), np.float64),
+                  BUF_Z0: ((D, ld), np.float32), BUF_Z1: ((D, ld), np.float32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dtype=dt)
         check(lib().smc_get_buffer(self.h, which, out.ctypes.data, out.nbytes, 0), "smc_get_buffer",
               self.h)
         if len(shape) == 2 and which != BUF_RUNSTATE:
             out = out[:, :N]
+        return out
+
+    def enable_flow(self, params, hidden: int, layers: int, train_every: int = 2, epochs: int = 10,
+                    lr: float = 1e-3):
+        """smc_flow_enable: the affine-coupling transport map (FP64 host params)."""
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        n = lib().smc_flow_num_params(self.dim, hidden, layers)
+        if p.size != n:
+            raise ValueError(f"flow needs {n} parameters, got {p.size}")
+        fc = SmcFlowConfig(hidden, layers, train_every, epochs, lr)
+        check(lib().smc_flow_enable(self.h, C.byref(fc), _dp(p)), "smc_flow_enable", self.h)
+        self.flow_shape = (hidden, layers)
+
+    def flow_params(self):
+        hidden, layers = self.flow_shape
+        out = np.empty(lib().smc_flow_num_params(self.dim, hidden, layers))
+        check(lib().smc_flow_get_params(self.h, _dp(out), out.size), "smc_flow_get_params", self.h)
         return out
 
     def runstate(self):

@@ -11,6 +11,7 @@
 
 #include "../../include/smc.h"
 #include "common.cuh"
+#include "flow.cuh"
 #include "smc_kernels.cuh"
 #include "traj.cuh"
 
@@ -87,11 +88,21 @@ struct smc_handle {
     bool profiling = false;
     // CUDA graph of two consecutive iterations (buffer parity 0 -> 1 -> 0)
     cudaGraphExec_t graph2 = nullptr;
+    bool graph_flow = false;               // whether graph2 runs the preconditioned move
     cudaStream_t graph_stream = nullptr;   // private stream the graph is captured and replayed on
     cudaEvent_t fork = nullptr, join = nullptr;
     std::vector<cudaEvent_t> events;
     size_t n_event_pairs = 0;
     int64_t kernel_launches = 0;
+    // learned preconditioner (transport map) and its training state
+    bool flow_on = false;
+    DevFlow flow{};
+    smc_flow_config flow_cfg{};
+    std::vector<float> flow_init;   // parameters at smc_flow_enable, restored by smc_reset
+    float* flow_partials = nullptr;
+    float* z0 = nullptr;            // latent start / end points of the last move
+    float* z1 = nullptr;
+    int32_t flow_t = 0;             // Adam step count
 };
 
 namespace {
@@ -275,7 +286,32 @@ StepBufs make_bufs(smc_handle* h) {
     b.p_final = h->p_final;
     b.dH = h->dH;
     b.alpha = h->alpha;
+    b.chees0 = h->flow_on ? h->z0 : nullptr;
+    b.chees1 = h->flow_on ? h->z1 : nullptr;
     return b;
+}
+
+// Whether iteration k trains the transport map (warm-up, every train_every).
+bool flow_trains_at(const smc_handle* h, int64_t k) {
+    const smc_flow_config& fc = h->flow_cfg;
+    return h->flow_on && fc.train_every > 0 && fc.epochs > 0 && k < h->cfg[0].n_warmup &&
+           (k - 1) % fc.train_every == 0;
+}
+
+// `epochs` Adam steps on the weighted NLL of the current particles (after
+// resampling: positions through src, weights 1/J or W), each followed by a
+// rebuild of the work copies.
+cudaError_t flow_train(smc_handle* h, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int32_t ep = 0; ep < h->flow_cfg.epochs && e == cudaSuccess; ++ep) {
+        e = flow_loss_grad(h->flow, h->theta[h->cur], h->ld, h->src, h->W, h->d_rstate, h->d_runs, h->N,
+                           h->flow_partials, s);
+        h->flow_t += 1;
+        if (e == cudaSuccess) e = flow_adam(h->flow, h->flow_t, h->flow_cfg.lr, s);
+        if (e == cudaSuccess) e = flow_refresh(h->flow, s);   // the next gradient sees the new map
+    }
+    if (h->profiling) h->kernel_launches += 4 * (int64_t)h->flow_cfg.epochs;
+    return e;
 }
 
 // Initial draw, target evaluation and initial weights (Algorithm 3, first
@@ -525,6 +561,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
     cudaError_t e = launch_weights_steps(b, s);
     if (e == cudaSuccess) e = launch_resample_scan(b, s);
     if (e == cudaSuccess) e = launch_sort(b, s);
+    if (e == cudaSuccess && flow_trains_at(h, h->iters_done + 1)) e = flow_train(h, s);
     if (e == cudaSuccess) {
         TrajArgs a{};
         a.theta_in = h->theta[h->cur];
@@ -554,12 +591,14 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
                 h->events.push_back(ev);
             }
             cudaEventRecord(h->events[i], s);
-            e = launch_traj(h->model.m, a, h->precision, s);
+            e = h->flow_on ? launch_traj_flow(h->model.m, h->flow, a, h->z0, h->z1, s)
+                           : launch_traj(h->model.m, a, h->precision, s);
             cudaEventRecord(h->events[i + 1], s);
             h->n_event_pairs += 1;
             h->kernel_launches += KERNELS_PER_ITERATION;
         } else {
-            e = launch_traj(h->model.m, a, h->precision, s);
+            e = h->flow_on ? launch_traj_flow(h->model.m, h->flow, a, h->z0, h->z1, s)
+                           : launch_traj(h->model.m, a, h->precision, s);
         }
     }
     if (e == cudaSuccess) e = launch_move_stats(b, s);
@@ -594,6 +633,7 @@ static smc_status capture_two_steps(smc_handle* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "smc_run capture");
     e = cudaGraphInstantiate(&h->graph2, graph, 0);
     cudaGraphDestroy(graph);
+    h->graph_flow = h->flow_on;
     if (e != cudaSuccess) {
         h->graph2 = nullptr;
         return cuda_fail(h, e, "smc_run graph instantiate");
@@ -607,13 +647,27 @@ smc_status smc_run(smc_handle* h, int64_t n_iters, smc_stats* per_iter) {
     // Graph replay when nothing has to be read back between iterations.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(h->stream, &cap);
-    const bool graphs = !per_iter && !h->profiling && n_iters >= 2 && cap == cudaStreamCaptureStatusNone;
     int64_t k = 0;
+    if (!per_iter && h->flow_on) {
+        // iterations that train the map are not graph-replayable (host loop of
+        // epochs, Adam step counts): run them one by one
+        while (k < n_iters && h->iters_done + 1 < h->cfg[0].n_warmup && h->flow_cfg.train_every > 0 &&
+               h->flow_cfg.epochs > 0) {
+            smc_status st = smc_step(h, nullptr);
+            if (st != SMC_OK) return st;
+            ++k;
+        }
+    }
+    const bool graphs = !per_iter && !h->profiling && n_iters - k >= 2 && cap == cudaStreamCaptureStatusNone;
     if (graphs) {
         if (h->cur != 0) {   // align to the captured buffer parity
             smc_status st = smc_step(h, nullptr);
             if (st != SMC_OK) return st;
             ++k;
+        }
+        if (h->graph2 && h->graph_flow != h->flow_on) {   // captured before the map was enabled
+            cudaGraphExecDestroy(h->graph2);
+            h->graph2 = nullptr;
         }
         if (!h->graph_stream) {
             cudaError_t e = cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking);
@@ -687,6 +741,8 @@ smc_status smc_get_buffer(const smc_handle* hc, int32_t which, void* dst, int64_
         case SMC_BUF_DH: srcp = h->dH; avail = h->N * 8; break;
         case SMC_BUF_ALPHA: srcp = h->alpha; avail = h->N * 8; break;
         case SMC_BUF_THETA_PREV: srcp = h->theta[1 - h->cur]; avail = nd * 4; break;
+        case SMC_BUF_Z0: srcp = h->z0; avail = h->flow_on ? nd * 4 : 0; break;
+        case SMC_BUF_Z1: srcp = h->z1; avail = h->flow_on ? nd * 4 : 0; break;
         case SMC_BUF_RUNSTATE: {
             std::vector<RunState> st((size_t)h->n_runs);
             cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,
@@ -766,6 +822,14 @@ smc_status smc_reset(smc_handle* h, uint64_t seed) {
                                     cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_rstate, st.data(), sizeof(RunState) * (size_t)h->n_runs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h->flow_on) {
+        e = cudaMemcpyAsync(h->flow.params, h->flow_init.data(), sizeof(float) * h->flow_init.size(),
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->flow.adam_m, 0, sizeof(float) * h->flow_init.size(), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->flow.adam_v, 0, sizeof(float) * h->flow_init.size(), s);
+        if (e == cudaSuccess) e = flow_refresh(h->flow, s);
+        h->flow_t = 0;
+    }
     // the staging vectors are pageable: the copies have consumed them on return
     if (e == cudaSuccess) e = initial_draw(h);
     if (e != cudaSuccess) return cuda_fail(h, e, "smc_reset");
@@ -940,6 +1004,147 @@ smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
     if (N < 1 || N > (1ll << 30) || !W || !q || !ancestors || !status_out || !scratch) return SMC_E_INVAL;
     return kstatus(launch_resample_flat(W, N, r64, reinterpret_cast<unsigned long long*>(q), ancestors, status_out,
                                         scratch, static_cast<cudaStream_t>(stream)));
+}
+
+// ------------------------------------------------------------------ transport map
+int64_t smc_flow_num_params(int64_t dim, int32_t hidden, int32_t layers) {
+    if (dim < 2 || hidden < 1 || layers < 1) return 0;
+    return flow_num_params(dim, hidden, layers);
+}
+
+smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const double* params) {
+    if (!h || !fc || !params) return SMC_E_INVAL;
+    if (h->sticky) return SMC_E_STATE;
+    auto reject = [&](const char* why) { return fail(h, SMC_E_INVAL, std::string("smc_flow_enable: ") + why); };
+    if (h->flow_on) return reject("already enabled");
+    if (h->iters_done != 0) return reject("must be called before the first iteration");
+    if (h->n_runs != 1) return reject("single-run handles only");
+    if (h->precision != SMC_PREC_FP32) return reject("precision must be SMC_PREC_FP32");
+    if (!flow_supported(h->model.m, fc->hidden, fc->layers))
+        return reject("needs a GAUSS_DENSE or BANANA model with even dim <= 128, hidden a multiple of 4 "
+                      "in [4, 128] and layers in [1, 8]");
+    if (fc->train_every < 0 || fc->epochs < 0 || !(fc->lr > 0.0) || !std::isfinite(fc->lr))
+        return reject("train_every and epochs must be >= 0 and lr > 0");
+    DevFlow f = flow_shape((int)h->D, fc->hidden, fc->layers);
+    std::vector<float> p32((size_t)f.n_params);
+    for (int64_t i = 0; i < f.n_params; ++i) {
+        if (!std::isfinite(params[i])) return reject("non-finite parameter");
+        p32[(size_t)i] = (float)params[i];
+    }
+    DevAlloc& A = h->mem;
+    f.params = A.get<float>((size_t)f.n_params);
+    f.adam_m = A.get<float>((size_t)f.n_params);
+    f.adam_v = A.get<float>((size_t)f.n_params);
+    f.grad = A.get<float>((size_t)f.n_params);
+    f.work = A.get<float>((size_t)(f.L * f.layer_work));
+    float* partials = A.get<float>((size_t)flow_partials_floats(f, h->N));
+    float* z0 = A.get<float>((size_t)(h->D * h->ld));
+    float* z1 = A.get<float>((size_t)(h->D * h->ld));
+    if (A.err != cudaSuccess) {
+        cudaError_t e = A.err;
+        A.err = cudaSuccess;
+        return cuda_fail(h, e, "smc_flow_enable allocation");
+    }
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaMemcpyAsync(f.params, p32.data(), sizeof(float) * p32.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f.adam_m, 0, sizeof(float) * p32.size(), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f.adam_v, 0, sizeof(float) * p32.size(), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(z0, 0, sizeof(float) * (size_t)(h->D * h->ld), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(z1, 0, sizeof(float) * (size_t)(h->D * h->ld), s);
+    if (e == cudaSuccess) e = flow_refresh(f, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // p32 is pageable
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_flow_enable");
+    h->flow = f;
+    h->flow_cfg = *fc;
+    h->flow_init = std::move(p32);
+    h->flow_partials = partials;
+    h->z0 = z0;
+    h->z1 = z1;
+    h->flow_t = 0;
+    h->flow_on = true;
+    return SMC_OK;
+}
+
+smc_status smc_flow_get_params(const smc_handle* hc, double* params, int64_t n) {
+    smc_handle* h = const_cast<smc_handle*>(hc);
+    if (!h || !params) return SMC_E_INVAL;
+    if (!h->flow_on || n != h->flow.n_params) return SMC_E_INVAL;
+    std::vector<float> p32((size_t)n);
+    cudaError_t e = cudaMemcpyAsync(p32.data(), h->flow.params, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smc_flow_get_params");
+    for (int64_t i = 0; i < n; ++i) params[i] = p32[(size_t)i];
+    return SMC_OK;
+}
+
+// Stand-alone flow of the given shape over caller-owned device parameters:
+// stream-ordered work copies (and partials) that the caller frees with release().
+namespace {
+struct TmpFlow {
+    DevFlow f{};
+    DevAlloc mem;
+    bool make(int64_t D, int32_t H, int32_t L, const float* params, int64_t n_partial_rows, cudaStream_t s) {
+        mem.s = s;
+        f = flow_shape((int)D, H, L);
+        f.params = const_cast<float*>(params);
+        f.work = mem.get<float>((size_t)(f.L * f.layer_work));
+        partials = n_partial_rows > 0 ? mem.get<float>((size_t)flow_partials_floats(f, n_partial_rows)) : nullptr;
+        return mem.err == cudaSuccess;
+    }
+    float* partials = nullptr;
+};
+}  // namespace
+
+smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, const float* params,
+                                const float* theta, const double* W, int64_t N, int64_t ld, float* grad,
+                                void* stream) {
+    if (!flow_shape_ok(dim, hidden, layers) || !params || !grad || N < 0 || ld < N) return SMC_E_INVAL;
+    if (N > 0 && (!theta || !W)) return SMC_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TmpFlow t;
+    if (!t.make(dim, hidden, layers, params, std::max<int64_t>(N, 1), s)) {
+        t.mem.release();
+        return SMC_E_NOMEM;
+    }
+    t.f.grad = grad;
+    cudaError_t e = flow_refresh(t.f, s);
+    if (e == cudaSuccess && N == 0) e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)t.f.n_params, s);
+    if (e == cudaSuccess && N > 0) e = flow_loss_grad(t.f, theta, ld, nullptr, W, nullptr, nullptr, N, t.partials, s);
+    t.mem.release();
+    return kstatus(e);
+}
+
+smc_status smc_k_flow_leapfrog(const smc_dev_model* m, int32_t hidden, int32_t layers, const float* params,
+                               float* theta, float* p, float* grad, double* logpi, const int32_t* steps, double eps,
+                               int64_t N, int64_t ld, float* z0, float* z1, double* dH, void* stream) {
+    if (!m || !params || N < 0 || ld < N || !(eps > 0.0)) return SMC_E_INVAL;
+    if (N > 0 && (!theta || !p || !grad || !logpi || !steps)) return SMC_E_INVAL;
+    if (!flow_supported(m->m, hidden, layers)) return SMC_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TmpFlow t;
+    if (!t.make(m->m.D, hidden, layers, params, 0, s)) {
+        t.mem.release();
+        return SMC_E_NOMEM;
+    }
+    TrajArgs a{};
+    a.theta_in = theta;
+    a.grad_in = grad;
+    a.logpi_in = logpi;
+    a.theta_out = theta;
+    a.grad_out = grad;
+    a.logpi_out = logpi;
+    a.p_in = p;
+    a.p_out = p;
+    a.dH = dH;
+    a.steps = steps;
+    a.eps_fixed = eps;
+    a.N = N;
+    a.ld = ld;
+    cudaError_t e = flow_refresh(t.f, s);
+    if (e == cudaSuccess) e = launch_traj_flow(m->m, t.f, a, z0, z1, s);
+    t.mem.release();
+    return kstatus(e);
 }
 
 }  // extern "C"

@@ -387,8 +387,9 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
         const int D = (int)b.D, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         const int64_t src = x.valid ? b.src[x.j] : 0;
         for (int d = 0; d < D; ++d) {
-            double v0 = x.valid ? (double)b.theta_prev[(int64_t)d * b.ld + src] : 0.0;
-            double v1 = x.valid ? (double)b.theta_new[(int64_t)d * b.ld + x.j] : 0.0;
+            const int64_t o = (int64_t)d * b.ld;
+            double v0 = x.valid ? (double)(b.chees0 ? b.chees0[o + x.j] : b.theta_prev[o + src]) : 0.0;
+            double v1 = x.valid ? (double)(b.chees1 ? b.chees1[o + x.j] : b.theta_new[o + x.j]) : 0.0;
             v0 = warp_sum(v0);
             v1 = warp_sum(v1);
             if (lane == 0) {
@@ -433,8 +434,9 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             const int64_t src = b.src[x.j];
             double sq0 = 0.0, sq1 = 0.0, proj = 0.0;
             for (int d = 0; d < D; ++d) {
-                const double e0 = (double)b.theta_prev[(int64_t)d * b.ld + src] - mean_s[d];
-                const double e1 = (double)b.theta_new[(int64_t)d * b.ld + x.j] - mean_s[D + d];
+                const int64_t o = (int64_t)d * b.ld;
+                const double e0 = (double)(b.chees0 ? b.chees0[o + x.j] : b.theta_prev[o + src]) - mean_s[d];
+                const double e1 = (double)(b.chees1 ? b.chees1[o + x.j] : b.theta_new[o + x.j]) - mean_s[D + d];
                 sq0 += e0 * e0;
                 sq1 += e1 * e1;
                 proj += e1 * (double)b.p_final[(int64_t)d * b.ld + x.j];

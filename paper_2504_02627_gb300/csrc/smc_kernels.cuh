@@ -65,6 +65,10 @@ struct StepBufs {
     const float* p_final;
     const double* dH;
     const double* alpha;
+    // latent start / end points [D x ld] of the preconditioned move (indexed
+    // by particle); when set, the ChEES statistics use them instead of theta
+    const float* chees0;
+    const float* chees1;
 };
 
 // One iteration = weights_steps, resample_scan, sort, trajectory kernel,

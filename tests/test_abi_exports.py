@@ -53,3 +53,11 @@ def test_invalid_config_is_rejected_without_gpu_work():
     cfg = g.make_config(16, 2, 1, 0.1)
     assert lib.smc_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.byref(m.struct), None) == -1
     assert lib.smc_init(None, ctypes.byref(cfg), ctypes.byref(m.struct), None) == -1
+
+
+def test_flow_parameter_count_matches_the_oracle_layout():
+    import oracle
+    lib = g.lib()
+    for D, H, L in [(4, 8, 2), (10, 32, 4), (50, 128, 4), (100, 128, 4)]:
+        assert lib.smc_flow_num_params(D, H, L) == oracle.num_flow_params(D, H, L)
+    assert lib.smc_flow_num_params(1, 8, 2) == 0

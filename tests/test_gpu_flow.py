@@ -1,0 +1,378 @@
+"""GPU parity of the learned preconditioner (affine-coupling transport map)
+against the FP64 oracle, through the C-ABI:
+
+* the training-loss gradient of every parameter (smc_k_flow_loss_grad);
+* latent-space trajectories: z0 = T^-1(theta), leapfrog on log pi_z,
+  theta' = T(z'), final momenta and the energy error in z
+  (smc_k_flow_leapfrog), on ragged step counts;
+* whole iterations with the map on (smc_flow_enable), stage by stage from the
+  GPU's own state: latent buffers, trajectories, reweighting and the ChEES
+  update computed in the latent space;
+* one training iteration: the parameters after `epochs` Adam steps;
+* the identity map (zero last layer) gives the plain sampler's results;
+* a trained map raises acceptance and ESS on an ill-conditioned Gaussian.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import dev, f32r, need_gpu, oracle_target, ptr, rounded_workload, stream, torch  # noqa: F401
+import oracle
+import paper_2504_02627_gb300 as g
+import workloads
+from paper_2504_02627_gb300 import _binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _params(D, H, L, seed, scale):
+    """He-initialised hidden layers plus a non-zero last layer of size `scale`
+    (a map away from the identity), rounded to FP32."""
+    rng = np.random.default_rng(seed)
+    p = workloads.flow_init(D, H, L, seed=seed)
+    Dh = D // 2
+    lsz = H * Dh + H + H * H + H + D * H + D
+    for l in range(L):
+        o = l * lsz + H * Dh + H + H * H + H
+        p[o:o + D * H + D] = scale * rng.standard_normal(D * H + D) / np.sqrt(H)
+    return f32r(p)
+
+
+def _targets():
+    ban = workloads.banana50()
+    ban["eps"] = 0.02
+    g10 = workloads.gauss10()
+    g10["eps"] = 0.05
+    g100 = workloads.gauss100_cond()
+    g100["eps"] = 0.002
+    return {"banana50": ban, "gauss10": g10, "gauss100": g100}
+
+
+@pytest.mark.parametrize("D,H,L", [(10, 32, 4), (50, 128, 4), (100, 128, 4), (4, 8, 2)])
+def test_loss_gradient_matches_oracle(D, H, L):
+    N = 300                                              # 9 full CTAs and a ragged one
+    rng = np.random.default_rng(D + H)
+    p = _params(D, H, L, seed=D, scale=0.3)
+    th = f32r(rng.standard_normal((N, D)) * 1.3)
+    W = rng.uniform(0.0, 1.0, N)
+    W /= W.sum()
+    _, g_o = oracle.flow_loss_grad(oracle.FlowSpec(D, H, L, p), th, W)
+    ld = 320
+    th_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    th_d[:, :N] = dev(th.T, torch.float32)
+    grad = torch.empty(p.size, dtype=torch.float32, device="cuda")
+    p_d, W_d = dev(p, torch.float32), dev(W)          # kept alive across the asynchronous calls
+    st = B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad), stream())
+    assert st == 0
+    torch.cuda.synchronize()
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    # per parameter block: FP32 sums over 300 particles through L layers
+    Dh = D // 2
+    sizes = [H * Dh, H, H * H, H, D * H, D]
+    o = 0
+    for l in range(L):
+        for sz in sizes:
+            go, gg = g_o[o:o + sz], g_gpu[o:o + sz]
+            rms = np.sqrt(np.mean(go**2)) + 1e-12
+            err = np.abs(gg - go) / (np.abs(go) + rms)
+            assert err.max() < 2e-4, (l, sz, err.max())
+            o += sz
+    # identical inputs give identical bits (fixed-order reduction)
+    grad2 = torch.empty_like(grad)
+    assert B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad2), stream()) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(grad, grad2)
+
+
+def oracle_flow_move(f, t, theta, p0, eps, S):
+    """Algorithm 1 on log pi_z from z0 = T^-1(theta) with momenta p0 and S_j
+    steps, through the oracle's flow_logpi_z; returns theta' = T(z'), p',
+    z0, z', log pi(theta'), Delta H in z, grad log pi(theta')."""
+    z0, ldi = oracle.flow_inverse(f, theta)
+    lpz, gz, x, gx, lpx = oracle.flow_logpi_z(f, t, z0)
+    H0 = 0.5 * (p0**2).sum(1) - lpz
+    z, p = z0.copy(), p0.copy()
+    for s in range(int(S.max())):
+        a = S > s
+        p[a] += 0.5 * eps * gz[a]
+        z[a] += eps * p[a]
+        lpz_a, gz_a, x_a, gx_a, lpx_a = oracle.flow_logpi_z(f, t, z[a])
+        lpz[a], gz[a], x[a], gx[a], lpx[a] = lpz_a, gz_a, x_a, gx_a, lpx_a
+        p[a] += 0.5 * eps * gz[a]
+    dH = 0.5 * (p**2).sum(1) - lpz - H0
+    return x, p, z0, z, lpx, dH, gx
+
+
+def _assert_close(a, b, S, what, rel=2e-5):
+    scale = np.sqrt(np.mean(b**2)) + 1e-3
+    tol = rel * S[:, None] * (np.abs(b) + scale)
+    r = np.abs(a - b) / tol
+    i, d = np.unravel_index(np.argmax(r), r.shape)
+    assert r.max() <= 1.0, (what, r.max(), "particle", i, "dim", d, a[i, d], b[i, d], "steps", S[i],
+                            "particles over", int((r.max(1) > 1).sum()))
+
+
+@pytest.mark.parametrize("name", ["banana50", "gauss10", "gauss100"])
+def test_latent_leapfrog_matches_oracle(name):
+    w = rounded_workload(_targets()[name])
+    D, eps = w["D"], w["eps"]
+    t = oracle_target(w)
+    H, L = (32, 4) if D <= 10 else (128, 4)
+    p = _params(D, H, L, seed=7, scale=0.1)
+    f = oracle.FlowSpec(D, H, L, p)
+    N = 77                                               # 2 full CTAs and a ragged one
+    rng = np.random.default_rng(3)
+    Sigma = w.get("Sigma")
+    if Sigma is not None:
+        th = f32r(rng.standard_normal((N, D)) @ np.linalg.cholesky(Sigma).T)
+    else:
+        xo = rng.standard_normal((N, D // 2)) * np.sqrt(w["a"])
+        xe = rng.standard_normal((N, D // 2)) + w["b"] * (xo**2 - w["a"])
+        th = f32r(np.stack([xo, xe], axis=2).reshape(N, D))
+    p0 = f32r(rng.standard_normal((N, D)))
+    S = rng.integers(1, 9, N).astype(np.int32)
+    lp, gr = oracle.logpi(t, th)
+    x_o, p_o, z0_o, z1_o, lpx_o, dH_o, gx_o = oracle_flow_move(f, t, th, p0, eps, S)
+
+    m = g.DevModel(g.ModelData.from_workload(w), stream())
+    ld = 96
+    def buf(a):
+        out = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+        out[:, :N] = dev(a.T, torch.float32)
+        return out
+    th_d, p_d, gr_d = buf(th), buf(p0), buf(f32r(gr))
+    lp_d = dev(lp)
+    z0_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    z1_d = torch.zeros_like(z0_d)
+    dH_d = torch.zeros(N, dtype=torch.float64, device="cuda")
+    par_d, S_d = dev(p, torch.float32), dev(S)       # kept alive across the asynchronous call
+    st = B.lib().smc_k_flow_leapfrog(m.h, H, L, ptr(par_d), ptr(th_d), ptr(p_d), ptr(gr_d), ptr(lp_d), ptr(S_d),
+                                     eps, N, ld, ptr(z0_d), ptr(z1_d), ptr(dH_d), stream())
+    assert st == 0
+    torch.cuda.synchronize()
+    host = lambda a: a[:, :N].cpu().numpy().T.astype(np.float64)
+    one = np.ones(N)
+    _assert_close(host(z0_d), z0_o, one, "z0")
+    _assert_close(host(z1_d), z1_o, S, "z'")
+    _assert_close(host(p_d), p_o, S, "p'")
+    _assert_close(host(th_d), x_o, S, "theta'")
+    _assert_close(host(gr_d), gx_o, S, "grad'")
+    lp1 = lp_d.cpu().numpy()
+    assert np.all(np.abs(lp1 - lpx_o) <= 2e-5 * S * (np.abs(lpx_o) + 1.0))
+    dH = dH_d.cpu().numpy()
+    dh_tol = 2e-5 * S * (np.abs(lpx_o) + 0.5 * (p_o**2).sum(1) + 1.0)
+    assert np.all(np.abs(dH - dH_o) <= dh_tol), np.max(np.abs(dH - dH_o) / dh_tol)
+    m.close()
+
+
+def _flow_case(name):
+    if name == "banana50":
+        w = workloads.banana50()
+        w["run"] = dict(n_particles=400, n_iters=5, n_warmup=3, step_size=0.02, traj_len0=0.2,
+                        max_steps=20, init_scale=1.0)
+        return w, (128, 4)
+    w = workloads.gauss10()
+    w["run"] = dict(n_particles=300, n_iters=6, n_warmup=4, step_size=0.05, traj_len0=0.3,
+                    max_steps=20, init_scale=2.0)
+    return w, (32, 4)
+
+
+@pytest.mark.parametrize("name", ["gauss10", "banana50"])
+def test_flow_iterations_match_oracle_stage_by_stage(name):
+    w, (H, L) = _flow_case(name)
+    w = rounded_workload(w)
+    run = w["run"]
+    t = oracle_target(w)
+    D, N, K, eps = w["D"], run["n_particles"], run["n_iters"], run["step_size"]
+    params = _params(D, H, L, seed=11, scale=0.1)
+    f = oracle.FlowSpec(D, H, L, params)
+    seed = 77
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, **run), stream())
+    smp.enable_flow(params, H, L, train_every=0, epochs=0)
+    ocfg = oracle.SMCConfig(seed=seed, n_particles=N, n_iters=K, n_warmup=run["n_warmup"], step_size=eps,
+                            traj_len0=run["traj_len0"], max_steps=run["max_steps"], init_scale=run["init_scale"])
+    for k in range(1, K + 1):
+        pre = {"theta": smp.buffer(B.BUF_THETA).T.astype(np.float64), "logw": smp.buffer(B.BUF_LOGW),
+               "rs": smp.runstate()[0]}
+        st = smp.step()[0]
+        lse, ess, W_o = oracle.normalise(pre["logw"])
+        W = smp.buffer(B.BUF_W)
+        np.testing.assert_allclose(W, W_o, rtol=1e-12, atol=1e-300)
+        if st["resampled"]:
+            _, q = oracle.quantise(W)
+            _, src = oracle.systematic(q, oracle.resample_r64(seed, k))
+            np.testing.assert_array_equal(smp.buffer(B.BUF_ANCESTORS), src)
+        else:
+            src = np.arange(N)
+        th_start = pre["theta"][src]
+        L_k = smp.runstate()[0]["L_last"]
+        h = np.array([oracle.halton2(j * K + k) for j in range(N)])
+        S = np.array([oracle.step_count(x, L_k, eps, run["max_steps"]) for x in h], dtype=np.int32)
+        np.testing.assert_array_equal(smp.buffer(B.BUF_STEPS), S)
+        p0 = f32r(np.stack([oracle.normals(seed, oracle.TAG_MOM, k, j, D) for j in range(N)]))
+        x_o, p_o, z0_o, z1_o, lpx_o, dH_o, _ = oracle_flow_move(f, t, th_start, p0, eps, S)
+        dH = smp.buffer(B.BUF_DH)
+        div = ~(np.abs(dH_o) < 50.0)
+        assert np.all(~(np.abs(dH[div]) < 30.0)), k
+        ok = ~div
+        assert ok.mean() > 0.5, (k, ok.mean())
+        _assert_close(smp.buffer(B.BUF_Z0).T[ok].astype(np.float64), z0_o[ok], np.ones(ok.sum()), "z0")
+        _assert_close(smp.buffer(B.BUF_Z1).T[ok].astype(np.float64), z1_o[ok], S[ok], "z'")
+        _assert_close(smp.buffer(B.BUF_P_FINAL).T[ok].astype(np.float64), p_o[ok], S[ok], "p'")
+        _assert_close(smp.buffer(B.BUF_THETA).T[ok].astype(np.float64), x_o[ok], S[ok], "theta'")
+        dh_tol = 2e-5 * S * (np.abs(lpx_o) + 0.5 * (p_o**2).sum(1) + 1.0)
+        assert np.all((np.abs(dH - dH_o) <= dh_tol)[ok]), k
+        alpha = smp.buffer(B.BUF_ALPHA)
+        base = np.full(N, -np.log(N)) if st["resampled"] else pre["logw"]
+        np.testing.assert_allclose(smp.buffer(B.BUF_LOGW), base - dH, rtol=1e-14, atol=1e-12)
+        # ChEES in the latent space, from the GPU's latent buffers
+        rs = smp.runstate()[0]
+        ch = oracle.CheesState(pre["rs"]["log_L"], pre["rs"]["adam_m"], pre["rs"]["adam_v"],
+                               int(pre["rs"]["adam_t"]), pre["rs"]["Lbar"])
+        if k < run["n_warmup"]:
+            z0 = smp.buffer(B.BUF_Z0).T.astype(np.float64)
+            z1 = smp.buffer(B.BUF_Z1).T.astype(np.float64)
+            p1 = smp.buffer(B.BUF_P_FINAL).T.astype(np.float64)
+            ghat, _ = oracle.chees_gradient(z0, z1, p1, h * L_k, alpha)
+            if ghat is not None:
+                oracle.chees_adam(ch, ghat, ocfg.adam_lr, ocfg.adam_b1, ocfg.adam_b2, ocfg.adam_eps, eps,
+                                  run["max_steps"])
+            ch.Lbar = 0.9 * ch.Lbar + 0.1 * np.exp(ch.log_L)
+        if k == run["n_warmup"] and ch.Lbar > 0:
+            ch.log_L = np.log(ch.Lbar)
+        assert abs(rs["log_L"] - ch.log_L) <= 1e-9 * max(1.0, abs(ch.log_L)), (k, rs["log_L"], ch.log_L)
+    smp.close()
+
+
+def _train_case(p_init, E, lr, seed=9):
+    """GPU iteration 1 with training on; returns the GPU parameters after it
+    and the oracle's parameters after E Adam steps on the same particles."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(n_particles=512, n_iters=6, n_warmup=4, step_size=0.05, traj_len0=0.3, max_steps=20,
+               init_scale=2.0)
+    D, H, L = 10, 32, 4
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, **run), stream())
+    smp.enable_flow(p_init, H, L, train_every=1, epochs=E, lr=lr)
+    th0 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+    logw0 = smp.buffer(B.BUF_LOGW)
+    st = smp.step()[0]
+    _, _, W = oracle.normalise(logw0)
+    if st["resampled"]:
+        _, q = oracle.quantise(smp.buffer(B.BUF_W))
+        _, src = oracle.systematic(q, oracle.resample_r64(seed, 1))
+        th, Wt = th0[src], np.full(run["n_particles"], 1.0 / run["n_particles"])
+    else:
+        th, Wt = th0, W
+    fs = oracle.new_flow_state(p_init, H, L)
+    for e in range(1, E + 1):
+        _, gr = oracle.flow_loss_grad(oracle.FlowSpec(D, H, L, fs["params"]), th, Wt)
+        oracle.flow_adam(fs["params"], gr, fs["m"], fs["v"], e, lr)
+    p_gpu = smp.flow_params()
+    smp.close()
+    return p_gpu, fs["params"]
+
+
+def test_training_from_the_identity_map_matches_oracle():
+    """From a zero last layer one Adam step moves only W3 and b3 (every other
+    gradient is exactly zero), each by lr * sign(gradient) up to Adam's eps;
+    a gradient below the FP32 noise may take the other sign."""
+    D, H, L, lr = 10, 32, 4, 1e-3
+    p_init = f32r(workloads.flow_init(D, H, L, seed=5))
+    p_gpu, p_o = _train_case(p_init, 1, lr)
+    Dh = D // 2
+    lsz = H * Dh + H + H * H + H + D * H + D
+    for l in range(L):
+        o = l * lsz
+        hid = slice(o, o + H * Dh + 2 * H + H * H)
+        np.testing.assert_array_equal(p_gpu[hid], p_init[hid])
+        last = slice(o + H * Dh + 2 * H + H * H, o + lsz)
+        d = np.abs(p_gpu[last] - p_o[last])
+        assert np.all(d <= 2 * lr + 1e-7)
+        assert np.mean(d <= 1e-3 * lr) > 0.99, np.mean(d <= 1e-3 * lr)
+
+
+def test_training_epochs_match_oracle_adam():
+    """Several Adam steps from a non-identity map.  Adam moves a parameter by
+    about lr * sign(gradient) early on, so one whose gradient is below the
+    FP32 noise may move the other way; what is unique is compared: almost
+    every parameter agrees closely, none is further than 2 * epochs * lr."""
+    D, H, L, E, lr = 10, 32, 4, 3, 1e-3
+    p_init = _params(D, H, L, seed=12, scale=0.3)
+    p_gpu, p_o = _train_case(p_init, E, lr)
+    d = np.abs(p_gpu - p_o)
+    assert np.all(d <= 2 * E * lr + 1e-6)
+    close = d <= 1e-2 * lr * E + 1e-7
+    assert np.mean(close) > 0.995, np.mean(close)
+
+
+def test_identity_map_gives_the_plain_sampler():
+    """With a zero last layer and no training, T is the identity (s = 0,
+    t = 0 exactly), so the preconditioned sampler must reproduce the plain
+    one: identical decisions and step counts, trajectories within FP32."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(n_particles=256, n_iters=8, n_warmup=4, step_size=0.05, traj_len0=0.3, max_steps=20,
+               init_scale=2.0)
+    plain = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=5, **run), stream())
+    flow = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=5, **run), stream())
+    flow.enable_flow(f32r(workloads.flow_init(10, 32, 4)), 32, 4, train_every=0, epochs=0)
+    for k in range(run["n_iters"]):
+        sp, sf = plain.step()[0], flow.step()[0]
+        assert sp["resampled"] == sf["resampled"]
+        np.testing.assert_array_equal(plain.buffer(B.BUF_STEPS), flow.buffer(B.BUF_STEPS))
+        np.testing.assert_allclose(flow.buffer(B.BUF_THETA), plain.buffer(B.BUF_THETA), rtol=2e-4, atol=2e-4)
+        np.testing.assert_allclose(flow.buffer(B.BUF_DH), plain.buffer(B.BUF_DH), rtol=1e-3, atol=2e-4)
+        src = flow.buffer(B.BUF_ANCESTORS) if sf["resampled"] else np.arange(run["n_particles"])
+        np.testing.assert_array_equal(flow.buffer(B.BUF_Z0), flow.buffer(B.BUF_THETA_PREV)[:, src])
+    plain.close()
+    flow.close()
+
+
+def test_trained_map_raises_acceptance_and_ess():
+    """Ill-conditioned 4-d Gaussian (variances 0.01 .. 4) at a step size the
+    stiff direction barely tolerates (the oracle's pin of the same claim):
+    training the map on the particles whitens the target."""
+    tgt = workloads._gauss_from_spectrum(np.array([0.01, 0.1, 1.0, 4.0]), 11)
+    w = rounded_workload(tgt)
+    run = dict(n_particles=512, n_iters=16, n_warmup=12, step_size=0.18, traj_len0=1.0, max_steps=500,
+               init_scale=1.0, adapt=0)
+    md = g.ModelData.from_workload(w)
+    plain = g.Sampler(md, g.make_config(seed=21, **run), stream())
+    flow = g.Sampler(md, g.make_config(seed=21, **run), stream())
+    flow.enable_flow(f32r(workloads.flow_init(4, 32, 4, seed=5)), 32, 4, train_every=1, epochs=60, lr=3e-3)
+    sp = [plain.step()[0] for _ in range(run["n_iters"])]
+    sf = []
+    for k in range(run["n_iters"]):
+        try:
+            sf.append(flow.step()[0])
+        except RuntimeError as e:
+            p = flow.flow_params()
+            raise AssertionError((k, str(e), "finite params", bool(np.isfinite(p).all()),
+                                  [(x["ess"], x["mean_alpha"]) for x in sf])) from e
+    last = lambda s, key: np.mean([x[key] for x in s[-4:]])
+    assert last(sf, "mean_alpha") > last(sp, "mean_alpha") + 0.1, (last(sf, "mean_alpha"), last(sp, "mean_alpha"))
+    assert last(sf, "ess") > 1.3 * last(sp, "ess"), (last(sf, "ess"), last(sp, "ess"))
+    plain.close()
+    flow.close()
+
+
+def test_flow_rejects_unsupported_configurations():
+    w = rounded_workload(workloads.logistic(n=100, d_features=5))
+    w["run"] = dict(n_particles=64, n_iters=4, n_warmup=2, step_size=0.01, traj_len0=0.1, max_steps=10,
+                    init_scale=1.0)
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=1, **w["run"]), stream())
+    with pytest.raises(RuntimeError):
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(6, 32, 4)), 32, 4)
+    smp.close()
+    w = rounded_workload(workloads.gauss10())
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=1, n_particles=64, n_iters=4, n_warmup=2,
+                                                                step_size=0.05), stream())
+    with pytest.raises(RuntimeError):
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 30, 4)), 30, 4)     # H not a multiple of 4
+    smp.step()
+    with pytest.raises(RuntimeError):                                                  # after the first iteration
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4)
+    smp.close()
