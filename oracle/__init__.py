@@ -61,7 +61,7 @@ class Config(C.Structure):
                 ("chees_initial_p", C.c_int32), ("adam_lr", C.c_double),
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
-                ("flow_lr", C.c_double)]
+                ("flow_lr", C.c_double), ("flow_min_ess", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -345,13 +345,14 @@ class SMCConfig:
     flow_train_every: int = 2
     flow_epochs: int = 10
     flow_lr: float = 1e-3
+    flow_min_ess: float = 0.25
 
     def struct(self):
         return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
                       self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
                       self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
                       self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
-                      self.flow_train_every, self.flow_epochs, self.flow_lr)
+                      self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess)
 
 
 def stats_to_dicts(arr):

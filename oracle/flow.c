@@ -196,6 +196,9 @@ double oracle_flow_loss_grad(const oracle_flow* f, const double* theta, const do
     double *co = o + D, *ch2 = co + D, *ch1 = ch2 + H;
     double loss = 0.0;
     for (int64_t j = 0; j < N; ++j) {
+        /* a particle of zero weight adds nothing to the weighted loss; its
+         * position may be non-finite (the end of a divergent trajectory) */
+        if (W[j] == 0.0) continue;
         memcpy(z, theta + j * D, (size_t)D * sizeof(double));
         double ssum = 0.0;
         /* inverse pass, layer L-1 first; ul[l] = input of inverse layer l */

@@ -163,6 +163,7 @@ typedef struct {
     int32_t flow_train_every; /* train the flow at warm-up iterations k with (k-1) % every == 0 */
     int32_t flow_epochs;    /* full-batch Adam steps per training event      */
     double flow_lr;
+    double flow_min_ess;    /* train only when the tested J_eff >= flow_min_ess * J */
 } oracle_config;
 
 typedef struct {

@@ -109,10 +109,14 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     }
 
     /* learned preconditioner: trained on the current weighted particles at
-     * warm-up iterations (k - 1) % every == 0, frozen afterwards */
+     * warm-up iterations (k - 1) % every == 0 whose tested J_eff is at least
+     * flow_min_ess * J (a near-degenerate weighted set holds a few distinct
+     * points, and fitting a density to them collapses the map), frozen
+     * afterwards */
     oracle_flow flow = {D, io->flow_H, io->flow_L, io->flow_params};
     const int use_flow = io->flow_params != 0;
-    if (use_flow && k < c->n_warmup && c->flow_train_every > 0 && (k - 1) % c->flow_train_every == 0) {
+    if (use_flow && k < c->n_warmup && c->flow_train_every > 0 && (k - 1) % c->flow_train_every == 0 &&
+        ess >= c->flow_min_ess * (double)N) {
         const int64_t np = oracle_flow_num_params(D, io->flow_H, io->flow_L);
         double* gradp = (double*)malloc((size_t)np * sizeof(double));
         for (int32_t e = 0; e < c->flow_epochs; ++e) {

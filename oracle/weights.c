@@ -89,14 +89,17 @@ void oracle_multinomial(const uint64_t* q, int64_t N, const uint64_t* u64, int32
 void oracle_moments(const double* theta, const double* logw, int64_t N, int64_t D,
                     double* mean, double* var) {
     /* Realised estimates sum_j W_j f(theta_j) (Sec. 3) for f = theta and
-     * f = (theta - mean)^2. */
+     * f = (theta - mean)^2.  A particle of zero weight is left out: its
+     * position may be non-finite (the end of a divergent trajectory). */
     double lse;
     oracle_normalise(logw, N, &lse, 0, 0);
     for (int64_t d = 0; d < D; ++d) {
         double m = 0.0;
-        for (int64_t j = 0; j < N; ++j) m += exp(logw[j] - lse) * theta[j * D + d];
+        for (int64_t j = 0; j < N; ++j)
+            if (logw[j] > -INFINITY) m += exp(logw[j] - lse) * theta[j * D + d];
         double v = 0.0;
         for (int64_t j = 0; j < N; ++j) {
+            if (!(logw[j] > -INFINITY)) continue;
             double e = theta[j * D + d] - m;
             v += exp(logw[j] - lse) * e * e;
         }

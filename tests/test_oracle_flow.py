@@ -127,3 +127,35 @@ def test_trained_flow_raises_acceptance_on_an_ill_conditioned_target():
     last = lambda r, key: np.mean([s[key] for s in r["stats"][-4:]])
     assert last(flow, "mean_alpha") > last(plain, "mean_alpha") + 0.1
     assert last(flow, "ess") > 1.3 * last(plain, "ess")
+
+
+def test_zero_weight_particles_are_left_out_of_training():
+    """A particle of zero weight (the end of a divergent trajectory, possibly
+    non-finite) changes neither the loss nor its gradient."""
+    f = _random_flow(13, scale=0.2)
+    rng = np.random.default_rng(14)
+    th = rng.standard_normal((6, D))
+    W = rng.uniform(0.1, 1.0, 6)
+    W /= W.sum()
+    loss, grad = oracle.flow_loss_grad(f, th, W)
+    th2 = np.vstack([th[:3], np.full((1, D), np.nan), th[3:]])
+    W2 = np.concatenate([W[:3], [0.0], W[3:]])
+    loss2, grad2 = oracle.flow_loss_grad(f, th2, W2)
+    assert loss2 == loss
+    np.testing.assert_array_equal(grad2, grad)
+
+
+def test_training_gate_on_the_tested_ess():
+    """With flow_min_ess = 1 no weighted set qualifies (J_eff < J whenever the
+    weights are uneven), so the map never trains and stays the identity."""
+    g = workloads.gauss10()
+    t = oracle.TargetSpec.gauss_dense(g["mu"], g["P"])
+    p0 = workloads.flow_init(10, 16, 4)
+    cfg = oracle.SMCConfig(n_particles=64, n_iters=4, n_warmup=3, step_size=0.1, traj_len0=1.0,
+                           init_scale=2.0, seed=3, flow_train_every=1, flow_epochs=5, flow_min_ess=1.0)
+    r = oracle.smc_run_flow(t, cfg, p0, 16, 4)
+    np.testing.assert_array_equal(r["flow"]["params"], p0)
+    assert r["flow"]["t"].value == 0
+    cfg.flow_min_ess = 0.0
+    r = oracle.smc_run_flow(t, cfg, p0, 16, 4)
+    assert r["flow"]["t"].value == 2 * 5          # k = 1, 2 train (k < M_warmup = 3)

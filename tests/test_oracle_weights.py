@@ -115,3 +115,17 @@ def test_moments_weighted():
     m, v = oracle.moments(th, lw)
     np.testing.assert_allclose(m, W @ th, rtol=1e-12)
     np.testing.assert_allclose(v, W @ (th - m) ** 2, rtol=1e-12)
+
+
+def test_moments_leave_out_zero_weight_particles():
+    """A particle of weight zero (possibly at a non-finite position after a
+    divergent trajectory) does not enter the estimates."""
+    rng = np.random.default_rng(2)
+    th = rng.standard_normal((50, 2))
+    lw = rng.standard_normal(50)
+    m, v = oracle.moments(th, lw)
+    th2 = np.vstack([th, [[np.nan, np.inf]]])
+    lw2 = np.concatenate([lw, [-np.inf]])
+    m2, v2 = oracle.moments(th2, lw2)
+    np.testing.assert_array_equal(m2, m)
+    np.testing.assert_array_equal(v2, v)
