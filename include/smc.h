@@ -242,12 +242,16 @@ void smc_destroy(smc_handle* h);
  * smc_flow_num_params values in all.  FP32 on the device.
  *
  * Training: at warm-up iterations k < M_warmup with (k - 1) % train_every ==
- * 0, after resampling and before the move, `epochs` Adam steps (beta1 0.9,
+ * 0 whose tested J_eff is at least min_ess_frac * J (a near-degenerate
+ * weighted set holds a few distinct points, and fitting a density to them
+ * collapses the map), after resampling and before the move, `epochs` Adam
+ * steps (beta1 0.9,
  * beta2 0.999, eps 1e-8, step lr) descend the weighted negative
  * log-likelihood of the particles under the flow density (without the
  * constant D/2 log 2 pi)
  *     sum_j W_j ( 1/2 |T^-1(theta_j)|^2 - log|det dT^-1/dtheta (theta_j)| ),
- * W_j = 1/J after resampling.  The map is frozen from k = M_warmup on.
+ * W_j = 1/J after resampling; particles of zero weight are left out.  The map
+ * is frozen from k = M_warmup on.
  */
 typedef struct {
     int32_t hidden;         /* H: multiple of 4 in [4, 128]                       */
@@ -255,6 +259,7 @@ typedef struct {
     int32_t train_every;    /* train at k - 1 = 0, train_every, ... (0: never)     */
     int32_t epochs;         /* Adam steps per training iteration (0: never train) */
     double lr;              /* Adam step size (> 0)                               */
+    double min_ess_frac;    /* train only when J_eff >= min_ess_frac * J, [0, 1]  */
 } smc_flow_config;
 
 /* Number of parameters of the flow (0 for an invalid shape). */

@@ -41,7 +41,7 @@ class SmcConfig(C.Structure):
 
 class SmcFlowConfig(C.Structure):
     _fields_ = [("hidden", C.c_int32), ("layers", C.c_int32), ("train_every", C.c_int32),
-                ("epochs", C.c_int32), ("lr", C.c_double)]
+                ("epochs", C.c_int32), ("lr", C.c_double), ("min_ess_frac", C.c_double)]
 
 
 class SmcStats(C.Structure):
@@ -277,13 +277,13 @@ class Sampler:
         return out
 
     def enable_flow(self, params, hidden: int, layers: int, train_every: int = 2, epochs: int = 10,
-                    lr: float = 1e-3):
+                    lr: float = 1e-3, min_ess_frac: float = 0.25):
         """smc_flow_enable: the affine-coupling transport map (FP64 host params)."""
         p = np.ascontiguousarray(params, dtype=np.float64)
         n = lib().smc_flow_num_params(self.dim, hidden, layers)
         if p.size != n:
             raise ValueError(f"flow needs {n} parameters, got {p.size}")
-        fc = SmcFlowConfig(hidden, layers, train_every, epochs, lr)
+        fc = SmcFlowConfig(hidden, layers, train_every, epochs, lr, min_ess_frac)
         check(lib().smc_flow_enable(self.h, C.byref(fc), _dp(p)), "smc_flow_enable", self.h)
         self.flow_shape = (hidden, layers)
 

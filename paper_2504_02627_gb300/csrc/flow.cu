@@ -29,9 +29,10 @@ size_t flow_smem_bytes(int D, int H, int L, int O4) {
 namespace {
 
 // -------------------------------------------------------------- work copies
-__global__ void k_flow_refresh(DevFlow f) {
+__global__ void k_flow_refresh(DevFlow f, bool bump, FlowGate gate) {
     const int64_t total = (int64_t)f.L * f.layer_work;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bump && i == 0 && gate.open()) *f.adam_t += 1;
     if (i >= total) return;
     const int l = (int)(i / f.layer_work);
     const int64_t e = i % f.layer_work;
@@ -506,8 +507,9 @@ __device__ __forceinline__ float rot_dot(const float* A, const float* B, int lan
 }
 
 __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* theta, int64_t ld,
-                                                      const int32_t* src, const double* W, const RunState* rstate,
-                                                      const RunParams* runs, int64_t N, float* partials) {
+                                                      const int32_t* src, const double* W, FlowGate gate, int64_t N,
+                                                      float* partials) {
+    if (!gate.open()) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FlowSmem s = flow_smem(smem_raw, f.D, f.H, f.L, f.O4);
     __shared__ float w_s[FG];
@@ -517,14 +519,17 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
         const int64_t j = slot0 + t;
         float wv = 0.0f;
         if (j < N) {
-            wv = (rstate && rstate->resample) ? (float)(1.0 / (double)runs->n) : (float)W[j];
+            wv = (gate.rs && gate.rs->resample) ? (float)(1.0 / (double)gate.rp->n) : (float)W[j];
         }
         w_s[t] = wv;
     }
+    __syncthreads();
+    // a particle of zero weight adds nothing; its position may be non-finite
+    // (the end of a divergent trajectory), so it enters as zeros
     for (int e = t; e < D * FG; e += FT) {
         const int d = e / FG, q = e % FG;
         const int64_t j = slot0 + q;
-        s.x[e] = j < N ? theta[(int64_t)d * ld + (src ? src[j] : j)] : 0.0f;
+        s.x[e] = (j < N && w_s[q] != 0.0f) ? theta[(int64_t)d * ld + (src ? src[j] : j)] : 0.0f;
     }
     __syncthreads();
     // inverse pass; zl[l] = input of inverse layer l
@@ -617,17 +622,19 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
 }
 
 // grad[i] = sum over CTAs of partials[c][i], in CTA order.
-__global__ void k_flow_reduce(const float* partials, int64_t n_blocks, int64_t n_params, float* grad) {
+__global__ void k_flow_reduce(const float* partials, int64_t n_blocks, int64_t n_params, float* grad,
+                              FlowGate gate) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_params) return;
+    if (i >= n_params || !gate.open()) return;
     float acc = 0.0f;
     for (int64_t c = 0; c < n_blocks; ++c) acc += partials[c * n_params + i];
     grad[i] = acc;
 }
 
-__global__ void k_flow_adam(DevFlow f, int32_t t, float lr) {
+__global__ void k_flow_adam(DevFlow f, float lr, FlowGate gate) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.n_params) return;
+    if (i >= f.n_params || !gate.open()) return;
+    const int32_t t = *f.adam_t + 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float g = f.grad[i];
     const float m = b1 * f.adam_m[i] + (1.0f - b1) * g;
@@ -665,9 +672,9 @@ DevFlow flow_shape(int D, int H, int L) {
     return f;
 }
 
-cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s) {
+cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s, bool bump, FlowGate gate) {
     const int64_t total = (int64_t)f.L * f.layer_work;
-    k_flow_refresh<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f);
+    k_flow_refresh<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f, bump, gate);
     return cudaGetLastError();
 }
 
@@ -691,22 +698,21 @@ cudaError_t launch_traj_flow(const DevModel& m, const DevFlow& f, const TrajArgs
 int64_t flow_partials_floats(const DevFlow& f, int64_t N) { return ((N + FG - 1) / FG) * f.n_params; }
 
 cudaError_t flow_loss_grad(const DevFlow& f, const float* theta, int64_t ld, const int32_t* src, const double* W,
-                           const RunState* rstate, const RunParams* runs, int64_t N, float* partials,
-                           cudaStream_t s) {
+                           FlowGate gate, int64_t N, float* partials, cudaStream_t s) {
     const int64_t grid = (N + FG - 1) / FG;
     if (grid == 0) return cudaSuccess;
     const size_t sm = flow_smem_bytes(f.D, f.H, f.L, f.O4);
     cudaError_t e = cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_flow_train<<<(unsigned)grid, FT, sm, s>>>(f, theta, ld, src, W, rstate, runs, N, partials);
+    k_flow_train<<<(unsigned)grid, FT, sm, s>>>(f, theta, ld, src, W, gate, N, partials);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_flow_reduce<<<(unsigned)((f.n_params + 255) / 256), 256, 0, s>>>(partials, grid, f.n_params, f.grad);
+    k_flow_reduce<<<(unsigned)((f.n_params + 255) / 256), 256, 0, s>>>(partials, grid, f.n_params, f.grad, gate);
     return cudaGetLastError();
 }
 
-cudaError_t flow_adam(const DevFlow& f, int32_t t, double lr, cudaStream_t s) {
-    k_flow_adam<<<(unsigned)((f.n_params + 255) / 256), 256, 0, s>>>(f, t, (float)lr);
+cudaError_t flow_adam(const DevFlow& f, double lr, FlowGate gate, cudaStream_t s) {
+    k_flow_adam<<<(unsigned)((f.n_params + 255) / 256), 256, 0, s>>>(f, (float)lr, gate);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,17 @@ struct DevFlow {
     float* adam_v;               // [n_params]
     float* grad;                 // [n_params]
     float* work;                 // [L x layer_work]
+    int32_t* adam_t;             // device Adam step count (steps taken)
+};
+
+// Training gate: a training epoch runs only when the run's tested ESS is at
+// least frac * n (rs == nullptr: always).  Evaluated on the device, so a
+// training iteration needs no host round trip.
+struct FlowGate {
+    const RunState* rs;
+    const RunParams* rp;
+    double frac;
+    __device__ bool open() const { return rs == nullptr || rs->ess_pre >= frac * (double)rp->n; }
 };
 
 // Offsets inside one layer of the work copies.
@@ -55,8 +66,9 @@ bool flow_supported(const DevModel& m, int H, int L);
 // Sizes of a flow of this shape; the pointers are left null.
 DevFlow flow_shape(int D, int H, int L);
 size_t flow_smem_bytes(int D, int H, int L, int O4);
-// Rebuild the padded / transposed work copies from params.
-cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s);
+// Rebuild the padded / transposed work copies from params.  With `bump`, the
+// launch also counts the Adam step that preceded it (when the gate was open).
+cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s, bool bump = false, FlowGate gate = FlowGate{});
 // HMC in z = T^-1(theta) with the frozen map (trajectory kernel); z0 and z1
 // (may be nullptr) receive the latent start and end points [D x ld].
 cudaError_t launch_traj_flow(const DevModel& m, const DevFlow& f, const TrajArgs& a, float* z0, float* z1,
@@ -65,11 +77,12 @@ cudaError_t launch_traj_flow(const DevModel& m, const DevFlow& f, const TrajArgs
 // weights 1/n after resampling, else W) into f.grad, using `partials`
 // (n_blocks x n_params floats) for a fixed-order reduction.
 int64_t flow_partials_floats(const DevFlow& f, int64_t N);
-// rstate / runs describe the single run of the handle (nullptr: weights W).
+// gate.rs / gate.rp describe the single run of the handle (nullptr: weights W
+// as given, always open).
 cudaError_t flow_loss_grad(const DevFlow& f, const float* theta, int64_t ld, const int32_t* src, const double* W,
-                           const RunState* rstate, const RunParams* runs, int64_t N, float* partials,
-                           cudaStream_t s);
-// One Adam step (descent) on f.params from f.grad; t is the 1-based step.
-cudaError_t flow_adam(const DevFlow& f, int32_t t, double lr, cudaStream_t s);
+                           FlowGate gate, int64_t N, float* partials, cudaStream_t s);
+// One Adam step (descent) on f.params from f.grad, step number *f.adam_t + 1
+// (the following flow_refresh with bump counts it).
+cudaError_t flow_adam(const DevFlow& f, double lr, FlowGate gate, cudaStream_t s);
 
 }  // namespace smc

@@ -102,7 +102,6 @@ struct smc_handle {
     float* flow_partials = nullptr;
     float* z0 = nullptr;            // latent start / end points of the last move
     float* z1 = nullptr;
-    int32_t flow_t = 0;             // Adam step count
 };
 
 namespace {
@@ -300,15 +299,15 @@ bool flow_trains_at(const smc_handle* h, int64_t k) {
 
 // `epochs` Adam steps on the weighted NLL of the current particles (after
 // resampling: positions through src, weights 1/J or W), each followed by a
-// rebuild of the work copies.
+// rebuild of the work copies; every kernel of it is a no-op on the device
+// when the tested ESS is below min_ess_frac * J.
 cudaError_t flow_train(smc_handle* h, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
+    const FlowGate gate{h->d_rstate, h->d_runs, h->flow_cfg.min_ess_frac};
     for (int32_t ep = 0; ep < h->flow_cfg.epochs && e == cudaSuccess; ++ep) {
-        e = flow_loss_grad(h->flow, h->theta[h->cur], h->ld, h->src, h->W, h->d_rstate, h->d_runs, h->N,
-                           h->flow_partials, s);
-        h->flow_t += 1;
-        if (e == cudaSuccess) e = flow_adam(h->flow, h->flow_t, h->flow_cfg.lr, s);
-        if (e == cudaSuccess) e = flow_refresh(h->flow, s);   // the next gradient sees the new map
+        e = flow_loss_grad(h->flow, h->theta[h->cur], h->ld, h->src, h->W, gate, h->N, h->flow_partials, s);
+        if (e == cudaSuccess) e = flow_adam(h->flow, h->flow_cfg.lr, gate, s);
+        if (e == cudaSuccess) e = flow_refresh(h->flow, s, true, gate);   // the next gradient sees the new map
     }
     if (h->profiling) h->kernel_launches += 4 * (int64_t)h->flow_cfg.epochs;
     return e;
@@ -795,11 +794,14 @@ smc_status smc_moments(const smc_handle* hc, double* mean, double* var) {
     if (!(m > -INFINITY)) return fail(h, SMC_E_DEGENERATE, "all weights are zero");
     double s = 0.0;
     for (int64_t j = 0; j < n; ++j) s += std::exp(lw[(size_t)j] - m);
+    // particles of zero weight are left out (their positions may be non-finite)
     for (int64_t d = 0; d < D; ++d) {
         double mu = 0.0;
-        for (int64_t j = 0; j < n; ++j) mu += std::exp(lw[(size_t)j] - m) / s * th[(size_t)(d * h->N + j)];
+        for (int64_t j = 0; j < n; ++j)
+            if (lw[(size_t)j] > -INFINITY) mu += std::exp(lw[(size_t)j] - m) / s * th[(size_t)(d * h->N + j)];
         double v = 0.0;
         for (int64_t j = 0; j < n; ++j) {
+            if (!(lw[(size_t)j] > -INFINITY)) continue;
             const double e = th[(size_t)(d * h->N + j)] - mu;
             v += std::exp(lw[(size_t)j] - m) / s * e * e;
         }
@@ -827,8 +829,8 @@ smc_status smc_reset(smc_handle* h, uint64_t seed) {
                             cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->flow.adam_m, 0, sizeof(float) * h->flow_init.size(), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->flow.adam_v, 0, sizeof(float) * h->flow_init.size(), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->flow.adam_t, 0, sizeof(int32_t), s);
         if (e == cudaSuccess) e = flow_refresh(h->flow, s);
-        h->flow_t = 0;
     }
     // the staging vectors are pageable: the copies have consumed them on return
     if (e == cudaSuccess) e = initial_draw(h);
@@ -1025,6 +1027,7 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
                       "in [4, 128] and layers in [1, 8]");
     if (fc->train_every < 0 || fc->epochs < 0 || !(fc->lr > 0.0) || !std::isfinite(fc->lr))
         return reject("train_every and epochs must be >= 0 and lr > 0");
+    if (!(fc->min_ess_frac >= 0.0 && fc->min_ess_frac <= 1.0)) return reject("min_ess_frac must be in [0, 1]");
     DevFlow f = flow_shape((int)h->D, fc->hidden, fc->layers);
     std::vector<float> p32((size_t)f.n_params);
     for (int64_t i = 0; i < f.n_params; ++i) {
@@ -1037,6 +1040,7 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     f.adam_v = A.get<float>((size_t)f.n_params);
     f.grad = A.get<float>((size_t)f.n_params);
     f.work = A.get<float>((size_t)(f.L * f.layer_work));
+    f.adam_t = A.get<int32_t>(1);
     float* partials = A.get<float>((size_t)flow_partials_floats(f, h->N));
     float* z0 = A.get<float>((size_t)(h->D * h->ld));
     float* z1 = A.get<float>((size_t)(h->D * h->ld));
@@ -1049,6 +1053,7 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     cudaError_t e = cudaMemcpyAsync(f.params, p32.data(), sizeof(float) * p32.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f.adam_m, 0, sizeof(float) * p32.size(), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f.adam_v, 0, sizeof(float) * p32.size(), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f.adam_t, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(z0, 0, sizeof(float) * (size_t)(h->D * h->ld), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(z1, 0, sizeof(float) * (size_t)(h->D * h->ld), s);
     if (e == cudaSuccess) e = flow_refresh(f, s);
@@ -1060,7 +1065,6 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     h->flow_partials = partials;
     h->z0 = z0;
     h->z1 = z1;
-    h->flow_t = 0;
     h->flow_on = true;
     return SMC_OK;
 }
@@ -1110,7 +1114,7 @@ smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, con
     t.f.grad = grad;
     cudaError_t e = flow_refresh(t.f, s);
     if (e == cudaSuccess && N == 0) e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)t.f.n_params, s);
-    if (e == cudaSuccess && N > 0) e = flow_loss_grad(t.f, theta, ld, nullptr, W, nullptr, nullptr, N, t.partials, s);
+    if (e == cudaSuccess && N > 0) e = flow_loss_grad(t.f, theta, ld, nullptr, W, FlowGate{}, N, t.partials, s);
     t.mem.release();
     return kstatus(e);
 }

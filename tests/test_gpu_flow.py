@@ -256,7 +256,7 @@ def _train_case(p_init, E, lr, seed=9):
                init_scale=2.0)
     D, H, L = 10, 32, 4
     smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, **run), stream())
-    smp.enable_flow(p_init, H, L, train_every=1, epochs=E, lr=lr)
+    smp.enable_flow(p_init, H, L, train_every=1, epochs=E, lr=lr, min_ess_frac=0.0)
     th0 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
     logw0 = smp.buffer(B.BUF_LOGW)
     st = smp.step()[0]
@@ -307,6 +307,21 @@ def test_training_epochs_match_oracle_adam():
     assert np.all(d <= 2 * E * lr + 1e-6)
     close = d <= 1e-2 * lr * E + 1e-7
     assert np.mean(close) > 0.995, np.mean(close)
+
+
+def test_training_gate_skips_a_degenerate_weighted_set():
+    """Iteration 1 of the 10-d Gaussian starts from N(0, 4 I): its tested ESS
+    is far below 0.9 J, so with min_ess_frac = 0.9 the map must not move."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(n_particles=512, n_iters=6, n_warmup=4, step_size=0.05, traj_len0=0.3, max_steps=20,
+               init_scale=2.0)
+    p_init = _params(10, 32, 4, seed=12, scale=0.3)
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=9, **run), stream())
+    smp.enable_flow(p_init, 32, 4, train_every=1, epochs=5, lr=1e-3, min_ess_frac=0.9)
+    st = smp.step()[0]
+    assert st["ess_pre"] < 0.9 * run["n_particles"]
+    np.testing.assert_array_equal(smp.flow_params(), p_init)
+    smp.close()
 
 
 def test_identity_map_gives_the_plain_sampler():
