@@ -17,6 +17,11 @@ roofline   = the trajectory kernel (dominant): algorithmic FLOPs per launch
              (4 n D per particle-gradient + 2 n D per particle for the endpoint
              energy) / its mean event-timed duration.
 cpu_baseline / --impl reference = the FP64 C oracle on the host cores.
+preconditioner = the learned transport map against the plain identity-metric
+             sampler on the 8192-particle 100-d Gaussian (condition number
+             1e4) and 50-d banana targets: ESS/s, grad-evals/s, acceptance,
+             moment accuracy against the closed forms, and the achieved
+             FLOP rate of the latent-space trajectory kernel.
 
 N > 1 (torchrun): independent replicas, one per GPU, different seeds
 ("replicas only": the method's particle sets do not exchange data).
@@ -166,6 +171,78 @@ def cpu_oracle_rate(w, run, seconds_target=20.0, iters=2):
     return ge / dt, cores, dt, done
 
 
+def _c5_truth(w):
+    """Closed-form log Z, mean and marginal variances of the C5 targets."""
+    D = w["D"]
+    if w["kind"] == "gauss_dense":
+        P = np.asarray(w["P"], np.float32).astype(np.float64)
+        _, ld = np.linalg.slogdet(P)
+        return 0.5 * D * np.log(2 * np.pi) - 0.5 * ld, np.zeros(D), np.diag(np.linalg.inv(P))
+    a, b = w["a"], w["b"]
+    return 0.0, np.zeros(D), np.tile([a, 1.0 + 2.0 * b * b * a * a], D // 2)
+
+
+def _flow_flops_per_grad(w, H, L):
+    """Algorithmic FLOPs of one latent-space gradient: per coupling layer the
+    conditioner forward 2(Dh H + H^2 + H D) and its vector-Jacobian product
+    (the same), plus the target's gradient."""
+    D, Dh = w["D"], w["D"] // 2
+    tgt = 2.0 * D * D if w["kind"] == "gauss_dense" else 8.0 * D
+    return L * 4.0 * (Dh * H + H * H + H * D) + tgt
+
+
+def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
+    """The learned preconditioner against the plain identity-metric sampler
+    on the two 8192-particle targets of the preconditioner workload: one
+    complete run each (K iterations, training during warm-up), device-timed,
+    L2 flushed before each; ESS/s, grad-evals/s, acceptance and the accuracy
+    of the posterior moments against the closed forms."""
+    out = {}
+    for name, w, eps in (("gauss100_cond1e4", workloads.gauss100_cond(), 0.01),
+                         ("banana50", workloads.banana50(), 0.05)):
+        lz_t, m_t, v_t = _c5_truth(w)
+        run = dict(w["run"], step_size=eps, n_iters=K, n_warmup=M)
+        md = g.ModelData.from_workload(w)
+        res = {}
+        for arm in ("plain", "flow"):
+            smp = g.Sampler(md, g.make_config(seed=4242, **run), stream)
+            if arm == "flow":
+                smp.enable_flow(workloads.flow_init(w["D"], H, L, seed=5), H, L, train_every=2, epochs=20,
+                                lr=1e-3, min_ess_frac=0.25)
+            smp.run(2)                      # first launches (function attributes, graph capture) untimed
+            smp.reset(777)
+            smp.profile(True)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stats = smp.run(K, with_stats=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            prof = smp.get_profile()
+            smp.profile(False)
+            summ = smp.summary()[0]
+            m, v = smp.moments()
+            smp.close()
+            r = {"ms": ms, "ess_per_s": summ["ess_sum_post_warmup"] / (ms / 1e3),
+                 "grad_evals_per_s": summ["grad_evals"] / (ms / 1e3),
+                 "mean_alpha_post_warmup": float(np.mean([x["mean_alpha"] for x in stats[M:]])),
+                 "mean_ess_post_warmup": float(np.mean([x["ess"] for x in stats[M:]])),
+                 "mean_err_sd_units": float(np.sqrt(np.mean((m - m_t) ** 2 / v_t))),
+                 "var_rel_err": float(np.sqrt(np.mean((v / v_t - 1.0) ** 2))),
+                 "log_z": summ["log_z"], "log_z_closed_form": lz_t,
+                 "traj_share": prof["traj_ms"] / ms}
+            if arm == "flow":
+                fl = _flow_flops_per_grad(w, H, L) * (summ["grad_evals"] + run["n_particles"] * K)
+                r["flow_traj_tflops"] = fl / (prof["traj_ms"] / 1e3) / 1e12
+                r["flow_traj_frac_of_fp32_peak"] = r["flow_traj_tflops"] / FP32_FMA_PEAK_TFLOPS
+            res[arm] = r
+        res["config"] = {"N": run["n_particles"], "K": K, "M_warmup": M, "eps": eps, "flow": f"{L} coupling layers, "
+                         f"width {H}, tanh, Adam lr 1e-3, 20 epochs every 2 warm-up iterations, ESS gate 0.25 J"}
+        out[name] = res
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle as it stands, on the host cores, one
     SMC iteration of the workload per step (bounded sample)."""
@@ -231,6 +308,8 @@ def main():
                     help="precisions also measured (fewer steps) and reported under 'variants'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precond", action="store_true",
+                    help="skip the learned-preconditioner comparison (two 8192-particle targets)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +456,11 @@ def main():
     roof["mean_launch_ms"] = traj_ms / traj_n
     roof["share_of_step_time"] = traj_ms / (dev_ms / args.steps) if dev_ms > 0 else None
 
+    # ---------------- learned preconditioner vs the plain sampler (rank 0, N=1)
+    precond = None
+    if not args.no_precond and world == 1 and args.workload == "logistic":
+        precond = precond_compare(g, torch, stream, flush)
+
     # ---------------- end to end through the C-ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -452,6 +536,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "variants": variants,
+        "preconditioner": precond,
         "gpu_launches": prof["kernel_launches"] * args.steps,
         "clocks": clk,
     }
