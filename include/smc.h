@@ -85,7 +85,12 @@ typedef struct {
 typedef enum {
     SMC_PREC_FP32 = 0,      /* FP32 SIMT, FP32 everywhere on the trajectory       */
     SMC_PREC_BF16X3 = 1,    /* tcgen05 BF16 x3 split products, FP32 accumulation  */
-    SMC_PREC_BF16 = 2       /* tcgen05 BF16 operands, FP32 accumulation           */
+    SMC_PREC_BF16 = 2,      /* tcgen05 BF16 operands, FP32 accumulation (data that
+                               do not fit on chip are streamed, see BF16X2)       */
+    SMC_PREC_BF16X2 = 3     /* tcgen05, streamed data (any n, dim <= 128): X rounded
+                               once to BF16, theta and the residuals r split into
+                               BF16 hi + lo (two products per GEMM), FP32
+                               accumulation                                      */
 } smc_precision;
 
 /* ------------------------------------------------------------------ config

@@ -17,7 +17,7 @@ from . import build as _build
 SMC_OK, SMC_E_INVAL, SMC_E_NOMEM, SMC_E_CUDA, SMC_E_DEGENERATE, SMC_E_TIMEOUT, SMC_E_STATE = \
     0, -1, -2, -3, -4, -5, -6
 GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
-PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
+PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
 (BUF_THETA, BUF_GRAD, BUF_LOGPI, BUF_LOGW, BUF_W, BUF_ANCESTORS, BUF_STEPS, BUF_P_FINAL,
  BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1) = range(14)
 

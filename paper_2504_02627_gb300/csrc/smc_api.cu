@@ -192,6 +192,36 @@ std::string upload_model(smc_dev_model* dm, const smc_model* md, cudaStream_t s)
             if (xl) cudaMemcpyAsync(xl, Xl.data(), Xl.size() * 2, cudaMemcpyHostToDevice, s);
             m.Xbf = xh;
             m.Xbf_lo = xl;
+            if (D <= 128) {
+                // per-chunk shared-memory images for the streamed tensor-core path:
+                // 128-byte swizzle (16-byte unit u of row r stored at unit u ^ (r & 7))
+                const int64_t C = STREAM_CHUNK, nch = (n + C - 1) / C, dk = round_up(D, 16);
+                std::vector<uint16_t> xk((size_t)(nch * 2 * C * 64), 0), xt((size_t)(nch * dk * C), 0);
+                std::vector<float> yi((size_t)(nch * C), 0.0f);
+                for (int64_t i = 0; i < n; ++i) {
+                    const int64_t c = i / C, r = i % C;
+                    yi[(size_t)i] = (float)md->y[i];
+                    for (int64_t d = 0; d < D; ++d) {
+                        const uint16_t v = Xh[(size_t)(i * Dp + d)];
+                        const int64_t atom = d / 64, u = (d % 64) / 8, e = d % 8;
+                        const int64_t bk = c * (2 * C * 128) + atom * (C * 128) + r * 128 + ((u ^ (r & 7)) << 4) + 2 * e;
+                        xk[(size_t)(bk / 2)] = v;
+                        const int64_t ut = r / 8, et = r % 8;
+                        const int64_t bt = c * (dk * 128) + d * 128 + ((ut ^ (d & 7)) << 4) + 2 * et;
+                        xt[(size_t)(bt / 2)] = v;
+                    }
+                }
+                uint16_t* xkd = dm->mem.get<uint16_t>(xk.size());
+                uint16_t* xtd = dm->mem.get<uint16_t>(xt.size());
+                if (xkd) cudaMemcpyAsync(xkd, xk.data(), xk.size() * 2, cudaMemcpyHostToDevice, s);
+                if (xtd) cudaMemcpyAsync(xtd, xt.data(), xt.size() * 2, cudaMemcpyHostToDevice, s);
+                m.xk_img = xkd;
+                m.xt_img = xtd;
+                m.y_img = up(yi);
+                m.dk = (int32_t)dk;
+                m.n_chunks = (int32_t)nch;
+                cudaStreamSynchronize(s);   // the staging vectors are pageable and local
+            }
             if (logit) {
                 m.lconst = -0.5 * (double)D * (LOG_2PI + 2.0 * std::log(tau));
             } else {
@@ -244,7 +274,7 @@ std::string check_config(const smc_config& c) {
     if (c.accept_reject != 0 && c.accept_reject != 1) return "accept_reject must be 0 or 1";
     if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
-    if (c.precision < 0 || c.precision > 2) return "unknown precision";
+    if (c.precision < 0 || c.precision > 3) return "unknown precision";
     return "";
 }
 

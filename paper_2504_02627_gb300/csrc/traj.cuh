@@ -25,7 +25,20 @@ struct DevModel {
     const uint16_t* Xbf_lo; // [n x Dp] bf16 residual x - bf16(x)
     double h0, h1;        // LOGISTIC: tau; LINEAR: sigma, tau; HIER: sigma; BANANA: a, b
     double lconst;        // theta-independent part of log pi
+    // Streamed tensor-core operands (GEMM-shaped models with D <= 128): X in
+    // BF16 as per-chunk shared-memory images of STREAM_CHUNK observations,
+    // already in the 128-byte-swizzled K-major layouts the MMAs read, so one
+    // contiguous bulk copy per chunk stages them:
+    //   xk_img chunk c: 2 atoms x [STREAM_CHUNK obs rows x 64 dims] (16 KB)
+    //   xt_img chunk c: [dkr dim rows x STREAM_CHUNK obs] (dkr x 128 bytes)
+    //   y_img  chunk c: STREAM_CHUNK floats (zero past n)
+    const uint16_t* xk_img;
+    const uint16_t* xt_img;
+    const float* y_img;
+    int32_t dk;           // D rounded up to 16 (MMA K of the first product, N of the second)
+    int32_t n_chunks;
 };
+constexpr int STREAM_CHUNK = 64;
 
 // What a trajectory launch reads and writes.  Slot t of the launch handles
 // particle j = perm ? perm[t] : t; it starts from source index src[j] (the
@@ -73,5 +86,9 @@ cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision,
 // tensor-core path (traj_tc.cu): logistic / linear regression, BF16 or BF16x3
 bool traj_tc_supported(const DevModel& m);
 cudaError_t launch_traj_tc(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
+// streamed tensor-core path (traj_tc_stream.cu): any n, D <= 128; np = 1
+// (BF16 state operands) or 2 (state operands split into BF16 hi + lo)
+bool traj_stream_supported(const DevModel& m);
+cudaError_t launch_traj_stream(const DevModel& m, const TrajArgs& a, int np, cudaStream_t s);
 
 }  // namespace smc

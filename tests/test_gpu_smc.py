@@ -207,9 +207,9 @@ def test_degenerate_target_reports_status():
     smp.close()
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_tensor_core_iterations_keep_exact_weights(precision):
-    """Tensor-core trajectories (BF16x3 / BF16 gradients): resampling and step
+    """Tensor-core trajectories (BF16x3 / BF16 / streamed BF16x2 gradients): resampling and step
     counts are still bit-exact, and the weights use the exact energy at the
     GPU's own end points -- Delta H from the oracle's FP64 log pi at the GPU
     positions and momenta matches to FP32 accuracy, so the sampler stays exact
@@ -247,7 +247,7 @@ def test_tensor_core_iterations_keep_exact_weights(precision):
         # the trajectories themselves stay close to the exact-gradient ones
         th1_o, _, _, _ = oracle.leapfrog(t, pre["theta"][src], p0, run["step_size"], S_o)
         rel = np.abs(th1 - th1_o) / (np.abs(th1_o) + np.sqrt(np.mean(th1_o**2)))
-        assert np.median(rel) < (1e-3 if precision == 1 else 5e-2)
+        assert np.median(rel) < {1: 1e-3, 2: 5e-2, 3: 1e-2}[precision]
     smp.close()
 
 
