@@ -13,13 +13,18 @@
 // it fits, is read once per tile and step.
 //
 // Roles (320 threads): warp 8 lane 0 issues the bulk copies; warp 9 lane 0
-// issues the MMAs (GEMM1 of chunk c before GEMM2 of chunk c-1, so the tensor
-// core works while the residuals of the previous chunk are formed); warps 0-7
-// form the residuals r = y - sigmoid(eta) (or (y - eta)/sigma^2) from TMEM
-// and hold the particle state: warp w owns TMEM lanes 32 (w % 4) .. + 31
-// (one particle per lane) and dimensions 64 (w / 4) .. + 63.  Every wait on
+// issues the MMAs, GEMM1 two chunks ahead of GEMM2 (three eta and three R
+// buffers in flight), so the tensor core works while residuals are formed;
+// warps 0-7 form the residuals r = y - sigmoid(eta) (or (y - eta)/sigma^2)
+// from TMEM and write them back to TMEM as BF16, where GEMM2 reads its A
+// operand (warps 0-3 the even chunks, 4-7 the odd ones), and they hold the
+// particle state: warp w owns TMEM lanes 32 (w % 4) .. + 31 (one particle per
+// lane) and dimensions 64 (w / 4) .. + 63.
+// TMEM columns: eta [0, 192), G [192, 192 + dk), R^T [320, 512).  Every wait on
 // an mbarrier is bounded (then *dev_err is set and the kernel still runs to
-// its end).
+// its end) in wall time (2 s of %globaltimer per wait), and a waiting thread
+// sleeps in hardware (try_wait suspend hint) instead of spinning on issue
+// slots the epilogue warps need.
 //
 // Precision: X is rounded once to BF16 (a fixed perturbation of the data the
 // integrator sees); with np = 2 the state operands Theta and r are split into
@@ -42,16 +47,17 @@ constexpr int S_EPI_WARPS = 8;
 constexpr int S_THREADS = 32 * (S_EPI_WARPS + 2);
 constexpr int S_PRODUCER_WARP = 8, S_MMA_WARP = 9;
 constexpr int TH_ATOM = SP * 128;             // 128 particle rows x 64 BF16 (one 128-byte swizzle atom)
-constexpr int R_PART = SP * 128;              // R^T part: 128 particle rows x 64 obs
 constexpr int XK_BYTES = 2 * SC * 128;        // X chunk, K-major over dims: 2 atoms of 64 obs rows
-constexpr uint32_t S_TMEM_COLS = 256;
-constexpr uint32_t S_COL_ETA = 0;             // two eta buffers of 64 columns
-constexpr uint32_t S_COL_G = 128;             // gradient accumulator, dk columns
+constexpr int S_NB = 3;                       // eta and R^T buffers in flight (both in TMEM)
+constexpr uint32_t S_TMEM_COLS = 512;
+constexpr uint32_t S_COL_ETA = 0;             // S_NB eta buffers of 64 FP32 columns
+constexpr uint32_t S_COL_G = 192;             // gradient accumulator, dk <= 128 columns
+constexpr uint32_t S_COL_R = 320;             // S_NB x np R^T parts of 32 columns (64 BF16 obs)
 constexpr int S_SMEM_MAX = 232448;            // opt-in shared memory per CTA
 
 struct SLayout {
     int dkr, stages, xt_bytes, stage_bytes;
-    int off_th, off_r, off_stage, off_y, off_misc, off_bar, total;
+    int off_th, off_stage, off_y, off_misc, off_bar, total;
 };
 
 // Byte layout of the dynamic shared memory (from a 1024-aligned base).
@@ -62,11 +68,10 @@ __host__ __device__ inline SLayout s_layout(int dk, int np, int stages) {
     L.xt_bytes = L.dkr * 128;
     L.stage_bytes = XK_BYTES + L.xt_bytes;        // multiple of 1024
     L.off_th = 0;                                 // [np][2 atoms]
-    L.off_r = L.off_th + np * 2 * TH_ATOM;        // [2 buffers][np]
-    L.off_stage = L.off_r + 2 * np * R_PART;      // [stages]
+    L.off_stage = L.off_th + np * 2 * TH_ATOM;    // [stages]
     L.off_y = L.off_stage + stages * L.stage_bytes;   // [stages][64] f32
     L.off_misc = L.off_y + stages * SC * 4;       // kin, sq, ll: [2][128] f64 each
-    L.off_bar = L.off_misc + 6 * SP * 8;          // mbarriers, TMEM base, step maximum
+    L.off_bar = L.off_misc + 6 * SP * 8;          // mbarriers, TMEM base, flags
     L.total = L.off_bar + 256 + 1024;             // + alignment slack of the base
     return L;
 }
@@ -90,9 +95,11 @@ __device__ __forceinline__ void pack_unit(const float* v, uint4& hi, uint4& lo) 
     lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
 }
 
+// Residual on the hardware exponential and fast division (a few ulp; the
+// value is then split into BF16 parts with 2^-16 relative resolution).
 template <bool LOGIT>
 __device__ __forceinline__ float residual(float y, float eta, float inv_s2) {
-    if (LOGIT) return y - 1.0f / (1.0f + __expf(-eta));
+    if (LOGIT) return y - __fdividef(1.0f, 1.0f + __expf(-eta));
     return (y - eta) * inv_s2;
 }
 
@@ -106,14 +113,16 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
     const int D = m.D, dk = m.dk, nch = m.n_chunks;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [4] stage filled
     uint64_t* empty = full + 4;                                      // [4] stage consumed by both GEMMs
-    uint64_t* eta_full = empty + 4;                                  // [2] GEMM1 done
-    uint64_t* eta_empty = eta_full + 2;                              // [2] eta read by the epilogue
-    uint64_t* r_full = eta_empty + 2;                                // [2] R^T written
-    uint64_t* r_empty = r_full + 2;                                  // [2] GEMM2 done with R^T
-    uint64_t* g_full = r_empty + 2;                                  // step's gradient complete
+    uint64_t* eta_full = empty + 4;                                  // [S_NB] GEMM1 done
+    uint64_t* eta_empty = eta_full + S_NB;                           // [S_NB] eta read by the epilogue
+    uint64_t* r_full = eta_empty + S_NB;                             // [S_NB] R^T written
+    uint64_t* r_empty = r_full + S_NB;                               // [S_NB] GEMM2 done with R^T
+    uint64_t* g_full = r_empty + S_NB;                               // step's gradient complete
     uint64_t* th_full = g_full + 1;                                  // next step's Theta^T written
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(th_full + 1);
+    uint64_t* fin = th_full + 1;                                     // every MMA issued has completed
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(fin + 1);
     int* smax_s = reinterpret_cast<int*>(tmem_s + 1);
+    volatile int* abort_s = smax_s + 1;                              // a bounded wait gave up
     double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [2][128] |p|^2 halves
     double* sq_s = kin_s + 2 * SP;                                   // [2][128] |theta|^2 halves
     double* ll_s = sq_s + 2 * SP;                                    // [2][128] log-likelihood halves
@@ -126,16 +135,18 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < S_NB; ++i) {
             tc::mbar_init(&eta_full[i], 1);
-            tc::mbar_init(&eta_empty[i], S_EPI_WARPS);
-            tc::mbar_init(&r_full[i], S_EPI_WARPS);
+            tc::mbar_init(&eta_empty[i], S_EPI_WARPS / 2);   // one group of four warps per chunk
+            tc::mbar_init(&r_full[i], S_EPI_WARPS / 2);
             tc::mbar_init(&r_empty[i], 1);
         }
         tc::mbar_init(g_full, 1);
         tc::mbar_init(th_full, S_EPI_WARPS);
+        tc::mbar_init(fin, 1);
         tc::fence_mbar_init();
         *smax_s = 0;
+        *abort_s = 0;
     }
     if (wid == 0) {
         tc::tmem_alloc(tmem_s, S_TMEM_COLS);
@@ -249,49 +260,58 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             const uint32_t bytes = (uint32_t)(XK_BYTES + L.xt_bytes + SC * 4);
+            // ring position (stage, its phase bit) and chunk, advanced without divisions
+            int st = 0, c = 0;
+            uint32_t ph = 0;
             for (int64_t it = 0; it < total; ++it) {
-                const int c = (int)(it % nch);
-                const int st = (int)(it % stages);
-                const uint32_t ph = (uint32_t)((it / stages) & 1);
-                tc::mbar_wait(&empty[st], ph ^ 1u, err);
+                tc::mbar_wait_timed(&empty[st], ph ^ 1u, err, abort_s);
                 tc::mbar_arrive_expect_tx(&full[st], bytes);
                 unsigned char* dst = sm + L.off_stage + st * L.stage_bytes;
                 tc::bulk_g2s(dst, m.xk_img + (int64_t)c * (XK_BYTES / 2), XK_BYTES, &full[st]);
                 tc::bulk_g2s(dst + XK_BYTES, m.xt_img + (int64_t)c * (L.xt_bytes / 2), (uint32_t)L.xt_bytes,
                              &full[st]);
                 tc::bulk_g2s(y_s + st * SC, m.y_img + (int64_t)c * SC, SC * 4, &full[st]);
+                if (++c == nch) c = 0;
+                if (++st == stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
             }
-            // every copy has landed before the stage memory is reused or the CTA exits
-            for (int64_t it = total > stages ? total - stages : 0; it < total; ++it)
-                tc::mbar_wait(&full[it % stages], (uint32_t)((it / stages) & 1), err);
+            // every copy has landed before the stage memory is reused or the CTA exits:
+            // the last `stages` fills are the most recent phase of each stage
+            const int64_t first = total > stages ? total - stages : 0;
+            for (int64_t it = first; it < total; ++it) {
+                const int sst = (int)(it % stages);
+                tc::mbar_wait_timed(&full[sst], (uint32_t)((it / stages) & 1), err, abort_s);
+            }
         }
     } else if (wid == S_MMA_WARP) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
-            auto gemm2 = [&](int64_t i) {
-                const int st = (int)(i % stages), b = (int)(i & 1);
-                const int ci = (int)(i % nch);
-                tc::mbar_wait(&r_full[b], (uint32_t)((i >> 1) & 1), err);
+            // GEMM2 of one chunk: A = R^T from TMEM buffer b, B = the chunk's X image
+            struct Pend { int st, b, ci; uint32_t bph; };
+            auto gemm2 = [&](const Pend& q2) {
+                tc::mbar_wait_timed(&r_full[q2.b], q2.bph, err, abort_s);
                 tc::fence_after_sync();
-                const uint32_t xt = s_base + L.off_stage + st * L.stage_bytes + XK_BYTES;
+                const uint32_t xt = s_base + L.off_stage + q2.st * L.stage_bytes + XK_BYTES;
                 for (int q = 0; q < NP; ++q)
                     for (int kk = 0; kk < SC / 16; ++kk) {
-                        const uint64_t ad = tc::smem_desc(s_base + L.off_r + (b * NP + q) * R_PART + kk * 32, 16, 1024,
-                                                          tc::SWZ_128B);
+                        const uint32_t at = tmem + S_COL_R + (uint32_t)((q2.b * NP + q) * 32 + kk * 8);
                         const uint64_t bd = tc::smem_desc(xt + kk * 32, 16, 1024, tc::SWZ_128B);
-                        tc::mma_bf16(tmem + S_COL_G, ad, bd, IDESC2, (ci > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                        tc::mma_bf16_ta(tmem + S_COL_G, at, bd, IDESC2, (q2.ci > 0 || q > 0 || kk > 0) ? 1u : 0u);
                     }
-                tc::mma_commit(&r_empty[b]);
-                tc::mma_commit(&empty[st]);
+                tc::mma_commit(&r_empty[q2.b]);
+                tc::mma_commit(&empty[q2.st]);
             };
+            int st = 0, b = 0;            // ring stage and buffer of the next chunk
+            uint32_t ph = 0, bph = 0;     // their phase bits
+            Pend p0{}, p1{};              // the two chunks whose GEMM2 is pending (oldest first)
             for (int s = 1; s <= nsteps; ++s) {
-                if (s >= 2) tc::mbar_wait(th_full, (uint32_t)((s - 2) & 1), err);
+                if (s >= 2) tc::mbar_wait_timed(th_full, (uint32_t)((s - 2) & 1), err, abort_s);
                 tc::fence_after_sync();
                 for (int c = 0; c < nch; ++c) {
-                    const int64_t it = (int64_t)(s - 1) * nch + c;
-                    const int st = (int)(it % stages), b = (int)(it & 1);
-                    tc::mbar_wait(&full[st], (uint32_t)((it / stages) & 1), err);
-                    tc::mbar_wait(&eta_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1), err);
+                    tc::mbar_wait_timed(&full[st], ph, err, abort_s);
+                    tc::mbar_wait_timed(&eta_empty[b], bph ^ 1u, err, abort_s);
                     tc::fence_after_sync();
                     const uint32_t xk = s_base + L.off_stage + st * L.stage_bytes;
                     for (int q = 0; q < NP; ++q)
@@ -303,52 +323,87 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
                             tc::mma_bf16(tmem + S_COL_ETA + b * SC, ad, bd, IDESC1, (q > 0 || kk > 0) ? 1u : 0u);
                         }
                     tc::mma_commit(&eta_full[b]);
-                    if (c > 0) gemm2(it - 1);
+                    // GEMM2 two chunks behind: the stage ring holds chunks c-2 .. c (+ prefetch)
+                    if (c >= 2) gemm2(p0);
+                    p0 = p1;
+                    p1 = Pend{st, b, c, bph};
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (++b == S_NB) {
+                        b = 0;
+                        bph ^= 1u;
+                    }
                 }
-                gemm2((int64_t)s * nch - 1);
+                if (nch >= 2) gemm2(p0);
+                gemm2(p1);
                 tc::mma_commit(g_full);
             }
+            tc::mma_commit(fin);   // lets the CTA drain its MMAs even after an aborted wait
         }
     } else {
         // ------------------------------------------------------------ residuals and state (warps 0-7)
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const float hf = 0.5f * ef;
+        // Warps 0-3 take the even chunks of a step and warps 4-7 the odd ones
+        // (all 64 observations of the chunk for their 32 particles), so one
+        // group's TMEM load and store latencies overlap the other's arithmetic.
+        // Every warp advances the ring counters for every chunk.
+        int st = 0, b = 0;
+        uint32_t sph = 0, bph = 0;
         for (int s = 1; s <= nsteps; ++s) {
             for (int c = 0; c < nch; ++c) {
-                const int64_t it = (int64_t)(s - 1) * nch + c;
-                const int st = (int)(it % stages), b = (int)(it & 1);
-                const uint32_t ph = (uint32_t)((it >> 1) & 1);
-                tc::mbar_wait(&eta_full[b], ph, err);
-                tc::fence_after_sync();
-                float eta[32];
-                tc::tmem_ld32(tmem + lane_base + S_COL_ETA + b * SC + 32 * dh, eta);
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&eta_empty[b]);
-                // the stage's y was written by the bulk copy: acquire its barrier
-                // phase (still current: the stage is refilled only after this
-                // chunk's GEMM2, which waits for these residuals)
-                tc::mbar_wait(&full[st], (uint32_t)((it / stages) & 1), err);
-                const float* yv = y_s + st * SC + 32 * dh;
-                float* r = eta;   // residuals overwrite eta in place
+                if ((c & 1) == dh) {
+                    // one lane waits, the warp follows (__syncwarp orders the rest)
+                    if (lane == 0) tc::mbar_wait_timed(&eta_full[b], bph, err, abort_s);
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    // the stage's y was written by the bulk copy: acquire its barrier
+                    // phase (still current: the stage is refilled only after this
+                    // chunk's GEMM2, which waits for these residuals)
+                    if (lane == 0) tc::mbar_wait_timed(&full[st], sph, err, abort_s);
+                    if (lane == 0) tc::mbar_wait_timed(&r_empty[b], bph ^ 1u, err, abort_s);
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    const uint32_t rcol = tmem + lane_base + S_COL_R + (uint32_t)(b * NP * 32);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) r[e] = residual<LOGIT>(yv[e], eta[e], inv_s2);
-                tc::mbar_wait(&r_empty[b], ph ^ 1u, err);
-                unsigned char* row = sm + L.off_r + b * NP * R_PART + prow * 128;
+                    for (int h = 0; h < 2; ++h) {
+                        float eta[32];
+                        tc::tmem_ld32(tmem + lane_base + S_COL_ETA + b * SC + 32 * h, eta);
+                        if (h == 1) {
+                            tc::fence_before_sync();
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&eta_empty[b]);
+                        }
+                        const float* yv = y_s + st * SC + 32 * h;
+                        uint32_t rh[16], rl[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    uint4 vh, vl;
-                    pack_unit(r + 8 * u, vh, vl);
-                    const int phys = ((4 * dh + u) ^ (prow & 7)) << 4;
-                    *reinterpret_cast<uint4*>(row + phys) = vh;
-                    if (NP == 2) *reinterpret_cast<uint4*>(row + R_PART + phys) = vl;
+                        for (int e = 0; e < 32; e += 2) {
+                            const float r0 = residual<LOGIT>(yv[e], eta[e], inv_s2);
+                            const float r1 = residual<LOGIT>(yv[e + 1], eta[e + 1], inv_s2);
+                            const float h0 = bf16_round(r0), h1 = bf16_round(r1);
+                            rh[e / 2] = pack_bf16(h0, h1);
+                            rl[e / 2] = pack_bf16(r0 - h0, r1 - h1);
+                        }
+                        tc::tmem_st16(rcol + 16 * h, rh);
+                        if (NP == 2) tc::tmem_st16(rcol + 32 + 16 * h, rl);
+                    }
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&r_full[b]);
                 }
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&r_full[b]);
+                if (++st == stages) {
+                    st = 0;
+                    sph ^= 1u;
+                }
+                if (++b == S_NB) {
+                    b = 0;
+                    bph ^= 1u;
+                }
             }
             // the step's gradient: G - theta / tau^2, then the leapfrog update
-            tc::mbar_wait(g_full, (uint32_t)((s - 1) & 1), err);
+            tc::mbar_wait_timed(g_full, (uint32_t)((s - 1) & 1), err, abort_s);
             tc::fence_after_sync();
             const bool live = j >= 0 && (a.eval_only || s <= S);
 #pragma unroll
@@ -386,10 +441,21 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
     }
 
     // ---------------------------------------------------------------- end point energy
-    // theta^T in FP32 over the drained stage ring, FP32 eta from the FP32 data,
-    // FP64 accumulation of the log-likelihood
+    // eta = X theta in FP32 from the FP32 data (register tile of 8
+    // observations x 4 particles per thread, X chunks double-buffered in
+    // shared memory by cp.async), FP64 accumulation of the log-likelihood.
+    // The whole dynamic shared memory is free again: all MMAs completed
+    // (g_full, and fin even if a wait gave up) and every bulk copy landed
+    // (the producer's drain).
+    if (tid == 0) {
+        volatile int ignore_abort = 0;   // this drain wait runs even after an abort
+        tc::mbar_wait_timed(fin, 0u, err, &ignore_abort, 4000000000ull);
+    }
     __syncthreads();
-    float* thT = reinterpret_cast<float*>(sm + L.off_stage);   // [dk][128]
+    const int Dp = m.Dp, n = m.n;
+    float* thT = reinterpret_cast<float*>(sm + L.off_th);      // [dk][128]
+    float* xs = thT + dk * SP;                                  // [2][SC][Dp]
+    double* llp = reinterpret_cast<double*>(xs + 2 * SC * Dp);  // [8][128]
     if (epi) {
         double sq = 0.0, kin = 0.0;
 #pragma unroll
@@ -405,32 +471,75 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
         sq_s[dh * SP + prow] = sq;
         kin_s[dh * SP + prow] = kin;     // the initial halves were consumed by H0
     }
-    __syncthreads();
+    auto issue_x = [&](int c, int buf) {
+        const int64_t row0 = (int64_t)c * SC;
+        const int64_t left = (int64_t)n - row0;
+        const int rows = left < SC ? (int)left : SC;
+        const int nvec = rows * Dp / 4;
+        float* dst = xs + buf * SC * Dp;
+        const float* srcx = m.X + row0 * Dp;
+        for (int v = tid; v < nvec; v += S_THREADS) tc::cp_async16(dst + 4 * v, srcx + 4 * v);
+        tc::cp_async_commit();
+    };
+    issue_x(0, 0);
     {
-        const int pp = tid & (SP - 1), half = tid >> 7;   // threads 256 .. 319 idle
-        if (half < 2) {
-            double ll = 0.0;
-            for (int i = half; i < m.n; i += 2) {
-                const float* x = m.X + (int64_t)i * m.Dp;
-                float e0 = 0.0f, e1 = 0.0f;
-                int d = 0;
-                for (; d + 1 < D; d += 2) {
-                    e0 = fmaf(__ldg(x + d), thT[d * SP + pp], e0);
-                    e1 = fmaf(__ldg(x + d + 1), thT[(d + 1) * SP + pp], e1);
+        const int pg = tid & 31, og = tid >> 5;     // warps 0-7 compute, 8-9 only copy
+        double ll[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) issue_x(c + 1, (c + 1) & 1);
+            else tc::cp_async_commit();             // keeps one group per iteration
+            tc::cp_async_wait<1>();                 // chunk c has landed (this thread's copies)
+            __syncthreads();                        // ... and everyone else's
+            if (og < 8) {
+                const float* xc = xs + (c & 1) * SC * Dp + og * 8 * Dp;
+                float acc[8][4];
+#pragma unroll
+                for (int o = 0; o < 8; ++o)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[o][q] = 0.0f;
+#pragma unroll 4
+                for (int d = 0; d < D; ++d) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(thT + d * SP + 4 * pg);
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const float x = xc[o * Dp + d];
+                        acc[o][0] = fmaf(x, t4.x, acc[o][0]);
+                        acc[o][1] = fmaf(x, t4.y, acc[o][1]);
+                        acc[o][2] = fmaf(x, t4.z, acc[o][2]);
+                        acc[o][3] = fmaf(x, t4.w, acc[o][3]);
+                    }
                 }
-                if (d < D) e0 = fmaf(__ldg(x + d), thT[d * SP + pp], e0);
-                const float eta = e0 + e1, yv = __ldg(m.y + i);
-                float term;
-                if (LOGIT) {
-                    const float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
-                    term = yv * eta - sp;
-                } else {
-                    const float z = (yv - eta) * inv_s;
-                    term = -0.5f * z * z;
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int64_t i = (int64_t)c * SC + og * 8 + o;
+                    if (i < n) {
+                        const float yv = __ldg(m.y + i);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float eta = acc[o][q];
+                            float term;
+                            if (LOGIT) {
+                                const float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
+                                term = yv * eta - sp;
+                            } else {
+                                const float z = (yv - eta) * inv_s;
+                                term = -0.5f * z * z;
+                            }
+                            ll[q] += (double)term;
+                        }
+                    }
                 }
-                ll += (double)term;
             }
-            ll_s[half * SP + pp] = ll;
+            __syncthreads();                        // buffer (c & 1) is refilled at iteration c + 1
+        }
+        if (og < 8)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) llp[og * SP + 4 * pg + q] = ll[q];
+        __syncthreads();
+        if (tid < SP) {
+            double tot = 0.0;
+            for (int w = 0; w < 8; ++w) tot += llp[w * SP + tid];   // fixed order
+            ll_s[tid] = tot;
         }
     }
     __syncthreads();
@@ -442,7 +551,7 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
         }
         if (dh == 0) {
             const double sq = sq_s[prow] + sq_s[SP + prow];
-            const double lp1 = ll_s[prow] + ll_s[SP + prow] - 0.5 * sq * inv_tau2_d + m.lconst;
+            const double lp1 = ll_s[prow] - 0.5 * sq * inv_tau2_d + m.lconst;
             a.logpi_out[j] = lp1;
             if (!a.eval_only) {
                 const double kin = kin_s[prow] + kin_s[SP + prow];
@@ -463,10 +572,15 @@ template <bool LOGIT, int NP>
 cudaError_t launch_stream(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     const int tiles = (int)((a.N + SP - 1) / SP);
     if (tiles == 0) return cudaSuccess;
+    // three stages are in use at once (GEMM2 runs two chunks behind GEMM1); a
+    // fourth lets the copy of the next chunk start early
     int stages = 4;
-    while (stages > 2 && s_layout(m.dk, NP, stages).total > S_SMEM_MAX) --stages;
-    const int bytes = s_layout(m.dk, NP, stages).total;
-    if (bytes > S_SMEM_MAX) return cudaErrorInvalidValue;
+    while (stages > 3 && s_layout(m.dk, NP, stages).total > S_SMEM_MAX) --stages;
+    const SLayout L = s_layout(m.dk, NP, stages);
+    if (L.total > S_SMEM_MAX) return cudaErrorInvalidValue;
+    // end-point staging (theta^T, two FP32 X chunks, partial sums) reuses [off_th, off_y)
+    if ((int64_t)m.dk * SP * 4 + 2LL * SC * m.Dp * 4 + 8LL * SP * 8 > L.off_y) return cudaErrorInvalidValue;
+    const int bytes = L.total;
     auto kern = traj_stream_kernel<LOGIT, NP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
