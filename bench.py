@@ -17,6 +17,8 @@ roofline   = the trajectory kernel (dominant): algorithmic FLOPs per launch
              (4 n D per particle-gradient + 2 n D per particle for the endpoint
              energy) / its mean event-timed duration.
 cpu_baseline / --impl reference = the FP64 C oracle on the host cores.
+large_logistic = the n=1e5, D=100, 16384-particle regression on the streamed
+             tensor-core kernel (BF16x2), with its roofline.
 preconditioner = the learned transport map against the plain identity-metric
              sampler on the 8192-particle 100-d Gaussian (condition number
              1e4) and 50-d banana targets: ESS/s, grad-evals/s, acceptance,
@@ -243,6 +245,50 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
     return out
 
 
+def large_logistic_line(g, torch, stream, flush, precision=3):
+    """The large Bayesian logistic regression (n = 1e5 observations, D = 100,
+    correlated features, 16384 particles, 30 iterations) on the streamed
+    tensor-core kernel: one untimed iteration (first launches), then one
+    complete device-timed run with the trajectory launches timed by events
+    inside the library.  Roofline of the trajectory kernel against the
+    sustained BF16 tensor peak: algorithmic FLOPs are 4 n D per gradient
+    (X theta and X' r) plus 2 n D per particle for the FP32 end-point energy."""
+    w = workloads.logistic_large()
+    run = dict(w["run"])
+    K, n, D = run["n_iters"], w["n"], w["D"]
+    md = g.ModelData.from_workload(w)
+    smp = g.Sampler(md, g.make_config(seed=5151, precision=precision, **run), stream)
+    smp.run(1)
+    smp.reset(6161)
+    smp.profile(True)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    smp.run(K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = smp.get_profile()
+    smp.profile(False)
+    summ = smp.summary()[0]
+    N = smp.n_total
+    smp.close()
+    peaks, kind = _peaks()
+    flops = 4.0 * n * D * summ["grad_evals"] + 2.0 * n * D * N * K
+    achieved = flops / (prof["traj_ms"] / 1e3) / 1e12
+    pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    return {"workload": WORKLOAD_DESC["logistic_large"], "precision": ["fp32", "bf16x3", "bf16", "bf16x2"][precision],
+            "value": summ["grad_evals"] / (ms / 1e3), "unit": "particle-grad-evals/s", "ms_per_run": ms,
+            "ess_per_s": summ["ess_sum_post_warmup"] / (ms / 1e3), "log_z": summ["log_z"],
+            "grad_evals": summ["grad_evals"], "traj_share": prof["traj_ms"] / ms,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                         "peak_source": f"bf16 dense sustained, {kind}",
+                         "kernel": "streamed tcgen05 trajectory kernel",
+                         "note": "algorithmic FLOPs; the kernel issues 2 products per GEMM (split state operands) "
+                                 "and pads D=100 to 112"},
+            "l2": "flushed before the run (256 MB write, outside the events)"}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle as it stands, on the host cores, one
     SMC iteration of the workload per step (bounded sample)."""
@@ -291,7 +337,9 @@ WORKLOAD_DESC = {
     "gauss10": "10-d correlated Gaussian, N=256, K=20",
     "hier": "batched hierarchical normal (non-centred, 50 groups x 20 obs, D=52), 64 independent runs with "
             "particle counts uniform on 512..8192 (seeded, 278k particles) in every launch, K=50, eps=0.01, L0=1, FP32",
-    "logistic_large": "logistic regression n=100000 D=100 N=16384 K=30",
+    "logistic_large": "Bayesian logistic regression, synthetic, n=100000, D=100 (N(0,1) features with pairwise "
+                      "correlation 0.3), N=16384 particles, K=30 SMC iterations, eps=1e-3 L0=5 max 500 steps, "
+                      "1-d Halton, streamed tcgen05 BF16x2 gradients",
 }
 
 
@@ -310,6 +358,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precond", action="store_true",
                     help="skip the learned-preconditioner comparison (two 8192-particle targets)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large logistic regression line (n=1e5, D=100, 16384 particles)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -460,6 +510,9 @@ def main():
     precond = None
     if not args.no_precond and world == 1 and args.workload == "logistic":
         precond = precond_compare(g, torch, stream, flush)
+    large = None
+    if not args.no_large and world == 1 and args.workload == "logistic":
+        large = large_logistic_line(g, torch, stream, flush)
 
     # ---------------- end to end through the C-ABI with host buffers
     e2e = None
@@ -537,6 +590,7 @@ def main():
         "e2e": e2e,
         "variants": variants,
         "preconditioner": precond,
+        "large_logistic": large,
         "gpu_launches": prof["kernel_launches"] * args.steps,
         "clocks": clk,
     }
