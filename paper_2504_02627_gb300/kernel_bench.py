@@ -1,0 +1,123 @@
+"""Single-launch kernel timings through the kernel-level entry points (a
+micro-benchmark and the profiling driver for one trajectory kernel at a time).
+
+    python -m paper_2504_02627_gb300.kernel_bench stream --n 20000 --particles 16384 --steps 40
+    python -m paper_2504_02627_gb300.kernel_bench flow --particles 8192 --steps 8
+    python -m paper_2504_02627_gb300.kernel_bench glm --particles 4096 --steps 20
+
+Each run makes seeded synthetic inputs (the workloads of this repository),
+launches one target evaluation and one leapfrog trajectory of `--steps` steps
+for every particle, and prints the event-timed duration of the trajectory
+launch as one JSON line.  Under a profiler, the trajectory launch is the
+second launch of the kernel (skip one with `-s 1`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+
+def _setup():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+    import workloads
+    from . import _binding as B
+    return torch, workloads, B
+
+
+def _time(torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_glm_like(args, streamed):
+    torch, workloads, B = _setup()
+    s = torch.cuda.current_stream().cuda_stream
+    if streamed:
+        w = workloads.logistic_large(n=args.n)
+        prec = args.precision
+    else:
+        w = workloads.logistic()
+        prec = B.PREC_FP32
+    N, D = args.particles, w["D"]
+    dm = B.DevModel(B.ModelData.from_workload(w), s)
+    rng = np.random.default_rng(0)
+    centre = w.get("beta_true", np.zeros(D))
+    th = torch.tensor((centre[None, :] + 0.01 * rng.standard_normal((N, D))).T.astype(np.float32)).cuda()
+    th = th.contiguous()
+    p = torch.randn(D, N, device="cuda")
+    gr = torch.zeros(D, N, device="cuda")
+    lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+    steps = torch.full((N,), args.steps, dtype=torch.int32, device="cuda")
+    lib = B.lib()
+    B.check(lib.smc_k_target(dm.h, th.data_ptr(), N, N, lp.data_ptr(), gr.data_ptr(), prec, s), "smc_k_target")
+    ms = _time(torch, lambda: B.check(lib.smc_k_leapfrog(dm.h, th.data_ptr(), p.data_ptr(), gr.data_ptr(),
+                                                         lp.data_ptr(), steps.data_ptr(), args.eps, N, N, prec, s),
+                                      "smc_k_leapfrog"))
+    n = w["n"]
+    flops = 4.0 * n * D * N * args.steps + 2.0 * n * D * N
+    return {"kernel": "streamed tcgen05" if streamed else "FP32 SIMT GLM", "n": n, "D": D, "particles": N,
+            "steps": args.steps, "precision": prec, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
+
+
+def run_flow(args):
+    torch, workloads, B = _setup()
+    s = torch.cuda.current_stream().cuda_stream
+    w = workloads.gauss100_cond()
+    D, H, L, N = w["D"], args.hidden, args.layers, args.particles
+    dm = B.DevModel(B.ModelData.from_workload(w), s)
+    rng = np.random.default_rng(1)
+    params = workloads.flow_init(D, H, L, seed=5)
+    Dh = D // 2
+    lsz = H * Dh + H + H * H + H + D * H + D
+    for l in range(L):
+        o = l * lsz + H * Dh + H + H * H + H
+        params[o:o + D * H + D] = 0.1 * rng.standard_normal(D * H + D) / np.sqrt(H)
+    par = torch.tensor(params.astype(np.float32)).cuda()
+    th = torch.tensor((0.01 * rng.standard_normal((D, N))).astype(np.float32)).cuda()
+    p = torch.randn(D, N, device="cuda")
+    gr = torch.zeros(D, N, device="cuda")
+    lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+    steps = torch.full((N,), args.steps, dtype=torch.int32, device="cuda")
+    lib = B.lib()
+    B.check(lib.smc_k_target(dm.h, th.data_ptr(), N, N, lp.data_ptr(), gr.data_ptr(), 0, s), "smc_k_target")
+    ms = _time(torch, lambda: B.check(lib.smc_k_flow_leapfrog(dm.h, H, L, par.data_ptr(), th.data_ptr(), p.data_ptr(),
+                                                              gr.data_ptr(), lp.data_ptr(), steps.data_ptr(), args.eps,
+                                                              N, N, None, None, None, s), "smc_k_flow_leapfrog"))
+    per_grad = L * 4.0 * (Dh * H + H * H + H * D) + 2.0 * D * D
+    flops = per_grad * N * (args.steps + 1)
+    return {"kernel": "latent-space flow trajectory (FP32 SIMT)", "D": D, "hidden": H, "layers": L, "particles": N,
+            "steps": args.steps, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("which", choices=["stream", "flow", "glm"])
+    ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
+    ap.add_argument("--particles", type=int, default=16384)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--precision", type=int, default=3, help="stream: 2 (BF16) or 3 (BF16x2)")
+    ap.add_argument("--hidden", type=int, default=128)
+    ap.add_argument("--layers", type=int, default=4)
+    args = ap.parse_args(argv)
+    if args.which == "flow":
+        out = run_flow(args)
+    else:
+        out = run_glm_like(args, streamed=args.which == "stream")
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
