@@ -219,13 +219,18 @@ __global__ void __launch_bounds__(128) traj_thread_kernel(DevModel m, TrajArgs a
 }
 
 // ============================================================ GLM kernel
-// G particles per CTA, 512 threads: thread -> (particle pl = tid % G, slice
-// sl = tid / G); slice sl owns observations i = sl, sl + SL, ... (SL = 512/G).
+// G particles per CTA, NT threads, PP particles per thread: thread ->
+// (particle group pl = tid % (G / PP), slice sl = tid / (G / PP)); the thread
+// carries particles pl, pl + G/PP, ... and slice sl owns observations
+// i = sl, sl + SL, ... (SL = NT / (G / PP)).  One X row loaded from shared
+// memory serves the PP particles of the thread.  The products run over the
+// first DR <= DP dimensions only (DR = D when the dimension is known at
+// compile time, so no padding FMAs).
 constexpr int GLM_THREADS = 512;
 
-template <int DP, int G>
+template <int DP, int G, int NT = GLM_THREADS>
 struct GlmSmem {
-    static constexpr int NW = GLM_THREADS / 32;
+    static constexpr int NW = NT / 32;
     static size_t bytes(int n) {
         size_t npad = (size_t)((n + 3) & ~3);
         return sizeof(float) * ((size_t)n * DP + npad + 3 * DP * G + (size_t)NW * DP * G) +
@@ -249,10 +254,11 @@ __device__ __forceinline__ float glm_loglik_term(float y, float eta, float inv_s
     return -0.5f * z * z;
 }
 
-template <int DP, int G, bool LOGIT>
-__global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, TrajArgs a) {
-    constexpr int NT = GLM_THREADS, NW = NT / 32, SL = NT / G;
+template <int DP, int G, bool LOGIT, int PP = 1, int NT = GLM_THREADS, int DR = DP>
+__global__ void __launch_bounds__(NT, 1) traj_glm_kernel(DevModel m, TrajArgs a) {
+    constexpr int NW = NT / 32, PG = G / PP, SL = NT / PG;
     static_assert(G <= 32 && (32 % G) == 0, "G must divide 32");
+    static_assert(PG * PP == G && DR <= DP, "PP must divide G; DR <= DP");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = m.n, D = m.D;
     const int npad = (n + 3) & ~3;
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, Tr
     int* smax_s = S_s + G;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int pl = tid % G, sl = tid / G;
+    const int pl = tid % PG, sl = tid / PG;
 
     // ---- model data into shared memory (whole trajectory reuses it)
     {
@@ -373,42 +379,56 @@ __global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, Tr
     const int nsteps = a.eval_only ? 1 : smax;
     for (int s = 1; s <= nsteps; ++s) {
         // ---- gradient X'(y - sigmoid(X theta)) for the G particles (phase B)
-        float th[DP], acc[DP];
+        float th[PP][DR], acc[PP][DR];
 #pragma unroll
-        for (int d = 0; d < DP; ++d) {
-            th[d] = th_s[d * G + pl];
-            acc[d] = 0.0f;
-        }
+        for (int k = 0; k < PP; ++k)
+#pragma unroll
+            for (int d = 0; d < DR; ++d) {
+                th[k][d] = th_s[d * G + pl + k * PG];
+                acc[k][d] = 0.0f;
+            }
         for (int i = sl; i < n; i += SL) {
             const float4* xr = reinterpret_cast<const float4*>(Xs + (size_t)i * DP);
-            float4 xv[DP / 4];
-#pragma unroll
-            for (int q = 0; q < DP / 4; ++q) xv[q] = xr[q];
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+            float xf[DP];
 #pragma unroll
             for (int q = 0; q < DP / 4; ++q) {
-                e0 = fmaf(xv[q].x, th[4 * q + 0], e0);
-                e1 = fmaf(xv[q].y, th[4 * q + 1], e1);
-                e2 = fmaf(xv[q].z, th[4 * q + 2], e2);
-                e3 = fmaf(xv[q].w, th[4 * q + 3], e3);
+                const float4 v = xr[q];
+                xf[4 * q] = v.x;
+                xf[4 * q + 1] = v.y;
+                xf[4 * q + 2] = v.z;
+                xf[4 * q + 3] = v.w;
             }
-            const float r = glm_resid<LOGIT>(ys[i], (e0 + e1) + (e2 + e3), inv_s2);
+            const float yi = ys[i];
+            float r[PP];
 #pragma unroll
-            for (int q = 0; q < DP / 4; ++q) {
-                acc[4 * q + 0] = fmaf(r, xv[q].x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(r, xv[q].y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(r, xv[q].z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(r, xv[q].w, acc[4 * q + 3]);
+            for (int k = 0; k < PP; ++k) {
+                float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < DR; d += 4) {
+                    e0 = fmaf(xf[d], th[k][d], e0);
+                    if (d + 1 < DR) e1 = fmaf(xf[d + 1], th[k][d + 1], e1);
+                    if (d + 2 < DR) e2 = fmaf(xf[d + 2], th[k][d + 2], e2);
+                    if (d + 3 < DR) e3 = fmaf(xf[d + 3], th[k][d + 3], e3);
+                }
+                r[k] = glm_resid<LOGIT>(yi, (e0 + e1) + (e2 + e3), inv_s2);
             }
+#pragma unroll
+            for (int k = 0; k < PP; ++k)
+#pragma unroll
+                for (int d = 0; d < DR; ++d) acc[k][d] = fmaf(r[k], xf[d], acc[k][d]);
         }
 #pragma unroll
-        for (int o = G; o < 32; o <<= 1) {
+        for (int o = PG; o < 32; o <<= 1) {
 #pragma unroll
-            for (int d = 0; d < DP; ++d) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+            for (int k = 0; k < PP; ++k)
+#pragma unroll
+                for (int d = 0; d < DR; ++d) acc[k][d] += __shfl_xor_sync(0xffffffffu, acc[k][d], o);
         }
-        if (lane < G) {
+        if (lane < PG) {
 #pragma unroll
-            for (int d = 0; d < DP; ++d) red[(wid * DP + d) * G + pl] = acc[d];
+            for (int k = 0; k < PP; ++k)
+#pragma unroll
+                for (int d = 0; d < DR; ++d) red[(wid * DP + d) * G + pl + k * PG] = acc[k][d];
         }
         __syncthreads();
         // ---- reduce, closing half kick of step s, opening kick + drift of s+1 (phase C)
@@ -437,26 +457,45 @@ __global__ void __launch_bounds__(GLM_THREADS, 1) traj_glm_kernel(DevModel m, Tr
 
     // ---- endpoint log pi in FP64 accumulation (energy error, Eq. for alpha)
     {
-        float th[DP];
+        float th[PP][DR];
 #pragma unroll
-        for (int d = 0; d < DP; ++d) th[d] = th_s[d * G + pl];
-        double ll = 0.0;
+        for (int k = 0; k < PP; ++k)
+#pragma unroll
+            for (int d = 0; d < DR; ++d) th[k][d] = th_s[d * G + pl + k * PG];
+        double ll[PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) ll[k] = 0.0;
         for (int i = sl; i < n; i += SL) {
             const float4* xr = reinterpret_cast<const float4*>(Xs + (size_t)i * DP);
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+            float xf[DP];
 #pragma unroll
             for (int q = 0; q < DP / 4; ++q) {
-                float4 x = xr[q];
-                e0 = fmaf(x.x, th[4 * q + 0], e0);
-                e1 = fmaf(x.y, th[4 * q + 1], e1);
-                e2 = fmaf(x.z, th[4 * q + 2], e2);
-                e3 = fmaf(x.w, th[4 * q + 3], e3);
+                const float4 v = xr[q];
+                xf[4 * q] = v.x;
+                xf[4 * q + 1] = v.y;
+                xf[4 * q + 2] = v.z;
+                xf[4 * q + 3] = v.w;
             }
-            ll += (double)glm_loglik_term<LOGIT>(ys[i], (e0 + e1) + (e2 + e3), inv_s);
+#pragma unroll
+            for (int k = 0; k < PP; ++k) {
+                float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < DR; d += 4) {
+                    e0 = fmaf(xf[d], th[k][d], e0);
+                    if (d + 1 < DR) e1 = fmaf(xf[d + 1], th[k][d + 1], e1);
+                    if (d + 2 < DR) e2 = fmaf(xf[d + 2], th[k][d + 2], e2);
+                    if (d + 3 < DR) e3 = fmaf(xf[d + 3], th[k][d + 3], e3);
+                }
+                ll[k] += (double)glm_loglik_term<LOGIT>(ys[i], (e0 + e1) + (e2 + e3), inv_s);
+            }
         }
 #pragma unroll
-        for (int o = G; o < 32; o <<= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-        if (lane < G) red64[wid * G + pl] = ll;
+        for (int o = PG; o < 32; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < PP; ++k) ll[k] += __shfl_xor_sync(0xffffffffu, ll[k], o);
+        if (lane < PG)
+#pragma unroll
+            for (int k = 0; k < PP; ++k) red64[wid * G + pl + k * PG] = ll[k];
         __syncthreads();
         if (tid < G) {
             double s = 0.0;
@@ -739,25 +778,26 @@ cudaError_t dispatch_thread_wide(const DevModel& m, const TrajArgs& a, cudaStrea
     return cudaErrorInvalidValue;
 }
 
-template <int DP, int G, bool LOGIT>
+template <int DP, int G, bool LOGIT, int PP = 1, int NT = GLM_THREADS, int DR = DP>
 cudaError_t launch_glm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
-    const size_t sm = GlmSmem<DP, G>::bytes(m.n);
-    auto kern = traj_glm_kernel<DP, G, LOGIT>;
+    const size_t sm = GlmSmem<DP, G, NT>::bytes(m.n);
+    auto kern = traj_glm_kernel<DP, G, LOGIT, PP, NT, DR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int64_t grid = (a.N + G - 1) / G;
     if (grid == 0) return cudaSuccess;
-    kern<<<(unsigned)grid, GLM_THREADS, sm, s>>>(m, a);
+    kern<<<(unsigned)grid, NT, sm, s>>>(m, a);
     return cudaGetLastError();
 }
 
 template <bool LOGIT>
 cudaError_t dispatch_glm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     switch (m.Dp) {
-        case 4: return launch_glm<4, 16, LOGIT>(m, a, s);
-        case 8: return launch_glm<8, 16, LOGIT>(m, a, s);
-        case 16: return launch_glm<16, 16, LOGIT>(m, a, s);
-        case 28: return launch_glm<28, 16, LOGIT>(m, a, s);
+        case 4: return launch_glm<4, 16, LOGIT, 2, 384>(m, a, s);
+        case 8: return launch_glm<8, 16, LOGIT, 2, 384>(m, a, s);
+        case 16: return launch_glm<16, 16, LOGIT, 2, 384>(m, a, s);
+        case 28:   // two particles per thread; the 25-dimensional regression without padding FMAs
+            return m.D == 25 ? launch_glm<28, 16, LOGIT, 2, 384, 25>(m, a, s) : launch_glm<28, 16, LOGIT, 2, 384>(m, a, s);
         case 32: return launch_glm<32, 16, LOGIT>(m, a, s);
         default: return cudaErrorInvalidValue;
     }
