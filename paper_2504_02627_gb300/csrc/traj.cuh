@@ -88,6 +88,10 @@ bool traj_tc_supported(const DevModel& m);
 cudaError_t launch_traj_tc(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
 // streamed tensor-core path (traj_tc_stream.cu): any n, D <= 128; np = 1
 // (BF16 state operands) or 2 (state operands split into BF16 hi + lo)
+// FP32 SIMT path for regression data that do not fit in shared memory
+// (traj_glm_stream.cu): X streamed in chunks, D <= 128
+bool traj_glm_stream_supported(const DevModel& m);
+cudaError_t launch_traj_glm_stream(const DevModel& m, const TrajArgs& a, cudaStream_t s);
 bool traj_stream_supported(const DevModel& m);
 cudaError_t launch_traj_stream(const DevModel& m, const TrajArgs& a, int np, cudaStream_t s);
 

@@ -839,7 +839,7 @@ bool traj_supported(const DevModel& m, int32_t precision) {
         case BANANA: return precision == 0 && m.D <= 64;
         case HIER_NORMAL: return precision == 0 && m.D <= 64;
         case LOGISTIC:
-        case LINEAR_GAUSS: return precision == 0 && glm_shape_ok(m);
+        case LINEAR_GAUSS: return precision == 0 && (glm_shape_ok(m) || traj_glm_stream_supported(m));
         default: return false;
     }
 }
@@ -854,8 +854,10 @@ cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision,
         case GAUSS_DENSE: return m.D <= 32 ? dispatch_thread<GaussDenseM>(m, a, s) : dispatch_dense(m, a, s);
         case BANANA: return dispatch_thread_wide<BananaM>(m, a, s);
         case HIER_NORMAL: return dispatch_thread_wide<HierM>(m, a, s);
-        case LOGISTIC: return dispatch_glm<true>(m, a, s);
-        case LINEAR_GAUSS: return dispatch_glm<false>(m, a, s);
+        case LOGISTIC:
+            return glm_shape_ok(m) ? dispatch_glm<true>(m, a, s) : launch_traj_glm_stream(m, a, s);
+        case LINEAR_GAUSS:
+            return glm_shape_ok(m) ? dispatch_glm<false>(m, a, s) : launch_traj_glm_stream(m, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

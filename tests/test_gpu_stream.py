@@ -10,6 +10,9 @@ accumulation.  The end-point log pi, which enters the importance weight, is
 compared with the oracle on the FP32 data themselves.  Shapes cover ragged
 observation chunks, ragged particle tiles, D = 7 .. 128 and the full
 1e5-observation, 100-dimensional, 16384-particle launch.
+
+The plain FP32 streamed kernel (precision 0 when X does not fit in shared
+memory) is compared with the oracle on the FP32 data, at the same shapes.
 """
 import numpy as np
 import pytest
@@ -195,4 +198,101 @@ def test_streamed_eval_is_deterministic_and_tile_independent():
         out.append((gr, lp))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+    dm.close()
+
+
+# ------------------------------------------------------------- FP32 streamed path
+# The plain FP32 kernel for data that do not fit in shared memory streams the
+# FP32 data themselves, so it is compared with the oracle on the same FP32
+# data: FP32 accumulation error of a few 2^-20 of the summand scale.
+FP32_GRAD_TOL = 2e-5
+
+
+def _fp32_cases():
+    return {
+        "logistic_mid": workloads.logistic_large(n=3000, D=100),            # D=100: quarters of 28
+        "logistic_d128": workloads.logistic_large(n=500, D=128),            # too wide for the resident kernel
+        "logistic_n3000_d25": workloads.logistic(n=3000, d_features=24),    # X too large for shared memory
+        "linear_n5000": workloads.linear_gauss(n=5000, D=6),
+    }
+
+
+@pytest.mark.parametrize("name", ["logistic_mid", "logistic_d128", "logistic_n3000_d25", "linear_n5000"])
+@pytest.mark.parametrize("N", [1, 45, 300])
+def test_fp32_streamed_target_value_and_gradient(name, N):
+    w = rounded_workload(_fp32_cases()[name])
+    t = oracle_target(w)
+    dm = g.DevModel(g.ModelData.from_workload(w), stream())
+    th = _theta(w, N)
+    ld = ((N + 31) // 32) * 32
+    t_d = _dev_state(th, ld)
+    g_d = torch.zeros_like(t_d)
+    lp_d = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    g.check(g.lib().smc_k_target(dm.h, ptr(t_d), N, ld, ptr(lp_d), ptr(g_d), B.PREC_FP32, stream()), "target")
+    lp_g, gr_g = lp_d.cpu().numpy()[:N], g_d.cpu().numpy()[:, :N].T
+    lp_o, gr_o = oracle.logpi(t, th)
+    gs, ls = _summand_scale(w, th)
+    err = np.abs(gr_g - gr_o) / (FP32_GRAD_TOL * gs + 1e-6)
+    assert err.max() <= 1.0, err.max()
+    assert np.all(np.abs(lp_g - lp_o) <= 1e-5 * ls), np.max(np.abs(lp_g - lp_o) / ls)
+    dm.close()
+
+
+@pytest.mark.parametrize("name,eps", [("logistic_mid", 2e-3), ("logistic_n3000_d25", 1e-3), ("linear_n5000", 2e-3)])
+def test_fp32_streamed_leapfrog_trajectories(name, eps):
+    """Ragged step counts 1..6 against the oracle's leapfrog on the same FP32
+    data: per step 1e-5 relative, plus what the FP32 gradient error moves."""
+    w = rounded_workload(_fp32_cases()[name])
+    t = oracle_target(w)
+    dm = g.DevModel(g.ModelData.from_workload(w), stream())
+    N = 173
+    th = _theta(w, N, seed=5)
+    p = f32r(np.random.default_rng(9).standard_normal((N, w["D"])))
+    S = np.random.default_rng(10).integers(1, 7, N).astype(np.int32)
+    ld = 192
+    t_d, p_d = _dev_state(th, ld), _dev_state(p, ld)
+    g_d = torch.zeros_like(t_d)
+    lp_d = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    g.check(g.lib().smc_k_target(dm.h, ptr(t_d), N, ld, ptr(lp_d), ptr(g_d), B.PREC_FP32, stream()), "target")
+    s_d = dev(S)
+    g.check(g.lib().smc_k_leapfrog(dm.h, ptr(t_d), ptr(p_d), ptr(g_d), ptr(lp_d), ptr(s_d), eps, N, ld,
+                                   B.PREC_FP32, stream()), "leapfrog")
+    th_g = t_d.cpu().numpy()[:, :N].T.astype(np.float64)
+    p_g = p_d.cpu().numpy()[:, :N].T.astype(np.float64)
+    lp_g = lp_d.cpu().numpy()[:N]
+    th_o, p_o, _, _ = oracle.leapfrog(t, th, p, eps, S)
+    gs0, _ = _summand_scale(w, th)
+    gs1, _ = _summand_scale(w, th_o)
+    dg = FP32_GRAD_TOL * np.maximum(gs0, gs1) + 1e-6
+    Sc = S[:, None].astype(np.float64)
+    rms = lambda a: np.sqrt(np.mean(a**2))
+    tol_p = Sc * eps * dg + 1e-5 * Sc * (np.abs(p_o) + rms(p_o))
+    tol_t = Sc**2 * eps**2 * dg + 1e-5 * Sc * (np.abs(th_o) + rms(th_o))
+    assert np.all(np.abs(p_g - p_o) <= tol_p), np.max(np.abs(p_g - p_o) / tol_p)
+    assert np.all(np.abs(th_g - th_o) <= tol_t), np.max(np.abs(th_g - th_o) / tol_t)
+    lp_at_g, _ = oracle.logpi(t, th_g)
+    _, ls = _summand_scale(w, th_g)
+    assert np.all(np.abs(lp_g - lp_at_g) <= 1e-5 * ls)
+    dm.close()
+
+
+def test_fp32_streamed_full_size_launch_on_sampled_particles():
+    """n = 1e5, D = 100, 16384 particles (256 CTAs of 64): gradients and
+    log pi of 24 sampled particles against the oracle."""
+    w = rounded_workload(workloads.logistic_large())
+    dm = g.DevModel(g.ModelData.from_workload(w), stream())
+    N = 16384
+    th = _theta(w, N, seed=7)
+    t_d = _dev_state(th, N)
+    g_d = torch.zeros_like(t_d)
+    lp_d = torch.zeros(N, dtype=torch.float64, device="cuda")
+    g.check(g.lib().smc_k_target(dm.h, ptr(t_d), N, N, ptr(lp_d), ptr(g_d), B.PREC_FP32, stream()), "target")
+    idx = np.sort(np.random.default_rng(11).choice(N, 24, replace=False))
+    idx[-1] = N - 1
+    lp_g, gr_g = lp_d.cpu().numpy()[idx], g_d.cpu().numpy()[:, idx].T
+    lp_o, gr_o = oracle.logpi(oracle_target(w), th[idx])
+    gs, ls = _summand_scale(w, th[idx])
+    err = np.abs(gr_g - gr_o) / (FP32_GRAD_TOL * gs + 1e-6)
+    assert err.max() <= 1.0, err.max()
+    assert np.all(np.abs(lp_g - lp_o) <= 1e-5 * ls)
     dm.close()
