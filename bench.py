@@ -277,7 +277,27 @@ def large_logistic_line(g, torch, stream, flush, precision=3):
     flops = 4.0 * n * D * summ["grad_evals"] + 2.0 * n * D * N * K
     achieved = flops / (prof["traj_ms"] / 1e3) / 1e12
     pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    # chosen vs plain on the same first iterations: the FP32 streamed kernel
+    # is ~16x slower per step, so both arms run the first `k_cmp` iterations
+    k_cmp = 2
+    cmp = {}
+    for name, prec in (("bf16x2", precision), ("fp32", 0)):
+        sv = g.Sampler(md, g.make_config(seed=5151, precision=prec, **run), stream)
+        flush.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        sv.run(k_cmp)
+        c1.record()
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        sm_ = sv.summary()[0]
+        sv.close()
+        cmp[name] = {"ms": cms, "grad_evals": sm_["grad_evals"], "value": sm_["grad_evals"] / (cms / 1e3),
+                     "unit": "particle-grad-evals/s"}
+    cmp["iterations"] = k_cmp
+    cmp["note"] = "first iterations of the same run (seed 5151): chosen BF16x2 tensor cores vs plain FP32 SIMT"
     return {"workload": WORKLOAD_DESC["logistic_large"], "precision": ["fp32", "bf16x3", "bf16", "bf16x2"][precision],
+            "chosen_vs_plain": cmp,
             "value": summ["grad_evals"] / (ms / 1e3), "unit": "particle-grad-evals/s", "ms_per_run": ms,
             "ess_per_s": summ["ess_sum_post_warmup"] / (ms / 1e3), "log_z": summ["log_z"],
             "grad_evals": summ["grad_evals"], "traj_share": prof["traj_ms"] / ms,
