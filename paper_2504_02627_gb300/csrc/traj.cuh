@@ -91,6 +91,10 @@ cudaError_t launch_traj_tc(const DevModel& m, const TrajArgs& a, bool x3, cudaSt
 // FP32 SIMT path for regression data that do not fit in shared memory
 // (traj_glm_stream.cu): X streamed in chunks, D <= 128
 bool traj_glm_stream_supported(const DevModel& m);
+// warp-level BF16 tensor-core path with X resident in shared memory
+// (traj_glm_mma.cu): D <= 32, n up to about 1300 (x3) / 2400 (BF16)
+bool traj_glm_mma_supported(const DevModel& m, bool x3);
+cudaError_t launch_traj_glm_mma(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
 cudaError_t launch_traj_glm_stream(const DevModel& m, const TrajArgs& a, cudaStream_t s);
 bool traj_stream_supported(const DevModel& m);
 cudaError_t launch_traj_stream(const DevModel& m, const TrajArgs& a, int np, cudaStream_t s);

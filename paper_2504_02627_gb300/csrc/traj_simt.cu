@@ -831,8 +831,8 @@ bool glm_shape_ok(const DevModel& m) {
 }  // namespace
 
 bool traj_supported(const DevModel& m, int32_t precision) {
-    if (precision == 1) return traj_tc_supported(m);
-    if (precision == 2) return traj_tc_supported(m) || traj_stream_supported(m);
+    if (precision == 1) return traj_glm_mma_supported(m, true) || traj_tc_supported(m);
+    if (precision == 2) return traj_glm_mma_supported(m, false) || traj_tc_supported(m) || traj_stream_supported(m);
     if (precision == 3) return traj_stream_supported(m);
     switch (m.kind) {
         case GAUSS_DENSE: return precision == 0 && m.D <= 128;
@@ -846,9 +846,12 @@ bool traj_supported(const DevModel& m, int32_t precision) {
 
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s) {
     if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
-    if (precision == 1) return launch_traj_tc(m, a, true, s);
-    if (precision == 2)
+    if (precision == 1)
+        return traj_glm_mma_supported(m, true) ? launch_traj_glm_mma(m, a, true, s) : launch_traj_tc(m, a, true, s);
+    if (precision == 2) {
+        if (traj_glm_mma_supported(m, false)) return launch_traj_glm_mma(m, a, false, s);
         return traj_tc_supported(m) ? launch_traj_tc(m, a, false, s) : launch_traj_stream(m, a, 1, s);
+    }
     if (precision == 3) return launch_traj_stream(m, a, 2, s);
     switch (m.kind) {
         case GAUSS_DENSE: return m.D <= 32 ? dispatch_thread<GaussDenseM>(m, a, s) : dispatch_dense(m, a, s);

@@ -46,10 +46,10 @@ def run_glm_like(args, streamed):
     s = torch.cuda.current_stream().cuda_stream
     if streamed:
         w = workloads.logistic_large(n=args.n)
-        prec = args.precision
+        prec = B.PREC_BF16X2 if args.precision is None else args.precision
     else:
         w = workloads.logistic()
-        prec = B.PREC_FP32
+        prec = B.PREC_FP32 if args.precision is None else args.precision
     N, D = args.particles, w["D"]
     dm = B.DevModel(B.ModelData.from_workload(w), s)
     rng = np.random.default_rng(0)
@@ -67,7 +67,8 @@ def run_glm_like(args, streamed):
                                       "smc_k_leapfrog"))
     n = w["n"]
     flops = 4.0 * n * D * N * args.steps + 2.0 * n * D * N
-    return {"kernel": "streamed tcgen05" if streamed else "FP32 SIMT GLM", "n": n, "D": D, "particles": N,
+    kname = "streamed tcgen05" if streamed else ("FP32 SIMT GLM" if prec == 0 else "warp-MMA GLM")
+    return {"kernel": kname, "n": n, "D": D, "particles": N,
             "steps": args.steps, "precision": prec, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
@@ -108,7 +109,8 @@ def main(argv=None):
     ap.add_argument("--particles", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--eps", type=float, default=1e-4)
-    ap.add_argument("--precision", type=int, default=3, help="stream: 2 (BF16) or 3 (BF16x2)")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="stream: 2 (BF16) or 3 (BF16x2, default); glm: 0 (FP32, default), 1 (BF16x3) or 2 (BF16)")
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)
     args = ap.parse_args(argv)

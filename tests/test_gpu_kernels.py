@@ -67,6 +67,12 @@ def _workloads():
         "gauss10": workloads.gauss10(),
         "logistic": workloads.logistic(),                              # n=1000, D=25
         "logistic_small": workloads.logistic(n=37, d_features=4),
+        "logistic_d4": workloads.logistic(n=123, d_features=3),        # Dp=4
+        "logistic_d12": workloads.logistic(n=400, d_features=11),      # Dp=16
+        "logistic_d28": workloads.logistic(n=500, d_features=27),      # Dp=28, no padding column
+        "logistic_n1300": workloads.logistic(n=1300),
+        "logistic_n1700": workloads.logistic(n=1700),                  # x3 operands too large for one CTA
+        "linear_d25": workloads.linear_gauss(n=700, D=25),
         "linear": workloads.linear_gauss(n=200, D=6),
         "hier": workloads.hier(),                                      # 50 groups, D=52
         "banana50": workloads.banana50(),
@@ -145,7 +151,8 @@ def _summand_scale(w, th):
     return gs, (0.5 * xo**2 / a + 0.5 * u**2).sum(1) + 10.0
 
 
-@pytest.mark.parametrize("name", ["gauss10", "logistic", "logistic_small", "linear", "hier", "banana50",
+@pytest.mark.parametrize("name", ["gauss10", "logistic", "logistic_small", "logistic_d4", "logistic_d12",
+                                  "logistic_d28", "logistic_n1300", "linear", "linear_d25", "hier", "banana50",
                                   "banana2", "gauss100", "illcond100"])
 @pytest.mark.parametrize("N", [1, 45, 300])
 def test_target_value_and_gradient(name, N):
@@ -183,7 +190,9 @@ def _rms(a):
 
 
 @pytest.mark.parametrize("name,eps", [("gauss10", 0.1), ("logistic", 1e-3), ("logistic_small", 0.01),
-                                      ("linear", 0.005), ("hier", 0.05), ("banana50", 0.01),
+                                      ("logistic_d4", 0.005), ("logistic_d12", 0.002), ("logistic_d28", 0.002),
+                                      ("logistic_n1300", 1e-3), ("linear", 0.005), ("linear_d25", 1e-3),
+                                      ("hier", 0.05), ("banana50", 0.01),
                                       ("banana2", 0.01), ("gauss100", 0.01), ("illcond100", 1e-3)])
 def test_one_leapfrog_step_within_1e5(name, eps):
     w = rounded_workload(_workloads()[name])
@@ -219,6 +228,32 @@ def test_ragged_trajectories(name, eps):
         np.testing.assert_allclose(p_g[j], p_o[j], rtol=tol, atol=tol * _rms(p_o[j]))
     _, ls = _summand_scale(w, th_o)
     assert np.all(np.abs(lp_g - lp_o) <= 1e-5 * steps.clip(1) * ls)
+
+
+@pytest.mark.parametrize("name", ["logistic", "linear_d25"])
+@pytest.mark.parametrize("N", [4096, 20000])
+def test_glm_trajectories_many_particles(name, N):
+    """The regression kernels at the particle counts of the benchmark and
+    above (several particle pairs per CTA, every CTA count regime): ragged
+    step counts 0..8, a seeded sample of 150 particles against the oracle."""
+    w = rounded_workload(_workloads()[name])
+    t = oracle_target(w)
+    dm = _model(w)
+    rng = np.random.default_rng(N)
+    th = _theta(w, N, seed=N + 1)
+    p = f32r(rng.standard_normal((N, w["D"])))
+    steps = rng.integers(0, 9, N)
+    eps = 1e-3
+    th_g, p_g, lp_g = _leapfrog_gpu(dm, th, p, steps, eps)
+    idx = np.sort(rng.choice(N, 150, replace=False))
+    idx[-1] = N - 1                                         # the ragged tail
+    th_o, p_o, _, lp_o = oracle.leapfrog(t, th[idx], p[idx], eps, steps[idx])
+    for a, j in enumerate(idx):
+        tol = 1e-5 * max(1, steps[j])
+        np.testing.assert_allclose(th_g[j], th_o[a], rtol=tol, atol=tol * _rms(th_o[a]))
+        np.testing.assert_allclose(p_g[j], p_o[a], rtol=tol, atol=tol * _rms(p_o[a]))
+    _, ls = _summand_scale(w, th_o)
+    assert np.all(np.abs(lp_g[idx] - lp_o) <= 1e-5 * steps[idx].clip(1) * ls)
 
 
 # ------------------------------------------------------------- weights
@@ -285,7 +320,8 @@ TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("name", ["logistic_small", "logistic", "linear"])
+@pytest.mark.parametrize("name", ["logistic_small", "logistic", "linear", "logistic_d28", "linear_d25",
+                                  "logistic_n1700"])
 @pytest.mark.parametrize("N", [1, 45, 300])
 def test_tc_target_value_and_gradient(name, N, precision):
     w = rounded_workload(_workloads()[name])
@@ -308,14 +344,18 @@ def test_tc_target_value_and_gradient(name, N, precision):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("name,eps", [("logistic", 1e-3), ("logistic_small", 0.01), ("linear", 0.005)])
-def test_tc_one_leapfrog_step(name, eps, precision):
+@pytest.mark.parametrize("name,eps,N", [("logistic", 1e-3, 257), ("logistic_small", 0.01, 257),
+                                        ("linear", 0.005, 257), ("logistic_d28", 0.002, 257),
+                                        ("linear_d25", 1e-3, 257), ("logistic_n1700", 1e-3, 257),
+                                        ("logistic", 1e-3, 4096), ("logistic", 1e-3, 20000)])
+def test_tc_one_leapfrog_step(name, eps, N, precision):
     """One step: theta_1 = theta_0 + eps (p_0 + eps/2 g_0), p_1 = p_0 + eps/2 (g_0 + g_1);
-    a gradient error dg moves p by at most eps*dg and theta by eps^2/2 dg."""
+    a gradient error dg moves p by at most eps*dg and theta by eps^2/2 dg.  At the
+    benchmark's particle count and above, a seeded sample of 200 particles is
+    checked (every CTA handles the same arithmetic)."""
     w = rounded_workload(_workloads()[name])
     t = oracle_target(w)
     dm = _model(w)
-    N = 257
     th = _theta(w, N)
     p = f32r(np.random.default_rng(9).standard_normal((N, w["D"])))
     ld = ((N + 31) // 32) * 32
@@ -333,6 +373,10 @@ def test_tc_one_leapfrog_step(name, eps, precision):
     th_g = t_d.cpu().numpy()[:, :N].T.astype(np.float64)
     p_g = p_d.cpu().numpy()[:, :N].T.astype(np.float64)
     lp_g = lp_d.cpu().numpy()[:N]
+    if N > 1000:
+        idx = np.sort(np.random.default_rng(N).choice(N, 200, replace=False))
+        idx[-1] = N - 1
+        th, p, th_g, p_g, lp_g = th[idx], p[idx], th_g[idx], p_g[idx], lp_g[idx]
     th_o, p_o, _, lp_o = oracle.leapfrog(t, th, p, eps, 1)
     gs0, _ = _summand_scale(w, th)
     gs1, ls1 = _summand_scale(w, th_o)
