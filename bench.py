@@ -72,6 +72,51 @@ def _workload(name):
     raise ValueError(name)
 
 
+def _timed_runs(torch, smp, K, seeds, flush):
+    """One full sampler run per seed, each bracketed by CUDA events on the
+    sampler's stream after an L2 flush; returns (device ms, gradient
+    evaluations, post-warm-up ESS sum, log Z per run)."""
+    ms, ge, ess, lz = 0.0, 0, 0.0, []
+    for sd in seeds:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        smp.reset(sd)
+        smp.run(K)                              # smc_run replays CUDA graphs
+        e1.record()
+        summ = smp.summary()                    # synchronises after the step; outside the events
+        ms += e0.elapsed_time(e1)
+        ge += sum(x["grad_evals"] for x in summ)
+        ess += sum(x["ess_sum_post_warmup"] for x in summ)
+        lz.append(summ[0]["log_z"])
+    torch.cuda.synchronize()
+    return ms, ge, ess, lz
+
+
+def _profiled_run(smp, K, seed, flush):
+    """Trajectory-kernel time and launch count: one more run with in-library
+    events around every trajectory launch (no graphs), outside the timed region."""
+    smp.profile(True)
+    flush.zero_()
+    smp.reset(seed)
+    smp.run(K)
+    ge = sum(x["grad_evals"] for x in smp.summary())
+    prof = smp.get_profile()
+    smp.profile(False)
+    return prof, ge
+
+
+def _mma_flops_per_grad(w, prec):
+    """MMA FLOPs the warp-level tensor-core kernel issues per gradient (two
+    products over the padded dimension 32 and observations padded to 16, three
+    BF16 products each in the compensated form) and per end point (none: the
+    end point is FP32)."""
+    if w["kind"] not in ("logistic", "linear_gauss") or w["D"] > 32 or prec not in (1, 2):
+        return None
+    n16 = -(-w["n"] // 16) * 16
+    return 2 * 2.0 * 32 * n16 * (3 if prec == 1 else 1), 0.0
+
+
 def _flops_per_grad(w):
     if w["kind"] in ("logistic", "linear_gauss"):
         return 4.0 * w["n"] * w["D"], 2.0 * w["n"] * w["D"]
@@ -370,9 +415,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="logistic")
-    ap.add_argument("--precision", type=int, default=0,
-                    help="0: FP32 SIMT, 1: tcgen05 BF16x3, 2: tcgen05 BF16 (the timed main line)")
-    ap.add_argument("--variants", default="0,1,2",
+    ap.add_argument("--precision", type=int, default=None,
+                    help="timed main line: 0 FP32 SIMT, 1 BF16x3 tensor cores (compensated), 2 BF16 tensor "
+                         "cores; default: the chosen form, BF16x3 where the model has a tensor-core kernel, "
+                         "else FP32")
+    ap.add_argument("--variants", default="2",
                     help="precisions also measured (fewer steps) and reported under 'variants'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -417,17 +464,22 @@ def main():
         return [g.make_config(seed=seed0 + r, precision=precision, **dict(run, n_particles=int(nr)))
                 for r, nr in enumerate(w["run_sizes"])]
 
-    smp = g.Sampler(md, make_configs(1000 + 1000 * rank, args.precision), stream)
+    prec = args.precision
+    if prec is None:
+        prec = 1
+        try:
+            g.Sampler(md, make_configs(1, 1), stream).close()
+        except RuntimeError:
+            prec = 0    # no tensor-core kernel for this model: the chosen form is FP32
+    smp = g.Sampler(md, make_configs(1000 + 1000 * rank, prec), stream)
     n_runs = smp.n_runs
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-
-    def one_run(seed):
-        smp.reset(seed)
-        smp.run(K)
+    seeds = [20_000 + 1000 * rank + i for i in range(args.steps)]
 
     for i in range(args.warmup):
-        one_run(10_000 + 1000 * rank + i)
+        smp.reset(10_000 + 1000 * rank + i)
+        smp.run(K)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -436,30 +488,11 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ge_total, ess_post, lz = 0, 0.0, []
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record()
-        one_run(20_000 + 1000 * rank + i)      # smc_run replays CUDA graphs
-        ev[i][1].record()
-        summ = smp.summary()                    # synchronises after the step; outside the events
-        ge_total += sum(x["grad_evals"] for x in summ)
-        ess_post += sum(x["ess_sum_post_warmup"] for x in summ)
-        lz.append(summ[0]["log_z"])
-    torch.cuda.synchronize()
+    dev_ms, ge_total, ess_post, lz = _timed_runs(torch, smp, K, seeds, flush)
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
-    # trajectory-kernel timing and launch count: one more run with in-library
-    # events around every trajectory launch (no graphs), outside the timed region
-    smp.profile(True)
-    flush.zero_()
-    one_run(30_000 + rank)
-    prof_ge = sum(x["grad_evals"] for x in smp.summary())
-    prof = smp.get_profile()
-    smp.profile(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof, prof_ge = _profiled_run(smp, K, 30_000 + rank, flush)
     t = torch.tensor([dev_ms, float(ge_total), ess_post], dtype=torch.float64, device="cuda")
     if dist:
         tmax = t.clone()
@@ -471,10 +504,35 @@ def main():
         ge_all, ess_all = float(ge_total), ess_post
     value = ge_all / (dev_ms / 1e3)
 
-    # ---------------- other precisions of the same workload (plain FP32 vs tensor-core forms)
+    # ---------------- plain FP32 on the same seeds: the comparison the metric names
+    plain = None
+    if prec != 0:
+        sp = g.Sampler(md, make_configs(1000 + 1000 * rank, 0), stream)
+        sp.reset(10_000 + 1000 * rank)
+        sp.run(K)
+        torch.cuda.synchronize()
+        p_ms, p_ge, p_ess, p_lz = _timed_runs(torch, sp, K, seeds, flush)
+        p_prof, p_prof_ge = _profiled_run(sp, K, 30_000 + rank, flush)
+        sp.close()
+        fl_grad, fl_end = _flops_per_grad(w)
+        p_flops = fl_grad * p_prof_ge + fl_end * smp.n_total * K
+        p_ach = p_flops / (p_prof["traj_ms"] / 1e3) / 1e12
+        d = np.asarray(lz) - np.asarray(p_lz)
+        plain = {"value": p_ge / (p_ms / 1e3), "unit": "particle-grad-evals/s", "ms_per_step": p_ms / len(seeds),
+                 "ess_per_s": p_ess / (p_ms / 1e3),
+                 "log_z": {"mean": float(np.mean(p_lz)), "sd": float(np.std(p_lz, ddof=1)) if len(p_lz) > 1 else None},
+                 "roofline": {"bound": "alu", "achieved": p_ach, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": p_ach / FP32_FMA_PEAK_TFLOPS, "kernel": "FP32 SIMT trajectory kernel"},
+                 "log_z_paired_diff": {"mean": float(np.mean(d)),
+                                       "sd": float(np.std(d, ddof=1)) if len(d) > 1 else None,
+                                       "note": "chosen minus plain, same seeds (same initial particles and "
+                                               "momentum streams); compare with the between-seed sd"},
+                 "seeds": "the timed seeds of the main line"}
+
+    # ---------------- other precisions of the same workload (tensor-core forms)
     variants = {}
     for pv in [int(x) for x in args.variants.split(",") if x.strip() != ""]:
-        if pv == args.precision:
+        if pv == prec or pv == 0:
             continue
         try:
             sv = g.Sampler(md, make_configs(1000 + 1000 * rank, pv), stream)
@@ -509,16 +567,22 @@ def main():
     traj_ms = prof["traj_ms"]
     traj_n = max(1, prof["traj_launches"])
     achieved = traj_flops / traj_n / (traj_ms / traj_n / 1e3) / 1e12
-    if args.precision == 0:
+    if prec == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_FMA_PEAK_TFLOPS,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (max SM clock)"}
         kfile = "traj_simt.cu"
     else:
-        pk = peaks["bf16_tflops"]
+        # a kernel inside a long step: the sustained bf16 peak
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "peak_source": f"bf16 dense, {peak_kind}"}
-        kfile = "traj_tc.cu"
+                "peak_source": f"bf16 dense sustained, {peak_kind}"}
+        kfile = "traj_glm_mma.cu" if w["kind"] in ("logistic", "linear_gauss") and w["D"] <= 32 else "traj_tc.cu"
+        ex = _mma_flops_per_grad(w, prec)
+        if ex is not None:
+            roof["executed"] = (ex[0] * prof_ge + ex[1] * n_part * K) / (traj_ms / 1e3) / 1e12
+            roof["executed_note"] = ("MMA FLOP/s actually issued: the three BF16 products of the compensated "
+                                     "form, the dimension padded to 32 and the observations to 16")
     tr = _traffic_for(kfile)
     roof["traffic"] = tr
     roof["kernel"] = "trajectory (leapfrog) kernel"
@@ -551,7 +615,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = C.c_void_p()
-            c2 = make_configs(30_000 + 100 * i + 1000 * rank, args.precision)
+            c2 = make_configs(30_000 + 100 * i + 1000 * rank, prec)
             if batched:
                 arr = (g._binding.SmcConfig * len(c2))(*c2)
                 g.check(lib.smc_init_batch(C.byref(h), len(c2), arr, C.byref(md.struct), C.c_void_p(stream)),
@@ -596,10 +660,10 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == 0 else "bf16",
+        "dtype": "f32" if prec == 0 else "bf16",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[args.workload], "step": f"one full sampler run ({K} iterations)",
-                   "precision": ["fp32", "bf16x3", "bf16"][args.precision],
+                   "precision": ["fp32", "bf16x3", "bf16"][prec],
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "ess_per_s": {"value": ess_all / (dev_ms / 1e3), "unit": "ESS/s",
@@ -608,6 +672,9 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "plain_fp32": plain,
+        "chosen_vs_plain": None if plain is None else {
+            "throughput": value / plain["value"], "ess_per_s": (ess_all / (dev_ms / 1e3)) / plain["ess_per_s"]},
         "variants": variants,
         "preconditioner": precond,
         "large_logistic": large,

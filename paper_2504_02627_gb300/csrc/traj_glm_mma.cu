@@ -45,11 +45,12 @@ constexpr int GM_W = 16;              // warps per CTA, each on a slice of the o
 constexpr int GM_T = 32 * GM_W;
 constexpr int GM_DK = 32;             // padded dimension: two k-steps of GEMM1, four n-tiles of GEMM2
 constexpr int GM_RS = 40;             // floats per particle row of the partial-gradient buffer
+constexpr int GM_TS = 40;             // floats per particle row of theta, p, grad (padding zero)
 constexpr int GM_CH = 16;             // observations per chunk (one k-step of GEMM2)
 static_assert(GM_W == GM_P, "the end point gives one warp to each particle");
 
 // Dynamic shared memory (bytes): X hi [n16][64] | X lo [n16][64] (x3) |
-// y [n16] f32 | theta, p, grad [16][32] f32 | partials [16 warps][16][40] f32 |
+// y [n16] f32 | theta, p, grad [16][40] f32 | partials [16 warps][16][40] f32 |
 // H0, log pi [16] f64.
 struct GmLayout {
     int n16;
@@ -60,9 +61,9 @@ struct GmLayout {
         xl = xh + (size_t)n16 * 64;
         y = xl + (x3 ? (size_t)n16 * 64 : 0);
         th = y + (size_t)n16 * 4;
-        p = th + GM_P * GM_DK * 4;
-        g = p + GM_P * GM_DK * 4;
-        red = g + GM_P * GM_DK * 4;
+        p = th + GM_P * GM_TS * 4;
+        g = p + GM_P * GM_TS * 4;
+        red = g + GM_P * GM_TS * 4;
         h0 = red + (size_t)GM_W * GM_P * GM_RS * 4;
         lp = h0 + GM_P * 8;
         bytes = lp + GM_P * 8;
@@ -77,15 +78,13 @@ __device__ __forceinline__ uint32_t gm_xoff(int r, int c) {
 __device__ __forceinline__ void ldsm4(uint32_t (&v)[4], uint32_t addr) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr)
-                 : "memory");
+                 : "r"(addr));
 }
 
 __device__ __forceinline__ void ldsm4_t(uint32_t (&v)[4], uint32_t addr) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr)
-                 : "memory");
+                 : "r"(addr));
 }
 
 // D += A . B, A 16x16 (row), B 16x8 (col), BF16 in, FP32 accumulate
@@ -204,8 +203,8 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
         for (int q = 0; q < GM_P; ++q) mx = max(mx, S_s[q]);
         smax_s = mx;
     }
-    for (int e = tid; e < GM_P * GM_DK; e += GM_T) {
-        const int q = e / GM_DK, d = e % GM_DK;
+    for (int e = tid; e < GM_P * GM_TS; e += GM_T) {
+        const int q = e / GM_TS, d = e % GM_TS;
         const int64_t src = src_s[q];
         float tv = 0.0f, gv = 0.0f, pv = 0.0f;
         if (src >= 0 && d < D) {
@@ -226,15 +225,15 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
             if (j_s[q] < 0) continue;
             double z0, z1;
             normal_pair(seed_s[q], (uint32_t)i, jl_s[q], k_s[q], TAG_MOM, z0, z1);
-            p_s[q * GM_DK + 2 * i] = (float)z0;
-            if (2 * i + 1 < D) p_s[q * GM_DK + 2 * i + 1] = (float)z1;
+            p_s[q * GM_TS + 2 * i] = (float)z0;
+            if (2 * i + 1 < D) p_s[q * GM_TS + 2 * i + 1] = (float)z1;
         }
         __syncthreads();
     }
     if (tid < GM_P && !a.eval_only) {
         double kin = 0.0;
         for (int d = 0; d < D; ++d) {
-            const double v = p_s[tid * GM_DK + d];
+            const double v = p_s[tid * GM_TS + d];
             kin += v * v;
         }
         H0_s[tid] = j_s[tid] >= 0 ? 0.5 * kin - a.logpi_in[src_s[tid]] : 0.0;
@@ -243,8 +242,8 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
     const int smax = smax_s;
 
     // ---- first half kick and drift of step 1
-    for (int e = tid; e < GM_P * GM_DK; e += GM_T) {
-        const int q = e / GM_DK, d = e % GM_DK;
+    for (int e = tid; e < GM_P * GM_TS; e += GM_T) {
+        const int q = e / GM_TS, d = e % GM_TS;
         if (d < D && S_s[q] >= 1) {
             const float ef = eps_s[q], he = 0.5f * ef;
             const float pv = fmaf(he, g_s[e], p_s[e]);
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
             for (int v = 0; v < 4; ++v) {
                 const int q = gq + 8 * (v & 1);                 // a0, a2: row g; a1, a3: row g + 8
                 const int d = 16 * ks + 2 * tq + 8 * (v >> 1);  // a0, a1: cols 2t; a2, a3: cols 2t + 8
-                const float2 tv = *reinterpret_cast<const float2*>(th_s + q * GM_DK + d);
+                const float2 tv = *reinterpret_cast<const float2*>(th_s + q * GM_TS + d);
                 gm_split(tv.x, tv.y, ah[ks][v], al[ks][v]);
             }
         }
@@ -276,14 +275,15 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
 #pragma unroll
             for (int v = 0; v < 4; ++v) gacc[nt][v] = 0.0f;
 
-        for (int c = wid; c < nch; c += GM_W) {
-            const int r0 = c * GM_CH;
-            // GEMM1: eta for observations r0 .. r0 + 15 (two n-tiles of 8)
-            float eta[2][4];
+        // GEMM1 of observations r0 .. r0 + 15 (two n-tiles of 8); in the x3
+        // mode the correction products accumulate apart from hi*hi, which
+        // halves the dependent chain of each accumulator
+        auto gemm1 = [&](int r0, float (&eta)[2][4]) {
+            float cor[2][4];
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) eta[j][v] = 0.0f;
+                for (int v = 0; v < 4; ++v) eta[j][v] = cor[j][v] = 0.0f;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 // matrices: (n-tile mi >> 1, dims 16 ks + 8 (mi & 1) .. + 7)
@@ -295,11 +295,26 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                 for (int j = 0; j < 2; ++j) {
                     mma_16816(eta[j], ah[ks], bh[2 * j], bh[2 * j + 1]);
                     if (X3) {
-                        mma_16816(eta[j], al[ks], bh[2 * j], bh[2 * j + 1]);
-                        mma_16816(eta[j], ah[ks], bl[2 * j], bl[2 * j + 1]);
+                        mma_16816(cor[j], al[ks], bh[2 * j], bh[2 * j + 1]);
+                        mma_16816(cor[j], ah[ks], bl[2 * j], bl[2 * j + 1]);
                     }
                 }
             }
+            if (X3)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) eta[j][v] += cor[j][v];
+        };
+
+        // chunks c = wid, wid + 16, ...: GEMM1 of the next chunk is issued
+        // before the residuals and GEMM2 of the current one
+        float eta[2][4], eta_nx[2][4];
+        if (wid < nch) gemm1(wid * GM_CH, eta);
+        for (int c = wid; c < nch; c += GM_W) {
+            const int r0 = c * GM_CH;
+            const bool more = c + GM_W < nch;
+            if (more) gemm1(r0 + GM_W * GM_CH, eta_nx);
             // residuals -> A operand of GEMM2 (rows g, g + 8; observations 2t, 2t + 1 (+ 8))
             uint32_t rh[4], rl[4];
 #pragma unroll
@@ -330,6 +345,11 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                     }
                 }
             }
+            if (more)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) eta[j][v] = eta_nx[j][v];
         }
         // ---- this warp's partial gradients (rows g, g + 8; dims 8 nt + 2t, + 1)
         {
@@ -346,42 +366,55 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
         for (int e = tid; e < GM_P * GM_DK; e += GM_T) {
             const int q = e / GM_DK, d = e % GM_DK;
             if (d >= D) continue;
+            const int ei = q * GM_TS + d;
             float gs = 0.0f;
 #pragma unroll
             for (int w = 0; w < GM_W; ++w) gs += red[(w * GM_P + q) * GM_RS + d];
-            gs -= th_s[e] * inv_tau2;
+            gs -= th_s[ei] * inv_tau2;
             if (a.eval_only) {
-                g_s[e] = gs;
+                g_s[ei] = gs;
             } else if (s <= S_s[q]) {
                 const float ef = eps_s[q], he = 0.5f * ef;
-                g_s[e] = gs;
-                float pv = fmaf(he, gs, p_s[e]);
+                g_s[ei] = gs;
+                float pv = fmaf(he, gs, p_s[ei]);
                 if (s + 1 <= S_s[q]) {
                     pv = fmaf(he, gs, pv);
-                    th_s[e] = fmaf(ef, pv, th_s[e]);
+                    th_s[ei] = fmaf(ef, pv, th_s[ei]);
                 }
-                p_s[e] = pv;
+                p_s[ei] = pv;
             }
         }
         __syncthreads();
     }
 
-    // ---- end-point log pi: FP32 products with the FP32 X (L2-resident), FP64
-    //      accumulation; warp q owns particle q
+    // ---- end-point log pi: FP32 products with the FP32 X (each row read once
+    //      per CTA, by one thread, for all 16 particles), FP64 accumulation
     {
-        const int q = wid;
-        double ll = 0.0;
-        if (j_s[q] >= 0) {
-            const float* thq = th_s + q * GM_DK;
-            for (int i = lane; i < n; i += 32) {
-                const float* x = m.X + (int64_t)i * m.Dp;
+        double ll[GM_P];
+#pragma unroll
+        for (int q = 0; q < GM_P; ++q) ll[q] = 0.0;
+        for (int i = tid; i < n; i += GM_T) {
+            float x[GM_DK];
+            const float4* xr = reinterpret_cast<const float4*>(m.X + (int64_t)i * m.Dp);
+#pragma unroll
+            for (int u = 0; u < GM_DK / 4; ++u) {
+                const float4 v = 4 * u < m.Dp ? __ldg(xr + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[4 * u] = v.x;
+                x[4 * u + 1] = v.y;
+                x[4 * u + 2] = v.z;
+                x[4 * u + 3] = v.w;
+            }
+            const float yv = y_s[i];
+#pragma unroll
+            for (int q = 0; q < GM_P; ++q) {
+                const float* thq = th_s + q * GM_TS;   // zero past D
                 float e0 = 0.0f, e1 = 0.0f;
-                for (int d = 0; d + 1 < D; d += 2) {
-                    e0 = fmaf(__ldg(x + d), thq[d], e0);
-                    e1 = fmaf(__ldg(x + d + 1), thq[d + 1], e1);
+#pragma unroll
+                for (int d = 0; d < GM_DK; d += 2) {
+                    e0 = fmaf(x[d], thq[d], e0);
+                    e1 = fmaf(x[d + 1], thq[d + 1], e1);
                 }
-                if (D & 1) e0 = fmaf(__ldg(x + D - 1), thq[D - 1], e0);
-                const float eta = e0 + e1, yv = y_s[i];
+                const float eta = e0 + e1;
                 float term;
                 if (LOGIT) {
                     const float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
@@ -390,18 +423,29 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                     const float z = (yv - eta) * inv_s;
                     term = -0.5f * z * z;
                 }
-                ll += (double)term;
+                ll[q] += (double)term;
             }
         }
+        // sum over the threads: lanes by shuffles, warps through shared memory
+        double* red64 = reinterpret_cast<double*>(red);   // [GM_W][GM_P]
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-        if (lane == 0) {
+        for (int q = 0; q < GM_P; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ll[q] += __shfl_xor_sync(0xffffffffu, ll[q], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < GM_P; ++q) red64[wid * GM_P + q] = ll[q];
+        __syncthreads();
+        if (tid < GM_P) {
+            double tot = 0.0;
+            for (int w = 0; w < GM_W; ++w) tot += red64[w * GM_P + tid];
             double sq = 0.0;
             for (int d = 0; d < D; ++d) {
-                const double v = th_s[q * GM_DK + d];
+                const double v = th_s[tid * GM_TS + d];
                 sq += v * v;
             }
-            lp_s[q] = ll - 0.5 * sq * inv_tau2_d + m.lconst;
+            lp_s[tid] = tot - 0.5 * sq * inv_tau2_d + m.lconst;
         }
     }
     __syncthreads();
@@ -411,9 +455,10 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
         const int q = e / GM_DK, d = e % GM_DK;
         const int64_t j = j_s[q];
         if (j < 0 || d >= D) continue;
-        if (!a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th_s[e];
-        a.grad_out[(int64_t)d * a.ld + j] = g_s[e];
-        if (a.p_out && !a.eval_only) a.p_out[(int64_t)d * a.ld + j] = p_s[e];
+        const int ei = q * GM_TS + d;
+        if (!a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th_s[ei];
+        a.grad_out[(int64_t)d * a.ld + j] = g_s[ei];
+        if (a.p_out && !a.eval_only) a.p_out[(int64_t)d * a.ld + j] = p_s[ei];
     }
     if (tid < GM_P && j_s[tid] >= 0) {
         const int64_t j = j_s[tid];
@@ -422,7 +467,7 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
         if (!a.eval_only) {
             double kin = 0.0;
             for (int d = 0; d < D; ++d) {
-                const double v = p_s[tid * GM_DK + d];
+                const double v = p_s[tid * GM_TS + d];
                 kin += v * v;
             }
             double dH = (0.5 * kin - lp1) - H0_s[tid];
