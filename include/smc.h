@@ -84,9 +84,13 @@ typedef struct {
 /* Likelihood arithmetic for the GEMM-shaped models (LOGISTIC, LINEAR_GAUSS). */
 typedef enum {
     SMC_PREC_FP32 = 0,      /* FP32 SIMT, FP32 everywhere on the trajectory       */
-    SMC_PREC_BF16X3 = 1,    /* tcgen05 BF16 x3 split products, FP32 accumulation  */
-    SMC_PREC_BF16 = 2,      /* tcgen05 BF16 operands, FP32 accumulation (data that
-                               do not fit on chip are streamed, see BF16X2)       */
+    SMC_PREC_BF16X3 = 1,    /* tensor cores, every operand split into BF16 hi + lo,
+                               three products (lo*lo dropped), FP32 accumulation;
+                               dim <= 32: warp-level MMAs with X in one CTA's
+                               shared memory, else the tcgen05 cluster kernel     */
+    SMC_PREC_BF16 = 2,      /* tensor cores, BF16 operands, FP32 accumulation (same
+                               kernels; data that do not fit on chip are streamed,
+                               see BF16X2)                                        */
     SMC_PREC_BF16X2 = 3     /* tcgen05, streamed data (any n, dim <= 128): X rounded
                                once to BF16, theta and the residuals r split into
                                BF16 hi + lo (two products per GEMM), FP32
