@@ -263,12 +263,18 @@ void smc_destroy(smc_handle* h);
  * is frozen from k = M_warmup on.
  */
 typedef struct {
-    int32_t hidden;         /* H: multiple of 4 in [4, 128]                       */
+    int32_t hidden;         /* H: multiple of 4 in [4, 128], at least dim / 2
+                               rounded up to a multiple of 4                      */
     int32_t layers;         /* L: [1, 8]                                          */
     int32_t train_every;    /* train at k - 1 = 0, train_every, ... (0: never)     */
     int32_t epochs;         /* Adam steps per training iteration (0: never train) */
     double lr;              /* Adam step size (> 0)                               */
     double min_ess_frac;    /* train only when J_eff >= min_ess_frac * J, [0, 1]  */
+    int32_t precision;      /* conditioner products of the trajectories:
+                               SMC_PREC_FP32 (0), or SMC_PREC_BF16 (2): BF16
+                               weights and activations on warp-level tensor-core
+                               MMAs with FP32 accumulation (hidden a multiple of
+                               16); training stays FP32                           */
 } smc_flow_config;
 
 /* Number of parameters of the flow (0 for an invalid shape). */
@@ -336,12 +342,14 @@ smc_status smc_k_leapfrog(const smc_dev_model* m, float* theta, float* p, float*
  * f64 [N] are updated in place (theta' = T(z'), its gradient and log pi, the
  * final latent momenta); steps i32 [N] (>= 1); z0, z1 (f32 [dim x ld], may be
  * NULL) receive T^-1(theta) and z'; dH (f64 [N], may be NULL) the energy
- * error in z.  Allocates (stream-ordered) and frees the padded work copies of
- * the weights. */
+ * error in z.  precision: SMC_PREC_FP32 or SMC_PREC_BF16 (conditioner products
+ * on BF16 warp MMAs, as smc_flow_config.precision).  Allocates (stream-ordered)
+ * and frees the padded work copies of the weights. */
 smc_status smc_k_flow_leapfrog(const smc_dev_model* m, int32_t hidden, int32_t layers,
                                const float* params, float* theta, float* p, float* grad,
                                double* logpi, const int32_t* steps, double eps, int64_t N,
-                               int64_t ld, float* z0, float* z1, double* dH, void* stream);
+                               int64_t ld, float* z0, float* z1, double* dH, int32_t precision,
+                               void* stream);
 
 /* Gradient of the weighted training loss of smc_flow_enable with respect to
  * every parameter: grad (device f32, smc_flow_num_params values) from params

@@ -10,8 +10,10 @@
 // L2 as 16-byte rows of padded work copies (a transposed copy serves the
 // backward products), each thread accumulating a 4 x 4 tile.  FP32 with the
 // trajectory end-point energy accumulated in FP64.
+#include <cuda_bf16.h>
 #include <math_constants.h>
 #include "flow.cuh"
+#include "tc_ptx.cuh"
 
 namespace smc {
 namespace {
@@ -25,6 +27,8 @@ constexpr int FT = 256;          // threads per CTA
 size_t flow_smem_bytes(int D, int H, int L, int O4) {
     return sizeof(float) * (size_t)FG * (6 * D + L * D + 3 * H + O4) + sizeof(double) * 9 * FG;
 }
+// ... plus the BF16 operand buffer of the MMA form: [32][K + 8] for K <= 128
+static size_t flow_pm_bytes() { return sizeof(uint16_t) * (size_t)FG * (128 + 8); }
 
 namespace {
 
@@ -79,6 +83,52 @@ __global__ void k_flow_refresh(DevFlow f, bool bump, FlowGate gate) {
     f.work[i] = v;
 }
 
+// BF16 operand fragments of the six conditioner matrices (layout in flow.cuh).
+// Element (r, c) of each logical matrix, zero outside the valid block.
+__global__ void k_flow_frag(DevFlow f) {
+    const int64_t total = (int64_t)f.L * f.layer_frag;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int l = (int)(i / f.layer_frag);
+    const int64_t e = i % f.layer_frag;
+    const int H = f.H, Dh = f.Dh, Dh4 = f.Dh4;
+    const FlowFragOff fo = flow_frag_off(H, f.kp1, f.o4p);
+    const int64_t lsz = (int64_t)H * Dh + H + (int64_t)H * H + H + (int64_t)f.D * H + f.D;
+    const float* P = f.params + l * lsz;
+    const float *W1 = P, *W2 = W1 + (int64_t)H * Dh + H, *W3 = W2 + (int64_t)H * H + H;
+    auto canon = [&](int rp) -> int { return rp < Dh ? rp : (rp >= Dh4 && rp < Dh4 + Dh ? Dh + (rp - Dh4) : -1); };
+    int which, ks_n;
+    int64_t base;
+    if (e < fo.W2) { which = 0; base = fo.W1; ks_n = f.kp1 / 16; }
+    else if (e < fo.W3) { which = 1; base = fo.W2; ks_n = H / 16; }
+    else if (e < fo.W1t) { which = 2; base = fo.W3; ks_n = H / 16; }
+    else if (e < fo.W2t) { which = 3; base = fo.W1t; ks_n = H / 16; }
+    else if (e < fo.W3t) { which = 4; base = fo.W2t; ks_n = H / 16; }
+    else { which = 5; base = fo.W3t; ks_n = f.o4p / 16; }
+    const int64_t local = e - base;
+    const int lane = (int)(local & 31);
+    const int64_t tile = local >> 5;
+    const int mt = (int)(tile / ks_n), ks = (int)(tile % ks_n);
+    auto A = [&](int r, int c) -> float {
+        switch (which) {
+            case 0: return c < Dh ? W1[(int64_t)r * Dh + c] : 0.0f;                  // W1 [h][k]
+            case 1: return W2[(int64_t)r * H + c];                                     // W2 [h][k]
+            case 2: { const int cr = canon(r); return cr >= 0 ? W3[(int64_t)cr * H + c] : 0.0f; }   // W3 [rp][h]
+            case 3: return r < Dh ? W1[(int64_t)c * Dh + r] : 0.0f;                  // W1t [k][h]
+            case 4: return W2[(int64_t)c * H + r];                                     // W2t [k][h]
+            default: { const int cr = canon(c); return cr >= 0 ? W3[(int64_t)cr * H + r] : 0.0f; }  // W3t [h][rp]
+        }
+    };
+    const int g = lane >> 2, t = lane & 3;
+    const int r0 = 16 * mt + g, r1 = r0 + 8, c0 = 16 * ks + 2 * t, c1 = c0 + 8;
+    auto pk = [](float x, float y) -> uint32_t {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    };
+    f.frag[i] = make_uint4(pk(A(r0, c0), A(r0, c0 + 1)), pk(A(r1, c0), A(r1, c0 + 1)), pk(A(r0, c1), A(r0, c1 + 1)),
+                           pk(A(r1, c1), A(r1, c1 + 1)));
+}
+
 // -------------------------------------------------------------- building blocks
 // Y[n][p] = act(sum_k At[k][n] X[k][p] + bias[n]) for n < Nout (multiple of 4,
 // at most 128), the CTA's 32 particles p; At rows are 16-byte aligned.
@@ -124,9 +174,105 @@ __device__ __forceinline__ void cta_mm(const float* __restrict__ At, int K, int 
     }
 }
 
+// FP32 rows X [R x 32] -> BF16 particle-major B [32][ldb] (k contiguous),
+// zero for R <= k < Kpad: the B operand of the next MMA.
+__device__ __forceinline__ void to_pm(const float* X, int R, int Kpad, __nv_bfloat16* B, int ldb) {
+    for (int e = threadIdx.x; e < FG * (Kpad / 2); e += FT) {
+        const int q = e & (FG - 1), k = 2 * (e / FG);
+        const float v0 = k < R ? X[k * FG + q] : 0.0f, v1 = k + 1 < R ? X[(k + 1) * FG + q] : 0.0f;
+        *reinterpret_cast<__nv_bfloat162*>(B + q * ldb + k) = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+__device__ __forceinline__ void fl_ldsm4(uint32_t (&v)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void fl_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Y[r][p] = act(sum_k A[r][k] B[k][p] + bias[r]) for rows r < Mvalid and the
+// CTA's 32 particles, on m16n8k16 BF16 MMAs with FP32 accumulation.  A: MT x KS
+// tiles of fragments (L2), B: BF16 particle-major [32][ldb] in shared memory
+// (ldb = K + 8: the eight 16-byte rows of a matrix load fall in distinct bank
+// groups).  A warp takes one m-tile and all four n-tiles when there are eight
+// or more m-tiles, else one m-tile and two n-tiles.
+template <bool TANH, bool BIAS>
+__device__ __noinline__ void cta_mma(const uint4* __restrict__ Af, int MT, int KS, const __nv_bfloat16* B, int ldb,
+                                        float* Y, const float* __restrict__ bias, int Mvalid) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int mi = lane >> 3, mr = lane & 7;
+    const bool full = MT >= FT / 32;
+    const int items = full ? MT : 2 * MT;
+    const uint32_t bbase = tc::smem_u32(B);
+    for (int it = wid; it < items; it += FT / 32) {
+        const int mt = full ? it : it >> 1;
+        const int nt0 = full ? 0 : 2 * (it & 1);
+        const int nh = full ? 2 : 1;          // n-tile pairs of this item
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        // every A fragment of this m-tile in flight at once (KS <= 8): the
+        // loads come from L2 and the products behind them are short
+        uint4 afr[8];
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks)
+            if (ks < KS) afr[ks] = __ldg(Af + ((int64_t)mt * KS + ks) * 32 + lane);
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+            if (ks >= KS) break;
+            const uint32_t av[4] = {afr[ks].x, afr[ks].y, afr[ks].z, afr[ks].w};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h < nh) {
+                    // matrices (n-tile nt0 + 2h + (mi >> 1), k half mi & 1)
+                    const int prow = 8 * (nt0 + 2 * h + (mi >> 1)) + mr;
+                    const int kcol = 16 * ks + 8 * (mi & 1);
+                    uint32_t b[4];
+                    fl_ldsm4(b, bbase + (uint32_t)(prow * ldb + kcol) * 2u);
+                    fl_mma(acc[2 * h], av, b[0], b[1]);
+                    fl_mma(acc[2 * h + 1], av, b[2], b[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (u < 2 * nh) {
+                const int pc = 8 * (nt0 + u) + 2 * t;
+                const int r0 = 16 * mt + g, r1 = r0 + 8;
+                float v0 = acc[u][0], v1 = acc[u][1], v2 = acc[u][2], v3 = acc[u][3];
+                if (BIAS) {
+                    const float b0 = r0 < Mvalid ? __ldg(bias + r0) : 0.0f, b1 = r1 < Mvalid ? __ldg(bias + r1) : 0.0f;
+                    v0 += b0;
+                    v1 += b0;
+                    v2 += b1;
+                    v3 += b1;
+                }
+                if (TANH) {
+                    v0 = tanhf(v0);
+                    v1 = tanhf(v1);
+                    v2 = tanhf(v2);
+                    v3 = tanhf(v3);
+                }
+                if (r0 < Mvalid) *reinterpret_cast<float2*>(Y + r0 * FG + pc) = make_float2(v0, v1);
+                if (r1 < Mvalid) *reinterpret_cast<float2*>(Y + r1 * FG + pc) = make_float2(v2, v3);
+            }
+        }
+    }
+}
+
 struct FlowSmem {
     float *z, *p, *gz, *x, *c, *gx, *zl, *h1, *h2, *o, *ch;
     double *ldp, *ld;    // [8][32] partials, [32]
+    __nv_bfloat16* pm;   // BF16 form: the B operand of the next product, [32][<= 136]
 };
 
 __device__ __forceinline__ FlowSmem flow_smem(unsigned char* base, int D, int H, int L, int O4) {
@@ -149,10 +295,31 @@ __device__ __forceinline__ FlowSmem flow_smem(unsigned char* base, int D, int H,
 }
 
 // Conditioner of layer l at rows [aoff, aoff + Dh) of `in`: h1, h2, o.
+// MMA: the three products on BF16 warp MMAs (operands rounded to BF16, FP32
+// accumulation, bias and tanh in FP32).
+template <bool MMA = false>
 __device__ __forceinline__ void conditioner(const DevFlow& f, int l, const float* in, FlowSmem& s) {
     const FlowLayerOff o = flow_layer_off(f.H, f.Dh, f.Dh4, f.O4);
     const float* w = f.work + (int64_t)l * f.layer_work;
     const int aoff = (l & 1) ? f.Dh : 0;
+    if (MMA) {
+        const uint4* fr = f.frag + (int64_t)l * f.layer_frag;
+        const FlowFragOff fo = flow_frag_off(f.H, f.kp1, f.o4p);
+        const int H = f.H;
+        to_pm(in + aoff * FG, f.Dh, f.kp1, s.pm, f.kp1 + 8);
+        __syncthreads();
+        cta_mma<true, true>(fr + fo.W1, H / 16, f.kp1 / 16, s.pm, f.kp1 + 8, s.h1, w + o.b1, H);
+        __syncthreads();
+        to_pm(s.h1, H, H, s.pm, H + 8);
+        __syncthreads();
+        cta_mma<true, true>(fr + fo.W2, H / 16, H / 16, s.pm, H + 8, s.h2, w + o.b2, H);
+        __syncthreads();
+        to_pm(s.h2, H, H, s.pm, H + 8);
+        __syncthreads();
+        cta_mma<false, true>(fr + fo.W3, f.o4p / 16, H / 16, s.pm, H + 8, s.o, w + o.b3, f.O4);
+        __syncthreads();
+        return;
+    }
     cta_mm<true, true>(w + o.W1t, f.Dh, f.H, in + aoff * FG, s.h1, w + o.b1);
     __syncthreads();
     cta_mm<true, true>(w + o.W2t, f.H, f.H, s.h1, s.h2, w + o.b2);
@@ -176,13 +343,14 @@ __device__ __forceinline__ void ld_accumulate(FlowSmem& s, double v, bool add_to
 }
 
 // x <- T(x), recording the input of every layer in zl; s.ld = log|det dT/dz|.
+template <bool MMA = false>
 __device__ void flow_forward(const DevFlow& f, FlowSmem& s, float* x) {
     const int t = threadIdx.x, D = f.D;
     if (t < FG) s.ld[t] = 0.0;
     for (int l = 0; l < f.L; ++l) {
         for (int e = t; e < D * FG; e += FT) s.zl[l * D * FG + e] = x[e];
         __syncthreads();
-        conditioner(f, l, x, s);
+        conditioner<MMA>(f, l, x, s);
         const int boff = (l & 1) ? 0 : f.Dh;
         double part = 0.0;
         for (int k = t >> 5; k < f.Dh; k += 8) {
@@ -198,12 +366,13 @@ __device__ void flow_forward(const DevFlow& f, FlowSmem& s, float* x) {
 
 // x <- T^-1(x), recording the output of every inverse layer (= the input of
 // forward layer l) in zl; s.ld = log|det dT^-1/dx| = -sum s.
+template <bool MMA = false>
 __device__ void flow_inverse(const DevFlow& f, FlowSmem& s, float* x) {
     const int t = threadIdx.x, D = f.D;
     if (t < FG) s.ld[t] = 0.0;
     __syncthreads();
     for (int l = f.L - 1; l >= 0; --l) {
-        conditioner(f, l, x, s);
+        conditioner<MMA>(f, l, x, s);
         const int boff = (l & 1) ? 0 : f.Dh;
         double part = 0.0;
         for (int k = t >> 5; k < f.Dh; k += 8) {
@@ -220,13 +389,14 @@ __device__ void flow_inverse(const DevFlow& f, FlowSmem& s, float* x) {
 }
 
 // c <- J_T(z)^T c + grad_z log|det dT/dz| using the recorded layer inputs.
+template <bool MMA = false>
 __device__ void flow_backward(const DevFlow& f, FlowSmem& s, float* c) {
     const int t = threadIdx.x, D = f.D;
     const FlowLayerOff off = flow_layer_off(f.H, f.Dh, f.Dh4, f.O4);
     for (int l = f.L - 1; l >= 0; --l) {
         const float* in = s.zl + l * D * FG;
         const float* w = f.work + (int64_t)l * f.layer_work;
-        conditioner(f, l, in, s);
+        conditioner<MMA>(f, l, in, s);
         const int boff = (l & 1) ? 0 : f.Dh, aoff = (l & 1) ? f.Dh : 0;
         for (int e = t; e < f.Dh4 * FG; e += FT) {
             const int k = e / FG, q = e % FG;
@@ -244,16 +414,39 @@ __device__ void flow_backward(const DevFlow& f, FlowSmem& s, float* c) {
             s.o[(f.Dh4 + k) * FG + q] = ct;
         }
         __syncthreads();
-        cta_mm<false, false>(w + off.W3, f.O4, f.H, s.o, s.ch, nullptr);
-        __syncthreads();
-        for (int e = t; e < f.H * FG; e += FT) s.h2[e] = s.ch[e] * (1.0f - s.h2[e] * s.h2[e]);
-        __syncthreads();
-        cta_mm<false, false>(w + off.W2, f.H, f.H, s.h2, s.ch, nullptr);
-        __syncthreads();
-        for (int e = t; e < f.H * FG; e += FT) s.h1[e] = s.ch[e] * (1.0f - s.h1[e] * s.h1[e]);
-        __syncthreads();
-        cta_mm<false, false>(w + off.W1, f.H, f.Dh4, s.h1, s.ch, nullptr);
-        __syncthreads();
+        if (MMA) {
+            // the transposed products: W3^T og, W2^T d2, W1^T d1 (BF16 operands)
+            const uint4* fr = f.frag + (int64_t)l * f.layer_frag;
+            const FlowFragOff fo = flow_frag_off(f.H, f.kp1, f.o4p);
+            const int H = f.H;
+            to_pm(s.o, f.O4, f.o4p, s.pm, f.o4p + 8);
+            __syncthreads();
+            cta_mma<false, false>(fr + fo.W3t, H / 16, f.o4p / 16, s.pm, f.o4p + 8, s.ch, nullptr, H);
+            __syncthreads();
+            for (int e = t; e < H * FG; e += FT) s.h2[e] = s.ch[e] * (1.0f - s.h2[e] * s.h2[e]);
+            __syncthreads();
+            to_pm(s.h2, H, H, s.pm, H + 8);
+            __syncthreads();
+            cta_mma<false, false>(fr + fo.W2t, H / 16, H / 16, s.pm, H + 8, s.ch, nullptr, H);
+            __syncthreads();
+            for (int e = t; e < H * FG; e += FT) s.h1[e] = s.ch[e] * (1.0f - s.h1[e] * s.h1[e]);
+            __syncthreads();
+            to_pm(s.h1, H, H, s.pm, H + 8);
+            __syncthreads();
+            cta_mma<false, false>(fr + fo.W1t, f.kp1 / 16, H / 16, s.pm, H + 8, s.ch, nullptr, f.Dh4);
+            __syncthreads();
+        } else {
+            cta_mm<false, false>(w + off.W3, f.O4, f.H, s.o, s.ch, nullptr);
+            __syncthreads();
+            for (int e = t; e < f.H * FG; e += FT) s.h2[e] = s.ch[e] * (1.0f - s.h2[e] * s.h2[e]);
+            __syncthreads();
+            cta_mm<false, false>(w + off.W2, f.H, f.H, s.h2, s.ch, nullptr);
+            __syncthreads();
+            for (int e = t; e < f.H * FG; e += FT) s.h1[e] = s.ch[e] * (1.0f - s.h1[e] * s.h1[e]);
+            __syncthreads();
+            cta_mm<false, false>(w + off.W1, f.H, f.Dh4, s.h1, s.ch, nullptr);
+            __syncthreads();
+        }
         for (int e = t; e < f.Dh * FG; e += FT) c[aoff * FG + e] += s.ch[e];
         __syncthreads();
     }
@@ -325,11 +518,12 @@ __device__ double target_logpi(const DevModel& m, const float* x, const float* g
 }
 
 // -------------------------------------------------------------- trajectories
-template <int TARGET>
+template <int TARGET, bool MMA>
 __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f, TrajArgs a, float* z0out,
                                                           float* z1out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FlowSmem s = flow_smem(smem_raw, f.D, f.H, f.L, f.O4);
+    s.pm = reinterpret_cast<__nv_bfloat16*>(s.ld + FG);   // past the FP64 block: flow_smem_bytes from the base
     __shared__ int64_t j_s[FG], src_s[FG];
     __shared__ int S_s[FG];
     __shared__ float eps_s[FG];
@@ -390,11 +584,11 @@ __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f,
     }
     const int smax = smax_s;
     // latent start z0 = T^-1(theta), its log pi_z and gradient
-    flow_inverse(f, s, s.x);                     // s.x = z0, s.ld = log|det dT^-1|
+    flow_inverse<MMA>(f, s, s.x);                // s.x = z0, s.ld = log|det dT^-1|
     for (int e = t; e < D * FG; e += FT) s.z[e] = s.x[e];
     if (t < FG) lp_s[t] = (src_s[t] >= 0 ? a.logpi_in[src_s[t]] : 0.0) - s.ld[t];   // log pi_z(z0)
     __syncthreads();
-    flow_backward(f, s, s.c);                    // s.c = grad_z log pi_z(z0)
+    flow_backward<MMA>(f, s, s.c);               // s.c = grad_z log pi_z(z0)
     for (int e = t; e < D * FG; e += FT) s.gz[e] = s.c[e];
     if (!a.p_in) {
         const int npairs = (D + 1) / 2;
@@ -433,12 +627,12 @@ __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f,
     for (int st = 1; st <= smax; ++st) {
         for (int e = t; e < D * FG; e += FT) s.x[e] = s.z[e];
         __syncthreads();
-        flow_forward(f, s, s.x);                 // s.x = T(z), s.ld = log|det dT/dz|
+        flow_forward<MMA>(f, s, s.x);            // s.x = T(z), s.ld = log|det dT/dz|
         target_grad<TARGET>(m, s.x, s.gx);       // grad_x log pi
         __syncthreads();
         for (int e = t; e < D * FG; e += FT) s.c[e] = s.gx[e];
         __syncthreads();
-        flow_backward(f, s, s.c);                // grad_z log pi_z
+        flow_backward<MMA>(f, s, s.c);           // grad_z log pi_z
         for (int e = t; e < D * FG; e += FT) {
             const int q = e % FG;
             if (st <= S_s[q]) {
@@ -652,11 +846,18 @@ bool flow_shape_ok(int64_t D, int64_t H, int64_t L) {
     if (H < 4 || H > 128 || (H & 3) || L < 1 || L > 8) return false;
     const int64_t Dh4 = ((D / 2) + 3) & ~3ll;
     if (2 * Dh4 > 128) return false;
+    if (H < Dh4) return false;   // the backward product into the input half writes Dh4 rows of an H-row buffer
     return flow_smem_bytes((int)D, (int)H, (int)L, (int)(2 * Dh4)) <= 220 * 1024;
 }
 
 bool flow_supported(const DevModel& m, int H, int L) {
     return (m.kind == GAUSS_DENSE || m.kind == BANANA) && flow_shape_ok(m.D, H, L);
+}
+
+bool flow_bf16_supported(int64_t D, int H, int L) {
+    if (!flow_shape_ok(D, H, L) || !flow_bf16_ok(H)) return false;
+    const int Dh4 = (int)(((D / 2) + 3) & ~3ll);
+    return flow_smem_bytes((int)D, H, L, 2 * Dh4) + flow_pm_bytes() <= 226 * 1024;
 }
 
 DevFlow flow_shape(int D, int H, int L) {
@@ -667,32 +868,46 @@ DevFlow flow_shape(int D, int H, int L) {
     f.Dh = D / 2;
     f.Dh4 = (f.Dh + 3) & ~3;
     f.O4 = 2 * f.Dh4;
+    f.kp1 = (f.Dh + 15) & ~15;
+    f.o4p = (f.O4 + 15) & ~15;
     f.n_params = flow_num_params(D, H, L);
     f.layer_work = flow_layer_work(H, f.Dh, f.Dh4, f.O4);
+    f.layer_frag = flow_bf16_ok(H) ? flow_frag_off(H, f.kp1, f.o4p).total : 0;
     return f;
 }
 
 cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s, bool bump, FlowGate gate) {
     const int64_t total = (int64_t)f.L * f.layer_work;
     k_flow_refresh<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f, bump, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && f.frag && f.layer_frag > 0) {
+        const int64_t nf = (int64_t)f.L * f.layer_frag;
+        k_flow_frag<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(f);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int TARGET, bool MMA>
+static cudaError_t launch_flow_t(const DevModel& m, const DevFlow& f, const TrajArgs& a, float* z0, float* z1,
+                                 int64_t grid, cudaStream_t s) {
+    const size_t sm = flow_smem_bytes(f.D, f.H, f.L, f.O4) + (MMA ? flow_pm_bytes() : 0);
+    auto kern = traj_flow_kernel<TARGET, MMA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, FT, sm, s>>>(m, f, a, z0, z1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_traj_flow(const DevModel& m, const DevFlow& f, const TrajArgs& a, float* z0, float* z1,
                              cudaStream_t s) {
-    const size_t sm = flow_smem_bytes(f.D, f.H, f.L, f.O4);
     const int64_t grid = (a.N + FG - 1) / FG;
     if (grid == 0) return cudaSuccess;
-    if (m.kind == GAUSS_DENSE) {
-        cudaError_t e = cudaFuncSetAttribute(traj_flow_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        traj_flow_kernel<0><<<(unsigned)grid, FT, sm, s>>>(m, f, a, z0, z1);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(traj_flow_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        traj_flow_kernel<1><<<(unsigned)grid, FT, sm, s>>>(m, f, a, z0, z1);
-    }
-    return cudaGetLastError();
+    const bool mma = f.bf16 != 0;
+    if (mma && (!f.frag || f.layer_frag <= 0)) return cudaErrorInvalidValue;
+    if (m.kind == GAUSS_DENSE)
+        return mma ? launch_flow_t<0, true>(m, f, a, z0, z1, grid, s) : launch_flow_t<0, false>(m, f, a, z0, z1, grid, s);
+    return mma ? launch_flow_t<1, true>(m, f, a, z0, z1, grid, s) : launch_flow_t<1, false>(m, f, a, z0, z1, grid, s);
 }
 
 int64_t flow_partials_floats(const DevFlow& f, int64_t N) { return ((N + FG - 1) / FG) * f.n_params; }

@@ -13,17 +13,47 @@ namespace smc {
 // b3 [D]; rows 0..Dh-1 of W3 give s_raw, rows Dh..D-1 give t).  The work
 // copies below are rebuilt from it after every update, padded so that every
 // row is 16-byte aligned (Dh4 = Dh rounded up to 4, O4 = 2 Dh4 output rows).
+// For the BF16 form the six conditioner matrices of every layer (W1, W2, W3
+// and their transposes for the backward products) are also kept as BF16
+// operand fragments of the m16n8k16 MMA: per 16 x 16 tile, 32 lanes x 16
+// bytes in the order the lanes load them (kp1 = Dh and o4p = O4 rounded up to
+// 16 are the padded tile extents).
 struct DevFlow {
     int32_t D, H, L, Dh, Dh4, O4;
+    int32_t kp1, o4p;            // Dh, O4 rounded up to 16
+    int32_t bf16;                // 1: conditioner products on warp-level BF16 MMAs
     int64_t n_params;            // canonical parameter count
     int64_t layer_work;          // floats per layer of the work copies
+    int64_t layer_frag;          // 16-byte fragments per layer of the BF16 copies
     float* params;               // [n_params]
     float* adam_m;               // [n_params]
     float* adam_v;               // [n_params]
     float* grad;                 // [n_params]
     float* work;                 // [L x layer_work]
+    uint4* frag;                 // [L x layer_frag]
     int32_t* adam_t;             // device Adam step count (steps taken)
 };
+
+// Offsets (in fragments) of the six BF16 operand matrices inside one layer:
+// W1 [H x kp1], W2 [H x H], W3 [o4p x H] (rows in the padded output order),
+// W1t [kp1 x H], W2t [H x H], W3t [H x o4p]; each 32 x (rows/16) x (cols/16).
+struct FlowFragOff {
+    int64_t W1, W2, W3, W1t, W2t, W3t, total;
+};
+__host__ __device__ inline FlowFragOff flow_frag_off(int H, int kp1, int o4p) {
+    const int64_t h = H / 16, k = kp1 / 16, o = o4p / 16;
+    FlowFragOff f;
+    f.W1 = 0;
+    f.W2 = f.W1 + 32 * h * k;
+    f.W3 = f.W2 + 32 * h * h;
+    f.W1t = f.W3 + 32 * o * h;
+    f.W2t = f.W1t + 32 * k * h;
+    f.W3t = f.W2t + 32 * h * h;
+    f.total = f.W3t + 32 * h * o;
+    return f;
+}
+// The BF16 form needs H a multiple of 16, at most 128.
+inline bool flow_bf16_ok(int H) { return H % 16 == 0 && H >= 16 && H <= 128; }
 
 // Training gate: a training epoch runs only when the run's tested ESS is at
 // least frac * n (rs == nullptr: always).  Evaluated on the device, so a
@@ -60,14 +90,18 @@ inline int64_t flow_layer_work(int H, int Dh, int Dh4, int O4) {
 inline int64_t flow_num_params(int64_t D, int64_t H, int64_t L) {
     return L * (H * (D / 2) + H + H * H + H + D * H + D);
 }
-// Shapes with a kernel: D even in [2, 128], H a multiple of 4 in [4, 128], L in [1, 8].
+// Shapes with a kernel: D even in [2, 128], H a multiple of 4 in [4, 128] and at
+// least D/2 rounded up to 4, L in [1, 8].
 bool flow_shape_ok(int64_t D, int64_t H, int64_t L);
 bool flow_supported(const DevModel& m, int H, int L);
+// ... and the BF16 form of it (H a multiple of 16, room for its operand buffer)
+bool flow_bf16_supported(int64_t D, int H, int L);
 // Sizes of a flow of this shape; the pointers are left null.
 DevFlow flow_shape(int D, int H, int L);
 size_t flow_smem_bytes(int D, int H, int L, int O4);
-// Rebuild the padded / transposed work copies from params.  With `bump`, the
-// launch also counts the Adam step that preceded it (when the gate was open).
+// Rebuild the padded / transposed work copies (and the BF16 fragments, when
+// f.frag is set) from params.  With `bump`, the launch also counts the Adam
+// step that preceded it (when the gate was open).
 cudaError_t flow_refresh(const DevFlow& f, cudaStream_t s, bool bump = false, FlowGate gate = FlowGate{});
 // HMC in z = T^-1(theta) with the frozen map (trajectory kernel); z0 and z1
 // (may be nullptr) receive the latent start and end points [D x ld].

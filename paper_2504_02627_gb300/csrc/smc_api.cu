@@ -339,7 +339,7 @@ cudaError_t flow_train(smc_handle* h, cudaStream_t s) {
         if (e == cudaSuccess) e = flow_adam(h->flow, h->flow_cfg.lr, gate, s);
         if (e == cudaSuccess) e = flow_refresh(h->flow, s, true, gate);   // the next gradient sees the new map
     }
-    if (h->profiling) h->kernel_launches += 4 * (int64_t)h->flow_cfg.epochs;
+    if (h->profiling) h->kernel_launches += (4 + (h->flow.frag ? 1 : 0)) * (int64_t)h->flow_cfg.epochs;
     return e;
 }
 
@@ -1054,11 +1054,16 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     if (h->precision != SMC_PREC_FP32) return reject("precision must be SMC_PREC_FP32");
     if (!flow_supported(h->model.m, fc->hidden, fc->layers))
         return reject("needs a GAUSS_DENSE or BANANA model with even dim <= 128, hidden a multiple of 4 "
-                      "in [4, 128] and layers in [1, 8]");
+                      "in [4, 128] and at least dim / 2 rounded up to 4, and layers in [1, 8]");
     if (fc->train_every < 0 || fc->epochs < 0 || !(fc->lr > 0.0) || !std::isfinite(fc->lr))
         return reject("train_every and epochs must be >= 0 and lr > 0");
     if (!(fc->min_ess_frac >= 0.0 && fc->min_ess_frac <= 1.0)) return reject("min_ess_frac must be in [0, 1]");
+    if (fc->precision != SMC_PREC_FP32 && fc->precision != SMC_PREC_BF16)
+        return reject("precision must be SMC_PREC_FP32 or SMC_PREC_BF16");
+    if (fc->precision == SMC_PREC_BF16 && !flow_bf16_supported(h->D, fc->hidden, fc->layers))
+        return reject("the BF16 form needs hidden a multiple of 16 in [16, 128]");
     DevFlow f = flow_shape((int)h->D, fc->hidden, fc->layers);
+    f.bf16 = fc->precision == SMC_PREC_BF16 ? 1 : 0;
     std::vector<float> p32((size_t)f.n_params);
     for (int64_t i = 0; i < f.n_params; ++i) {
         if (!std::isfinite(params[i])) return reject("non-finite parameter");
@@ -1070,6 +1075,7 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     f.adam_v = A.get<float>((size_t)f.n_params);
     f.grad = A.get<float>((size_t)f.n_params);
     f.work = A.get<float>((size_t)(f.L * f.layer_work));
+    if (f.bf16) f.frag = A.get<uint4>((size_t)(f.L * f.layer_frag));
     f.adam_t = A.get<int32_t>(1);
     float* partials = A.get<float>((size_t)flow_partials_floats(f, h->N));
     float* z0 = A.get<float>((size_t)(h->D * h->ld));
@@ -1118,11 +1124,16 @@ namespace {
 struct TmpFlow {
     DevFlow f{};
     DevAlloc mem;
-    bool make(int64_t D, int32_t H, int32_t L, const float* params, int64_t n_partial_rows, cudaStream_t s) {
+    bool make(int64_t D, int32_t H, int32_t L, const float* params, int64_t n_partial_rows, cudaStream_t s,
+              bool bf16 = false) {
         mem.s = s;
         f = flow_shape((int)D, H, L);
         f.params = const_cast<float*>(params);
         f.work = mem.get<float>((size_t)(f.L * f.layer_work));
+        if (bf16) {
+            f.bf16 = 1;
+            f.frag = mem.get<uint4>((size_t)(f.L * f.layer_frag));
+        }
         partials = n_partial_rows > 0 ? mem.get<float>((size_t)flow_partials_floats(f, n_partial_rows)) : nullptr;
         return mem.err == cudaSuccess;
     }
@@ -1151,13 +1162,17 @@ smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, con
 
 smc_status smc_k_flow_leapfrog(const smc_dev_model* m, int32_t hidden, int32_t layers, const float* params,
                                float* theta, float* p, float* grad, double* logpi, const int32_t* steps, double eps,
-                               int64_t N, int64_t ld, float* z0, float* z1, double* dH, void* stream) {
+                               int64_t N, int64_t ld, float* z0, float* z1, double* dH, int32_t precision,
+                               void* stream) {
     if (!m || !params || N < 0 || ld < N || !(eps > 0.0)) return SMC_E_INVAL;
     if (N > 0 && (!theta || !p || !grad || !logpi || !steps)) return SMC_E_INVAL;
     if (!flow_supported(m->m, hidden, layers)) return SMC_E_INVAL;
+    if (precision != SMC_PREC_FP32 && precision != SMC_PREC_BF16) return SMC_E_INVAL;
+    const bool bf16 = precision == SMC_PREC_BF16;
+    if (bf16 && !flow_bf16_supported(m->m.D, hidden, layers)) return SMC_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TmpFlow t;
-    if (!t.make(m->m.D, hidden, layers, params, 0, s)) {
+    if (!t.make(m->m.D, hidden, layers, params, 0, s, bf16)) {
         t.mem.release();
         return SMC_E_NOMEM;
     }

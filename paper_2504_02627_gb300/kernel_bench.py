@@ -93,12 +93,14 @@ def run_flow(args):
     steps = torch.full((N,), args.steps, dtype=torch.int32, device="cuda")
     lib = B.lib()
     B.check(lib.smc_k_target(dm.h, th.data_ptr(), N, N, lp.data_ptr(), gr.data_ptr(), 0, s), "smc_k_target")
+    prec = B.PREC_FP32 if args.precision is None else args.precision
     ms = _time(torch, lambda: B.check(lib.smc_k_flow_leapfrog(dm.h, H, L, par.data_ptr(), th.data_ptr(), p.data_ptr(),
                                                               gr.data_ptr(), lp.data_ptr(), steps.data_ptr(), args.eps,
-                                                              N, N, None, None, None, s), "smc_k_flow_leapfrog"))
+                                                              N, N, None, None, None, prec, s), "smc_k_flow_leapfrog"))
     per_grad = L * 4.0 * (Dh * H + H * H + H * D) + 2.0 * D * D
     flops = per_grad * N * (args.steps + 1)
-    return {"kernel": "latent-space flow trajectory (FP32 SIMT)", "D": D, "hidden": H, "layers": L, "particles": N,
+    return {"kernel": "latent-space flow trajectory (" + ("BF16 warp MMA" if prec == B.PREC_BF16 else "FP32 SIMT") + ")",
+            "D": D, "hidden": H, "layers": L, "particles": N,
             "steps": args.steps, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
@@ -110,7 +112,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--precision", type=int, default=None,
-                    help="stream: 2 (BF16) or 3 (BF16x2, default); glm: 0 (FP32, default), 1 (BF16x3) or 2 (BF16)")
+                    help="stream: 2 (BF16) or 3 (BF16x2, default); glm: 0 (FP32, default), 1 (BF16x3) or 2 (BF16); "
+                         "flow: 0 (FP32, default) or 2 (BF16 conditioner products)")
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)
     args = ap.parse_args(argv)

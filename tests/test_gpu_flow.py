@@ -151,7 +151,7 @@ def test_latent_leapfrog_matches_oracle(name):
     dH_d = torch.zeros(N, dtype=torch.float64, device="cuda")
     par_d, S_d = dev(p, torch.float32), dev(S)       # kept alive across the asynchronous call
     st = B.lib().smc_k_flow_leapfrog(m.h, H, L, ptr(par_d), ptr(th_d), ptr(p_d), ptr(gr_d), ptr(lp_d), ptr(S_d),
-                                     eps, N, ld, ptr(z0_d), ptr(z1_d), ptr(dH_d), stream())
+                                     eps, N, ld, ptr(z0_d), ptr(z1_d), ptr(dH_d), 0, stream())
     assert st == 0
     torch.cuda.synchronize()
     host = lambda a: a[:, :N].cpu().numpy().T.astype(np.float64)
@@ -324,16 +324,17 @@ def test_training_gate_skips_a_degenerate_weighted_set():
     smp.close()
 
 
-def test_identity_map_gives_the_plain_sampler():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_identity_map_gives_the_plain_sampler(precision):
     """With a zero last layer and no training, T is the identity (s = 0,
-    t = 0 exactly), so the preconditioned sampler must reproduce the plain
-    one: identical decisions and step counts, trajectories within FP32."""
+    t = 0 exactly, in BF16 too), so the preconditioned sampler must reproduce
+    the plain one: identical decisions and step counts, trajectories within FP32."""
     w = rounded_workload(workloads.gauss10())
     run = dict(n_particles=256, n_iters=8, n_warmup=4, step_size=0.05, traj_len0=0.3, max_steps=20,
                init_scale=2.0)
     plain = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=5, **run), stream())
     flow = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=5, **run), stream())
-    flow.enable_flow(f32r(workloads.flow_init(10, 32, 4)), 32, 4, train_every=0, epochs=0)
+    flow.enable_flow(f32r(workloads.flow_init(10, 32, 4)), 32, 4, train_every=0, epochs=0, precision=precision)
     for k in range(run["n_iters"]):
         sp, sf = plain.step()[0], flow.step()[0]
         assert sp["resampled"] == sf["resampled"]
@@ -346,10 +347,12 @@ def test_identity_map_gives_the_plain_sampler():
     flow.close()
 
 
-def test_trained_map_raises_acceptance_and_ess():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_trained_map_raises_acceptance_and_ess(precision):
     """Ill-conditioned 4-d Gaussian (variances 0.01 .. 4) at a step size the
     stiff direction barely tolerates (the oracle's pin of the same claim):
-    training the map on the particles whitens the target."""
+    training the map on the particles whitens the target (with the map's
+    products in FP32 or BF16; training is FP32 in both)."""
     tgt = workloads._gauss_from_spectrum(np.array([0.01, 0.1, 1.0, 4.0]), 11)
     w = rounded_workload(tgt)
     run = dict(n_particles=512, n_iters=16, n_warmup=12, step_size=0.18, traj_len0=1.0, max_steps=500,
@@ -357,7 +360,8 @@ def test_trained_map_raises_acceptance_and_ess():
     md = g.ModelData.from_workload(w)
     plain = g.Sampler(md, g.make_config(seed=21, **run), stream())
     flow = g.Sampler(md, g.make_config(seed=21, **run), stream())
-    flow.enable_flow(f32r(workloads.flow_init(4, 32, 4, seed=5)), 32, 4, train_every=1, epochs=60, lr=3e-3)
+    flow.enable_flow(f32r(workloads.flow_init(4, 32, 4, seed=5)), 32, 4, train_every=1, epochs=60, lr=3e-3,
+                     precision=precision)
     sp = [plain.step()[0] for _ in range(run["n_iters"])]
     sf = []
     for k in range(run["n_iters"]):
@@ -387,7 +391,112 @@ def test_flow_rejects_unsupported_configurations():
                                                                 step_size=0.05), stream())
     with pytest.raises(RuntimeError):
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 30, 4)), 30, 4)     # H not a multiple of 4
+    with pytest.raises(RuntimeError):                                                  # BF16: H not a multiple of 16
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 40, 4)), 40, 4, precision=2)
     smp.step()
     with pytest.raises(RuntimeError):                                                  # after the first iteration
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4)
     smp.close()
+
+
+# ------------------------------------------------------------- BF16 conditioner products
+def _gpu_flow_move(w, H, L, p, th, p0, S, eps, precision):
+    """smc_k_flow_leapfrog on the given particles; returns host arrays
+    (theta', p', z0, z', grad', log pi', dH) and the starting log pi, grad."""
+    D = w["D"]
+    N = th.shape[0]
+    t = oracle_target(w)
+    lp, gr = oracle.logpi(t, th)
+    m = g.DevModel(g.ModelData.from_workload(w), stream())
+    ld = ((N + 31) // 32) * 32
+
+    def buf(a):
+        out = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+        out[:, :N] = dev(a.T, torch.float32)
+        return out
+    th_d, p_d, gr_d = buf(th), buf(p0), buf(f32r(gr))
+    lp_d = dev(lp)
+    z0_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    z1_d = torch.zeros_like(z0_d)
+    dH_d = torch.zeros(N, dtype=torch.float64, device="cuda")
+    par_d, S_d = dev(p, torch.float32), dev(S)
+    st = B.lib().smc_k_flow_leapfrog(m.h, H, L, ptr(par_d), ptr(th_d), ptr(p_d), ptr(gr_d), ptr(lp_d), ptr(S_d),
+                                     eps, N, ld, ptr(z0_d), ptr(z1_d), ptr(dH_d), precision, stream())
+    assert st == 0
+    torch.cuda.synchronize()
+    host = lambda a: a[:, :N].cpu().numpy().T.astype(np.float64)
+    out = (host(th_d), host(p_d), host(z0_d), host(z1_d), host(gr_d), lp_d.cpu().numpy(), dH_d.cpu().numpy())
+    m.close()
+    return out, lp, gr
+
+
+def _start_points(w, N, seed):
+    rng = np.random.default_rng(seed)
+    D = w["D"]
+    Sigma = w.get("Sigma")
+    if Sigma is not None:
+        th = f32r(rng.standard_normal((N, D)) @ np.linalg.cholesky(Sigma).T)
+    else:
+        xo = rng.standard_normal((N, D // 2)) * np.sqrt(w["a"])
+        xe = rng.standard_normal((N, D // 2)) + w["b"] * (xo**2 - w["a"])
+        th = f32r(np.stack([xo, xe], axis=2).reshape(N, D))
+    return th, f32r(rng.standard_normal((N, D)))
+
+
+@pytest.mark.parametrize("name", ["banana50", "gauss10", "gauss100"])
+def test_bf16_transport_round_trip_is_exact(name):
+    """The BF16 map is a deterministic affine coupling, so T(T^-1(theta)) =
+    theta up to the FP32 affine arithmetic and the energy of a particle that
+    does not move is unchanged: the property that keeps the preconditioned
+    sampler exact with reduced-precision conditioners."""
+    w = rounded_workload(_targets()[name])
+    D, eps = w["D"], w["eps"]
+    H, L = (32, 4) if D <= 10 else (128, 4)
+    p = _params(D, H, L, seed=7, scale=0.3)
+    N = 77
+    th, p0 = _start_points(w, N, 3)
+    S = np.random.default_rng(4).integers(1, 5, N).astype(np.int32)
+    S[::2] = 0                                            # half the particles stay at z0
+    (th1, p1, z0, z1, gr1, lp1, dH), lp, gr = _gpu_flow_move(w, H, L, p, th, p0, S, eps, 2)
+    for a in (th1, p1, z0, z1, gr1, lp1, dH):
+        assert np.all(np.isfinite(a))
+    still = S == 0
+    scale = np.sqrt(np.mean(th**2))
+    np.testing.assert_allclose(th1[still], th[still], rtol=1e-4, atol=1e-4 * scale)
+    np.testing.assert_array_equal(z1[still], z0[still])
+    np.testing.assert_array_equal(p1[still], p0[still])
+    gs = np.sqrt(np.mean(gr**2))
+    np.testing.assert_allclose(gr1[still], gr[still], rtol=1e-3, atol=1e-3 * gs)
+    np.testing.assert_allclose(lp1[still], lp[still], rtol=1e-5, atol=1e-4)
+    assert np.all(np.abs(dH[still]) <= 2e-3 + 1e-6 * np.abs(lp[still])), np.abs(dH[still]).max()
+
+
+@pytest.mark.parametrize("name,N", [("banana50", 77), ("gauss10", 77), ("gauss100", 77), ("gauss100", 8192)])
+def test_bf16_latent_leapfrog_near_oracle(name, N):
+    """One latent leapfrog step with BF16 conditioner products against the FP64
+    oracle map.  BF16 rounds weights and activations (relative 2^-9): the map
+    (z0, theta') carries errors of about 2e-3 of its scale (bound 2e-2), and the
+    latent gradient, whose vector-Jacobian products pass through the twelve
+    BF16 products of the four layers twice, up to 5e-2 of the gradient scale
+    (median 4e-3; bound 0.1).  A wrong fragment or operand layout gives order
+    one.  At the benchmark's 8192 particles a seeded sample of 100 is checked."""
+    w = rounded_workload(_targets()[name])
+    D, eps = w["D"], w["eps"]
+    t = oracle_target(w)
+    H, L = (32, 4) if D <= 10 else (128, 4)
+    p = _params(D, H, L, seed=7, scale=0.1)
+    f = oracle.FlowSpec(D, H, L, p)
+    th, p0 = _start_points(w, N, 5)
+    S = np.ones(N, dtype=np.int32)
+    (th1, p1, z0, z1, gr1, lp1, dH), _, _ = _gpu_flow_move(w, H, L, p, th, p0, S, eps, 2)
+    idx = np.arange(N) if N <= 100 else np.sort(np.random.default_rng(N).choice(N, 100, replace=False))
+    x_o, p_o, z0_o, z1_o, lpx_o, dH_o, gx_o = oracle_flow_move(f, t, th[idx], p0[idx], eps, S[idx])
+    rel = lambda a, b: np.abs(a - b) / (np.abs(b) + np.sqrt(np.mean(b**2)) + 1e-6)
+    assert rel(z0[idx], z0_o).max() < 2e-2, rel(z0[idx], z0_o).max()
+    assert rel(th1[idx], x_o).max() < 2e-2, rel(th1[idx], x_o).max()
+    # p' = p0 + eps/2 (g0 + g1): the latent gradients carry the conditioner error
+    _, g0_o, _, _, _ = oracle.flow_logpi_z(f, t, z0_o)
+    _, g1_o, _, _, _ = oracle.flow_logpi_z(f, t, z1_o)
+    gscale = np.abs(g0_o) + np.abs(g1_o) + np.sqrt(np.mean(g0_o**2))
+    assert np.all(np.abs(p1[idx] - p_o) <= 0.5 * eps * 0.1 * gscale + 1e-5 * (np.abs(p_o) + 1.0))
+    assert rel(lp1[idx], lpx_o).max() < 2e-2
