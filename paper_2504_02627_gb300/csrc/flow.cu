@@ -175,12 +175,22 @@ __device__ __forceinline__ void cta_mm(const float* __restrict__ At, int K, int 
 }
 
 // FP32 rows X [R x 32] -> BF16 particle-major B [32][ldb] (k contiguous),
-// zero for R <= k < Kpad: the B operand of the next MMA.
-__device__ __forceinline__ void to_pm(const float* X, int R, int Kpad, __nv_bfloat16* B, int ldb) {
-    for (int e = threadIdx.x; e < FG * (Kpad / 2); e += FT) {
-        const int q = e & (FG - 1), k = 2 * (e / FG);
-        const float v0 = k < R ? X[k * FG + q] : 0.0f, v1 = k + 1 < R ? X[(k + 1) * FG + q] : 0.0f;
-        *reinterpret_cast<__nv_bfloat162*>(B + q * ldb + k) = __floats2bfloat162_rn(v0, v1);
+// zero for R <= k < Kpad: the B operand of the next MMA.  A thread converts
+// eight consecutive k of one particle (lanes = particles: the row reads are
+// conflict-free, and the 16-byte stores at a row stride of ldb = K + 8 fall
+// in distinct bank groups).
+__device__ __noinline__ void to_pm(const float* X, int R, int Kpad, __nv_bfloat16* B, int ldb) {
+    for (int e = threadIdx.x; e < FG * (Kpad / 8); e += FT) {
+        const int q = e & (FG - 1), k0 = 8 * (e / FG);
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int k = k0 + 2 * h;
+            const float v0 = k < R ? X[k * FG + q] : 0.0f, v1 = k + 1 < R ? X[(k + 1) * FG + q] : 0.0f;
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+            w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(B + q * ldb + k0) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
