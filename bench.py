@@ -176,16 +176,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _traffic_for(kernel_file):
+def _traffic_for(kernel_file, workload):
     """Per-launch DRAM bytes of the trajectory kernel from a committed ncu
-    summary, if it was taken on the current source of that kernel."""
+    summary, if it was taken on the current source of that kernel and for
+    this bench workload (one file holds the kernels of several models)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         src = os.path.join(ROOT, "paper_2504_02627_gb300", "csrc", kernel_file)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         e = t.get(kernel_file)
-        if e and e.get("source_sha256_16") == h:
+        if e and e.get("source_sha256_16") == h and e.get("bench_workload") == workload:
             return e.get("bytes_per_launch_full")
     except (OSError, ValueError):
         pass
@@ -589,7 +590,7 @@ def main():
             roof["executed"] = (ex[0] * prof_ge + ex[1] * n_part * K) / (traj_ms / 1e3) / 1e12
             roof["executed_note"] = ("MMA FLOP/s actually issued: the three BF16 products of the compensated "
                                      "form, the dimension padded to 32 and the observations to 16")
-    tr = _traffic_for(kfile)
+    tr = _traffic_for(kfile, args.workload)
     roof["traffic"] = tr
     roof["kernel"] = "trajectory (leapfrog) kernel"
     roof["launches_profiled"] = prof["traj_launches"]

@@ -111,6 +111,23 @@ __device__ __forceinline__ void normal_pair(uint64_t seed, uint32_t i, uint32_t 
     z1 = r * s;
 }
 
+// The same pair from the same Philox block with the transform in FP32: the
+// top 24 bits of words x and z as uniforms (m + 1/2) 2^-24, FP32 log, sqrt
+// and sincospi.  Differs from the FP64 pair by about 1e-7 relative; used
+// where a thread draws a whole particle's momentum, since FP64 runs at a
+// small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t i, uint32_t j, uint32_t k,
+                                                uint32_t tag, float& z0, float& z1) {
+    Philox4 w = philox4x32_10(Philox4{i, j, k, tag}, seed);
+    const float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
+    const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
 // ---------------------------------------------------------------- jitter
 // Base-2 radical inverse of n: bit reversal of the 32-bit integer, times 2^-32
 // (exact in FP64 for n < 2^32).

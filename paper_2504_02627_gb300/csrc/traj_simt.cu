@@ -124,14 +124,21 @@ struct HierM {
         g[0] = dmu - mu;
         g[1] = dlt - logtau;
     }
+    // FP32 terms per group, FP64 accumulation (as the GEMM-shaped models'
+    // end points): FP64 runs at a small fraction of the FP32 rate here
     __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM]) {
-        const double s2 = m.h0 * m.h0;
-        const double mu = th[0], logtau = th[1], tau = exp(logtau);
-        double s = -0.5 * mu * mu - 0.5 * logtau * logtau;
-        for (int k = 0; k < m.n; ++k) {
-            double eta = th[2 + k];
-            double dev = (double)sm[k] - (mu + tau * eta);
-            s += -0.5 * ((double)sm[2 * m.n + k] + (double)sm[m.n + k] * dev * dev) / s2 - 0.5 * eta * eta;
+        const float inv_2s2 = (float)(0.5 / (m.h0 * m.h0));
+        const float mu = th[0], logtau = th[1], tau = expf(logtau);
+        double s = -0.5 * (double)mu * (double)mu - 0.5 * (double)logtau * (double)logtau;
+#pragma unroll
+        for (int d = 2; d < DM; ++d) {
+            if (d < m.D) {
+                const int k = d - 2;
+                const float eta = th[d];
+                const float dev = sm[k] - fmaf(tau, eta, mu);
+                const float term = -fmaf(sm[m.n + k] * dev, dev, sm[2 * m.n + k]) * inv_2s2 - 0.5f * eta * eta;
+                s += (double)term;
+            }
         }
         return s + m.lconst;
     }
@@ -177,10 +184,10 @@ __global__ void __launch_bounds__(128) traj_thread_kernel(DevModel m, TrajArgs a
     } else {
 #pragma unroll
         for (int d = 0; d < DM; d += 2) {
-            double z0 = 0.0, z1 = 0.0;
-            if (d < D) normal_pair(seed, (uint32_t)(d >> 1), jl, kk, TAG_MOM, z0, z1);
-            p[d] = d < D ? (float)z0 : 0.0f;
-            if (d + 1 < DM) p[d + 1] = d + 1 < D ? (float)z1 : 0.0f;
+            float z0 = 0.0f, z1 = 0.0f;
+            if (d < D) normal_pair_f32(seed, (uint32_t)(d >> 1), jl, kk, TAG_MOM, z0, z1);
+            p[d] = d < D ? z0 : 0.0f;
+            if (d + 1 < DM) p[d + 1] = d + 1 < D ? z1 : 0.0f;
         }
     }
     double kin0 = 0.0;
