@@ -685,6 +685,7 @@ def main():
         "variants": variants,
         "preconditioner": precond,
         "large_logistic": large,
+        "autotune": smp.plan(),
         "gpu_launches": prof["kernel_launches"] * args.steps,
         "clocks": clk,
     }

@@ -225,6 +225,22 @@ smc_status smc_profile(smc_handle* h, int32_t enable);
 smc_status smc_get_profile(smc_handle* h, double* traj_ms, int64_t* traj_launches,
                            int64_t* kernel_launches);
 
+/* Launch plan of the trajectory kernel.  smc_init / smc_init_batch run an
+ * autotuner once, after the initial draw: every launch-configuration variant
+ * of the model's trajectory kernel (CTA size, register cap of the
+ * thread-per-particle kernels) runs a 16-step trajectory of the handle's own
+ * initial particles into the scratch half of the state, timed with CUDA
+ * events (best of three), and the fastest is kept.  Variants run the same
+ * arithmetic in the same order, so the choice changes speed only, never a
+ * result.  smc_get_plan returns the variant in use, the number of variants
+ * (1: nothing to tune for this model and precision) and, when tile_ms is not
+ * NULL, the measured times in ms (n_tiles values; 0 when not measured). */
+smc_status smc_get_plan(const smc_handle* h, int32_t* traj_tile, int32_t* n_tiles, double* tile_ms);
+
+/* Forces variant traj_tile (0 <= traj_tile < n_tiles) from the next iteration
+ * on (the captured graph is dropped).  Errors: SMC_E_INVAL. */
+smc_status smc_set_plan(smc_handle* h, int32_t traj_tile);
+
 /* Copies the last error text (NUL-terminated, truncated to len). */
 smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len);
 

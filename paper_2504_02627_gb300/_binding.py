@@ -74,6 +74,8 @@ EXPORTS = {
     "smc_reset": (C.c_int, [C.c_void_p, C.c_uint64]),
     "smc_get_summary": (C.c_int, [C.c_void_p, C.POINTER(SmcSummary)]),
     "smc_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "smc_get_plan": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP]),
+    "smc_set_plan": (C.c_int, [C.c_void_p, C.c_int32]),
     "smc_get_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
     "smc_destroy": (None, [C.c_void_p]),
@@ -241,6 +243,18 @@ class Sampler:
         check(lib().smc_get_profile(self.h, C.byref(ms), C.byref(n), C.byref(k)), "smc_get_profile",
               self.h)
         return {"traj_ms": ms.value, "traj_launches": n.value, "kernel_launches": k.value}
+
+    def plan(self):
+        """smc_get_plan: the trajectory-kernel variant the autotuner chose."""
+        tile, n = C.c_int32(), C.c_int32()
+        check(lib().smc_get_plan(self.h, C.byref(tile), C.byref(n), None), "smc_get_plan", self.h)
+        ms = np.zeros(n.value)
+        check(lib().smc_get_plan(self.h, None, None, _dp(ms)), "smc_get_plan", self.h)
+        return {"traj_tile": tile.value, "n_tiles": n.value, "tile_ms": ms.tolist()}
+
+    def set_plan(self, traj_tile: int):
+        """smc_set_plan: force a trajectory-kernel variant."""
+        check(lib().smc_set_plan(self.h, int(traj_tile)), "smc_set_plan", self.h)
 
     def log_evidence(self):
         out = np.empty(self.n_runs)

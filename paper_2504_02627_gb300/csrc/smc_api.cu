@@ -102,6 +102,9 @@ struct smc_handle {
     float* flow_partials = nullptr;
     float* z0 = nullptr;            // latent start / end points of the last move
     float* z1 = nullptr;
+    // launch plan chosen by the autotuner
+    int32_t traj_tile = 0, n_traj_tiles = 1;
+    std::vector<double> tile_ms;
 };
 
 namespace {
@@ -369,6 +372,78 @@ cudaError_t initial_draw(smc_handle* h) {
     return ce;
 }
 
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// The autotuner: every launch variant of the model's trajectory kernel runs a
+// 16-step trajectory (capped at the largest step count) from the initial
+// particles in buffer 0 into buffer 1, p_final, dH and alpha, all of which
+// the first iteration rewrites before reading; best of three event-timed
+// launches per variant.  Variants share their arithmetic, so nothing here
+// can change a result.
+cudaError_t autotune(smc_handle* h) {
+    const int32_t nt = traj_tile_count(h->model.m, h->precision);
+    h->n_traj_tiles = nt;
+    h->traj_tile = 0;
+    h->tile_ms.assign((size_t)nt, 0.0);
+    if (nt <= 1 || h->N == 0) return cudaSuccess;
+    cudaStream_t s = h->stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) return e;   // keep the default
+    const int32_t S = std::max<int32_t>(1, std::min<int32_t>(16, h->max_steps_all));
+    k_fill_i32<<<(unsigned)((h->N + 255) / 256), 256, 0, s>>>(h->steps, h->N, S);
+    e = cudaGetLastError();
+    TrajArgs a{};
+    a.theta_in = h->theta[0];
+    a.grad_in = h->grad[0];
+    a.logpi_in = h->logpi[0];
+    a.theta_out = h->theta[1];
+    a.grad_out = h->grad[1];
+    a.logpi_out = h->logpi[1];
+    a.p_out = h->p_final;
+    a.dH = h->dH;
+    a.alpha = h->alpha;
+    a.steps = h->steps;
+    a.run_of = h->d_run_of;
+    a.runs = h->d_runs;
+    a.rstate = h->d_rstate;
+    a.N = h->N;
+    a.ld = h->ld;
+    a.dev_err = h->dev_err;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int32_t v = 0; v < nt && e == cudaSuccess; ++v) {   // first launches (function attributes) untimed
+        a.tile = v;
+        e = launch_traj(h->model.m, a, h->precision, s);
+    }
+    std::vector<double> best((size_t)nt, 1e30);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        for (int32_t v = 0; v < nt && e == cudaSuccess; ++v) {
+            a.tile = v;
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_traj(h->model.m, a, h->precision, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess) best[(size_t)v] = std::min(best[(size_t)v], (double)ms);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    int32_t arg = 0;
+    for (int32_t v = 1; v < nt; ++v)
+        if (best[(size_t)v] < best[(size_t)arg]) arg = v;
+    h->traj_tile = arg;
+    h->tile_ms = best;
+    return cudaSuccess;
+}
+
 RunState initial_state(const RunParams& rp, const smc_config& c) {
     RunState st{};
     st.log_L = std::fmin(std::fmax(std::log(c.traj_len0), rp.log_L_lo), rp.log_L_hi);
@@ -527,6 +602,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
 
     h->cfg.assign(cfg, cfg + n_runs);
     cudaError_t ce = initial_draw(h);
+    if (ce == cudaSuccess) ce = autotune(h);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
         smc_status st = cuda_fail(h, ce, "smc_init");
@@ -611,6 +687,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
         a.N = h->N;
         a.ld = h->ld;
         a.dev_err = h->dev_err;
+        a.tile = h->traj_tile;
         if (h->profiling) {
             const size_t i = 2 * h->n_event_pairs;
             while (h->events.size() < i + 2) {
@@ -915,6 +992,27 @@ smc_status smc_get_profile(smc_handle* h, double* traj_ms, int64_t* traj_launche
     if (traj_ms) *traj_ms = total;
     if (traj_launches) *traj_launches = (int64_t)h->n_event_pairs;
     if (kernel_launches) *kernel_launches = h->kernel_launches;
+    return SMC_OK;
+}
+
+smc_status smc_get_plan(const smc_handle* h, int32_t* traj_tile, int32_t* n_tiles, double* tile_ms) {
+    if (!h) return SMC_E_INVAL;
+    if (traj_tile) *traj_tile = h->traj_tile;
+    if (n_tiles) *n_tiles = h->n_traj_tiles;
+    if (tile_ms)
+        for (int32_t v = 0; v < h->n_traj_tiles; ++v)
+            tile_ms[v] = (size_t)v < h->tile_ms.size() ? h->tile_ms[(size_t)v] : 0.0;
+    return SMC_OK;
+}
+
+smc_status smc_set_plan(smc_handle* h, int32_t traj_tile) {
+    if (!h || traj_tile < 0 || traj_tile >= h->n_traj_tiles) return SMC_E_INVAL;
+    if (traj_tile != h->traj_tile && h->graph2) {   // the captured graph launches the old variant
+        if (h->graph_stream) cudaStreamSynchronize(h->graph_stream);
+        cudaGraphExecDestroy(h->graph2);
+        h->graph2 = nullptr;
+    }
+    h->traj_tile = traj_tile;
     return SMC_OK;
 }
 

@@ -59,7 +59,7 @@ struct TrajArgs {
     double eps_fixed;       // step size when runs == nullptr
     int64_t N, ld;
     int32_t eval_only;      // 1: compute log pi and grad at theta_in, no move
-    int32_t pad;
+    int32_t tile;           // launch-configuration variant of the model's kernel (0: default)
     int* dev_err;           // set to 1 when a bounded device wait gives up (may be nullptr)
 };
 
@@ -82,6 +82,15 @@ __device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& 
 // Launchers (kernels in traj_simt.cu / traj_tc.cu).  Return cudaError_t of
 // the launch; `supported` reports whether the model/shape has a kernel.
 bool traj_supported(const DevModel& m, int32_t precision);
+// Launch-configuration variants of the model's trajectory kernel that the
+// host autotuner may choose between (1: nothing to choose).  Every variant
+// runs the same arithmetic in the same order, so the choice never changes a
+// result, only its speed.
+int32_t traj_tile_count(const DevModel& m, int32_t precision);
+// thread-per-particle kernels (traj_thread.cu): dense Gaussian D <= 32,
+// banana, hierarchical normal; FP32
+cudaError_t launch_traj_thread(const DevModel& m, const TrajArgs& a, cudaStream_t s);
+int32_t traj_thread_tiles(const DevModel& m);
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s);
 // tensor-core path (traj_tc.cu): logistic / linear regression, BF16 or BF16x3
 bool traj_tc_supported(const DevModel& m);

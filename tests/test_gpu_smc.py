@@ -286,3 +286,44 @@ def test_metropolis_variant_matches_oracle():
         assert np.all(err <= 1e-5 * S[acc, None])
     assert n_rej > 0            # the step size makes some proposals fail
     smp.close()
+
+
+# ------------------------------------------------------------- autotuned launch plan
+@pytest.mark.parametrize("name,n_tiles", [("hier", 4), ("banana50", 4), ("gauss10", 1), ("logistic", 1)])
+def test_autotuner_plan(name, n_tiles):
+    """smc_init times every launch variant of the model's trajectory kernel on
+    the handle's own particles and keeps the fastest."""
+    w = rounded_workload(workloads.hier() if name == "hier" else _cases()[name])
+    run = dict(w["run"], n_particles=1500, n_iters=2, n_warmup=1)
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=3, **run), stream())
+    plan = smp.plan()
+    smp.close()
+    assert plan["n_tiles"] == n_tiles
+    assert 0 <= plan["traj_tile"] < n_tiles
+    if n_tiles > 1:
+        assert all(np.isfinite(t) and t > 0 for t in plan["tile_ms"])
+        assert plan["tile_ms"][plan["traj_tile"]] == min(plan["tile_ms"])
+
+
+@pytest.mark.parametrize("name", ["hier", "banana50"])
+def test_autotuner_variants_give_identical_results(name):
+    """The variants differ only in launch configuration (CTA size, register
+    cap): forcing each one reproduces the same particles, weights and evidence
+    bit for bit, so the autotuner can never change a result."""
+    w = rounded_workload(workloads.hier() if name == "hier" else _cases()[name])
+    run = dict(w["run"], n_particles=1500, n_iters=6, n_warmup=3)
+    md = g.ModelData.from_workload(w)
+    outs = []
+    for v in range(4):
+        smp = g.Sampler(md, g.make_config(seed=77, **run), stream())
+        smp.set_plan(v)
+        smp.run(run["n_iters"])                # graph replay with variant v
+        th, lw = smp.particles()
+        outs.append((th.copy(), lw.copy(), smp.log_evidence().copy()))
+        with pytest.raises(RuntimeError):
+            smp.set_plan(4)
+        smp.close()
+    for th, lw, lz in outs[1:]:
+        np.testing.assert_array_equal(th, outs[0][0])
+        np.testing.assert_array_equal(lw, outs[0][1])
+        np.testing.assert_array_equal(lz, outs[0][2])
