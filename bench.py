@@ -590,6 +590,12 @@ def main():
             roof["executed"] = (ex[0] * prof_ge + ex[1] * n_part * K) / (traj_ms / 1e3) / 1e12
             roof["executed_note"] = ("MMA FLOP/s actually issued: the three BF16 products of the compensated "
                                      "form, the dimension padded to 32 and the observations to 16")
+            ceil = C.c_double()
+            if g.lib().smc_k_mma_peak(1 << 14, C.byref(ceil), C.c_void_p(stream)) == 0:
+                roof["warp_mma_ceiling"] = ceil.value
+                roof["executed_frac_of_warp_mma_ceiling"] = roof["executed"] / ceil.value
+                roof["ceiling_note"] = ("issue-rate ceiling of warp-level BF16 MMAs (mma.sync m16n8k16) measured "
+                                        "live by smc_k_mma_peak; the kernel's MMAs are of that kind")
     tr = _traffic_for(kfile, args.workload)
     roof["traffic"] = tr
     roof["kernel"] = "trajectory (leapfrog) kernel"

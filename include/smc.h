@@ -241,6 +241,15 @@ smc_status smc_get_plan(const smc_handle* h, int32_t* traj_tile, int32_t* n_tile
  * on (the captured graph is dropped).  Errors: SMC_E_INVAL. */
 smc_status smc_set_plan(smc_handle* h, int32_t traj_tile);
 
+/* Measurement: the issue-rate ceiling of warp-level BF16 tensor-core MMAs
+ * (mma.sync m16n8k16, FP32 accumulation) on the current device, in TFLOP/s:
+ * one launch of `iters` iterations of eight independent MMA chains per warp,
+ * two 256-thread CTAs per SM, event-timed on `stream` after a warm-up launch.
+ * The denominator for the issued MMA rate of the warp-MMA trajectory kernels.
+ * Allocates and frees (stream-ordered) a small output buffer.  Errors:
+ * SMC_E_INVAL (iters outside [1, 2^24]), SMC_E_CUDA. */
+smc_status smc_k_mma_peak(int64_t iters, double* tflops, void* stream);
+
 /* Copies the last error text (NUL-terminated, truncated to len). */
 smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len);
 

@@ -76,6 +76,7 @@ EXPORTS = {
     "smc_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "smc_get_plan": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP]),
     "smc_set_plan": (C.c_int, [C.c_void_p, C.c_int32]),
+    "smc_k_mma_peak": (C.c_int, [C.c_int64, _DP, C.c_void_p]),
     "smc_get_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
     "smc_destroy": (None, [C.c_void_p]),

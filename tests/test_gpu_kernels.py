@@ -386,3 +386,14 @@ def test_tc_one_leapfrog_step(name, eps, N, precision):
     # the end-point energy is exact to FP32 accuracy at the GPU's own end point
     lp_at_g, _ = oracle.logpi(t, th_g)
     assert np.all(np.abs(lp_g - lp_at_g) <= 1e-5 * ls1)
+
+
+def test_warp_mma_ceiling_probe():
+    """smc_k_mma_peak measures the warp-level BF16 MMA rate the warp-MMA
+    trajectory kernels are held against: finite, and between a tenth of and
+    the full dense BF16 rate of the part."""
+    import ctypes as C
+    v = C.c_double()
+    assert g.lib().smc_k_mma_peak(1 << 12, C.byref(v), stream()) == 0
+    assert np.isfinite(v.value) and 100.0 < v.value < 2500.0, v.value
+    assert g.lib().smc_k_mma_peak(0, C.byref(v), stream()) != 0
