@@ -72,10 +72,12 @@ def _workload(name):
     raise ValueError(name)
 
 
-def _timed_runs(torch, smp, K, seeds, flush):
+def _timed_runs(torch, smp, K, seeds, flush, moments=None):
     """One full sampler run per seed, each bracketed by CUDA events on the
     sampler's stream after an L2 flush; returns (device ms, gradient
-    evaluations, post-warm-up ESS sum, log Z per run)."""
+    evaluations, post-warm-up ESS sum, log Z per run).  With a list in
+    `moments`, the weighted posterior mean and variance of every run are
+    appended to it (read back after the events)."""
     ms, ge, ess, lz = 0.0, 0, 0.0, []
     for sd in seeds:
         flush.zero_()
@@ -89,6 +91,8 @@ def _timed_runs(torch, smp, K, seeds, flush):
         ge += sum(x["grad_evals"] for x in summ)
         ess += sum(x["ess_sum_post_warmup"] for x in summ)
         lz.append(summ[0]["log_z"])
+        if moments is not None:
+            moments.append(smp.moments())
     torch.cuda.synchronize()
     return ms, ge, ess, lz
 
@@ -495,7 +499,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    dev_ms, ge_total, ess_post, lz = _timed_runs(torch, smp, K, seeds, flush)
+    mom_c = [] if not batched else None
+    dev_ms, ge_total, ess_post, lz = _timed_runs(torch, smp, K, seeds, flush, mom_c)
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
@@ -518,7 +523,8 @@ def main():
         sp.reset(10_000 + 1000 * rank)
         sp.run(K)
         torch.cuda.synchronize()
-        p_ms, p_ge, p_ess, p_lz = _timed_runs(torch, sp, K, seeds, flush)
+        mom_p = [] if not batched else None
+        p_ms, p_ge, p_ess, p_lz = _timed_runs(torch, sp, K, seeds, flush, mom_p)
         p_prof, p_prof_ge = _profiled_run(sp, K, 30_000 + rank, flush)
         sp.close()
         fl_grad, fl_end = _flops_per_grad(w)
@@ -535,6 +541,12 @@ def main():
                                        "note": "chosen minus plain, same seeds (same initial particles and "
                                                "momentum streams); compare with the between-seed sd"},
                  "seeds": "the timed seeds of the main line"}
+        if mom_c and mom_p:
+            # posterior means, chosen minus plain per seed, in posterior sd units
+            dm = [np.max(np.abs(mc[0] - mp[0]) / np.sqrt(mp[1])) for mc, mp in zip(mom_c, mom_p)]
+            plain["mean_paired_diff_sd_units"] = {"max_over_dims_mean_over_seeds": float(np.mean(dm)),
+                                                  "note": "compare with the Monte Carlo error of a mean, "
+                                                          "about 1/sqrt(ESS) sd"}
 
     # ---------------- other precisions of the same workload (tensor-core forms)
     variants = {}
