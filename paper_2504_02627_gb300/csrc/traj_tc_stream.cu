@@ -95,12 +95,23 @@ __device__ __forceinline__ void pack_unit(const float* v, uint4& hi, uint4& lo) 
     lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
 }
 
-// Residual on the hardware exponential and fast division (a few ulp; the
-// value is then split into BF16 parts with 2^-16 relative resolution).
+// Residual on the SFU's base-2 exponential and reciprocal in their flush-to-
+// zero forms (a few ulp; the value is then split into BF16 parts with 2^-16
+// relative resolution); e^-eta overflowing to +inf gives residual y.
 template <bool LOGIT>
 __device__ __forceinline__ float residual(float y, float eta, float inv_s2) {
-    if (LOGIT) return y - __fdividef(1.0f, 1.0f + __expf(-eta));
+    if (LOGIT) return y - tc::rcp_approx(1.0f + tc::ex2_approx(-1.4426950408889634f * eta));
     return (y - eta) * inv_s2;
+}
+
+// (a, b) -> BF16 pair hi (round to nearest even) and the BF16 pair of the
+// remainders (a - hi, b - hi): one conversion per pair for each part.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 template <bool LOGIT, int NP>
@@ -376,15 +387,17 @@ __global__ void __launch_bounds__(S_THREADS, 1) traj_stream_kernel(DevModel m, T
                             __syncwarp();
                             if (lane == 0) tc::mbar_arrive(&eta_empty[b]);
                         }
-                        const float* yv = y_s + st * SC + 32 * h;
+                        const float4* yv = reinterpret_cast<const float4*>(y_s + st * SC + 32 * h);
                         uint32_t rh[16], rl[16];
 #pragma unroll
-                        for (int e = 0; e < 32; e += 2) {
-                            const float r0 = residual<LOGIT>(yv[e], eta[e], inv_s2);
-                            const float r1 = residual<LOGIT>(yv[e + 1], eta[e + 1], inv_s2);
-                            const float h0 = bf16_round(r0), h1 = bf16_round(r1);
-                            rh[e / 2] = pack_bf16(h0, h1);
-                            rl[e / 2] = pack_bf16(r0 - h0, r1 - h1);
+                        for (int e = 0; e < 32; e += 4) {
+                            const float4 y4 = yv[e / 4];     // the same four y for every lane
+                            const float r0 = residual<LOGIT>(y4.x, eta[e], inv_s2);
+                            const float r1 = residual<LOGIT>(y4.y, eta[e + 1], inv_s2);
+                            const float r2 = residual<LOGIT>(y4.z, eta[e + 2], inv_s2);
+                            const float r3 = residual<LOGIT>(y4.w, eta[e + 3], inv_s2);
+                            split_pair(r0, r1, rh[e / 2], rl[e / 2]);
+                            split_pair(r2, r3, rh[e / 2 + 1], rl[e / 2 + 1]);
                         }
                         tc::tmem_st16(rcol + 16 * h, rh);
                         if (NP == 2) tc::tmem_st16(rcol + 32 + 16 * h, rl);
