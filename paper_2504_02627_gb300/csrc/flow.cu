@@ -462,12 +462,23 @@ __device__ void flow_backward(const DevFlow& f, FlowSmem& s, float* c) {
     }
 }
 
-// grad log pi at x (dense Gaussian: -P (x - mu) with symmetric P read from L2;
-// banana pairs: closed form), into g.
+// grad log pi at x (dense Gaussian: -P (x - mu); banana pairs: closed form),
+// into g.  For the Gaussian, P and mu are first staged in `scratch` (the
+// conditioner's activation buffers, idle between a forward pass and the
+// backward pass) when they fit (`fits`), else read from L2.
 template <int TARGET>
-__device__ void target_grad(const DevModel& m, const float* x, float* g) {
+__device__ void target_grad(const DevModel& m, const float* x, float* g, float* scratch, bool fits) {
     const int t = threadIdx.x, D = m.D;
     if constexpr (TARGET == 0) {
+        const float* Pm = m.P;
+        const float* mu = m.mu;
+        if (fits) {
+            for (int e = t; e < D * D; e += FT) scratch[e] = __ldg(m.P + e);
+            for (int e = t; e < D; e += FT) scratch[D * D + e] = __ldg(m.mu + e);
+            __syncthreads();
+            Pm = scratch;
+            mu = scratch + D * D;
+        }
         const int db = t >> 3, pb = t & 7;
         if (4 * db < D) {
             float acc[4][4];
@@ -476,13 +487,13 @@ __device__ void target_grad(const DevModel& m, const float* x, float* g) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[i][q] = 0.0f;
             for (int k = 0; k < D; ++k) {
-                const float mk = __ldg(m.mu + k);
+                const float mk = mu[k];
                 const float4 x4 = *reinterpret_cast<const float4*>(x + k * FG + 4 * pb);
                 const float b0 = x4.x - mk, b1 = x4.y - mk, b2 = x4.z - mk, b3 = x4.w - mk;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int d = 4 * db + i;
-                    const float a = d < D ? __ldg(m.P + (int64_t)d * D + k) : 0.0f;
+                    const float a = d < D ? Pm[(int64_t)d * D + k] : 0.0f;
                     acc[i][0] = fmaf(a, b0, acc[i][0]);
                     acc[i][1] = fmaf(a, b1, acc[i][1]);
                     acc[i][2] = fmaf(a, b2, acc[i][2]);
@@ -534,6 +545,8 @@ __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FlowSmem s = flow_smem(smem_raw, f.D, f.H, f.L, f.O4);
     s.pm = reinterpret_cast<__nv_bfloat16*>(s.ld + FG);   // past the FP64 block: flow_smem_bytes from the base
+    // h1, h2, o and ch are contiguous: (3 H + O4) x 32 floats of scratch for P and mu
+    const bool pfits = m.kind == GAUSS_DENSE && m.D * m.D + m.D <= (3 * f.H + f.O4) * FG;
     __shared__ int64_t j_s[FG], src_s[FG];
     __shared__ int S_s[FG];
     __shared__ float eps_s[FG];
@@ -583,7 +596,7 @@ __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f,
     __syncthreads();
     if (a.eval_only) {
         // theta-space target evaluation (initial weights): no transport involved
-        target_grad<TARGET>(m, s.x, s.gx);
+        target_grad<TARGET>(m, s.x, s.gx, s.h1, pfits);
         __syncthreads();
         if (t < FG && j_s[t] >= 0) a.logpi_out[j_s[t]] = target_logpi<TARGET>(m, s.x, s.gx, t);
         for (int e = t; e < D * FG; e += FT) {
@@ -638,7 +651,7 @@ __global__ void __launch_bounds__(FT, 1) traj_flow_kernel(DevModel m, DevFlow f,
         for (int e = t; e < D * FG; e += FT) s.x[e] = s.z[e];
         __syncthreads();
         flow_forward<MMA>(f, s, s.x);            // s.x = T(z), s.ld = log|det dT/dz|
-        target_grad<TARGET>(m, s.x, s.gx);       // grad_x log pi
+        target_grad<TARGET>(m, s.x, s.gx, s.h1, pfits);       // grad_x log pi
         __syncthreads();
         for (int e = t; e < D * FG; e += FT) s.c[e] = s.gx[e];
         __syncthreads();
