@@ -37,18 +37,18 @@ struct GaussDenseM {
             g[a] = -acc;
         }
     }
-    // log pi = c - 1/2 (theta - mu)' P (theta - mu), in FP64
-    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM]) {
-        const int D = m.D;
-        const float* P = sm;
-        const float* mu = sm + D * D;
+    // log pi = c - 1/2 (theta - mu)' P (theta - mu) = c + 1/2 (theta - mu)' g
+    // with g = -P (theta - mu) the FP32 gradient at theta: FP32 products,
+    // FP64 accumulation (the FP64 quadratic form costs D^2 operations at the
+    // FP64 rate, a small fraction of the FP32 rate here)
+    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM],
+                                   const float (&g)[DM]) {
+        const float* mu = sm + m.D * m.D;
         double q = 0.0;
-        for (int a = 0; a < D; ++a) {
-            double row = 0.0;
-            for (int b = 0; b < D; ++b) row += (double)P[a * D + b] * ((double)th[b] - (double)mu[b]);
-            q += ((double)th[a] - (double)mu[a]) * row;
-        }
-        return m.lconst - 0.5 * q;
+#pragma unroll
+        for (int d = 0; d < DM; ++d)
+            if (d < m.D) q += (double)((th[d] - mu[d]) * g[d]);
+        return m.lconst + 0.5 * q;
     }
 };
 
@@ -73,12 +73,17 @@ struct BananaM {
         }
         if (DM & 1) g[DM - 1] = 0.0f;
     }
-    __device__ static double logpi(const DevModel& m, const float*, const float (&th)[DM]) {
+    // FP32 terms per pair, FP64 accumulation
+    __device__ static double logpi(const DevModel& m, const float*, const float (&th)[DM], const float (&)[DM]) {
+        const float a = (float)m.h0, b = (float)m.h1, half_inva = (float)(0.5 / m.h0);
         double s = 0.0;
-        for (int i = 0; i + 1 < m.D; i += 2) {
-            double xo = th[i], xe = th[i + 1];
-            double u = xe - m.h1 * (xo * xo - m.h0);
-            s += -0.5 * xo * xo / m.h0 - 0.5 * u * u;
+#pragma unroll
+        for (int i = 0; i + 1 < DM; i += 2) {
+            if (i + 1 < m.D) {
+                const float xo = th[i], xe = th[i + 1];
+                const float u = xe - b * (xo * xo - a);
+                s += (double)(-half_inva * xo * xo - 0.5f * u * u);
+            }
         }
         return s + m.lconst;
     }
@@ -118,7 +123,7 @@ struct HierM {
     }
     // FP32 terms per group, FP64 accumulation (as the GEMM-shaped models'
     // end points): FP64 runs at a small fraction of the FP32 rate here
-    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM]) {
+    __device__ static double logpi(const DevModel& m, const float* sm, const float (&th)[DM], const float (&)[DM]) {
         const float inv_2s2 = (float)(0.5 / (m.h0 * m.h0));
         const float mu = th[0], logtau = th[1], tau = expf(logtau);
         double s = -0.5 * (double)mu * (double)mu - 0.5 * (double)logtau * (double)logtau;
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajA
 
     if (a.eval_only) {
         M::grad(m, sm, th, g);
-        double lp = M::logpi(m, sm, th);
+        double lp = M::logpi(m, sm, th, g);
 #pragma unroll
         for (int d = 0; d < DM; ++d)
             if (d < D) a.grad_out[(int64_t)d * a.ld + j] = g[d];
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajA
 #pragma unroll
         for (int d = 0; d < DM; ++d) p[d] = fmaf(he, g[d], p[d]);
     }
-    const double lp1 = M::logpi(m, sm, th);
+    const double lp1 = M::logpi(m, sm, th, g);
     double kin1 = 0.0;
 #pragma unroll
     for (int d = 0; d < DM; ++d) kin1 += (double)p[d] * (double)p[d];
