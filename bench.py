@@ -72,6 +72,19 @@ def _workload(name):
     raise ValueError(name)
 
 
+def aggregate_ranks(torch, dist, dev_ms, grad_evals, ess, device):
+    """Whole-job numbers of independent replicas: the device time is the
+    slowest rank's (max over ranks), work and ESS add up (sum over ranks).
+    Without a process group the rank's own numbers are returned."""
+    if not dist:
+        return float(dev_ms), float(grad_evals), float(ess)
+    t = torch.tensor([dev_ms, float(grad_evals), ess], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), float(t[2])
+
+
 def _timed_runs(torch, smp, K, seeds, flush, moments=None):
     """One full sampler run per seed, each bracketed by CUDA events on the
     sampler's stream after an L2 flush; returns (device ms, gradient
@@ -505,15 +518,7 @@ def main():
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
     prof, prof_ge = _profiled_run(smp, K, 30_000 + rank, flush)
-    t = torch.tensor([dev_ms, float(ge_total), ess_post], dtype=torch.float64, device="cuda")
-    if dist:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dev_ms = float(tmax[0])
-        ge_all, ess_all = float(t[1]), float(t[2])
-    else:
-        ge_all, ess_all = float(ge_total), ess_post
+    dev_ms, ge_all, ess_all = aggregate_ranks(torch, dist, dev_ms, ge_total, ess_post, "cuda")
     value = ge_all / (dev_ms / 1e3)
 
     # ---------------- plain FP32 on the same seeds: the comparison the metric names

@@ -397,3 +397,28 @@ def test_warp_mma_ceiling_probe():
     assert g.lib().smc_k_mma_peak(1 << 12, C.byref(v), stream()) == 0
     assert np.isfinite(v.value) and 100.0 < v.value < 2500.0, v.value
     assert g.lib().smc_k_mma_peak(0, C.byref(v), stream()) != 0
+
+
+@pytest.mark.parametrize("name,N,eps", [("banana50", 8192, 0.05), ("hier", 278_000, 0.01)])
+def test_thread_kernel_trajectories_at_bench_size(name, N, eps):
+    """The thread-per-particle kernels at the particle counts the benchmark
+    runs (the banana of the preconditioner comparison, the 278 k particles of
+    the batched hierarchical workload): ragged step counts 0..12, a seeded
+    sample of 150 particles and the last one against the oracle."""
+    w = rounded_workload(_workloads()[name])
+    t = oracle_target(w)
+    dm = _model(w)
+    rng = np.random.default_rng(N)
+    th = _theta(w, N, seed=N + 7)
+    p = f32r(rng.standard_normal((N, w["D"])))
+    steps = rng.integers(0, 13, N)
+    th_g, p_g, lp_g = _leapfrog_gpu(dm, th, p, steps, eps)
+    idx = np.sort(rng.choice(N, 150, replace=False))
+    idx[-1] = N - 1
+    th_o, p_o, _, lp_o = oracle.leapfrog(t, th[idx], p[idx], eps, steps[idx])
+    for a, j in enumerate(idx):
+        tol = 1e-5 * max(1, steps[j])
+        np.testing.assert_allclose(th_g[j], th_o[a], rtol=tol, atol=tol * _rms(th_o[a]))
+        np.testing.assert_allclose(p_g[j], p_o[a], rtol=tol, atol=tol * _rms(p_o[a]))
+    _, ls = _summand_scale(w, th_o)
+    assert np.all(np.abs(lp_g[idx] - lp_o) <= 1e-5 * steps[idx].clip(1) * ls)
