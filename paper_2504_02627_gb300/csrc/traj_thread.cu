@@ -93,25 +93,29 @@ struct BananaM {
 // theta = (mu, log tau, eta_1..eta_G), b_g = mu + tau eta_g.
 template <int DM>
 struct HierM {
-    static size_t smem_bytes(const DevModel& m) { return (size_t)3 * m.n * sizeof(float); }
+    // shared memory: (ybar_g, n_g / sigma^2) pairs for the gradient (one 8-byte
+    // load per group), then n_g and the within-group sums of squares
+    static size_t smem_bytes(const DevModel& m) { return (size_t)4 * m.n * sizeof(float); }
     __device__ static void load(const DevModel& m, float* sm) {
+        const float inv_s2 = (float)(1.0 / (m.h0 * m.h0));
         for (int i = threadIdx.x; i < m.n; i += blockDim.x) {
-            sm[i] = m.gmean[i];
-            sm[m.n + i] = m.gn[i];
-            sm[2 * m.n + i] = m.gss[i];
+            sm[2 * i] = m.gmean[i];
+            sm[2 * i + 1] = m.gn[i] * inv_s2;
+            sm[2 * m.n + i] = m.gn[i];
+            sm[3 * m.n + i] = m.gss[i];
         }
     }
     __device__ static void grad(const DevModel& m, const float* sm, const float (&th)[DM], float (&g)[DM]) {
-        const float inv_s2 = (float)(1.0 / (m.h0 * m.h0));
+        const float2* st = reinterpret_cast<const float2*>(sm);
         const float mu = th[0], logtau = th[1], tau = expf(logtau);
         float dmu = 0.0f, dlt = 0.0f;
 #pragma unroll
         for (int d = 2; d < DM; ++d) {
             float gd = 0.0f;
             if (d < m.D) {
-                const int k = d - 2;
-                float eta = th[d];
-                float r = sm[m.n + k] * (sm[k] - fmaf(tau, eta, mu)) * inv_s2;
+                const float2 yn = st[d - 2];               // ybar_g, n_g / sigma^2
+                const float eta = th[d];
+                const float r = yn.y * (yn.x - fmaf(tau, eta, mu));
                 dmu += r;
                 dlt = fmaf(r * tau, eta, dlt);
                 gd = fmaf(r, tau, -eta);
@@ -132,8 +136,8 @@ struct HierM {
             if (d < m.D) {
                 const int k = d - 2;
                 const float eta = th[d];
-                const float dev = sm[k] - fmaf(tau, eta, mu);
-                const float term = -fmaf(sm[m.n + k] * dev, dev, sm[2 * m.n + k]) * inv_2s2 - 0.5f * eta * eta;
+                const float dev = sm[2 * k] - fmaf(tau, eta, mu);
+                const float term = -fmaf(sm[2 * m.n + k] * dev, dev, sm[3 * m.n + k]) * inv_2s2 - 0.5f * eta * eta;
                 s += (double)term;
             }
         }
