@@ -269,9 +269,12 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
         run = dict(w["run"], step_size=eps, n_iters=K, n_warmup=M)
         md = g.ModelData.from_workload(w)
         res = {}
-        for arm in ("plain", "flow", "flow_bf16"):
-            smp = g.Sampler(md, g.make_config(seed=4242, **run), stream)
-            if arm != "plain":
+        arms = ("plain", "plain_bf16x3", "flow", "flow_bf16") if w["kind"] == "gauss_dense" else \
+            ("plain", "flow", "flow_bf16")
+        for arm in arms:
+            prec = 1 if arm == "plain_bf16x3" else 0
+            smp = g.Sampler(md, g.make_config(seed=4242, precision=prec, **run), stream)
+            if arm.startswith("flow"):
                 smp.enable_flow(workloads.flow_init(w["D"], H, L, seed=5), H, L, train_every=2, epochs=20,
                                 lr=1e-3, min_ess_frac=0.25, precision=2 if arm == "flow_bf16" else 0)
             smp.run(2)                      # first launches (function attributes, graph capture) untimed
@@ -297,7 +300,7 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
                  "var_rel_err": float(np.sqrt(np.mean((v / v_t - 1.0) ** 2))),
                  "log_z": summ["log_z"], "log_z_closed_form": lz_t,
                  "traj_share": prof["traj_ms"] / ms}
-            if arm != "plain":
+            if arm.startswith("flow"):
                 fl = _flow_flops_per_grad(w, H, L) * (summ["grad_evals"] + run["n_particles"] * K)
                 r["flow_traj_tflops"] = fl / (prof["traj_ms"] / 1e3) / 1e12
                 if arm == "flow":
@@ -309,7 +312,8 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
             res[arm] = r
         res["config"] = {"N": run["n_particles"], "K": K, "M_warmup": M, "eps": eps, "flow": f"{L} coupling layers, "
                          f"width {H}, tanh, Adam lr 1e-3, 20 epochs every 2 warm-up iterations, ESS gate 0.25 J; "
-                         f"flow: FP32 conditioner products, flow_bf16: BF16 warp-MMA products (training FP32)"}
+                         f"flow: FP32 conditioner products, flow_bf16: BF16 warp-MMA products (training FP32); "
+                         f"plain_bf16x3: no map, the Gaussian's P (theta - mu) on BF16x3 warp MMAs"}
         out[name] = res
     return out
 

@@ -103,6 +103,9 @@ bool traj_glm_stream_supported(const DevModel& m);
 // warp-level BF16 tensor-core path with X resident in shared memory
 // (traj_glm_mma.cu): D <= 32, n up to about 1300 (x3) / 2400 (BF16)
 bool traj_glm_mma_supported(const DevModel& m, bool x3);
+// warp-level BF16 tensor-core path for the dense Gaussian (traj_gauss_mma.cu): D <= 128
+bool traj_gauss_mma_supported(const DevModel& m);
+cudaError_t launch_traj_gauss_mma(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
 cudaError_t launch_traj_glm_mma(const DevModel& m, const TrajArgs& a, bool x3, cudaStream_t s);
 cudaError_t launch_traj_glm_stream(const DevModel& m, const TrajArgs& a, cudaStream_t s);
 bool traj_stream_supported(const DevModel& m);

@@ -594,8 +594,11 @@ bool glm_shape_ok(const DevModel& m) {
 }  // namespace
 
 bool traj_supported(const DevModel& m, int32_t precision) {
-    if (precision == 1) return traj_glm_mma_supported(m, true) || traj_tc_supported(m);
-    if (precision == 2) return traj_glm_mma_supported(m, false) || traj_tc_supported(m) || traj_stream_supported(m);
+    if (precision == 1 || precision == 2) {
+        if (m.kind == GAUSS_DENSE) return traj_gauss_mma_supported(m);
+        if (precision == 1) return traj_glm_mma_supported(m, true) || traj_tc_supported(m);
+        return traj_glm_mma_supported(m, false) || traj_tc_supported(m) || traj_stream_supported(m);
+    }
     if (precision == 3) return traj_stream_supported(m);
     switch (m.kind) {
         case GAUSS_DENSE: return precision == 0 && m.D <= 128;
@@ -615,6 +618,8 @@ int32_t traj_tile_count(const DevModel& m, int32_t precision) {
 
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s) {
     if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
+    if ((precision == 1 || precision == 2) && m.kind == GAUSS_DENSE)
+        return launch_traj_gauss_mma(m, a, precision == 1, s);
     if (precision == 1)
         return traj_glm_mma_supported(m, true) ? launch_traj_glm_mma(m, a, true, s) : launch_traj_tc(m, a, true, s);
     if (precision == 2) {

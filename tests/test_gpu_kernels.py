@@ -321,7 +321,7 @@ TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
 
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("name", ["logistic_small", "logistic", "linear", "logistic_d28", "linear_d25",
-                                  "logistic_n1700"])
+                                  "logistic_n1700", "gauss10", "gauss100", "illcond100"])
 @pytest.mark.parametrize("N", [1, 45, 300])
 def test_tc_target_value_and_gradient(name, N, precision):
     w = rounded_workload(_workloads()[name])
@@ -347,7 +347,9 @@ def test_tc_target_value_and_gradient(name, N, precision):
 @pytest.mark.parametrize("name,eps,N", [("logistic", 1e-3, 257), ("logistic_small", 0.01, 257),
                                         ("linear", 0.005, 257), ("logistic_d28", 0.002, 257),
                                         ("linear_d25", 1e-3, 257), ("logistic_n1700", 1e-3, 257),
-                                        ("logistic", 1e-3, 4096), ("logistic", 1e-3, 20000)])
+                                        ("logistic", 1e-3, 4096), ("logistic", 1e-3, 20000),
+                                        ("gauss10", 0.1, 257), ("gauss100", 0.005, 257),
+                                        ("illcond100", 1e-3, 257), ("gauss100", 0.005, 8192)])
 def test_tc_one_leapfrog_step(name, eps, N, precision):
     """One step: theta_1 = theta_0 + eps (p_0 + eps/2 g_0), p_1 = p_0 + eps/2 (g_0 + g_1);
     a gradient error dg moves p by at most eps*dg and theta by eps^2/2 dg.  At the

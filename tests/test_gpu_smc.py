@@ -207,14 +207,15 @@ def test_degenerate_target_reports_status():
     smp.close()
 
 
-@pytest.mark.parametrize("precision", [1, 2, 3])
-def test_tensor_core_iterations_keep_exact_weights(precision):
+@pytest.mark.parametrize("name,precision", [("logistic", 1), ("logistic", 2), ("logistic", 3),
+                                            ("gauss10", 1), ("gauss10", 2)])
+def test_tensor_core_iterations_keep_exact_weights(name, precision):
     """Tensor-core trajectories (BF16x3 / BF16 / streamed BF16x2 gradients): resampling and step
     counts are still bit-exact, and the weights use the exact energy at the
     GPU's own end points -- Delta H from the oracle's FP64 log pi at the GPU
     positions and momenta matches to FP32 accuracy, so the sampler stays exact
     whatever the gradient precision."""
-    w = rounded_workload(_cases()["logistic"])
+    w = rounded_workload(_cases()[name])
     run = w["run"]
     t = oracle_target(w)
     seed = 77
