@@ -111,16 +111,24 @@ __device__ __forceinline__ void normal_pair(uint64_t seed, uint32_t i, uint32_t 
     z1 = r * s;
 }
 
-// The same pair from the same Philox block with the transform in FP32: the
-// top 24 bits of words x and z as uniforms (m + 1/2) 2^-24, FP32 log, sqrt
-// and sincospi.  Differs from the FP64 pair by about 1e-7 relative; used
-// where a thread draws a whole particle's momentum, since FP64 runs at a
-// small fraction of the FP32 rate on this GPU.
+// The same pair from the same Philox block with the transform in FP32.  Each
+// uniform is the FP64 pair's (m + 1/2) 2^-52 (m the same 52-bit integer)
+// rounded to FP32 with relative error below 2^-23: the high 24 bits of m are
+// exact in FP32, the low 28 bits plus the half are converted once and added
+// with one rounding.  Keeping the relative precision of u1 matters in the
+// tail, where log u1 amplifies it.  FP32 log, sqrt and sincospi then put the
+// pair within about 1e-7 relative of the FP64 one; used where a thread draws
+// whole particles' momenta, since FP64 runs at a small fraction of the FP32
+// rate on this GPU.
+__device__ __forceinline__ float u01_52_f32(uint32_t a, uint32_t b) {
+    const float hi = (float)(a >> 8);                                    // bits 51..28 of m
+    const float lo = (float)((((a >> 6) & 3u) << 26) | (b >> 6)) + 0.5f;  // bits 27..0, plus 1/2
+    return fmaf(lo, 3.7252902984619140625e-9f, hi) * 5.9604644775390625e-8f;   // (hi + lo 2^-28) 2^-24
+}
 __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t i, uint32_t j, uint32_t k,
                                                 uint32_t tag, float& z0, float& z1) {
     Philox4 w = philox4x32_10(Philox4{i, j, k, tag}, seed);
-    const float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
-    const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u1 = u01_52_f32(w.x, w.y), u2 = u01_52_f32(w.z, w.w);
     const float r = sqrtf(-2.0f * logf(u1));
     float s, c;
     sincospif(2.0f * u2, &s, &c);

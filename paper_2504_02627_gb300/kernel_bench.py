@@ -4,6 +4,7 @@ micro-benchmark and the profiling driver for one trajectory kernel at a time).
     python -m paper_2504_02627_gb300.kernel_bench stream --n 20000 --particles 16384 --steps 40
     python -m paper_2504_02627_gb300.kernel_bench flow --particles 8192 --steps 8
     python -m paper_2504_02627_gb300.kernel_bench glm --particles 4096 --steps 20
+    python -m paper_2504_02627_gb300.kernel_bench gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
 
 Each run makes seeded synthetic inputs (the workloads of this repository),
 launches one target evaluation and one leapfrog trajectory of `--steps` steps
@@ -72,6 +73,31 @@ def run_glm_like(args, streamed):
             "steps": args.steps, "precision": prec, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
+def run_gauss(args):
+    """The 100-d Gaussian (condition 1e4): FP32 dense kernel (precision 0) or
+    the warp-MMA kernel (1: BF16x3, 2: BF16)."""
+    torch, workloads, B = _setup()
+    s = torch.cuda.current_stream().cuda_stream
+    w = workloads.gauss100_cond()
+    prec = B.PREC_FP32 if args.precision is None else args.precision
+    N, D = args.particles, w["D"]
+    dm = B.DevModel(B.ModelData.from_workload(w), s)
+    rng = np.random.default_rng(2)
+    th = torch.tensor((0.05 * rng.standard_normal((D, N))).astype(np.float32)).cuda()
+    p = torch.randn(D, N, device="cuda")
+    gr = torch.zeros(D, N, device="cuda")
+    lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+    steps = torch.full((N,), args.steps, dtype=torch.int32, device="cuda")
+    lib = B.lib()
+    B.check(lib.smc_k_target(dm.h, th.data_ptr(), N, N, lp.data_ptr(), gr.data_ptr(), prec, s), "smc_k_target")
+    ms = _time(torch, lambda: B.check(lib.smc_k_leapfrog(dm.h, th.data_ptr(), p.data_ptr(), gr.data_ptr(),
+                                                         lp.data_ptr(), steps.data_ptr(), args.eps, N, N, prec, s),
+                                      "smc_k_leapfrog"))
+    flops = 2.0 * D * D * N * (args.steps + 1)
+    return {"kernel": "dense Gaussian " + ("FP32" if prec == 0 else "warp-MMA"), "D": D, "particles": N,
+            "steps": args.steps, "precision": prec, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
+
+
 def run_flow(args):
     torch, workloads, B = _setup()
     s = torch.cuda.current_stream().cuda_stream
@@ -106,7 +132,7 @@ def run_flow(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["stream", "flow", "glm"])
+    ap.add_argument("which", choices=["stream", "flow", "glm", "gauss"])
     ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
     ap.add_argument("--particles", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=40)
@@ -119,6 +145,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.which == "flow":
         out = run_flow(args)
+    elif args.which == "gauss":
+        out = run_gauss(args)
     else:
         out = run_glm_like(args, streamed=args.which == "stream")
     print(json.dumps(out), flush=True)
