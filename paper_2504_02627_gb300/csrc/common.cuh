@@ -165,6 +165,25 @@ __device__ __forceinline__ T warp_max(T v) {
     return v;
 }
 
+// Warp sums of 16 values per lane: on return each lane holds the total over
+// the 32 lanes of value (lane >> 1) & 15.  A reduce-scatter butterfly: at
+// each level a lane keeps half of its values and adds the partner's copy of
+// that half, 16 additions per lane instead of 80 for 16 separate butterflies.
+// The order is fixed, and both lanes of a pair get the same bits.
+__device__ __forceinline__ double warp_sum16_scatter(double (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const double send = up ? v[k] : v[k + h];
+            const double keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Block-wide reduction through shared memory; every thread gets the result.
 // `buf` needs blockDim.x / 32 entries.
 template <typename T, typename Op>

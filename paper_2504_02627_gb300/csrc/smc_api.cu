@@ -195,6 +195,10 @@ std::string upload_model(smc_dev_model* dm, const smc_model* md, cudaStream_t s)
             if (xl) cudaMemcpyAsync(xl, Xl.data(), Xl.size() * 2, cudaMemcpyHostToDevice, s);
             m.Xbf = xh;
             m.Xbf_lo = xl;
+            if (D <= 32 && n <= 4096 && xh && xl) {   // the warp-MMA kernel keeps X on chip
+                uint16_t* img = dm->mem.get<uint16_t>((size_t)glm_mma_image_elems(n));
+                if (img && build_glm_mma_image(xh, xl, n, (int)D, (int)Dp, img, s) == cudaSuccess) m.xmma_img = img;
+            }
             if (D <= 128) {
                 // per-chunk shared-memory images for the streamed tensor-core path:
                 // 128-byte swizzle (16-byte unit u of row r stored at unit u ^ (r & 7))

@@ -23,6 +23,10 @@ struct DevModel {
     const float* gss;     // [n]         within-group sums of squares
     const uint16_t* Xbf;  // [n x Dp] bf16 (high part), tensor-core paths
     const uint16_t* Xbf_lo; // [n x Dp] bf16 residual x - bf16(x)
+    // D <= 32: X hi and lo as two [n16][32] bf16 row blocks (rows padded to a
+    // multiple of 16, dims to 32, zeros) in the warp-MMA kernel's swizzled
+    // shared-memory order, so staging them is a straight 16-byte copy
+    const uint16_t* xmma_img;
     double h0, h1;        // LOGISTIC: tau; LINEAR: sigma, tau; HIER: sigma; BANANA: a, b
     double lconst;        // theta-independent part of log pi
     // Streamed tensor-core operands (GEMM-shaped models with D <= 128): X in
@@ -82,6 +86,11 @@ __device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& 
 // Launchers (kernels in traj_simt.cu / traj_tc.cu).  Return cudaError_t of
 // the launch; `supported` reports whether the model/shape has a kernel.
 bool traj_supported(const DevModel& m, int32_t precision);
+// warp-MMA GLM kernel's X image (DevModel::xmma_img): elements to allocate for
+// n observations, and the kernel that fills it from the BF16 hi / lo rows
+int64_t glm_mma_image_elems(int64_t n);
+cudaError_t build_glm_mma_image(const uint16_t* xh, const uint16_t* xl, int64_t n, int D, int Dp,
+                                uint16_t* img, cudaStream_t s);
 // Launch-configuration variants of the model's trajectory kernel that the
 // host autotuner may choose between (1: nothing to choose).  Every variant
 // runs the same arithmetic in the same order, so the choice never changes a

@@ -25,10 +25,11 @@ namespace smc {
 namespace {
 
 constexpr int GG_P = 16;   // particles per CTA (the M of the MMA)
+constexpr int AT_LD = 20;  // row stride of the end point's (theta - mu) rows: conflict-free stores
 
 // Dynamic shared memory (bytes), DK = D rounded up to 16:
 //   A operand: two buffers of (hi, lo) [16][DK + 8] bf16; at the end point
-//     the same bytes hold (theta - mu) [DK][16] f32 |
+//     the same bytes hold (theta - mu) [DK][20] f32 |
 //   P [D][D + 1] f32 (end point) | kinetic partials [2][8][16] f64 |
 //   end-point partial sums [32 KS][4] f64
 struct GgLayout {
@@ -80,6 +81,13 @@ __device__ __forceinline__ double gg_quad_sum(double v) {
     return v;
 }
 
+// sum of the squares of a thread's four momentum elements of particle half h
+__device__ __forceinline__ float gg_sq4(const float (&pp)[2][4], int h) {
+    const float a = fmaf(pp[0][2 * h], pp[0][2 * h], pp[0][2 * h + 1] * pp[0][2 * h + 1]);
+    const float b = fmaf(pp[1][2 * h], pp[1][2 * h], pp[1][2 * h + 1] * pp[1][2 * h + 1]);
+    return a + b;
+}
+
 // KS = DK / 16 k-steps and warps.  Thread (warp w, lane 4 gq + tq) holds the
 // state elements (u, 2 h + v), u, h, v in {0, 1}: particle gq + 8 h of the
 // CTA, dimension 16 w + 8 u + 2 tq + v -- the m16n8 accumulator layout of
@@ -102,6 +110,7 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
     __shared__ uint64_t seed_s[GG_P];
     __shared__ uint32_t k_s[GG_P], jl_s[GG_P];
     __shared__ int S_s[GG_P];
+    __shared__ double lp_s[GG_P];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int gq = lane >> 2, tq = lane & 3;
@@ -208,16 +217,12 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
                 }
             }
     }
-    // kinetic energy of the starting momenta, per (warp, particle)
+    // kinetic energy of the starting momenta, per (warp, particle): a thread's
+    // four squares summed in FP32, FP64 from the quad sum on
     if (!a.eval_only) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            double k = 0.0;
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int v = 0; v < 2; ++v) k += (double)pp[u][2 * h + v] * (double)pp[u][2 * h + v];
-            k = gg_quad_sum(k);
+            const double k = gg_quad_sum((double)gg_sq4(pp, h));
             if (tq == 0) kin_s[wid * GG_P + gq + 8 * h] = k;
         }
     }
@@ -263,11 +268,14 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
         const int buf = (s - 1) & 1;
         const uint32_t ahb = a_lane + (uint32_t)(2 * buf) * a_mat;
         // ---- G = -(Theta - mu)^T P for this warp's 16 output dimensions
-        float acc[2][4];
+        // two accumulators per n-tile halve the dependent MMA chain: hi*hi in
+        // acc and the two correction products in cor (x3), or even and odd
+        // k-steps (plain BF16)
+        float acc[2][4], cor[2][4];
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[u][e] = 0.0f;
+            for (int e = 0; e < 4; ++e) acc[u][e] = cor[u][e] = 0.0f;
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
             uint32_t ah[4], al[4];
@@ -275,17 +283,19 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
             if (X3) gg_ldsm4(al, ahb + a_mat + 32 * ks);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                gg_mma(acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
                 if (X3) {
-                    gg_mma(acc[u], al, bh[ks][u][0], bh[ks][u][1]);
-                    gg_mma(acc[u], ah, bl[ks][u][0], bl[ks][u][1]);
+                    gg_mma(acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
+                    gg_mma(cor[u], al, bh[ks][u][0], bh[ks][u][1]);
+                    gg_mma(cor[u], ah, bl[ks][u][0], bl[ks][u][1]);
+                } else {
+                    gg_mma((ks & 1) ? cor[u] : acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) gr[u][e] = -acc[u][e];
+            for (int e = 0; e < 4; ++e) gr[u][e] = -(acc[u][e] + cor[u][e]);
         // ---- closing half kick of step s; opening kick + drift of step s + 1
         //      and its A operand into the other buffer (its readers, step
         //      s - 1, finished at the previous barrier)
@@ -309,63 +319,67 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
         __syncthreads();
     }
 
-    // ---- end point.  (theta - mu) transposed [DK][16] f32 over the A tiles
+    // ---- end point.  (theta - mu) transposed [DK][AT_LD] f32 over the A tiles
     //      (free after the last barrier); kinetic energy of the final momenta
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int d = 16 * wid + 8 * u + 2 * tq + (e & 1), q = gq + 8 * (e >> 1);
-            at_s[d * GG_P + q] = th[u][e] - mu[u][e & 1];
+            at_s[d * AT_LD + q] = th[u][e] - mu[u][e & 1];
         }
     if (!a.eval_only) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            double k = 0.0;
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int v = 0; v < 2; ++v) k += (double)pp[u][2 * h + v] * (double)pp[u][2 * h + v];
-            k = gg_quad_sum(k);
+            const double k = gg_quad_sum((double)gg_sq4(pp, h));
             if (tq == 0) kin_s[(8 + wid) * GG_P + gq + 8 * h] = k;
         }
     }
     tc::cp_async_wait<0>();
     __syncthreads();
     // (theta - mu)' P (theta - mu): thread t takes particles 4 (t & 3) .. + 3 and
-    // rows t / 4, t / 4 + NTH / 4, ...; each row product in FP32, the terms
-    // accumulated in FP64, the per-thread sums added in thread order
+    // rows t / 4, t / 4 + NTH / 4, ... (at most two, as 8 KS >= D / 2); each
+    // row product in FP32, a thread's terms summed in FP32, FP64 from there on
     {
         const int g4 = tid & 3;
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int r = tid >> 2; r < D; r += NTH / 4) {
             const float* prow = pf_s + r * (D + 1);
             float row[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             for (int c = 0; c < D; ++c) {
                 const float pv = prow[c];
-                const float4 av = *reinterpret_cast<const float4*>(at_s + c * GG_P + 4 * g4);
+                const float4 av = *reinterpret_cast<const float4*>(at_s + c * AT_LD + 4 * g4);
                 row[0] = fmaf(pv, av.x, row[0]);
                 row[1] = fmaf(pv, av.y, row[1]);
                 row[2] = fmaf(pv, av.z, row[2]);
                 row[3] = fmaf(pv, av.w, row[3]);
             }
-            const float4 ar = *reinterpret_cast<const float4*>(at_s + r * GG_P + 4 * g4);
-            s4[0] += (double)(ar.x * row[0]);
-            s4[1] += (double)(ar.y * row[1]);
-            s4[2] += (double)(ar.z * row[2]);
-            s4[3] += (double)(ar.w * row[3]);
+            const float4 ar = *reinterpret_cast<const float4*>(at_s + r * AT_LD + 4 * g4);
+            s4[0] = fmaf(ar.x, row[0], s4[0]);
+            s4[1] = fmaf(ar.y, row[1], s4[1]);
+            s4[2] = fmaf(ar.z, row[2], s4[2]);
+            s4[3] = fmaf(ar.w, row[3], s4[3]);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) part_s[tid * 4 + i] = s4[i];
+        for (int i = 0; i < 4; ++i) part_s[tid * 4 + i] = (double)s4[i];
+    }
+    __syncthreads();
+    // per particle q: the NTH / 4 partial sums of threads (q >> 2) + 4 r, in
+    // four interleaved chains (items 4 q .. 4 q + 3, one quad of lanes) joined
+    // by a quad sum; 4 GG_P = 64 items, so whole warps take part
+    for (int e = tid; e < 4 * GG_P; e += NTH) {
+        const int q = e >> 2, c = e & 3;
+        double qf = 0.0;
+        for (int r = c; r < NTH / 4; r += 4) qf += part_s[((q >> 2) + 4 * r) * 4 + (q & 3)];
+        qf = gg_quad_sum(qf);
+        if (c == 0) lp_s[q] = qf;
     }
     __syncthreads();
     if (tid < GG_P) {
         const int q = tid;
         const int64_t j = j_s[q];
         if (j >= 0) {
-            double qf = 0.0;
-            for (int t = q >> 2; t < NTH; t += 4) qf += part_s[t * 4 + (q & 3)];
-            const double lp1 = m.lconst - 0.5 * qf;
+            const double lp1 = m.lconst - 0.5 * lp_s[q];
             a.logpi_out[j] = lp1;
             if (!a.eval_only) {
                 double kin0 = 0.0, kin1 = 0.0;

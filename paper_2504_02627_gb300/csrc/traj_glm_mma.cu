@@ -143,27 +143,15 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int gq = lane >> 2, tq = lane & 3;   // MMA fragment row group / column pair
 
-    // ---- X (BF16 hi, lo) and y into shared memory; rows past n are zero
-    for (int e = tid; e < L.n16 * 4; e += GM_T) {
-        const int r = e >> 2, c = e & 3;
-        uint32_t hv[4] = {0u, 0u, 0u, 0u}, lv[4] = {0u, 0u, 0u, 0u};
-        if (r < n) {
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int d = 8 * c + 2 * h;
-                const uint32_t h0 = d < D ? m.Xbf[(int64_t)r * m.Dp + d] : 0u;
-                const uint32_t h1 = d + 1 < D ? m.Xbf[(int64_t)r * m.Dp + d + 1] : 0u;
-                hv[h] = h0 | (h1 << 16);
-                if (X3) {
-                    const uint32_t l0 = d < D ? m.Xbf_lo[(int64_t)r * m.Dp + d] : 0u;
-                    const uint32_t l1 = d + 1 < D ? m.Xbf_lo[(int64_t)r * m.Dp + d + 1] : 0u;
-                    lv[h] = l0 | (l1 << 16);
-                }
-            }
-        }
-        const uint32_t off = gm_xoff(r, c);
-        *reinterpret_cast<uint4*>(smem_raw + L.xh + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        if (X3) *reinterpret_cast<uint4*>(smem_raw + L.xl + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    // ---- X (BF16 hi, lo): the pre-swizzled image copied asynchronously
+    //      (waited on before the first product); y; rows past n are zero
+    {
+        const uint4* img = reinterpret_cast<const uint4*>(m.xmma_img);
+        const int nv = L.n16 * 4;   // 16-byte units per block
+        for (int e = tid; e < nv; e += GM_T) tc::cp_async16(smem_raw + L.xh + 16 * (size_t)e, img + e);
+        if (X3)
+            for (int e = tid; e < nv; e += GM_T) tc::cp_async16(smem_raw + L.xl + 16 * (size_t)e, img + nv + e);
+        tc::cp_async_commit();
     }
     for (int i = tid; i < L.n16; i += GM_T) y_s[i] = i < n ? m.y[i] : 0.0f;
     const float inv_tau2 = LOGIT ? (float)(1.0 / (m.h0 * m.h0)) : (float)(1.0 / (m.h1 * m.h1));
@@ -251,6 +239,7 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
             th_s[e] = fmaf(ef, pv, th_s[e]);
         }
     }
+    tc::cp_async_wait<0>();
     __syncthreads();
 
     // ldmatrix lane roles: matrix mi = lane / 8, row lane % 8 of it
@@ -388,11 +377,12 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
     }
 
     // ---- end-point log pi: FP32 products with the FP32 X (each row read once
-    //      per CTA, by one thread, for all 16 particles), FP64 accumulation
+    //      per CTA, by one thread, for all 16 particles); a thread's few terms
+    //      (ceil(n / 512) observations) summed in FP32, FP64 from there on
     {
-        double ll[GM_P];
+        float llf[GM_P];
 #pragma unroll
-        for (int q = 0; q < GM_P; ++q) ll[q] = 0.0;
+        for (int q = 0; q < GM_P; ++q) llf[q] = 0.0f;
         for (int i = tid; i < n; i += GM_T) {
             float x[GM_DK];
             const float4* xr = reinterpret_cast<const float4*>(m.X + (int64_t)i * m.Dp);
@@ -423,19 +413,17 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                     const float z = (yv - eta) * inv_s;
                     term = -0.5f * z * z;
                 }
-                ll[q] += (double)term;
+                llf[q] += term;
             }
         }
-        // sum over the threads: lanes by shuffles, warps through shared memory
+        // sum over the threads: lanes by a reduce-scatter butterfly (lane pair
+        // 2 q, 2 q + 1 ends with particle q), warps through shared memory
         double* red64 = reinterpret_cast<double*>(red);   // [GM_W][GM_P]
+        double ll[GM_P];
 #pragma unroll
-        for (int q = 0; q < GM_P; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ll[q] += __shfl_xor_sync(0xffffffffu, ll[q], o);
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < GM_P; ++q) red64[wid * GM_P + q] = ll[q];
+        for (int q = 0; q < GM_P; ++q) ll[q] = (double)llf[q];
+        const double wsum = warp_sum16_scatter(ll, lane);
+        if ((lane & 1) == 0) red64[wid * GM_P + (lane >> 1)] = wsum;
         __syncthreads();
         if (tid < GM_P) {
             double tot = 0.0;
@@ -490,11 +478,48 @@ cudaError_t launch_gm(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The X image: unit c (dims 8c .. 8c + 7) of row r of the hi block at byte
+// gm_xoff(r, c), the lo block after it
+__global__ void k_glm_mma_image(const uint16_t* __restrict__ xh, const uint16_t* __restrict__ xl, int n, int n16,
+                                int D, int Dp, uint16_t* __restrict__ img) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n16 * 4) return;
+    const int r = e >> 2, c = e & 3;
+    uint32_t hv[4] = {0u, 0u, 0u, 0u}, lv[4] = {0u, 0u, 0u, 0u};
+    if (r < n) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int d = 8 * c + 2 * h;
+            const uint32_t h0 = d < D ? xh[(int64_t)r * Dp + d] : 0u;
+            const uint32_t h1 = d + 1 < D ? xh[(int64_t)r * Dp + d + 1] : 0u;
+            const uint32_t l0 = d < D ? xl[(int64_t)r * Dp + d] : 0u;
+            const uint32_t l1 = d + 1 < D ? xl[(int64_t)r * Dp + d + 1] : 0u;
+            hv[h] = h0 | (h1 << 16);
+            lv[h] = l0 | (l1 << 16);
+        }
+    }
+    unsigned char* base = reinterpret_cast<unsigned char*>(img);
+    const uint32_t off = gm_xoff(r, c);
+    *reinterpret_cast<uint4*>(base + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<uint4*>(base + (size_t)n16 * 64 + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+}
+
 }  // namespace
+
+int64_t glm_mma_image_elems(int64_t n) { return 2 * ((n + GM_CH - 1) / GM_CH * GM_CH) * GM_DK; }
+
+cudaError_t build_glm_mma_image(const uint16_t* xh, const uint16_t* xl, int64_t n, int D, int Dp, uint16_t* img,
+                                cudaStream_t s) {
+    if (!xh || !xl || !img || n < 1 || n > (1 << 24) || D < 1 || D > GM_DK) return cudaErrorInvalidValue;
+    const int n16 = (int)((n + GM_CH - 1) / GM_CH * GM_CH);
+    const int items = n16 * 4;
+    k_glm_mma_image<<<(items + 255) / 256, 256, 0, s>>>(xh, xl, (int)n, n16, D, Dp, img);
+    return cudaGetLastError();
+}
 
 bool traj_glm_mma_supported(const DevModel& m, bool x3) {
     if (m.kind != LOGISTIC && m.kind != LINEAR_GAUSS) return false;
-    if (m.D < 1 || m.D > GM_DK || m.n < 1 || !m.Xbf || !m.Xbf_lo) return false;
+    if (m.D < 1 || m.D > GM_DK || m.n < 1 || !m.xmma_img) return false;
     return GmLayout(m.n, x3).bytes <= 220 * 1024;
 }
 

@@ -7,10 +7,11 @@ micro-benchmark and the profiling driver for one trajectory kernel at a time).
     python -m paper_2504_02627_gb300.kernel_bench gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
 
 Each run makes seeded synthetic inputs (the workloads of this repository),
-launches one target evaluation and one leapfrog trajectory of `--steps` steps
-for every particle, and prints the event-timed duration of the trajectory
-launch as one JSON line.  Under a profiler, the trajectory launch is the
-second launch of the kernel (skip one with `-s 1`).
+launches one target evaluation, then leapfrog trajectories of `--steps` steps
+for every particle (one untimed, ten timed back to back, each continuing
+from the last), and prints the average event-timed duration of a trajectory
+launch as one JSON line.  Under a profiler, the first trajectory launch is
+the second launch of the kernel (skip one with `-s 1`).
 """
 from __future__ import annotations
 
@@ -32,14 +33,19 @@ def _setup():
     return torch, workloads, B
 
 
-def _time(torch, fn):
+def _time(torch, fn, reps=10):
+    """Device time of one call: one untimed call, then `reps` back-to-back
+    calls between two events on the current stream, averaged (the host's
+    launch latency overlaps the previous call's execution)."""
+    fn()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    fn()
+    for _ in range(reps):
+        fn()
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    return e0.elapsed_time(e1) / reps
 
 
 def run_glm_like(args, streamed):
