@@ -33,7 +33,8 @@ struct RunParams {
     int32_t pad;
 };
 
-constexpr int SLICE = 256;  // particles per CTA in the weight / statistics kernels
+constexpr int SLICE = 128;  // particles per CTA in the weight / statistics kernels (four warps:
+                             // their FP64 work spreads over twice as many SMs as 256 would)
 
 // Per-run mutable state (device).  The first 8 doubles are what
 // smc_get_buffer(RUNSTATE) returns.

@@ -348,7 +348,6 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
     __shared__ double buf[32];
     __shared__ long long lbuf[32];
     __shared__ int ibuf[32];
-    __shared__ double wcol[SLICE / 32][2 * MAX_CHEES_DIM];
     const SliceIdx x = slice_idx(b);
     const RunParams& rp = b.runs[x.r];
     const RunState& st = b.rstate[x.r];
@@ -383,25 +382,35 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
     part.g_den = 0.0;
     if (threadIdx.x == 0) b.parts[c] = part;
     if (rp.adapt && st.k < rp.n_warmup) {
-        // ChEES column sums: pre-move states (after resampling) and proposals
+        // ChEES column sums of the pre-move states (after resampling) and the
+        // proposals: warp w takes dimensions w, w + SLICE / 32, ...; a lane
+        // sums its particles lane, lane + 32, ... of the slice in order, then
+        // the warp adds its lanes (fixed order)
+        constexpr int PL = SLICE / 32;   // particles per lane
         const int D = (int)b.D, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const int64_t src = x.valid ? b.src[x.j] : 0;
-        for (int d = 0; d < D; ++d) {
+        const int64_t i0 = b.slice_start[c];
+        int64_t jj[PL], ss[PL];
+#pragma unroll
+        for (int u = 0; u < PL; ++u) {
+            const int64_t i = i0 + lane + 32 * u;
+            jj[u] = i < rp.n ? rp.off + i : -1;
+            ss[u] = (jj[u] >= 0 && !b.chees0) ? b.src[jj[u]] : 0;
+        }
+        for (int d = wid; d < D; d += SLICE / 32) {
             const int64_t o = (int64_t)d * b.ld;
-            double v0 = x.valid ? (double)(b.chees0 ? b.chees0[o + x.j] : b.theta_prev[o + src]) : 0.0;
-            double v1 = x.valid ? (double)(b.chees1 ? b.chees1[o + x.j] : b.theta_new[o + x.j]) : 0.0;
+            double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+            for (int u = 0; u < PL; ++u) {
+                if (jj[u] < 0) continue;
+                v0 += (double)(b.chees0 ? b.chees0[o + jj[u]] : b.theta_prev[o + ss[u]]);
+                v1 += (double)(b.chees1 ? b.chees1[o + jj[u]] : b.theta_new[o + jj[u]]);
+            }
             v0 = warp_sum(v0);
             v1 = warp_sum(v1);
             if (lane == 0) {
-                wcol[wid][d] = v0;
-                wcol[wid][D + d] = v1;
+                b.colsum[(int64_t)c * 2 * D + d] = v0;
+                b.colsum[(int64_t)c * 2 * D + D + d] = v1;
             }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < 2 * D; t += blockDim.x) {
-            double s = 0.0;
-            for (int w = 0; w < SLICE / 32; ++w) s += wcol[w][t];
-            b.colsum[(int64_t)c * 2 * D + t] = s;
         }
     }
 }
