@@ -61,7 +61,8 @@ class Config(C.Structure):
                 ("chees_initial_p", C.c_int32), ("adam_lr", C.c_double),
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
-                ("flow_lr", C.c_double), ("flow_min_ess", C.c_double)]
+                ("flow_lr", C.c_double), ("flow_min_ess", C.c_double),
+                ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -86,7 +87,8 @@ class IterIO(C.Structure):
                 ("chees", C.POINTER(CheesState)), ("log_z", _DP),
                 ("ancestors", _I32P), ("steps", _I32P), ("p0", _DP), ("p1", _DP),
                 ("dH", _DP), ("alpha", _DP), ("flow_params", _DP), ("flow_m", _DP), ("flow_v", _DP),
-                ("flow_t", C.POINTER(C.c_int32)), ("flow_H", C.c_int64), ("flow_L", C.c_int64)]
+                ("flow_t", C.POINTER(C.c_int32)), ("flow_H", C.c_int64), ("flow_L", C.c_int64),
+                ("eps", _DP)]
 
 
 class Flow(C.Structure):
@@ -124,6 +126,10 @@ def lib():
         L.oracle_multinomial.argtypes = [_U64P, C.c_int64, _U64P, _I32P]
         L.oracle_chees_gradient.argtypes = [_DP, _DP, _DP, _DP, _DP, C.c_int64, C.c_int64, _DP, _DP]
         L.oracle_chees_gradient.restype = C.c_int
+        L.oracle_harmonic_mean_alpha.argtypes = [_DP, C.c_int64]
+        L.oracle_harmonic_mean_alpha.restype = C.c_double
+        L.oracle_step_size_update.argtypes = [C.c_double, _DP, C.c_int64, C.c_double, C.c_double]
+        L.oracle_step_size_update.restype = C.c_double
         L.oracle_chees_adam.argtypes = [C.POINTER(CheesState), C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_double, C.c_int32]
         L.oracle_smc_init.argtypes = [C.POINTER(Target), C.POINTER(Config), _DP, _DP, _DP, _DP, C.c_int32]
@@ -314,6 +320,17 @@ def chees_gradient(theta0, theta1, p, l, alpha):
     return (g.value if ok else None), per
 
 
+def harmonic_mean_alpha(alpha):
+    a = _f64(alpha)
+    return lib().oracle_harmonic_mean_alpha(_dp(a), a.size)
+
+
+def step_size_update(eps, alpha, rate, target=0.651):
+    """Optional warm-up step-size rule: log eps += rate (a_h - target)."""
+    a = _f64(alpha)
+    return lib().oracle_step_size_update(float(eps), _dp(a), a.size, float(rate), float(target))
+
+
 def chees_adam(state: CheesState, ghat, lr, b1, b2, adam_eps, eps, max_steps):
     lib().oracle_chees_adam(C.byref(state), float(ghat), lr, b1, b2, adam_eps, eps, max_steps)
     return state
@@ -346,13 +363,16 @@ class SMCConfig:
     flow_epochs: int = 10
     flow_lr: float = 1e-3
     flow_min_ess: float = 0.25
+    step_adapt_rate: float = 0.0      # 0: fixed epsilon, as in the paper
+    step_adapt_target: float = 0.651
 
     def struct(self):
         return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
                       self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
                       self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
                       self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
-                      self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess)
+                      self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess,
+                      self.step_adapt_rate, self.step_adapt_target)
 
 
 def stats_to_dicts(arr):
@@ -447,10 +467,11 @@ def flow_adam(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: int = 0):
     """One iteration (Algorithm 3 body) on a state dict as returned by
-    ``smc_init`` plus ``chees`` (CheesState), and optionally ``flow`` (dict
-    with params, m, v, t (c_int32), H, L) for the learned preconditioner.
-    Mutates theta/grad/logpi/logw/log_z/chees/flow in place and returns the
-    per-iteration intermediates."""
+    ``smc_init`` plus ``chees`` (CheesState), optionally ``flow`` (dict
+    with params, m, v, t (c_int32), H, L) for the learned preconditioner, and
+    optionally ``eps`` (c_double, the current step size; absent: the fixed
+    ``cfg.step_size``).  Mutates theta/grad/logpi/logw/log_z/chees/flow/eps in
+    place and returns the per-iteration intermediates."""
     N, D = cfg.n_particles, t.D
     for key in ("theta", "grad", "logpi", "logw"):
         state[key] = _f64(state[key])
@@ -465,7 +486,8 @@ def smc_iteration(t: TargetSpec, cfg: SMCConfig, k: int, state: dict, nthreads: 
                 _dp(out["p0"]), _dp(out["p1"]), _dp(out["dH"]), _dp(out["alpha"]),
                 _dp(fl["params"]) if fl else None, _dp(fl["m"]) if fl else None,
                 _dp(fl["v"]) if fl else None, C.pointer(fl["t"]) if fl else None,
-                int(fl["H"]) if fl else 0, int(fl["L"]) if fl else 0)
+                int(fl["H"]) if fl else 0, int(fl["L"]) if fl else 0,
+                C.pointer(state["eps"]) if "eps" in state else None)
     st = Stats()
     c = cfg.struct()
     out["status"] = lib().oracle_smc_iteration(C.byref(t.struct), C.byref(c), int(k),
@@ -486,6 +508,7 @@ def smc_run_flow(t: TargetSpec, cfg: SMCConfig, flow_params, H, L, nthreads: int
     st = smc_init(t, cfg, nthreads)
     st["chees"] = initial_chees_state(cfg)
     st["flow"] = new_flow_state(flow_params, H, L)
+    st["eps"] = C.c_double(cfg.step_size)
     stats, status = [], 0
     for k in range(1, cfg.n_iters + 1):
         out = smc_iteration(t, cfg, k, st, nthreads)

@@ -63,3 +63,18 @@ void oracle_chees_adam(oracle_chees_state* s, double ghat, double lr, double b1,
     if (s->log_L < lo) s->log_L = lo;
     if (s->log_L > hi) s->log_L = hi;
 }
+
+double oracle_harmonic_mean_alpha(const double* alpha, int64_t N) {
+    /* N / sum_j 1/alpha_j; a zero acceptance makes the harmonic mean 0 */
+    double inv = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (!(alpha[j] > 0.0)) return 0.0;
+        inv += 1.0 / alpha[j];
+    }
+    return (double)N / inv;
+}
+
+double oracle_step_size_update(double eps, const double* alpha, int64_t N, double rate, double target) {
+    const double ah = oracle_harmonic_mean_alpha(alpha, N);
+    return exp(log(eps) + rate * (ah - target));
+}

@@ -140,6 +140,16 @@ typedef struct {
 void oracle_chees_adam(oracle_chees_state* s, double ghat, double lr, double b1, double b2,
                        double adam_eps, double eps, int32_t max_steps);
 
+/* Optional step-size adaptation (not in the paper, which fixes epsilon per
+ * experiment and names its adaptation as future work, Sec. 5): after the
+ * ChEES update of a warm-up iteration, log epsilon moves by
+ * rate * (a_h - target), where a_h = N / sum_j 1/alpha_j is the harmonic mean
+ * of the acceptance probabilities (0 when some alpha_j is 0) and the target
+ * is the asymptotically optimal HMC acceptance 0.651 (Beskos et al., 2013).
+ * Returns the new epsilon. */
+double oracle_harmonic_mean_alpha(const double* alpha, int64_t N);
+double oracle_step_size_update(double eps, const double* alpha, int64_t N, double rate, double target);
+
 /* ---------------------------------------------------------------------------
  * The SMC sampler (Algorithm 3) with the ChEES-HMC proposal and the
  * momentum change-of-variable L-kernel (Sec. 3.1), so the incremental
@@ -164,6 +174,9 @@ typedef struct {
     int32_t flow_epochs;    /* full-batch Adam steps per training event      */
     double flow_lr;
     double flow_min_ess;    /* train only when the tested J_eff >= flow_min_ess * J */
+    double step_adapt_rate; /* kappa: 0 keeps epsilon fixed (the paper); > 0 applies
+                               oracle_step_size_update during warm-up        */
+    double step_adapt_target; /* harmonic-mean acceptance target (0.651)      */
 } oracle_config;
 
 typedef struct {
@@ -193,6 +206,9 @@ typedef struct {
     int32_t* ancestors; int32_t* steps; double* p0; double* p1; double* dH; double* alpha;
     /* learned preconditioner (NULL: HMC in theta space) and its Adam state */
     double* flow_params; double* flow_m; double* flow_v; int32_t* flow_t; int64_t flow_H, flow_L;
+    /* current step size, updated in place when step_adapt_rate > 0 (NULL:
+     * step_size, fixed) */
+    double* eps;
 } oracle_iter_io;
 int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t k,
                          oracle_iter_io* io, oracle_stats* st, int32_t nthreads);

@@ -129,12 +129,15 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     }
     z0 = use_flow ? (double*)malloc((size_t)(N * D) * sizeof(double)) : 0;
 
+    /* the step size of this iteration: fixed, or the adapted value */
+    const double eps = io->eps ? *io->eps : c->step_size;
+
     /* (c) jittered trajectory lengths l_j = h_j L and step counts. */
     const double L = exp(io->chees->log_L);
     for (int64_t j = 0; j < N; ++j) {
         double h = c->jitter ? oracle_halton2((uint32_t)(j * K + k)) : 1.0;
         l[j] = h * L;
-        S[j] = oracle_step_count(h, L, c->step_size, c->max_steps);
+        S[j] = oracle_step_count(h, L, eps, c->max_steps);
     }
 
     /* (d, e) momentum, leapfrog, energy error and acceptance probability. */
@@ -149,7 +152,7 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
         double H0, H1;
         if (!use_flow) {
             H0 = oracle_hamiltonian(pj, D, lp1[j]);
-            oracle_leapfrog(t, th1 + j * D, pj, g1 + j * D, lp1 + j, c->step_size, S[j]);
+            oracle_leapfrog(t, th1 + j * D, pj, g1 + j * D, lp1 + j, eps, S[j]);
             H1 = oracle_hamiltonian(pj, D, lp1[j]);
         } else {
             /* HMC in z = T^-1(theta) on log pi_z (Algorithm 1 in latent space) */
@@ -163,10 +166,10 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
             H0 = oracle_hamiltonian(pj, D, lpz);
             double lpx = lp1[j];
             for (int32_t l = 0; l < S[j]; ++l) {
-                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * c->step_size * gz[d];
-                for (int64_t d = 0; d < D; ++d) zz[d] += c->step_size * pj[d];
+                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * eps * gz[d];
+                for (int64_t d = 0; d < D; ++d) zz[d] += eps * pj[d];
                 lpz = oracle_flow_logpi_z(&flow, t, zz, gz, x, g1 + j * D, &lpx);
-                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * c->step_size * gz[d];
+                for (int64_t d = 0; d < D; ++d) pj[d] += 0.5 * eps * gz[d];
             }
             if (S[j] > 0) {
                 memcpy(th1 + j * D, x, (size_t)D * sizeof(double));
@@ -212,10 +215,14 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
         free(z1);
         if (okg)
             oracle_chees_adam(io->chees, ghat, c->adam_lr, c->adam_b1, c->adam_b2,
-                              c->adam_eps, c->step_size, c->max_steps);
+                              c->adam_eps, eps, c->max_steps);
         io->chees->Lbar = 0.9 * io->chees->Lbar + 0.1 * exp(io->chees->log_L);
     }
     if (c->adapt && k == c->n_warmup && io->chees->Lbar > 0.0) io->chees->log_L = log(io->chees->Lbar);
+    /* optional step-size adaptation during warm-up, after the ChEES update;
+     * epsilon stays where it is from M_warmup on */
+    if (c->step_adapt_rate > 0.0 && k < c->n_warmup && io->eps)
+        *io->eps = oracle_step_size_update(eps, alpha, N, c->step_adapt_rate, c->step_adapt_target);
 
     /* (h) move: without accept-reject every particle takes its proposal; with
      * it, the Metropolis rule u < alpha decides and the weight is unchanged. */
@@ -284,9 +291,10 @@ int oracle_smc_run(const oracle_target* t, const oracle_config* c, double* theta
     double lo = log(c->step_size), hi = log((double)c->max_steps * c->step_size);
     if (ch.log_L < lo) ch.log_L = lo;
     if (ch.log_L > hi) ch.log_L = hi;
+    double eps = c->step_size;
     int status = 0;
     for (int64_t k = 1; k <= c->n_iters && status == 0; ++k) {
-        oracle_iter_io io = {theta, grad, logpi, logw, &ch, &lz, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        oracle_iter_io io = {theta, grad, logpi, logw, &ch, &lz, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, &eps};
         status = oracle_smc_iteration(t, c, k, &io, stats ? stats + (k - 1) : 0, nthreads);
     }
     if (theta_out) memcpy(theta_out, theta, (size_t)(N * D) * sizeof(double));
