@@ -122,6 +122,15 @@ typedef struct {
     double init_scale;      /* q_init = N(0, init_scale^2 I)                      */
     int32_t precision;      /* smc_precision                                      */
     int32_t pad;
+    /* Optional step-size adaptation (not in the paper, which fixes epsilon and
+     * names its adaptation as future work, Sec. 5).  0 keeps epsilon fixed.
+     * rate > 0: after the ChEES update of each warm-up iteration (k <
+     * M_warmup), log epsilon += rate * (a_h - step_adapt_target), a_h = J /
+     * sum_j 1/alpha_j the harmonic mean of the acceptance probabilities (0 if
+     * some alpha_j = 0); epsilon is frozen from M_warmup on.  The current
+     * epsilon is the ninth double of smc_get_buffer(SMC_BUF_RUNSTATE).      */
+    double step_adapt_rate;
+    double step_adapt_target;   /* in (0, 1); 0.651 in the Python binding          */
 } smc_config;
 
 typedef struct {
@@ -190,7 +199,8 @@ typedef enum {
     SMC_BUF_DH = 8,         /* f64 [N]          Delta H                           */
     SMC_BUF_ALPHA = 9,      /* f64 [N]          acceptance probabilities          */
     SMC_BUF_THETA_PREV = 10,/* f32 [dim x ld]   positions before the move (after resampling) */
-    SMC_BUF_RUNSTATE = 11,  /* f64 [n_runs x 8] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS */
+    SMC_BUF_RUNSTATE = 11,  /* f64 [n_runs x 9] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS,
+                               the step size of the next iteration */
     SMC_BUF_Z0 = 12,        /* f32 [dim x ld]   latent start points z0 = T^-1(theta) of the last move (transport map on) */
     SMC_BUF_Z1 = 13         /* f32 [dim x ld]   latent end points z' of the last move (transport map on) */
 } smc_buffer;

@@ -36,7 +36,8 @@ class SmcConfig(C.Structure):
                 ("jitter", C.c_int32), ("ess_frac", C.c_double), ("seed", C.c_uint64),
                 ("accept_reject", C.c_int32), ("adapt", C.c_int32), ("adam_lr", C.c_double),
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
-                ("init_scale", C.c_double), ("precision", C.c_int32), ("pad", C.c_int32)]
+                ("init_scale", C.c_double), ("precision", C.c_int32), ("pad", C.c_int32),
+                ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double)]
 
 
 class SmcFlowConfig(C.Structure):
@@ -179,12 +180,13 @@ class ModelData:
 
 def make_config(n_particles, n_iters, n_warmup, step_size, traj_len0=5.0, max_steps=500, jitter=1,
                 ess_frac=0.5, seed=1000, adapt=1, adam_lr=0.025, adam_b1=0.9, adam_b2=0.999,
-                adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32, accept_reject=0) -> SmcConfig:
+                adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32, accept_reject=0,
+                step_adapt_rate=0.0, step_adapt_target=0.651) -> SmcConfig:
     return SmcConfig(int(n_particles), int(n_iters), int(n_warmup), float(step_size), float(traj_len0),
                      int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), int(accept_reject),
                      int(adapt),
                      float(adam_lr), float(adam_b1), float(adam_b2), float(adam_eps), float(init_scale),
-                     int(precision), 0)
+                     int(precision), 0, float(step_adapt_rate), float(step_adapt_target))
 
 
 def stats_dicts(arr):
@@ -282,7 +284,7 @@ class Sampler:
                   BUF_LOGPI: ((N,), np.float64), BUF_LOGW: ((N,), np.float64),
                   BUF_W: ((N,), np.float64), BUF_DH: ((N,), np.float64),
                   BUF_ALPHA: ((N,), np.float64), BUF_ANCESTORS: ((N,), np.int32),
-                  BUF_STEPS: ((N,), np.int32), BUF_RUNSTATE: ((self.n_runs, 8), np.float64),
+                  BUF_STEPS: ((N,), np.int32), BUF_RUNSTATE: ((self.n_runs, 9), np.float64),
                   BUF_Z0: ((D, ld), np.float32), BUF_Z1: ((D, ld), np.float32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dtype=dt)
@@ -312,7 +314,7 @@ class Sampler:
 
     def runstate(self):
         rs = self.buffer(BUF_RUNSTATE)
-        keys = ["log_z", "log_L", "adam_m", "adam_v", "Lbar", "adam_t", "L_last", "ess"]
+        keys = ["log_z", "log_L", "adam_m", "adam_v", "Lbar", "adam_t", "L_last", "ess", "eps"]
         return [dict(zip(keys, row)) for row in rs]
 
     def close(self):

@@ -31,12 +31,14 @@ struct RunParams {
     int32_t n_slices;
     int32_t accept_reject;  // 1: Metropolis select after the move, weight unchanged
     int32_t pad;
+    double step_rate;       // optional warm-up step-size rule: log eps += step_rate (a_h - step_target)
+    double step_target;
 };
 
 constexpr int SLICE = 128;  // particles per CTA in the weight / statistics kernels (four warps:
                              // their FP64 work spreads over twice as many SMs as 256 would)
 
-// Per-run mutable state (device).  The first 8 doubles are what
+// Per-run mutable state (device).  The first 9 doubles are what
 // smc_get_buffer(RUNSTATE) returns.
 struct RunState {
     double log_z;       // running log evidence
@@ -46,6 +48,8 @@ struct RunState {
     double adam_t;      // Adam step count (stored as double for the readout)
     double L_last;      // L used by the last completed iteration
     double ess;         // ESS after the last reweighting
+    double eps;         // leapfrog step size of the iteration about to run (the
+                        // configured one unless the step-size rule is on)
     // ---- decision for the iteration about to run (written by the previous
     //      iteration's finisher or by the initial weighting)
     double lse;         // log-sum-exp of the current log-weights

@@ -281,6 +281,9 @@ std::string check_config(const smc_config& c) {
     if (c.accept_reject != 0 && c.accept_reject != 1) return "accept_reject must be 0 or 1";
     if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
+    if (!(c.step_adapt_rate >= 0.0) || !std::isfinite(c.step_adapt_rate)) return "step_adapt_rate must be >= 0";
+    if (c.step_adapt_rate > 0.0 && !(c.step_adapt_target > 0.0 && c.step_adapt_target < 1.0))
+        return "step_adapt_target must be in (0, 1)";
     if (c.precision < 0 || c.precision > 3) return "unknown precision";
     return "";
 }
@@ -453,6 +456,7 @@ RunState initial_state(const RunParams& rp, const smc_config& c) {
     st.log_L = std::fmin(std::fmax(std::log(c.traj_len0), rp.log_L_lo), rp.log_L_hi);
     st.k = 1;
     st.L_used = std::exp(st.log_L);
+    st.eps = rp.eps;
     return st;
 }
 
@@ -528,6 +532,8 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.n_iters = cfg[r].n_iters;
         rp.n_warmup = cfg[r].n_warmup;
         rp.accept_reject = cfg[r].accept_reject;
+        rp.step_rate = cfg[r].step_adapt_rate;
+        rp.step_target = cfg[r].step_adapt_target;
         rp.slice0 = (int32_t)slices;
         rp.n_slices = (int32_t)((rp.n + SLICE - 1) / SLICE);
         slices += rp.n_slices;
@@ -859,8 +865,8 @@ smc_status smc_get_buffer(const smc_handle* hc, int32_t which, void* dst, int64_
                                             cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "smc_get_buffer");
-            runstate.resize((size_t)(8 * h->n_runs));
-            for (int64_t r = 0; r < h->n_runs; ++r) std::memcpy(&runstate[(size_t)(8 * r)], &st[(size_t)r], 64);
+            runstate.resize((size_t)(9 * h->n_runs));
+            for (int64_t r = 0; r < h->n_runs; ++r) std::memcpy(&runstate[(size_t)(9 * r)], &st[(size_t)r], 72);
             if (bytes > (int64_t)(runstate.size() * 8)) return SMC_E_INVAL;
             if (device_ptrs) {
                 e = cudaMemcpyAsync(dst, runstate.data(), (size_t)bytes, cudaMemcpyHostToDevice, h->stream);

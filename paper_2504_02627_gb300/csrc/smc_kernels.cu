@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(SLICE) k_weights_steps(StepBufs b) {
                 b.q[j] = qi;
             }
             const double h = rp.jitter ? halton2((uint32_t)(i * rp.n_iters + st.k)) : 1.0;
-            S = step_count(h, st.L_used, rp.eps, rp.max_steps);
+            S = step_count(h, st.L_used, st.eps, rp.max_steps);
         }
         b.steps[j] = S;
         atomicAdd(&b.hist[b.max_steps_all - S], 1);
@@ -375,6 +375,8 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
     part.w_e1 = block_reduce(e, buf, OpSum());
     part.w_e2 = block_reduce(e * e, buf, OpSum());
     part.alpha_sum = block_reduce(al, buf, OpSum());
+    const bool step_rule = rp.step_rate > 0.0 && st.k < rp.n_warmup;
+    part.inv_alpha_sum = step_rule ? block_reduce(x.valid ? 1.0 / al : 0.0, buf, OpSum()) : 0.0;
     part.steps_sum = block_reduce(S, lbuf, OpSum());
     part.smin = block_reduce(smin, ibuf, OpMin());
     part.smax = block_reduce(smax, ibuf, OpMax());
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     }
     za_m = block_reduce(za_m, buf, OpMax());
     w_m = block_reduce(w_m, buf, OpMax());
-    double za_s = 0.0, w_e1 = 0.0, w_e2 = 0.0, asum = 0.0, gnum = 0.0, gden = 0.0;
+    double za_s = 0.0, w_e1 = 0.0, w_e2 = 0.0, asum = 0.0, gnum = 0.0, gden = 0.0, iasum = 0.0;
     long long ssum = 0;
     int smin = 0x7fffffff, smax = 0;
     for (int q = threadIdx.x; q < rp.n_slices; q += blockDim.x) {
@@ -507,6 +509,7 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             w_e2 += p->w_e2 * f * f;
         }
         asum += p->alpha_sum;
+        iasum += p->inv_alpha_sum;
         gnum += p->g_num;
         gden += p->g_den;
         ssum += p->steps_sum;
@@ -517,6 +520,7 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     w_e1 = block_reduce(w_e1, buf, OpSum());
     w_e2 = block_reduce(w_e2, buf, OpSum());
     asum = block_reduce(asum, buf, OpSum());
+    iasum = block_reduce(iasum, buf, OpSum());
     gnum = block_reduce(gnum, buf, OpSum());
     gden = block_reduce(gden, buf, OpSum());
     ssum = block_reduce(ssum, reinterpret_cast<long long*>(buf), OpSum());
@@ -533,11 +537,19 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             const double mh = st.adam_m / (1.0 - pow(rp.adam_b1, st.adam_t));
             const double vh = st.adam_v / (1.0 - pow(rp.adam_b2, st.adam_t));
             st.log_L += rp.adam_lr * mh / (sqrt(vh) + rp.adam_eps);
-            st.log_L = fmin(fmax(st.log_L, rp.log_L_lo), rp.log_L_hi);
+            // clamp L to [eps, max_steps eps] of this iteration's step size
+            const double lo = rp.step_rate > 0.0 ? log(st.eps) : rp.log_L_lo;
+            const double hi = rp.step_rate > 0.0 ? log((double)rp.max_steps * st.eps) : rp.log_L_hi;
+            st.log_L = fmin(fmax(st.log_L, lo), hi);
         }
         st.Lbar = 0.9 * st.Lbar + 0.1 * exp(st.log_L);
     }
     if (rp.adapt && k == rp.n_warmup && st.Lbar > 0.0) st.log_L = log(st.Lbar);
+    // optional warm-up step-size rule (not in the paper), after the ChEES
+    // update: log eps += rate (a_h - target), a_h = n / sum 1/alpha_j the
+    // harmonic mean (0 when some alpha_j = 0: the sum is +inf)
+    if (rp.step_rate > 0.0 && k < rp.n_warmup)
+        st.eps = exp(log(st.eps) + rp.step_rate * ((double)rp.n / iasum - rp.step_target));
     const double inc = za_m > -CUDART_INF ? za_m + log(za_s) : -CUDART_INF;
     st.log_z += inc;
     st.log_z_inc = inc;

@@ -23,6 +23,7 @@ struct SlicePart {
     double za_m, za_s;      // log-sum-exp pieces of log W_j - Delta H_j
     double w_m, w_e1, w_e2; // max, sum exp, sum exp^2 of the new log-weights
     double alpha_sum;
+    double inv_alpha_sum;   // sum 1/alpha_j (step-size rule; +inf if some alpha_j = 0)
     double g_num, g_den;    // ChEES: sum alpha_j g_j, sum alpha_j
     long long steps_sum;
     int smin, smax;

@@ -72,7 +72,7 @@ __device__ __forceinline__ void particle_run(const TrajArgs& a, int64_t j, int& 
                                              uint64_t& seed, uint32_t& kk, uint32_t& jl) {
     r = a.run_of ? a.run_of[j] : 0;
     if (a.runs) {
-        eps = a.runs[r].eps;
+        eps = a.rstate ? a.rstate[r].eps : a.runs[r].eps;
         seed = a.runs[r].seed;
         jl = (uint32_t)(j - a.runs[r].off);
     } else {

@@ -328,3 +328,49 @@ def test_autotuner_variants_give_identical_results(name):
         np.testing.assert_array_equal(th, outs[0][0])
         np.testing.assert_array_equal(lw, outs[0][1])
         np.testing.assert_array_equal(lz, outs[0][2])
+
+
+@pytest.mark.parametrize("name,precision", [("gauss10", 0), ("logistic", 1)])
+def test_step_size_rule_matches_oracle(name, precision):
+    """Optional warm-up step-size rule (not in the paper): each warm-up
+    iteration the GPU's new epsilon is the oracle's rule applied to the GPU's
+    acceptance probabilities (to FP64 rounding); step counts are bit-exact
+    with the GPU's epsilon of that iteration, the trajectories follow the
+    oracle's leapfrog with it, and epsilon is frozen from M_warmup on."""
+    w = rounded_workload(_cases()[name])
+    rate = 0.5
+    run = dict(w["run"], step_adapt_rate=rate, precision=precision)
+    if name == "gauss10":
+        run.update(n_iters=7, n_warmup=5, step_size=0.25)    # near the stable limit 0.307: the rule shrinks it
+    t = oracle_target(w)
+    seed = 4321
+    smp = g.Sampler(g.ModelData.from_workload(w), _cfg(run, seed), stream())
+    N, D, K, M = run["n_particles"], w["D"], run["n_iters"], run["n_warmup"]
+    eps = smp.runstate()[0]["eps"]
+    assert eps == run["step_size"]
+    moved = False
+    for k in range(1, K + 1):
+        th_pre = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        st = smp.step()[0]
+        rs = smp.runstate()[0]
+        src = smp.buffer(B.BUF_ANCESTORS) if st["resampled"] else np.arange(N)
+        S_o = np.array([oracle.step_count(oracle.halton2(j * K + k), rs["L_last"], eps, run["max_steps"])
+                        for j in range(N)])
+        np.testing.assert_array_equal(smp.buffer(B.BUF_STEPS), S_o)
+        p0 = f32r(np.stack([oracle.normals(seed, oracle.TAG_MOM, k, j, D) for j in range(N)]))
+        th1_o, _, _, _ = oracle.leapfrog(t, th_pre[src], p0, eps, S_o)
+        th1 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        rel = np.abs(th1 - th1_o) / (np.abs(th1_o) + np.sqrt(np.mean(th1_o ** 2)))
+        assert np.median(rel) < 1e-4, (k, np.median(rel))
+        alpha = smp.buffer(B.BUF_ALPHA)
+        want = oracle.step_size_update(eps, alpha, rate, 0.651) if k < M else eps
+        assert abs(rs["eps"] - want) <= 1e-12 * want, (k, rs["eps"], want)
+        moved |= rs["eps"] != eps
+        eps = rs["eps"]
+    assert moved
+    smp.close()
+    # rate 0: the configured step throughout
+    smp = g.Sampler(g.ModelData.from_workload(w), _cfg(dict(run, step_adapt_rate=0.0), seed), stream())
+    smp.run(3)
+    assert smp.runstate()[0]["eps"] == run["step_size"]
+    smp.close()
