@@ -62,7 +62,8 @@ class Config(C.Structure):
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
                 ("flow_lr", C.c_double), ("flow_min_ess", C.c_double),
-                ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double)]
+                ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double),
+                ("resample_scheme", C.c_int32), ("pad2", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -109,6 +110,8 @@ def lib():
         L.oracle_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, _DP]
         L.oracle_resample_r64.argtypes = [C.c_uint64, C.c_uint32]
         L.oracle_resample_r64.restype = C.c_uint64
+        L.oracle_multinomial_u64.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        L.oracle_multinomial_u64.restype = C.c_uint64
         L.oracle_halton2.argtypes = [C.c_uint32]
         L.oracle_halton2.restype = C.c_double
         L.oracle_step_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
@@ -258,6 +261,10 @@ def resample_r64(seed, k):
     return int(lib().oracle_resample_r64(C.c_uint64(int(seed)), int(k)))
 
 
+def multinomial_u64(seed, k, i):
+    return int(lib().oracle_multinomial_u64(C.c_uint64(int(seed)), int(k), int(i)))
+
+
 def halton2(n):
     return lib().oracle_halton2(int(n))
 
@@ -365,6 +372,7 @@ class SMCConfig:
     flow_min_ess: float = 0.25
     step_adapt_rate: float = 0.0      # 0: fixed epsilon, as in the paper
     step_adapt_target: float = 0.651
+    resample_scheme: int = 0          # 0 systematic, 1 multinomial (the paper's choice)
 
     def struct(self):
         return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
@@ -372,7 +380,7 @@ class SMCConfig:
                       self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
                       self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
                       self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess,
-                      self.step_adapt_rate, self.step_adapt_target)
+                      self.step_adapt_rate, self.step_adapt_target, self.resample_scheme, 0)
 
 
 def stats_to_dicts(arr):

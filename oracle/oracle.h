@@ -46,6 +46,10 @@ double oracle_u01(uint32_t w0, uint32_t w1);
 void oracle_normals(uint64_t seed, uint32_t tag, uint32_t k, uint32_t j, int64_t D, double* out);
 /* 64-bit uniform integer used by systematic resampling at iteration k. */
 uint64_t oracle_resample_r64(uint64_t seed, uint32_t k);
+/* Uniform 64-bit integer of output i for multinomial resampling at iteration
+ * k: Philox block (1, i, k, RESAMPLE), words 0 and 1 (the systematic draw
+ * above uses block (0, 0, k, RESAMPLE)). */
+uint64_t oracle_multinomial_u64(uint64_t seed, uint32_t k, uint32_t i);
 
 /* ---------------------------------------------------------------------------
  * Jitter of the trajectory length (Sec. "Random Number Generators", item
@@ -177,6 +181,10 @@ typedef struct {
     double step_adapt_rate; /* kappa: 0 keeps epsilon fixed (the paper); > 0 applies
                                oracle_step_size_update during warm-up        */
     double step_adapt_target; /* harmonic-mean acceptance target (0.651)      */
+    int32_t resample_scheme;  /* 0: systematic (fixed point, the default); 1:
+                                 multinomial, the paper's choice (Sec. 3), with
+                                 the uniforms of oracle_multinomial_u64         */
+    int32_t pad2;
 } oracle_config;
 
 typedef struct {

@@ -65,6 +65,12 @@ uint64_t oracle_resample_r64(uint64_t seed, uint32_t k) {
     return ((uint64_t)w[0] << 32) | (uint64_t)w[1];
 }
 
+uint64_t oracle_multinomial_u64(uint64_t seed, uint32_t k, uint32_t i) {
+    uint32_t ctr[4] = {1u, i, k, (uint32_t)ORACLE_TAG_RESAMPLE}, w[4];
+    oracle_philox4x32_10(ctr, seed, w);
+    return ((uint64_t)w[0] << 32) | (uint64_t)w[1];
+}
+
 double oracle_halton2(uint32_t n) {
     /* Radical inverse in base 2 (Halton 1960), digit by digit: the d-th binary
      * digit of n (least significant first) contributes digit * 2^-(d+1). */

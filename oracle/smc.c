@@ -87,7 +87,19 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     if (resampled) {
         uint64_t* q = (uint64_t*)malloc((size_t)N * sizeof(uint64_t));
         oracle_quantise(W, N, q);
-        uint64_t T = oracle_systematic(q, N, oracle_resample_r64(c->seed, (uint32_t)k), anc);
+        uint64_t T = 0;
+        if (c->resample_scheme == 1) {
+            /* multinomial: N independent draws from the fixed-point weights */
+            uint64_t* u = (uint64_t*)malloc((size_t)N * sizeof(uint64_t));
+            for (int64_t i = 0; i < N; ++i) {
+                u[i] = oracle_multinomial_u64(c->seed, (uint32_t)k, (uint32_t)i);
+                T += q[i];
+            }
+            if (T > 0) oracle_multinomial(q, N, u, anc);
+            free(u);
+        } else {
+            T = oracle_systematic(q, N, oracle_resample_r64(c->seed, (uint32_t)k), anc);
+        }
         free(q);
         if (T == 0) { status = -4; goto done; }
         double* tmp = (double*)malloc((size_t)(N * D) * sizeof(double));

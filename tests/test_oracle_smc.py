@@ -131,3 +131,40 @@ def test_table1_shape_gaussian_1d_halton():
         ej.append(np.mean([x["ess"] / (x["grad_evals"] + 1000) for x in r["stats"]]))
     assert ge_paper / 3 < np.mean(ge) < ge_paper * 3
     assert ej_paper / 3 < np.mean(ej) < ej_paper * 3
+
+
+def test_multinomial_scheme_moments_evidence_and_draws():
+    """resample_scheme = 1 (multinomial, the paper's choice): the same closed
+    forms within 3 MCSE; the per-output uniforms are the Philox blocks
+    (1, i, k, RESAMPLE) -- uniform by a chi-square test on their top bits and
+    distinct from the systematic draw (0, 0, k, RESAMPLE); with the sampler's
+    resampled ancestors matching the stand-alone multinomial rule on those
+    uniforms."""
+    mu = np.array([0.5, -0.3, 0.2])
+    var = np.array([0.5, 1.0, 2.0])
+    t = oracle.TargetSpec.gauss_dense(mu, np.diag(1.0 / var))
+    kw = dict(n_particles=512, n_iters=12, n_warmup=6, step_size=0.1, traj_len0=2.0, init_scale=1.5,
+              resample_scheme=1)
+    res = _runs(t, **kw)
+    log_z_true = 0.5 * 3 * np.log(2 * np.pi) + 0.5 * np.log(var).sum()
+    assert _within_3_mcse([r[0] for r in res], log_z_true)
+    assert np.all(_within_3_mcse([r[1] for r in res], mu))
+    assert np.all(_within_3_mcse([r[2] for r in res], var))
+    assert any(s["resampled"] for r in res for s in r[3])
+    # the uniforms
+    u = np.array([oracle.multinomial_u64(77, 3, i) for i in range(20000)], dtype=np.uint64)
+    top = (u >> np.uint64(60)).astype(np.int64)
+    _, p = stats.chisquare(np.bincount(top, minlength=16))
+    assert p > 1e-4
+    assert oracle.resample_r64(77, 3) not in set(u.tolist())
+    # one resampling iteration of the sampler against the stand-alone rule
+    cfg = oracle.SMCConfig(seed=91, **dict(kw, n_iters=3, init_scale=3.0))
+    st = oracle.smc_init(t, cfg)
+    st["chees"] = oracle.initial_chees_state(cfg)
+    lw = st["logw"].copy()
+    out = oracle.smc_iteration(t, cfg, 1, st)
+    assert out["stats"]["resampled"] == 1
+    _, _, W = oracle.normalise(lw)
+    _, q = oracle.quantise(W)
+    uu = np.array([oracle.multinomial_u64(91, 1, i) for i in range(cfg.n_particles)], dtype=np.uint64)
+    np.testing.assert_array_equal(out["ancestors"], oracle.multinomial(q, uu))
