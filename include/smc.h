@@ -131,6 +131,13 @@ typedef struct {
      * epsilon is the ninth double of smc_get_buffer(SMC_BUF_RUNSTATE).      */
     double step_adapt_rate;
     double step_adapt_target;   /* in (0, 1); 0.651 in the Python binding          */
+    int32_t resample_scheme;    /* 0: systematic (fixed point, the default); 1:
+                                   multinomial, the paper's scheme (Sec. 3): output
+                                   i takes the first particle j whose inclusive
+                                   prefix C_j of the fixed-point weights exceeds
+                                   floor(u_i T / 2^64), u_i the 64-bit word pair of
+                                   Philox block (1, i, k, RESAMPLE)             */
+    int32_t pad2;
 } smc_config;
 
 typedef struct {

@@ -30,7 +30,7 @@ struct RunParams {
     int32_t slice0;         // first particle slice (SLICE particles) of the run
     int32_t n_slices;
     int32_t accept_reject;  // 1: Metropolis select after the move, weight unchanged
-    int32_t pad;
+    int32_t resample_scheme;   // 0 systematic, 1 multinomial
     double step_rate;       // optional warm-up step-size rule: log eps += step_rate (a_h - step_target)
     double step_target;
 };

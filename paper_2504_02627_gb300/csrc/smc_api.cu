@@ -69,6 +69,7 @@ struct smc_handle {
     float* p_final = nullptr;
     double *logw = nullptr, *W = nullptr, *dH = nullptr, *alpha = nullptr;
     unsigned long long* q = nullptr;
+    unsigned long long* cprefix = nullptr;   // multinomial runs only
     int32_t *anc = nullptr, *src = nullptr, *steps = nullptr, *perm = nullptr, *hist = nullptr;
     unsigned int* counter = nullptr;
     TileDesc* tiles = nullptr;
@@ -282,6 +283,7 @@ std::string check_config(const smc_config& c) {
     if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
     if (!(c.step_adapt_rate >= 0.0) || !std::isfinite(c.step_adapt_rate)) return "step_adapt_rate must be >= 0";
+    if (c.resample_scheme != 0 && c.resample_scheme != 1) return "resample_scheme must be 0 or 1";
     if (c.step_adapt_rate > 0.0 && !(c.step_adapt_target > 0.0 && c.step_adapt_target < 1.0))
         return "step_adapt_target must be in (0, 1)";
     if (c.precision < 0 || c.precision > 3) return "unknown precision";
@@ -301,6 +303,8 @@ StepBufs make_bufs(smc_handle* h) {
     b.logw = h->logw;
     b.W = h->W;
     b.q = h->q;
+    b.cprefix = h->cprefix;
+    b.any_multinomial = h->cprefix != nullptr;
     b.anc = h->anc;
     b.src = h->src;
     b.steps = h->steps;
@@ -533,6 +537,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.n_warmup = cfg[r].n_warmup;
         rp.accept_reject = cfg[r].accept_reject;
         rp.step_rate = cfg[r].step_adapt_rate;
+        rp.resample_scheme = cfg[r].resample_scheme;
         rp.step_target = cfg[r].step_adapt_target;
         rp.slice0 = (int32_t)slices;
         rp.n_slices = (int32_t)((rp.n + SLICE - 1) / SLICE);
@@ -575,6 +580,11 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->dH = A.get<double>((size_t)h->ld);
     h->alpha = A.get<double>((size_t)h->ld);
     h->q = A.get<unsigned long long>((size_t)h->ld);
+    for (int64_t r = 0; r < n_runs; ++r)
+        if (cfg[r].resample_scheme == 1) {
+            h->cprefix = A.get<unsigned long long>((size_t)h->ld);
+            break;
+        }
     h->anc = A.get<int32_t>((size_t)h->ld);
     h->src = A.get<int32_t>((size_t)h->ld);
     h->steps = A.get<int32_t>((size_t)h->ld);

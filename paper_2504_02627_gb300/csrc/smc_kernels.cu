@@ -258,12 +258,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
     }
     __syncthreads();
     const unsigned long long off = excl_s + thread_excl;
-    // scatter: particle i of the run owns output slots [cnt(C_{i-1}), cnt(C_i))
+    // systematic: particle i of the run owns output slots [cnt(C_{i-1}),
+    // cnt(C_i)); multinomial: the prefix is kept for k_multinomial_search
+    const bool multi = rp.resample_scheme == 1;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const int64_t i = base + (int64_t)tid * SCAN_ITEMS + k;
         if (i >= rp.n) break;
         const unsigned long long Ci = off + v[k];
+        if (multi) {
+            b.cprefix[rp.off + i] = Ci;
+            continue;
+        }
         const unsigned long long Cp = Ci - b.q[rp.off + i];
         const unsigned long long lo = systematic_count(Cp, N, T, U), hi = systematic_count(Ci, N, T, U);
         for (unsigned long long o = lo; o < hi; ++o) {
@@ -271,6 +277,32 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
             if (b.src) b.src[rp.off + (int64_t)o] = (int32_t)(rp.off + i);
         }
     }
+}
+
+// Multinomial resampling (the paper's scheme, Sec. 3) after the scan: output
+// i of a resampling run takes the first particle j whose inclusive prefix C_j
+// exceeds P_i = floor(u_i T / 2^64), u_i the 64-bit word pair of Philox block
+// (1, i, k, RESAMPLE): a binary search over the run's prefix (C_{n-1} = T > P_i).
+__global__ void k_multinomial_search(StepBufs b) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= b.N) return;
+    const int r = b.run_of ? b.run_of[o] : 0;
+    const RunParams& rp = b.runs[r];
+    const RunState& st = b.rstate[r];
+    if (rp.resample_scheme != 1 || !st.resample || st.status != 0) return;
+    const int64_t i = o - rp.off;
+    const Philox4 w = philox4x32_10(Philox4{1u, (uint32_t)i, (uint32_t)st.k, TAG_RESAMPLE}, rp.seed);
+    const unsigned long long u = ((unsigned long long)w.x << 32) | w.y;
+    const unsigned long long P = __umul64hi(u, st.T);
+    const unsigned long long* C = b.cprefix + rp.off;
+    int64_t lo = 0, hi = rp.n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (C[mid] > P) hi = mid;
+        else lo = mid + 1;
+    }
+    b.anc[o] = (int32_t)lo;
+    if (b.src) b.src[o] = (int32_t)(rp.off + lo);
 }
 
 // ============================================================ sort by steps
@@ -589,6 +621,7 @@ cudaError_t launch_weights_steps(const StepBufs& b, cudaStream_t s) {
 }
 cudaError_t launch_resample_scan(const StepBufs& b, cudaStream_t s) {
     k_resample_scan<<<(unsigned)b.n_tiles, SCAN_THREADS, 0, s>>>(b);
+    if (b.any_multinomial && b.N > 0) k_multinomial_search<<<(unsigned)((b.N + 255) / 256), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 cudaError_t launch_sort(const StepBufs& b, cudaStream_t s) {

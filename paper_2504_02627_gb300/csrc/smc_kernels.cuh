@@ -39,6 +39,7 @@ struct StepBufs {
     double* logw;               // [N]
     double* W;                  // [N]
     unsigned long long* q;      // [N]
+    unsigned long long* cprefix;  // [N] inclusive prefix of q within each multinomial run (scan output)
     int32_t* anc;               // [N] run-local ancestor of each output slot
     int32_t* src;               // [N] global source index of each particle
     int32_t* steps;             // [N]
@@ -48,7 +49,7 @@ struct StepBufs {
     TileDesc* tiles;
     int64_t n_tiles;
     int32_t max_steps_all;
-    int32_t pad;
+    int32_t any_multinomial;    // some run resamples multinomially
     // particle slices of the weight / statistics kernels
     const int32_t* slice_run;   // slice -> run
     const int32_t* slice_start; // slice -> first run-local particle

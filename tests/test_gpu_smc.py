@@ -374,3 +374,27 @@ def test_step_size_rule_matches_oracle(name, precision):
     smp.run(3)
     assert smp.runstate()[0]["eps"] == run["step_size"]
     smp.close()
+
+
+@pytest.mark.parametrize("N", [256, 20011])
+def test_multinomial_resampling_bit_exact(N):
+    """resample_scheme = 1 (multinomial, the paper's scheme, Sec. 3): in every
+    resampling iteration the ancestors equal the oracle's multinomial rule on
+    the GPU's normalised weights (quantised to the same fixed point) and the
+    Philox per-output draws, bit for bit; N = 20011 spans many scan tiles with
+    a ragged tail."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(w["run"], n_particles=N, n_iters=4, n_warmup=2, resample_scheme=1)
+    seed = 555
+    smp = g.Sampler(g.ModelData.from_workload(w), _cfg(run, seed), stream())
+    n_res = 0
+    for k in range(1, run["n_iters"] + 1):
+        st = smp.step()[0]
+        if not st["resampled"]:
+            continue
+        n_res += 1
+        _, q = oracle.quantise(smp.buffer(B.BUF_W))
+        u = np.array([oracle.multinomial_u64(seed, k, i) for i in range(N)], dtype=np.uint64)
+        np.testing.assert_array_equal(smp.buffer(B.BUF_ANCESTORS), oracle.multinomial(q, u))
+    assert n_res >= 1
+    smp.close()
