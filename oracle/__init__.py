@@ -112,6 +112,14 @@ def lib():
         L.oracle_resample_r64.restype = C.c_uint64
         L.oracle_multinomial_u64.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
         L.oracle_multinomial_u64.restype = C.c_uint64
+        L.oracle_jitter.argtypes = [C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int64]
+        L.oracle_jitter.restype = C.c_double
+        L.oracle_nth_prime.argtypes = [C.c_int64]
+        L.oracle_nth_prime.restype = C.c_int64
+        L.oracle_radical_inverse.argtypes = [C.c_uint64, C.c_uint64]
+        L.oracle_radical_inverse.restype = C.c_double
+        L.oracle_shuffle_index.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.oracle_shuffle_index.restype = C.c_uint32
         L.oracle_halton2.argtypes = [C.c_uint32]
         L.oracle_halton2.restype = C.c_double
         L.oracle_step_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
@@ -263,6 +271,32 @@ def resample_r64(seed, k):
 
 def multinomial_u64(seed, k, i):
     return int(lib().oracle_multinomial_u64(C.c_uint64(int(seed)), int(k), int(i)))
+
+
+# jitter schemes (Sec. 3.2.1): names of the `jitter` values
+JITTER = {"none": 0, "halton1": 1, "uniform": 2, "halton_nd": 3, "halton_nd_inv": 4, "primes": 5,
+          "primes_inv": 6, "golden": 7, "equidistant": 8, "equidistant_offset": 9, "sobol1": 10}
+
+
+def jitter(scheme, seed, j, k, J, K):
+    return lib().oracle_jitter(int(scheme), C.c_uint64(int(seed)), int(j), int(k), int(J), int(K))
+
+
+def jitter_matrix(scheme, seed, J, K):
+    """h [J, K] (particle j, iteration k = 1..K)."""
+    return np.array([[jitter(scheme, seed, j, k, J, K) for k in range(1, K + 1)] for j in range(J)])
+
+
+def nth_prime(m):
+    return int(lib().oracle_nth_prime(int(m)))
+
+
+def radical_inverse(n, b):
+    return lib().oracle_radical_inverse(C.c_uint64(int(n)), C.c_uint64(int(b)))
+
+
+def shuffle_index(seed, k, j, J):
+    return int(lib().oracle_shuffle_index(C.c_uint64(int(seed)), int(k), int(j), int(J)))
 
 
 def halton2(n):

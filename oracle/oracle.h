@@ -37,7 +37,8 @@ extern "C" {
  * Counter = (i, j, k, tag): i = block index inside one particle's stream,
  * j = particle slot, k = SMC iteration, tag = purpose below.
  * ------------------------------------------------------------------------- */
-enum { ORACLE_TAG_INIT = 1, ORACLE_TAG_MOM = 2, ORACLE_TAG_RESAMPLE = 3, ORACLE_TAG_MH = 4 };
+enum { ORACLE_TAG_INIT = 1, ORACLE_TAG_MOM = 2, ORACLE_TAG_RESAMPLE = 3, ORACLE_TAG_MH = 4,
+       ORACLE_TAG_JITTER = 5, ORACLE_TAG_SHUFFLE = 6 };
 
 void oracle_philox4x32_10(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]);
 /* Uniform on the open interval (0,1) from 52 random bits: (k + 0.5) * 2^-52. */
@@ -58,6 +59,33 @@ uint64_t oracle_multinomial_u64(uint64_t seed, uint32_t k, uint32_t i);
  * to [1, max_steps].
  * ------------------------------------------------------------------------- */
 double oracle_halton2(uint32_t n);
+
+/* Jitter schemes of Sec. 3.2.1 for particle j (0-based: the paper's j - 1) at
+ * iteration k (1-based) of J particles and K iterations:
+ *   0 none (1);  1 1-d Halton, base 2, of n = jK + k;  2 uniform, the FP64
+ *   uniform of Philox block (0, j, k, JITTER);  3 N-d Halton: radical
+ *   inverse of j + 1 in base P_k (the k-th prime);  4 N-d inverse Halton:
+ *   base P_{K+1-k};  5 N-d primes: frac((j + 1) sqrt(P_k));  6 N-d inverse
+ *   primes: P_{K+1-k};  7 1-d golden ratio: frac((jK + k)(sqrt(5) - 1)/2);
+ *   8 equidistant: (pi_k(j) + 1) / J, pi_k the shuffle of iteration k;
+ *   9 offset equidistant: that plus 0.1 u, u the FP64 uniform of Philox block
+ *   (1, j, k, JITTER);  10 1-d Sobol: radical inverse base 2 of the Gray
+ *   code g = n ^ (n >> 1) of n = jK + k (the first Sobol dimension in Gray-
+ *   code order).
+ * Every value is a correctly rounded FP64 operation sequence: radical
+ * inverses as one division of two exact integers, sqrt, products and frac
+ * each rounded once. */
+double oracle_jitter(int32_t scheme, uint64_t seed, int64_t j, int64_t k, int64_t J, int64_t K);
+/* the m-th prime (m >= 1; m <= 65536) */
+int64_t oracle_nth_prime(int64_t m);
+/* radical inverse of n in base b: the base-b digits of n reversed behind the
+ * point (Halton 1960), as the exact fraction rev / b^digits rounded once */
+double oracle_radical_inverse(uint64_t n, uint64_t b);
+/* shuffle of iteration k: a bijection of {0..J-1}, the four-round Feistel
+ * network on 2 ceil(log4 J) bits with round function F_r(x) = word 0 of
+ * Philox block (x, r, k, SHUFFLE) masked to half the bits, applied to j
+ * repeatedly until the result is below J (cycle walking) */
+uint32_t oracle_shuffle_index(uint64_t seed, uint32_t k, uint32_t j, uint32_t J);
 int32_t oracle_step_count(double h, double L, double eps, int32_t max_steps);
 
 /* ---------------------------------------------------------------------------

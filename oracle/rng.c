@@ -91,3 +91,93 @@ int32_t oracle_step_count(double h, double L, double eps, int32_t max_steps) {
     if (s >= (double)max_steps) return max_steps;
     return (int32_t)s;
 }
+
+/* ---------------------------------------------------------------- jitter */
+#define ORACLE_MAX_PRIME_INDEX 65536
+#define ORACLE_SIEVE_TOP 821642   /* the 65536th prime is 821641 */
+
+int64_t oracle_nth_prime(int64_t m) {
+    static int32_t* table = 0;
+    if (m < 1 || m > ORACLE_MAX_PRIME_INDEX) return 0;
+    if (!table) {
+        /* sieve of Eratosthenes up to ORACLE_SIEVE_TOP */
+        unsigned char* comp = (unsigned char*)calloc(ORACLE_SIEVE_TOP + 1, 1);
+        int32_t* t = (int32_t*)malloc(sizeof(int32_t) * ORACLE_MAX_PRIME_INDEX);
+        int64_t cnt = 0;
+        for (int64_t p = 2; p <= ORACLE_SIEVE_TOP && cnt < ORACLE_MAX_PRIME_INDEX; ++p) {
+            if (comp[p]) continue;
+            t[cnt++] = (int32_t)p;
+            for (int64_t q = p * p; q <= ORACLE_SIEVE_TOP; q += p) comp[q] = 1;
+        }
+        free(comp);
+        table = t;
+    }
+    return table[m - 1];
+}
+
+double oracle_radical_inverse(uint64_t n, uint64_t b) {
+    uint64_t num = 0, den = 1;
+    while (n != 0) {
+        num = num * b + n % b;   /* next digit, least significant first */
+        den *= b;
+        n /= b;
+    }
+    return (double)num / (double)den;
+}
+
+uint32_t oracle_shuffle_index(uint64_t seed, uint32_t k, uint32_t j, uint32_t J) {
+    int m = 2;
+    while ((1ull << m) < (uint64_t)J) m += 2;
+    const int half = m / 2;
+    const uint32_t mask = (1u << half) - 1u;
+    uint32_t v = j;
+    for (;;) {
+        uint32_t L = v >> half, R = v & mask;
+        for (uint32_t r = 0; r < 4; ++r) {
+            uint32_t ctr[4] = {R, r, k, (uint32_t)ORACLE_TAG_SHUFFLE}, w[4];
+            oracle_philox4x32_10(ctr, seed, w);
+            const uint32_t t = L ^ (w[0] & mask);
+            L = R;
+            R = t;
+        }
+        v = (L << half) | R;
+        if (v < J) return v;
+    }
+}
+
+static double frac_pos(double x) { return x - floor(x); }
+
+double oracle_jitter(int32_t scheme, uint64_t seed, int64_t j, int64_t k, int64_t J, int64_t K) {
+    switch (scheme) {
+        case 0: return 1.0;
+        case 1: return oracle_halton2((uint32_t)(j * K + k));
+        case 2: {
+            uint32_t ctr[4] = {0u, (uint32_t)j, (uint32_t)k, (uint32_t)ORACLE_TAG_JITTER}, w[4];
+            oracle_philox4x32_10(ctr, seed, w);
+            return oracle_u01(w[0], w[1]);
+        }
+        case 3: return oracle_radical_inverse((uint64_t)(j + 1), (uint64_t)oracle_nth_prime(k));
+        case 4: return oracle_radical_inverse((uint64_t)(j + 1), (uint64_t)oracle_nth_prime(K + 1 - k));
+        case 5: return frac_pos((double)(j + 1) * sqrt((double)oracle_nth_prime(k)));
+        case 6: return frac_pos((double)(j + 1) * sqrt((double)oracle_nth_prime(K + 1 - k)));
+        case 7: {
+            const double g = (sqrt(5.0) - 1.0) * 0.5;
+            return frac_pos((double)(j * K + k) * g);
+        }
+        case 8:
+        case 9: {
+            double h = (double)(oracle_shuffle_index(seed, (uint32_t)k, (uint32_t)j, (uint32_t)J) + 1) / (double)J;
+            if (scheme == 9) {
+                uint32_t ctr[4] = {1u, (uint32_t)j, (uint32_t)k, (uint32_t)ORACLE_TAG_JITTER}, w[4];
+                oracle_philox4x32_10(ctr, seed, w);
+                h += 0.1 * oracle_u01(w[0], w[1]);
+            }
+            return h;
+        }
+        case 10: {
+            const uint32_t n = (uint32_t)(j * K + k);
+            return oracle_halton2(n ^ (n >> 1));
+        }
+        default: return 1.0;
+    }
+}

@@ -147,7 +147,7 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     /* (c) jittered trajectory lengths l_j = h_j L and step counts. */
     const double L = exp(io->chees->log_L);
     for (int64_t j = 0; j < N; ++j) {
-        double h = c->jitter ? oracle_halton2((uint32_t)(j * K + k)) : 1.0;
+        double h = oracle_jitter(c->jitter, c->seed, j, k, N, K);
         l[j] = h * L;
         S[j] = oracle_step_count(h, L, eps, c->max_steps);
     }
