@@ -110,7 +110,12 @@ typedef struct {
     double step_size;       /* epsilon                                            */
     double traj_len0;       /* L_0 in time units, clamped to [eps, max_steps*eps] */
     int32_t max_steps;      /* leapfrog cap (>= 1)                                */
-    int32_t jitter;         /* 0: h = 1; 1: base-2 Halton of n = j*K + k          */
+    int32_t jitter;         /* trajectory-length jitter h (Sec. 3.2.1; smc_k_jitter):
+                               0 none (h = 1); 1 1-d Halton of n = j*K + k; 2
+                               uniform; 3 N-d Halton; 4 N-d inverse Halton; 5 N-d
+                               primes; 6 N-d inverse primes; 7 1-d golden ratio;
+                               8 equidistant; 9 offset equidistant; 10 1-d Sobol.
+                               3-6 need n_iters <= 65536                       */
     double ess_frac;        /* resample when ESS < ess_frac * J                   */
     uint64_t seed;          /* Philox4x32-10 key                                  */
     int32_t accept_reject;  /* 0: the paper's SMC-ChEES (every particle moves, log w
@@ -359,11 +364,33 @@ smc_status smc_k_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int
                          double* out, int64_t ld, void* stream);
 
 /* Jittered step counts (Algorithm 2: ceil(h L / eps), clipped to [1, max]):
- * h_j = radical inverse base 2 of n = j*K + k (jitter = 1) or 1 (jitter = 0);
+ * h_j = radical inverse base 2 of n = j*K + k (jitter = 1) or 1 (jitter = 0;
+ * the other schemes: smc_k_jitter);
  * out_h [N] f64 (may be NULL), out_steps [N] i32. */
 smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps,
                        int32_t max_steps, int32_t jitter, double* out_h, int32_t* out_steps,
                        void* stream);
+
+/* Jitter h of particles j = 0..J-1 (the paper's j - 1) at iteration k (1 <= k
+ * <= K) under scheme 0..10 (Sec. 3.2.1; the list at smc_config.jitter), as the
+ * sampler computes it: out_h [J] f64, device.  For j (0-based), iteration k:
+ *   1 1-d Halton: radical inverse base 2 of n = j*K + k;
+ *   2 uniform: (m + 1/2) 2^-52, m the 52-bit integer of words 0, 1 of Philox
+ *     block (0, j, k, 5);
+ *   3 / 4 N-d Halton / inverse: radical inverse of j + 1 in base P_k /
+ *     P_{K+1-k} (P_m the m-th prime), the exact fraction rounded once;
+ *   5 / 6 N-d primes / inverse: frac((j + 1) sqrt(P_k)) / with P_{K+1-k};
+ *   7 golden ratio: frac((j*K + k)(sqrt(5) - 1)/2);
+ *   8 equidistant: (s_k(j) + 1) / J, s_k the shuffle of iteration k: the
+ *     four-round Feistel network on 2 ceil(log4 J) bits whose round r xors
+ *     word 0 of Philox block (x, r, k, 6) (masked to half the bits) into the
+ *     other half, applied until the value is below J;
+ *   9 offset equidistant: that + 0.1 u, u the uniform of block (1, j, k, 5);
+ *   10 1-d Sobol: radical inverse base 2 of g = n ^ (n >> 1), n = j*K + k.
+ * Every FP64 operation rounds once, in the order written.  Errors:
+ * SMC_E_INVAL (scheme, sizes, J*K + k >= 2^32, K > 65536 for 3-6). */
+smc_status smc_k_jitter(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k, double* out_h,
+                        void* stream);
 
 /* log pi and grad log pi (Sec. 2) at theta [D x ld] f32: logpi [N] f64,
  * grad [D x ld] f32. */

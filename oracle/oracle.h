@@ -72,6 +72,7 @@ double oracle_halton2(uint32_t n);
  *   (1, j, k, JITTER);  10 1-d Sobol: radical inverse base 2 of the Gray
  *   code g = n ^ (n >> 1) of n = jK + k (the first Sobol dimension in Gray-
  *   code order).
+ * Schemes 3-6 reuse their K dimensions cyclically past iteration K.
  * Every value is a correctly rounded FP64 operation sequence: radical
  * inverses as one division of two exact integers, sqrt, products and frac
  * each rounded once. */

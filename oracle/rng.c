@@ -148,6 +148,7 @@ uint32_t oracle_shuffle_index(uint64_t seed, uint32_t k, uint32_t j, uint32_t J)
 static double frac_pos(double x) { return x - floor(x); }
 
 double oracle_jitter(int32_t scheme, uint64_t seed, int64_t j, int64_t k, int64_t J, int64_t K) {
+    if (scheme >= 3 && scheme <= 6) k = (k - 1) % K + 1;   /* dimensions reused past K */
     switch (scheme) {
         case 0: return 1.0;
         case 1: return oracle_halton2((uint32_t)(j * K + k));

@@ -18,6 +18,9 @@ SMC_OK, SMC_E_INVAL, SMC_E_NOMEM, SMC_E_CUDA, SMC_E_DEGENERATE, SMC_E_TIMEOUT, S
     0, -1, -2, -3, -4, -5, -6
 GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
+# trajectory-length jitter schemes (Sec. 3.2.1), smc_config.jitter
+(JITTER_NONE, JITTER_HALTON1, JITTER_UNIFORM, JITTER_HALTON_ND, JITTER_HALTON_ND_INV, JITTER_PRIMES,
+ JITTER_PRIMES_INV, JITTER_GOLDEN, JITTER_EQUIDISTANT, JITTER_EQUIDISTANT_OFFSET, JITTER_SOBOL1) = range(11)
 (BUF_THETA, BUF_GRAD, BUF_LOGPI, BUF_LOGW, BUF_W, BUF_ANCESTORS, BUF_STEPS, BUF_P_FINAL,
  BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1) = range(14)
 
@@ -89,6 +92,8 @@ EXPORTS = {
                                 C.c_int64, C.c_void_p]),
     "smc_k_steps": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int32,
                               C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_k_jitter": (C.c_int, [C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                               C.c_void_p]),
     "smc_k_target": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                C.c_int32, C.c_void_p]),
     "smc_k_leapfrog": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -95,7 +95,7 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(Philox4 c, uint64_t se
     return c;
 }
 
-enum : uint32_t { TAG_INIT = 1, TAG_MOM = 2, TAG_RESAMPLE = 3, TAG_MH = 4 };
+enum : uint32_t { TAG_INIT = 1, TAG_MOM = 2, TAG_RESAMPLE = 3, TAG_MH = 4, TAG_JITTER = 5, TAG_SHUFFLE = 6 };
 
 // Uniform on (0,1): 26 high bits of each word form a 52-bit integer m and the
 // value is (m + 0.5) 2^-52, exact in FP64.
@@ -146,6 +146,94 @@ __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint32_t i, uint3
 // (exact in FP64 for n < 2^32).
 __device__ __forceinline__ double halton2(uint32_t n) {
     return (double)__brev(n) * 2.3283064365386962890625e-10;  // 2^-32
+}
+
+// Radical inverse of n in base b (Halton 1960): the base-b digits of n
+// reversed behind the point, as the exact fraction rev / b^digits rounded once
+// (both integers stay below 2^53 for n <= 2^30 and b below 2^20).
+__device__ __forceinline__ double radical_inverse(uint64_t n, uint64_t b) {
+    uint64_t num = 0, den = 1;
+    while (n != 0) {
+        num = num * b + n % b;
+        den *= b;
+        n /= b;
+    }
+    return __ddiv_rn((double)num, (double)den);
+}
+
+// Shuffle of iteration k, a bijection of {0..J-1} (1 <= J <= 2^30): a
+// four-round Feistel network on 2 ceil(log4 J) bits, round r mixing in word 0
+// of Philox block (x, r, k, SHUFFLE) masked to half the bits, applied to j
+// until the value falls below J (cycle walking; the orbit of j < J returns
+// below J, within the 2^bits bound of the loop).
+__device__ __forceinline__ uint32_t shuffle_index(uint64_t seed, uint32_t k, uint32_t j, uint32_t J) {
+    int m = 2;
+    while ((1ull << m) < (unsigned long long)J) m += 2;
+    const int half = m / 2;
+    const uint32_t mask = (1u << half) - 1u;
+    uint32_t v = j;
+    for (uint64_t it = 0; it < (1ull << m); ++it) {
+        uint32_t L = v >> half, R = v & mask;
+#pragma unroll
+        for (uint32_t r = 0; r < 4; ++r) {
+            const uint32_t t = L ^ (philox4x32_10(Philox4{R, r, k, TAG_SHUFFLE}, seed).x & mask);
+            L = R;
+            R = t;
+        }
+        v = (L << half) | R;
+        if (v < J) return v;
+    }
+    return j;
+}
+
+__device__ __forceinline__ double frac_rn(double x) { return __dsub_rn(x, floor(x)); }
+
+// Jitter h of particle i (0-based within its run, the paper's j - 1) at
+// iteration k (1-based), J particles, K iterations (Sec. 3.2.1): 0 none; 1
+// 1-d Halton of n = iK + k; 2 uniform (Philox block (0, i, k, JITTER)); 3 / 4
+// N-d Halton of i + 1 in base P_k / P_{K+1-k}; 5 / 6 N-d primes
+// frac((i + 1) sqrt(P_k)) / P_{K+1-k}; 7 golden ratio frac((iK + k)(sqrt 5 -
+// 1)/2); 8 equidistant (shuffle_k(i) + 1) / J; 9 offset equidistant: that +
+// 0.1 u (Philox block (1, i, k, JITTER)); 10 1-d Sobol: radical inverse base
+// 2 of the Gray code of iK + k.  primes[m - 1] is the m-th prime (schemes
+// 3-6, which reuse their K dimensions cyclically past iteration K).  Every
+// FP64 operation is rounded once, in the order written.
+__device__ __forceinline__ double jitter_h(int32_t scheme, uint64_t seed, int64_t i, int64_t k, int64_t J,
+                                          int64_t K, const int32_t* primes) {
+    if (scheme >= 3 && scheme <= 6) k = (k - 1) % K + 1;
+    switch (scheme) {
+        case 0: return 1.0;
+        case 1: return halton2((uint32_t)(i * K + k));
+        case 2: {
+            const Philox4 w = philox4x32_10(Philox4{0u, (uint32_t)i, (uint32_t)k, TAG_JITTER}, seed);
+            return u01_52(w.x, w.y);
+        }
+        case 3: return radical_inverse((uint64_t)(i + 1), (uint64_t)primes[k - 1]);
+        case 4: return radical_inverse((uint64_t)(i + 1), (uint64_t)primes[K - k]);
+        case 5:
+        case 6: {
+            const int32_t p = primes[scheme == 5 ? k - 1 : K - k];
+            return frac_rn(__dmul_rn((double)(i + 1), __dsqrt_rn((double)p)));
+        }
+        case 7: {
+            const double g = __dmul_rn(__dsub_rn(__dsqrt_rn(5.0), 1.0), 0.5);
+            return frac_rn(__dmul_rn((double)(i * K + k), g));
+        }
+        case 8:
+        case 9: {
+            double h = __ddiv_rn((double)(shuffle_index(seed, (uint32_t)k, (uint32_t)i, (uint32_t)J) + 1), (double)J);
+            if (scheme == 9) {
+                const Philox4 w = philox4x32_10(Philox4{1u, (uint32_t)i, (uint32_t)k, TAG_JITTER}, seed);
+                h = __dadd_rn(h, __dmul_rn(0.1, u01_52(w.x, w.y)));
+            }
+            return h;
+        }
+        case 10: {
+            const uint32_t n = (uint32_t)(i * K + k);
+            return halton2(n ^ (n >> 1));
+        }
+        default: return 1.0;
+    }
 }
 
 // Algorithm 2: ceil(h L / eps), at least 1 and at most max_steps.

@@ -44,6 +44,28 @@ struct DevAlloc {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// The first m primes (sieve of Eratosthenes), for the N-d jitter schemes.
+std::vector<int32_t> first_primes(int64_t m) {
+    std::vector<int32_t> out;
+    if (m < 1) return out;
+    out.reserve((size_t)m);
+    int64_t top = 64;
+    for (;;) {
+        std::vector<char> comp((size_t)top + 1, 0);
+        out.clear();
+        for (int64_t p = 2; p <= top && (int64_t)out.size() < m; ++p) {
+            if (comp[(size_t)p]) continue;
+            out.push_back((int32_t)p);
+            for (int64_t q = p * p; q <= top; q += p) comp[(size_t)q] = 1;
+        }
+        if ((int64_t)out.size() == m) return out;
+        top *= 2;
+    }
+}
+
+bool jitter_needs_primes(int32_t scheme) { return scheme >= 3 && scheme <= 6; }
+constexpr int64_t MAX_JITTER_PRIME_INDEX = 65536;   // P_m < 2^20: radical inverses stay exact
+
 }  // namespace
 
 struct smc_dev_model {
@@ -61,6 +83,7 @@ struct smc_handle {
     RunParams* d_runs = nullptr;
     RunState* d_rstate = nullptr;
     int32_t* d_run_of = nullptr;
+    int32_t* d_primes = nullptr;   // N-d jitter schemes only
     int32_t* d_tile_run = nullptr;
     float* theta[2] = {nullptr, nullptr};
     float* grad[2] = {nullptr, nullptr};
@@ -278,7 +301,9 @@ std::string check_config(const smc_config& c) {
     if (!(c.step_size > 0.0) || !std::isfinite(c.step_size)) return "step_size must be > 0";
     if (!(c.traj_len0 > 0.0)) return "traj_len0 must be > 0";
     if (c.max_steps < 1 || c.max_steps > 65536) return "max_steps must be in [1, 65536]";
-    if (c.jitter != 0 && c.jitter != 1) return "jitter must be 0 or 1";
+    if (c.jitter < 0 || c.jitter > 10) return "jitter must be in [0, 10]";
+    if (jitter_needs_primes(c.jitter) && c.n_iters > MAX_JITTER_PRIME_INDEX)
+        return "the N-d jitter schemes need n_iters <= 65536";
     if (c.accept_reject != 0 && c.accept_reject != 1) return "accept_reject must be 0 or 1";
     if (!(c.init_scale > 0.0)) return "init_scale must be > 0";
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
@@ -304,6 +329,7 @@ StepBufs make_bufs(smc_handle* h) {
     b.W = h->W;
     b.q = h->q;
     b.cprefix = h->cprefix;
+    b.primes = h->d_primes;
     b.any_multinomial = h->cprefix != nullptr;
     b.anc = h->anc;
     b.src = h->src;
@@ -585,6 +611,17 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
             h->cprefix = A.get<unsigned long long>((size_t)h->ld);
             break;
         }
+    {
+        int64_t kp = 0;
+        for (int64_t r = 0; r < n_runs; ++r)
+            if (jitter_needs_primes(cfg[r].jitter)) kp = std::max(kp, cfg[r].n_iters);
+        if (kp > 0) {
+            const std::vector<int32_t> pr = first_primes(kp);
+            int32_t* d = A.get<int32_t>(pr.size());
+            if (d) cudaMemcpyAsync(d, pr.data(), pr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+            h->d_primes = d;
+        }
+    }
     h->anc = A.get<int32_t>((size_t)h->ld);
     h->src = A.get<int32_t>((size_t)h->ld);
     h->steps = A.get<int32_t>((size_t)h->ld);
@@ -1102,9 +1139,34 @@ smc_status smc_k_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int
 smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps, int32_t max_steps, int32_t jitter,
                        double* out_h, int32_t* out_steps, void* stream) {
     if (N < 0 || K < 1 || k < 0 || !(eps > 0.0) || max_steps < 1 || (N > 0 && !out_steps)) return SMC_E_INVAL;
-    if (N * K + k >= (1ll << 32)) return SMC_E_INVAL;
+    if (N * K + k >= (1ll << 32) || jitter < 0 || jitter > 1) return SMC_E_INVAL;
     return kstatus(launch_steps_only(N, K, k, L, eps, max_steps, jitter, out_h, out_steps,
                                      static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_jitter(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k, double* out_h,
+                        void* stream) {
+    if (scheme < 0 || scheme > 10 || J < 0 || J > (1ll << 30) || K < 1 || k < 1 || k > K) return SMC_E_INVAL;
+    if (J > 0 && !out_h) return SMC_E_INVAL;
+    if (J * K + k >= (1ll << 32)) return SMC_E_INVAL;
+    if (jitter_needs_primes(scheme) && K > MAX_JITTER_PRIME_INDEX) return SMC_E_INVAL;
+    if (J == 0) return SMC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t* d = nullptr;
+    if (jitter_needs_primes(scheme)) {
+        const std::vector<int32_t> pr = first_primes(K);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), pr.size() * sizeof(int32_t), s);
+        if (e != cudaSuccess) return kstatus(e);
+        // pageable source: the call returns once the host data is staged
+        e = cudaMemcpyAsync(d, pr.data(), pr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(d, s);
+            return kstatus(e);
+        }
+    }
+    cudaError_t e = launch_jitter_only(scheme, seed, J, K, k, d, out_h, s);
+    if (d) cudaFreeAsync(d, s);
+    return kstatus(e);
 }
 
 smc_status smc_k_target(const smc_dev_model* m, const float* theta, int64_t N, int64_t ld, double* logpi,

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(SLICE) k_weights_steps(StepBufs b) {
                 qi = v > 0.0 ? __double2ull_rz(v) : 0ull;
                 b.q[j] = qi;
             }
-            const double h = rp.jitter ? halton2((uint32_t)(i * rp.n_iters + st.k)) : 1.0;
+            const double h = jitter_h(rp.jitter, rp.seed, i, st.k, rp.n, rp.n_iters, b.primes);
             S = step_count(h, st.L_used, st.eps, rp.max_steps);
         }
         b.steps[j] = S;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
                 sq1 += e1 * e1;
                 proj += e1 * (double)b.p_final[(int64_t)d * b.ld + x.j];
             }
-            const double h = rp.jitter ? halton2((uint32_t)(x.i * rp.n_iters + st.k)) : 1.0;
+            const double h = jitter_h(rp.jitter, rp.seed, x.i, st.k, rp.n, rp.n_iters, b.primes);
             const double a = b.alpha[x.j];
             num = a * ((h * st.L_used) * (sq1 - sq0) * proj);
             den = a;
@@ -671,6 +671,18 @@ cudaError_t launch_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, i
     return cudaGetLastError();
 }
 
+__global__ void k_jitter_only(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k,
+                              const int32_t* primes, double* out_h) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= J) return;
+    out_h[i] = jitter_h(scheme, seed, i, k, J, K, primes);
+}
+cudaError_t launch_jitter_only(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k,
+                               const int32_t* primes, double* out_h, cudaStream_t s) {
+    if (J <= 0) return cudaSuccess;
+    k_jitter_only<<<(unsigned)((J + 255) / 256), 256, 0, s>>>(scheme, seed, J, K, k, primes, out_h);
+    return cudaGetLastError();
+}
 __global__ void k_steps_only(int64_t N, int64_t K, int64_t k, double L, double eps, int32_t max_steps,
                              int32_t jitter, double* out_h, int32_t* out_steps) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

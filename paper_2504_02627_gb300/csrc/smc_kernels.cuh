@@ -40,6 +40,7 @@ struct StepBufs {
     double* W;                  // [N]
     unsigned long long* q;      // [N]
     unsigned long long* cprefix;  // [N] inclusive prefix of q within each multinomial run (scan output)
+    const int32_t* primes;      // the first K primes (N-d jitter schemes), else nullptr
     int32_t* anc;               // [N] run-local ancestor of each output slot
     int32_t* src;               // [N] global source index of each particle
     int32_t* steps;             // [N]
@@ -88,6 +89,8 @@ constexpr int MAX_CHEES_DIM = 256;         // D handled by the fused ChEES stati
 cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n, cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t tag, uint32_t k, int64_t N, int64_t D, double* out,
                            int64_t ld, cudaStream_t s);
+cudaError_t launch_jitter_only(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k,
+                               const int32_t* primes, double* out_h, cudaStream_t s);
 cudaError_t launch_steps_only(int64_t N, int64_t K, int64_t k, double L, double eps, int32_t max_steps,
                               int32_t jitter, double* out_h, int32_t* out_steps, cudaStream_t s);
 cudaError_t launch_normalise_flat(const double* logw, int64_t N, double* W, double* lse, double* ess,

@@ -46,6 +46,22 @@ def test_normals_match_oracle(D):
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("scheme", range(11))
+@pytest.mark.parametrize("J,K", [(1000, 50), (37, 9)])
+def test_jitter_schemes_bit_exact(scheme, J, K):
+    """The jitter schemes of Sec. 3.2.1 (smc_k_jitter): every h bit-exact
+    against the oracle (integer radical inverses, correctly rounded sqrt,
+    products and frac, Philox uniforms, the Feistel shuffle with cycle
+    walking at a non-power-of-4 J)."""
+    seed = 0xC0FFEE
+    out = torch.zeros(J, dtype=torch.float64, device="cuda")
+    for k in sorted({1, 2, K // 2, K}):
+        g.check(g.lib().smc_k_jitter(scheme, seed, J, K, k, ptr(out), stream()), "smc_k_jitter")
+        got = out.cpu().numpy()
+        want = np.array([oracle.jitter(scheme, seed, j, k, J, K) for j in range(J)])
+        np.testing.assert_array_equal(got, want)
+
+
 @pytest.mark.parametrize("K,k,L,eps,jitter", [(50, 1, 0.5, 1e-3, 1), (50, 50, 0.123456, 1e-3, 1),
                                              (20, 7, 4.8, 0.1, 1), (20, 3, 0.75, 0.1, 0)])
 def test_halton_and_step_counts_bit_exact(K, k, L, eps, jitter):

@@ -398,3 +398,22 @@ def test_multinomial_resampling_bit_exact(N):
         np.testing.assert_array_equal(smp.buffer(B.BUF_ANCESTORS), oracle.multinomial(q, u))
     assert n_res >= 1
     smp.close()
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 6, 7, 8, 9, 10])
+def test_sampler_jitter_schemes_step_counts(scheme):
+    """The sampler's step counts under each jitter scheme (Sec. 3.2.1) are
+    bit-exact against the oracle's h with the GPU's L (gauss10, a ragged
+    particle count)."""
+    w = rounded_workload(workloads.gauss10())
+    run = dict(w["run"], n_particles=301, n_iters=6, n_warmup=3, jitter=scheme)
+    seed = 808
+    smp = g.Sampler(g.ModelData.from_workload(w), _cfg(run, seed), stream())
+    N, K = run["n_particles"], run["n_iters"]
+    for k in (1, 2, 3):
+        smp.step()
+        L = smp.runstate()[0]["L_last"]
+        want = [oracle.step_count(oracle.jitter(scheme, seed, j, k, N, K), L, run["step_size"], run["max_steps"])
+                for j in range(N)]
+        np.testing.assert_array_equal(smp.buffer(B.BUF_STEPS), want)
+    smp.close()
