@@ -63,7 +63,7 @@ class Config(C.Structure):
                 ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
                 ("flow_lr", C.c_double), ("flow_min_ess", C.c_double),
                 ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double),
-                ("resample_scheme", C.c_int32), ("pad2", C.c_int32)]
+                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -407,6 +407,7 @@ class SMCConfig:
     step_adapt_rate: float = 0.0      # 0: fixed epsilon, as in the paper
     step_adapt_target: float = 0.651
     resample_scheme: int = 0          # 0 systematic, 1 multinomial (the paper's choice)
+    mcmc: int = 0                     # 1: Algorithm 2 as independent chains (no weights)
 
     def struct(self):
         return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
@@ -414,7 +415,7 @@ class SMCConfig:
                       self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
                       self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
                       self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess,
-                      self.step_adapt_rate, self.step_adapt_target, self.resample_scheme, 0)
+                      self.step_adapt_rate, self.step_adapt_target, self.resample_scheme, self.mcmc)
 
 
 def stats_to_dicts(arr):

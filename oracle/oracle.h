@@ -213,7 +213,10 @@ typedef struct {
     int32_t resample_scheme;  /* 0: systematic (fixed point, the default); 1:
                                  multinomial, the paper's choice (Sec. 3), with
                                  the uniforms of oracle_multinomial_u64         */
-    int32_t pad2;
+    int32_t mcmc;             /* 1: Algorithm 2 as J independent chains: no
+                                 importance weights (log w = 0 from the start,
+                                 so J_eff = J and nothing resamples), the
+                                 Metropolis select of accept_reject, log Z = 0 */
 } oracle_config;
 
 typedef struct {

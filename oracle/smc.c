@@ -53,7 +53,7 @@ double oracle_smc_init(const oracle_target* t, const oracle_config* c, double* t
         double logq = -0.5 * zz - 0.5 * (double)D * (LOG_2PI + 2.0 * log(s));
         double lp = oracle_logpi(t, th, grad + j * D);
         logpi[j] = lp;
-        logw[j] = isfinite(lp) ? lp - logq : -INFINITY;
+        logw[j] = c->mcmc ? 0.0 : (isfinite(lp) ? lp - logq : -INFINITY);
     }
     return lse(logw, N) - log((double)N);
 }
@@ -201,7 +201,8 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
     /* (f) reweight with the momentum L-kernel: log w += -Delta H, and the
      * evidence factor sum_j W_j exp(-Delta H_j). */
     double log_z_inc = 0.0;
-    if (!c->accept_reject) {
+    const int mh_select = c->accept_reject || c->mcmc;
+    if (!mh_select) {
         double* a = (double*)malloc((size_t)N * sizeof(double));
         for (int64_t j = 0; j < N; ++j) a[j] = log(W[j]) - dH[j];
         log_z_inc = lse(a, N);
@@ -240,7 +241,7 @@ int oracle_smc_iteration(const oracle_target* t, const oracle_config* c, int64_t
      * it, the Metropolis rule u < alpha decides and the weight is unchanged. */
     for (int64_t j = 0; j < N; ++j) {
         int take = 1;
-        if (c->accept_reject) {
+        if (mh_select) {
             uint32_t ctr[4] = {0u, (uint32_t)j, (uint32_t)k, (uint32_t)ORACLE_TAG_MH}, w[4];
             oracle_philox4x32_10(ctr, c->seed, w);
             take = oracle_u01(w[0], w[1]) < alpha[j];
