@@ -142,7 +142,11 @@ typedef struct {
                                    prefix C_j of the fixed-point weights exceeds
                                    floor(u_i T / 2^64), u_i the 64-bit word pair of
                                    Philox block (1, i, k, RESAMPLE)             */
-    int32_t pad2;
+    int32_t mcmc;               /* 1: Algorithm 2 as J independent ChEES-HMC
+                                   chains: the initial draw carries no importance
+                                   weight (log w = 0, J_eff = J, nothing resamples),
+                                   every move takes the Metropolis select of
+                                   accept_reject, log Z stays 0               */
 } smc_config;
 
 typedef struct {

@@ -41,7 +41,7 @@ class SmcConfig(C.Structure):
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("precision", C.c_int32), ("pad", C.c_int32),
                 ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double),
-                ("resample_scheme", C.c_int32), ("pad2", C.c_int32)]
+                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32)]
 
 
 class SmcFlowConfig(C.Structure):
@@ -187,13 +187,13 @@ class ModelData:
 def make_config(n_particles, n_iters, n_warmup, step_size, traj_len0=5.0, max_steps=500, jitter=1,
                 ess_frac=0.5, seed=1000, adapt=1, adam_lr=0.025, adam_b1=0.9, adam_b2=0.999,
                 adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32, accept_reject=0,
-                step_adapt_rate=0.0, step_adapt_target=0.651, resample_scheme=0) -> SmcConfig:
+                step_adapt_rate=0.0, step_adapt_target=0.651, resample_scheme=0, mcmc=0) -> SmcConfig:
     return SmcConfig(int(n_particles), int(n_iters), int(n_warmup), float(step_size), float(traj_len0),
                      int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), int(accept_reject),
                      int(adapt),
                      float(adam_lr), float(adam_b1), float(adam_b2), float(adam_eps), float(init_scale),
                      int(precision), 0, float(step_adapt_rate), float(step_adapt_target),
-                     int(resample_scheme), 0)
+                     int(resample_scheme), int(mcmc))
 
 
 def stats_dicts(arr):

@@ -33,6 +33,8 @@ struct RunParams {
     int32_t resample_scheme;   // 0 systematic, 1 multinomial
     double step_rate;       // optional warm-up step-size rule: log eps += step_rate (a_h - step_target)
     double step_target;
+    int32_t mcmc;           // 1: Algorithm 2 as independent chains (no importance weights)
+    int32_t pad;
 };
 
 constexpr int SLICE = 128;  // particles per CTA in the weight / statistics kernels (four warps:

@@ -309,6 +309,7 @@ std::string check_config(const smc_config& c) {
     if (!(c.ess_frac >= 0.0 && c.ess_frac <= 1.0)) return "ess_frac must be in [0, 1]";
     if (!(c.step_adapt_rate >= 0.0) || !std::isfinite(c.step_adapt_rate)) return "step_adapt_rate must be >= 0";
     if (c.resample_scheme != 0 && c.resample_scheme != 1) return "resample_scheme must be 0 or 1";
+    if (c.mcmc != 0 && c.mcmc != 1) return "mcmc must be 0 or 1";
     if (c.step_adapt_rate > 0.0 && !(c.step_adapt_target > 0.0 && c.step_adapt_target < 1.0))
         return "step_adapt_target must be in (0, 1)";
     if (c.precision < 0 || c.precision > 3) return "unknown precision";
@@ -561,7 +562,8 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.tile0 = tiles;
         rp.n_iters = cfg[r].n_iters;
         rp.n_warmup = cfg[r].n_warmup;
-        rp.accept_reject = cfg[r].accept_reject;
+        rp.accept_reject = cfg[r].accept_reject || cfg[r].mcmc;
+        rp.mcmc = cfg[r].mcmc;
         rp.step_rate = cfg[r].step_adapt_rate;
         rp.resample_scheme = cfg[r].resample_scheme;
         rp.step_target = cfg[r].step_adapt_target;

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(RUN_THREADS) k_init_finish(StepBufs b, const d
     for (int64_t i = threadIdx.x; i < rp.n; i += blockDim.x) {
         const int64_t j = rp.off + i;
         const double lp = logpi[j];
-        const double lw = isfinite(lp) ? lp - b.logw[j] : -CUDART_INF;
+        // independent chains (Algorithm 2) carry no importance weight
+        const double lw = rp.mcmc ? 0.0 : (isfinite(lp) ? lp - b.logw[j] : -CUDART_INF);
         b.logw[j] = lw;
         m = fmax(m, lw);
     }

@@ -252,14 +252,22 @@ def test_tensor_core_iterations_keep_exact_weights(name, precision):
     smp.close()
 
 
-def test_metropolis_variant_matches_oracle():
+@pytest.mark.parametrize("mode", ["accept_reject", "mcmc"])
+def test_metropolis_variant_matches_oracle(mode):
     """accept_reject = 1: Metropolis select u < alpha (Philox block (0, j, k, MH))
-    after the move, weights unchanged, ChEES on the proposals (Algorithm 2)."""
+    after the move, weights unchanged, ChEES on the proposals (Algorithm 2).
+    mcmc = 1 (Algorithm 2 as independent chains): the same select, and no
+    importance weights at all (log w = 0 throughout, nothing resampled, log Z
+    = 0)."""
     w = rounded_workload(workloads.gauss10())
     run = dict(w["run"], n_iters=6, n_warmup=3, step_size=0.3)
     t = oracle_target(w)
     seed = 31
-    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, accept_reject=1, **run), stream())
+    flags = {"accept_reject": 1} if mode == "accept_reject" else {"mcmc": 1}
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, **flags, **run), stream())
+    if mode == "mcmc":
+        np.testing.assert_array_equal(smp.buffer(B.BUF_LOGW), 0.0)
+        assert smp.log_evidence()[0] == 0.0
     N, D, K = run["n_particles"], w["D"], run["n_iters"]
     n_rej = 0
     for k in range(1, K + 1):
@@ -268,6 +276,9 @@ def test_metropolis_variant_matches_oracle():
         st = smp.step()[0]
         assert st["log_z_inc"] == 0.0
         src = np.arange(N)
+        if mode == "mcmc":
+            assert not st["resampled"]
+            np.testing.assert_array_equal(smp.buffer(B.BUF_LOGW), 0.0)
         if st["resampled"]:
             _, q = oracle.quantise(smp.buffer(B.BUF_W))
             _, src = oracle.systematic(q, oracle.resample_r64(seed, k))
