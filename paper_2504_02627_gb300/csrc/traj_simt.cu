@@ -618,6 +618,7 @@ int32_t traj_tile_count(const DevModel& m, int32_t precision) {
 
 cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision, cudaStream_t s) {
     if (!traj_supported(m, precision)) return cudaErrorInvalidValue;
+    if (a.N <= 0) return cudaSuccess;   // nothing to launch (a zero-size grid is an error)
     if ((precision == 1 || precision == 2) && m.kind == GAUSS_DENSE)
         return launch_traj_gauss_mma(m, a, precision == 1, s);
     if (precision == 1)
