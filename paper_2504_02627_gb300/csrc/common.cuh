@@ -69,6 +69,8 @@ struct RunState {
     // ---- cumulative counters since the initial draw
     int64_t iters_total, grad_evals_total, resamples_total;
     double ess_sum, ess_sum_post;
+    // Adam bias-correction powers b1^t, b2^t, kept as running products
+    double adam_b1t, adam_b2t;
 };
 
 // ---------------------------------------------------------------- Philox4x32-10

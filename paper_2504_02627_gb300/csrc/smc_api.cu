@@ -488,6 +488,8 @@ RunState initial_state(const RunParams& rp, const smc_config& c) {
     st.k = 1;
     st.L_used = std::exp(st.log_L);
     st.eps = rp.eps;
+    st.adam_b1t = 1.0;
+    st.adam_b2t = 1.0;
     return st;
 }
 

@@ -431,20 +431,39 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
             jj[u] = i < rp.n ? rp.off + i : -1;
             ss[u] = (jj[u] >= 0 && !b.chees0) ? b.src[jj[u]] : 0;
         }
-        for (int d = wid; d < D; d += SLICE / 32) {
-            const int64_t o = (int64_t)d * b.ld;
-            double v0 = 0.0, v1 = 0.0;
+        // two dimensions per pass, their loads issued together
+        const float* t0 = b.chees0 ? b.chees0 : b.theta_prev;
+        const float* t1 = b.chees1 ? b.chees1 : b.theta_new;
+        for (int d = wid; d < D; d += 2 * (SLICE / 32)) {
+            const int d2 = d + SLICE / 32;
+            float a0[2][PL], a1[2][PL];
 #pragma unroll
-            for (int u = 0; u < PL; ++u) {
-                if (jj[u] < 0) continue;
-                v0 += (double)(b.chees0 ? b.chees0[o + jj[u]] : b.theta_prev[o + ss[u]]);
-                v1 += (double)(b.chees1 ? b.chees1[o + jj[u]] : b.theta_new[o + jj[u]]);
+            for (int h = 0; h < 2; ++h) {
+                const int dd = h ? d2 : d;
+                const int64_t o = (int64_t)dd * b.ld;
+#pragma unroll
+                for (int u = 0; u < PL; ++u) {
+                    const bool in = jj[u] >= 0 && dd < D;
+                    a0[h][u] = in ? t0[o + (b.chees0 ? jj[u] : ss[u])] : 0.0f;
+                    a1[h][u] = in ? t1[o + jj[u]] : 0.0f;
+                }
             }
-            v0 = warp_sum(v0);
-            v1 = warp_sum(v1);
-            if (lane == 0) {
-                b.colsum[(int64_t)c * 2 * D + d] = v0;
-                b.colsum[(int64_t)c * 2 * D + D + d] = v1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int dd = h ? d2 : d;
+                double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+                for (int u = 0; u < PL; ++u) {
+                    if (jj[u] < 0) continue;
+                    v0 += (double)a0[h][u];
+                    v1 += (double)a1[h][u];
+                }
+                v0 = warp_sum(v0);
+                v1 = warp_sum(v1);
+                if (lane == 0 && dd < D) {
+                    b.colsum[(int64_t)c * 2 * D + dd] = v0;
+                    b.colsum[(int64_t)c * 2 * D + D + dd] = v1;
+                }
             }
         }
     }
@@ -467,23 +486,51 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     const int D = (int)b.D;
     const bool adapting = rp.adapt && st.k < rp.n_warmup;
     if (adapting) {
+        // loads are issued in batches ahead of the sums (the sums keep their
+        // order): a serial load-then-add loop waits one L2 round trip per term
+        constexpr int BQ = 8;
         for (int t = threadIdx.x; t < 2 * D; t += blockDim.x) {
             double s = 0.0;
-            for (int q = 0; q < rp.n_slices; ++q) s += b.colsum[(int64_t)(rp.slice0 + q) * 2 * D + t];
+            const double* cs = b.colsum + (int64_t)rp.slice0 * 2 * D + t;
+            int q = 0;
+            for (; q + BQ <= rp.n_slices; q += BQ) {
+                double v[BQ];
+#pragma unroll
+                for (int u = 0; u < BQ; ++u) v[u] = cs[(int64_t)(q + u) * 2 * D];
+#pragma unroll
+                for (int u = 0; u < BQ; ++u) s += v[u];
+            }
+            for (; q < rp.n_slices; ++q) s += cs[(int64_t)q * 2 * D];
             mean_s[t] = s / (double)rp.n;
         }
         __syncthreads();
         double num = 0.0, den = 0.0;
         if (x.valid) {
             const int64_t src = b.src[x.j];
+            const int64_t j0 = b.chees0 ? x.j : src;
+            const float* t0 = b.chees0 ? b.chees0 : b.theta_prev;
+            const float* t1 = b.chees1 ? b.chees1 : b.theta_new;
             double sq0 = 0.0, sq1 = 0.0, proj = 0.0;
-            for (int d = 0; d < D; ++d) {
-                const int64_t o = (int64_t)d * b.ld;
-                const double e0 = (double)(b.chees0 ? b.chees0[o + x.j] : b.theta_prev[o + src]) - mean_s[d];
-                const double e1 = (double)(b.chees1 ? b.chees1[o + x.j] : b.theta_new[o + x.j]) - mean_s[D + d];
-                sq0 += e0 * e0;
-                sq1 += e1 * e1;
-                proj += e1 * (double)b.p_final[(int64_t)d * b.ld + x.j];
+            constexpr int BD = 8;
+            for (int d0 = 0; d0 < D; d0 += BD) {
+                float v0[BD], v1[BD], vp[BD];
+#pragma unroll
+                for (int u = 0; u < BD; ++u) {
+                    const int64_t o = (int64_t)(d0 + u) * b.ld;
+                    const bool in = d0 + u < D;
+                    v0[u] = in ? t0[o + j0] : 0.0f;
+                    v1[u] = in ? t1[o + x.j] : 0.0f;
+                    vp[u] = in ? b.p_final[o + x.j] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < BD; ++u) {
+                    if (d0 + u >= D) break;
+                    const double e0 = (double)v0[u] - mean_s[d0 + u];
+                    const double e1 = (double)v1[u] - mean_s[D + d0 + u];
+                    sq0 += e0 * e0;
+                    sq1 += e1 * e1;
+                    proj += e1 * (double)vp[u];
+                }
             }
             const double h = jitter_h(rp.jitter, rp.seed, x.i, st.k, rp.n, rp.n_iters, b.primes);
             const double a = b.alpha[x.j];
@@ -522,11 +569,13 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     __threadfence();
     // fixed-order combination of the run's slices: thread t takes slices
     // t, t + SLICE, ... and the block reduces in a fixed tree
+    // (the other slices' parts are read from L2 with cache-global loads, after
+    // the fence that followed the ticket, so no stale L1 copy is seen)
     double za_m = -CUDART_INF, w_m = -CUDART_INF;
     for (int q = threadIdx.x; q < rp.n_slices; q += blockDim.x) {
-        const volatile SlicePart* p = b.parts + rp.slice0 + q;
-        za_m = fmax(za_m, p->za_m);
-        w_m = fmax(w_m, p->w_m);
+        const SlicePart* p = b.parts + rp.slice0 + q;
+        za_m = fmax(za_m, __ldcg(&p->za_m));
+        w_m = fmax(w_m, __ldcg(&p->w_m));
     }
     za_m = block_reduce(za_m, buf, OpMax());
     w_m = block_reduce(w_m, buf, OpMax());
@@ -534,20 +583,33 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     long long ssum = 0;
     int smin = 0x7fffffff, smax = 0;
     for (int q = threadIdx.x; q < rp.n_slices; q += blockDim.x) {
-        const volatile SlicePart* p = b.parts + rp.slice0 + q;
-        if (p->za_m > -CUDART_INF) za_s += p->za_s * exp(p->za_m - za_m);
-        if (p->w_m > -CUDART_INF) {
-            const double f = exp(p->w_m - w_m);
-            w_e1 += p->w_e1 * f;
-            w_e2 += p->w_e2 * f * f;
+        const SlicePart* pp = b.parts + rp.slice0 + q;
+        SlicePart p;
+        p.za_m = __ldcg(&pp->za_m);
+        p.za_s = __ldcg(&pp->za_s);
+        p.w_m = __ldcg(&pp->w_m);
+        p.w_e1 = __ldcg(&pp->w_e1);
+        p.w_e2 = __ldcg(&pp->w_e2);
+        p.alpha_sum = __ldcg(&pp->alpha_sum);
+        p.inv_alpha_sum = __ldcg(&pp->inv_alpha_sum);
+        p.g_num = __ldcg(&pp->g_num);
+        p.g_den = __ldcg(&pp->g_den);
+        p.steps_sum = __ldcg(&pp->steps_sum);
+        p.smin = __ldcg(&pp->smin);
+        p.smax = __ldcg(&pp->smax);
+        if (p.za_m > -CUDART_INF) za_s += p.za_s * exp(p.za_m - za_m);
+        if (p.w_m > -CUDART_INF) {
+            const double f = exp(p.w_m - w_m);
+            w_e1 += p.w_e1 * f;
+            w_e2 += p.w_e2 * f * f;
         }
-        asum += p->alpha_sum;
-        iasum += p->inv_alpha_sum;
-        gnum += p->g_num;
-        gden += p->g_den;
-        ssum += p->steps_sum;
-        smin = min(smin, p->smin);
-        smax = max(smax, p->smax);
+        asum += p.alpha_sum;
+        iasum += p.inv_alpha_sum;
+        gnum += p.g_num;
+        gden += p.g_den;
+        ssum += p.steps_sum;
+        smin = min(smin, p.smin);
+        smax = max(smax, p.smax);
     }
     za_s = block_reduce(za_s, buf, OpSum());
     w_e1 = block_reduce(w_e1, buf, OpSum());
@@ -567,8 +629,10 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             st.adam_t += 1.0;
             st.adam_m = rp.adam_b1 * st.adam_m + (1.0 - rp.adam_b1) * gh;
             st.adam_v = rp.adam_b2 * st.adam_v + (1.0 - rp.adam_b2) * gh * gh;
-            const double mh = st.adam_m / (1.0 - pow(rp.adam_b1, st.adam_t));
-            const double vh = st.adam_v / (1.0 - pow(rp.adam_b2, st.adam_t));
+            st.adam_b1t *= rp.adam_b1;     // b1^t, b2^t by running products (no FP64 pow)
+            st.adam_b2t *= rp.adam_b2;
+            const double mh = st.adam_m / (1.0 - st.adam_b1t);
+            const double vh = st.adam_v / (1.0 - st.adam_b2t);
             st.log_L += rp.adam_lr * mh / (sqrt(vh) + rp.adam_eps);
             // clamp L to [eps, max_steps eps] of this iteration's step size
             const double lo = rp.step_rate > 0.0 ? log(st.eps) : rp.log_L_lo;
