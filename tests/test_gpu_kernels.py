@@ -95,6 +95,11 @@ def _workloads():
         "banana2": workloads.paper_banana2(),
         "gauss100": workloads.gauss100_cond(),       # dense precision, D=100 (CTA kernel)
         "illcond100": workloads.paper_illcond100(),  # Sec. 4 ill-conditioned Gaussian
+        # dense Gaussians for the warp-MMA kernel's shapes: one k-step (D = 1),
+        # a ragged second k-step (D = 17), the eight-warp maximum (D = 128)
+        "gauss_d1": workloads._gauss_from_spectrum(np.array([2.0]), 7),
+        "gauss_d17": workloads._gauss_from_spectrum(np.geomspace(1.0, 100.0, 17), 7),
+        "gauss_d128": workloads._gauss_from_spectrum(np.geomspace(1.0, 1000.0, 128), 7),
     }
 
 
@@ -337,7 +342,8 @@ TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
 
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("name", ["logistic_small", "logistic", "linear", "logistic_d28", "linear_d25",
-                                  "logistic_n1700", "gauss10", "gauss100", "illcond100"])
+                                  "logistic_n1700", "gauss10", "gauss100", "illcond100", "gauss_d1",
+                                  "gauss_d17", "gauss_d128"])
 @pytest.mark.parametrize("N", [1, 45, 300])
 def test_tc_target_value_and_gradient(name, N, precision):
     w = rounded_workload(_workloads()[name])
@@ -365,7 +371,9 @@ def test_tc_target_value_and_gradient(name, N, precision):
                                         ("linear_d25", 1e-3, 257), ("logistic_n1700", 1e-3, 257),
                                         ("logistic", 1e-3, 4096), ("logistic", 1e-3, 20000),
                                         ("gauss10", 0.1, 257), ("gauss100", 0.005, 257),
-                                        ("illcond100", 1e-3, 257), ("gauss100", 0.005, 8192)])
+                                        ("illcond100", 1e-3, 257), ("gauss100", 0.005, 8192),
+                                        ("gauss_d1", 0.1, 257), ("gauss_d17", 0.02, 257),
+                                        ("gauss_d128", 0.005, 257)])
 def test_tc_one_leapfrog_step(name, eps, N, precision):
     """One step: theta_1 = theta_0 + eps (p_0 + eps/2 g_0), p_1 = p_0 + eps/2 (g_0 + g_1);
     a gradient error dg moves p by at most eps*dg and theta by eps^2/2 dg.  At the
