@@ -248,6 +248,55 @@ __device__ __forceinline__ int32_t step_count(double h, double L, double eps, in
     return (int32_t)s;
 }
 
+// ---------------------------------------------------------------- FP32 pairs
+// An unevaluated pair hi + lo of FP32 values carries about 48 significant
+// bits.  Sums use Knuth's TwoSum and products the FMA form of Dekker's
+// TwoProduct (both error-free transformations); pair + pair follows the
+// accurate double-double addition of Hida, Li and Bailey.  On this GPU FP64
+// runs at about 1/64 of the FP32 rate, so the statistics kernels accumulate
+// in pairs and convert to FP64 once per partial sum.
+struct f2sum {
+    float hi, lo;
+};
+__device__ __forceinline__ f2sum two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2sum quick_two_sum(float a, float b) {   // needs |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2sum f2_add(f2sum x, f2sum y) {
+    f2sum s = two_sum(x.hi, y.hi);
+    const f2sum t = two_sum(x.lo, y.lo);
+    s = quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ f2sum f2_add_f(f2sum x, float y) {
+    const f2sum s = two_sum(x.hi, y);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ f2sum f2_mul(f2sum x, f2sum y) {           // lo * lo dropped
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.hi, -p);                          // exact error of p
+    return quick_two_sum(p, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ double f2_to_double(f2sum x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ f2sum f2_from_double(double v) {
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+// butterfly sum over the warp (pair addition is commutative bit for bit)
+__device__ __forceinline__ f2sum warp_sum_f2(f2sum v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const f2sum w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = f2_add(v, w);
+    }
+    return v;
+}
+
 // ---------------------------------------------------------------- reductions
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -451,18 +451,18 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int dd = h ? d2 : d;
-                double v0 = 0.0, v1 = 0.0;
+                f2sum v0{0.0f, 0.0f}, v1{0.0f, 0.0f};    // FP32 pairs (about 48 bits)
 #pragma unroll
                 for (int u = 0; u < PL; ++u) {
                     if (jj[u] < 0) continue;
-                    v0 += (double)a0[h][u];
-                    v1 += (double)a1[h][u];
+                    v0 = f2_add_f(v0, a0[h][u]);
+                    v1 = f2_add_f(v1, a1[h][u]);
                 }
-                v0 = warp_sum(v0);
-                v1 = warp_sum(v1);
+                v0 = warp_sum_f2(v0);
+                v1 = warp_sum_f2(v1);
                 if (lane == 0 && dd < D) {
-                    b.colsum[(int64_t)c * 2 * D + dd] = v0;
-                    b.colsum[(int64_t)c * 2 * D + D + dd] = v1;
+                    b.colsum[(int64_t)c * 2 * D + dd] = f2_to_double(v0);
+                    b.colsum[(int64_t)c * 2 * D + D + dd] = f2_to_double(v1);
                 }
             }
         }
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
 // M_warmup, statistics, and the weight decision of the next iteration.
 __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
     __shared__ double buf[32];
-    __shared__ double mean_s[2 * MAX_CHEES_DIM];
+    __shared__ float mean_s[4 * MAX_CHEES_DIM];   // negated means as FP32 pairs: hi [2D], lo [2D]
     __shared__ bool last_s;
     const SliceIdx x = slice_idx(b);
     const RunParams& rp = b.runs[x.r];
@@ -501,7 +501,10 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
                 for (int u = 0; u < BQ; ++u) s += v[u];
             }
             for (; q < rp.n_slices; ++q) s += cs[(int64_t)q * 2 * D];
-            mean_s[t] = s / (double)rp.n;
+            // the mean as a negated FP32 pair, ready to add to each value
+            const f2sum m = f2_from_double(s / (double)rp.n);
+            mean_s[t] = -m.hi;
+            mean_s[2 * D + t] = -m.lo;
         }
         __syncthreads();
         double num = 0.0, den = 0.0;
@@ -510,7 +513,8 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             const int64_t j0 = b.chees0 ? x.j : src;
             const float* t0 = b.chees0 ? b.chees0 : b.theta_prev;
             const float* t1 = b.chees1 ? b.chees1 : b.theta_new;
-            double sq0 = 0.0, sq1 = 0.0, proj = 0.0;
+            // |t - mean|^2 and the projection accumulated in FP32 pairs
+            f2sum sq0{0.0f, 0.0f}, sq1{0.0f, 0.0f}, proj{0.0f, 0.0f};
             constexpr int BD = 8;
             for (int d0 = 0; d0 < D; d0 += BD) {
                 float v0[BD], v1[BD], vp[BD];
@@ -524,17 +528,18 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
                 }
 #pragma unroll
                 for (int u = 0; u < BD; ++u) {
-                    if (d0 + u >= D) break;
-                    const double e0 = (double)v0[u] - mean_s[d0 + u];
-                    const double e1 = (double)v1[u] - mean_s[D + d0 + u];
-                    sq0 += e0 * e0;
-                    sq1 += e1 * e1;
-                    proj += e1 * (double)vp[u];
+                    const int d = d0 + u;
+                    if (d >= D) break;
+                    const f2sum e0 = f2_add_f(f2sum{mean_s[d], mean_s[2 * D + d]}, v0[u]);
+                    const f2sum e1 = f2_add_f(f2sum{mean_s[D + d], mean_s[3 * D + d]}, v1[u]);
+                    sq0 = f2_add(sq0, f2_mul(e0, e0));
+                    sq1 = f2_add(sq1, f2_mul(e1, e1));
+                    proj = f2_add(proj, f2_mul(e1, f2sum{vp[u], 0.0f}));
                 }
             }
             const double h = jitter_h(rp.jitter, rp.seed, x.i, st.k, rp.n, rp.n_iters, b.primes);
             const double a = b.alpha[x.j];
-            num = a * ((h * st.L_used) * (sq1 - sq0) * proj);
+            num = a * ((h * st.L_used) * (f2_to_double(sq1) - f2_to_double(sq0)) * f2_to_double(proj));
             den = a;
         }
         num = block_reduce(num, buf, OpSum());
