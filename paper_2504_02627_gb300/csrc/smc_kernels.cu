@@ -91,6 +91,18 @@ __global__ void __launch_bounds__(RUN_THREADS) k_init_finish(StepBufs b, const d
     }
 }
 
+// atomicAdd(&counter[key], number of active lanes with this key) once per
+// distinct key in the warp; returns this lane's old-value-plus-rank (the
+// warp-aggregated form: particles of a warp often share a step count)
+__device__ __forceinline__ int warp_agg_inc(int* counter, int key) {
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter + key, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 // ============================================================ weights + steps
 // Per particle slice: normalised weight W_j = exp(log w_j - LSE), the
 // fixed-point weight q_j = floor(W_j 2^S) with S = 62 - ceil(log2 N) when the
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(SLICE) k_weights_steps(StepBufs b) {
             S = step_count(h, st.L_used, st.eps, rp.max_steps);
         }
         b.steps[j] = S;
-        atomicAdd(&b.hist[b.max_steps_all - S], 1);
+        warp_agg_inc(b.hist, b.max_steps_all - S);
     }
     if (ok && st.resample) {
         qi = block_reduce(qi, ubuf, OpSum());
@@ -347,7 +359,7 @@ __global__ void __launch_bounds__(1024) k_hist_scan(StepBufs b) {
 __global__ void k_sort_scatter(StepBufs b) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= b.N) return;
-    const int slot = atomicAdd(&b.hist[b.max_steps_all - b.steps[j]], 1);
+    const int slot = warp_agg_inc(b.hist, b.max_steps_all - b.steps[j]);
     b.perm[slot] = (int32_t)j;
 }
 
