@@ -47,14 +47,16 @@ constexpr int GM_DK = 32;             // padded dimension: two k-steps of GEMM1,
 constexpr int GM_RS = 40;             // floats per particle row of the partial-gradient buffer
 constexpr int GM_TS = 40;             // floats per particle row of theta, p, grad (padding zero)
 constexpr int GM_CH = 16;             // observations per chunk (one k-step of GEMM2)
+constexpr int GM_AS = 40;             // bf16 per row of the theta operand tile (80 bytes: an odd
+                                      // number of 16-byte units, conflict-free 8x8 matrix loads)
 static_assert(GM_W == GM_P, "the end point gives one warp to each particle");
 
 // Dynamic shared memory (bytes): X hi [n16][64] | X lo [n16][64] (x3) |
 // y [n16] f32 | theta, p, grad [16][40] f32 | partials [16 warps][16][40] f32 |
-// H0, log pi [16] f64.
+// theta operand hi, lo [16][40] bf16 | H0, log pi [16] f64.
 struct GmLayout {
     int n16;
-    size_t xh, xl, y, th, p, g, red, h0, lp, bytes;
+    size_t xh, xl, y, th, p, g, red, at, h0, lp, bytes;
     __host__ __device__ GmLayout(int n, bool x3) {
         n16 = (n + GM_CH - 1) / GM_CH * GM_CH;
         xh = 0;
@@ -64,7 +66,8 @@ struct GmLayout {
         p = th + GM_P * GM_TS * 4;
         g = p + GM_P * GM_TS * 4;
         red = g + GM_P * GM_TS * 4;
-        h0 = red + (size_t)GM_W * GM_P * GM_RS * 4;
+        at = red + (size_t)GM_W * GM_P * GM_RS * 4;
+        h0 = at + 2 * (size_t)GM_P * GM_AS * 2;
         lp = h0 + GM_P * 8;
         bytes = lp + GM_P * 8;
     }
@@ -133,6 +136,16 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
     double* lp_s = reinterpret_cast<double*>(smem_raw + L.lp);
     const uint32_t xh_base = tc::smem_u32(smem_raw + L.xh);
     const uint32_t xl_base = tc::smem_u32(smem_raw + L.xl);
+    // theta as the A operand of GEMM1: BF16 hi and lo rows [16][GM_AS], written
+    // by the threads that move theta, read by every warp with 8x8 matrix loads
+    const uint32_t at_base = tc::smem_u32(smem_raw + L.at);
+    constexpr uint32_t AT_LO = GM_P * GM_AS * 2;   // bytes from the hi tile to the lo tile
+    auto put_at = [&](int q, int d, float v) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(smem_raw + L.at) + q * GM_AS + d;
+        t[0] = h;
+        if (X3) t[GM_P * GM_AS] = __float2bfloat16_rn(v - __bfloat162float(h));
+    };
     __shared__ int64_t j_s[GM_P], src_s[GM_P];
     __shared__ float eps_s[GM_P];
     __shared__ uint64_t seed_s[GM_P];
@@ -204,6 +217,9 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
         g_s[e] = gv;
         p_s[e] = pv;
     }
+    // the theta operand tile starts at zero (columns past D stay zero)
+    for (int e = tid; e < GM_P * GM_AS; e += GM_T)   // 32-bit words: both tiles
+        reinterpret_cast<uint32_t*>(smem_raw + L.at)[e] = 0u;
     __syncthreads();
     if (!a.p_in && !a.eval_only) {
         // momentum p ~ N(0, I) from the (seed, i, j, k, MOM) Philox stream
@@ -238,6 +254,7 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
             p_s[e] = pv;
             th_s[e] = fmaf(ef, pv, th_s[e]);
         }
+        if (d < D) put_at(q, d, th_s[e]);
     }
     tc::cp_async_wait<0>();
     __syncthreads();
@@ -246,17 +263,14 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
     const int mi = lane >> 3, mr = lane & 7;
     const int nsteps = a.eval_only ? 1 : smax;
     for (int s = 1; s <= nsteps; ++s) {
-        // ---- Theta as the A operand of GEMM1 (hi, lo) for the two k-steps
+        // ---- Theta as the A operand of GEMM1 (hi, lo) for the two k-steps:
+        //      matrices (particles 8 (mi & 1) .., dims 16 ks + 8 (mi >> 1) ..)
         uint32_t ah[2][4], al[2][4];
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int q = gq + 8 * (v & 1);                 // a0, a2: row g; a1, a3: row g + 8
-                const int d = 16 * ks + 2 * tq + 8 * (v >> 1);  // a0, a1: cols 2t; a2, a3: cols 2t + 8
-                const float2 tv = *reinterpret_cast<const float2*>(th_s + q * GM_TS + d);
-                gm_split(tv.x, tv.y, ah[ks][v], al[ks][v]);
-            }
+            const uint32_t aoff = (uint32_t)(((8 * (mi & 1) + mr) * GM_AS + 16 * ks + 8 * (mi >> 1)) * 2);
+            ldsm4(ah[ks], at_base + aoff);
+            if (X3) ldsm4(al[ks], at_base + AT_LO + aoff);
         }
         float gacc[4][4];
 #pragma unroll
@@ -369,6 +383,7 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                 if (s + 1 <= S_s[q]) {
                     pv = fmaf(he, gs, pv);
                     th_s[ei] = fmaf(ef, pv, th_s[ei]);
+                    put_at(q, d, th_s[ei]);
                 }
                 p_s[ei] = pv;
             }
