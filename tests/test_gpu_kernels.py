@@ -334,9 +334,12 @@ def test_resampling_one_hot_and_degenerate():
 
 
 # ------------------------------------------------------------- tensor-core path
-# Gradient error bounds of the split-BF16 products (derived in the design doc):
-# x3 (hi*hi + lo*hi + hi*lo, lo*lo dropped): a few 2^-16 of the summand scale;
-# plain BF16: a few 2^-8.  The end-point log pi is FP32 in every mode.
+# Gradient error bounds of the split-BF16 products, relative to the sum of
+# absolute summands: each operand x = hi + lo with |x - hi| <= 2^-9 |x| and
+# |x - hi - lo| <= 2^-17 |x|, so the x3 form (hi*hi + lo*hi + hi*lo, lo*lo
+# dropped) errs by about 2^-16 per product plus FP32 accumulation, and plain
+# BF16 by about 2^-8; the bounds below allow a few times that.  The end-point
+# log pi is FP32 in every mode.
 TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
 
 
