@@ -194,19 +194,6 @@ __device__ __noinline__ void to_pm(const float* X, int R, int Kpad, __nv_bfloat1
     }
 }
 
-__device__ __forceinline__ void fl_ldsm4(uint32_t (&v)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void fl_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // Y[r][p] = act(sum_k A[r][k] B[k][p] + bias[r]) for rows r < Mvalid and the
 // CTA's 32 particles, on m16n8k16 BF16 MMAs with FP32 accumulation.  A: MT x KS
 // tiles of fragments (L2), B: BF16 particle-major [32][ldb] in shared memory
@@ -247,9 +234,9 @@ __device__ __noinline__ void cta_mma(const uint4* __restrict__ Af, int MT, int K
                     const int prow = 8 * (nt0 + 2 * h + (mi >> 1)) + mr;
                     const int kcol = 16 * ks + 8 * (mi & 1);
                     uint32_t b[4];
-                    fl_ldsm4(b, bbase + (uint32_t)(prow * ldb + kcol) * 2u);
-                    fl_mma(acc[2 * h], av, b[0], b[1]);
-                    fl_mma(acc[2 * h + 1], av, b[2], b[3]);
+                    tc::ldsm4(b, bbase + (uint32_t)(prow * ldb + kcol) * 2u);
+                    tc::mma_bf16_16816(acc[2 * h], av, b[0], b[1]);
+                    tc::mma_bf16_16816(acc[2 * h + 1], av, b[2], b[3]);
                 }
             }
         }

@@ -1,8 +1,10 @@
 // tc_ptx.cuh -- inline-PTX wrappers for the sm_103a tensor-core path:
 // tcgen05 (TMEM allocation, MMA, commit, loads, fences), mbarriers with
-// bounded waits, thread-block-cluster barriers and distributed shared memory.
+// bounded waits, thread-block-cluster barriers and distributed shared memory,
+// and the warp-level BF16 MMA path (8x8 matrix loads, m16n8k16, BF16 splits).
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace smc {
@@ -251,6 +253,40 @@ __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// ------------------------------------------------------------------ warp-level MMA
+// Four 8x8 b16 matrices from shared memory: lane l gives the address of row
+// l % 8 of matrix l / 8 (16-byte aligned); register i of every lane holds its
+// part of matrix i.  The .trans form transposes each matrix on the way.
+__device__ __forceinline__ void ldsm4(uint32_t (&v)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm4_t(uint32_t (&v)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(addr));
+}
+
+// d += a . b for one m16n8k16 tile: A 16x16 row-major, B 16x8 column-major,
+// BF16 operands, FP32 accumulation
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (a, b) -> packed BF16 pairs hi = rn(a, b) and lo = rn(a - hi, b - hi), so
+// that hi + lo carries about 16 significant bits of each value
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 }  // namespace tc

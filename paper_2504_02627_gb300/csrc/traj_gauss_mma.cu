@@ -47,27 +47,6 @@ struct GgLayout {
     }
 };
 
-__device__ __forceinline__ void gg_ldsm4(uint32_t (&v)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void gg_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void gg_split(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 // 4-byte asynchronous global -> shared copy
 __device__ __forceinline__ void gg_cp_async4(uint32_t dst_smem, const float* src_gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst_smem), "l"(src_gmem) : "memory");
@@ -134,7 +113,7 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
                 const int n = 16 * wid + 8 * u + gq, k = 16 * ks + 8 * hk + 2 * tq;
                 const float v0 = (n < D && k < D) ? __ldg(m.P + (int64_t)n * D + k) : 0.0f;
                 const float v1 = (n < D && k + 1 < D) ? __ldg(m.P + (int64_t)n * D + k + 1) : 0.0f;
-                gg_split(v0, v1, bh[ks][u][hk], bl[ks][u][hk]);
+                tc::split_bf16x2(v0, v1, bh[ks][u][hk], bl[ks][u][hk]);
             }
 
     // ---- particle scalars of this CTA
@@ -234,7 +213,7 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t hi, lo;
-                gg_split(th[u][2 * h] - mu[u][0], th[u][2 * h + 1] - mu[u][1], hi, lo);
+                tc::split_bf16x2(th[u][2 * h] - mu[u][0], th[u][2 * h + 1] - mu[u][1], hi, lo);
                 const uint32_t off = (uint32_t)(((gq + 8 * h) * LDP + 16 * wid + 8 * u + 2 * tq) * 2);
                 unsigned char* base = smem_raw + L.a + (size_t)2 * buf * a_mat;
                 *reinterpret_cast<uint32_t*>(base + off) = hi;
@@ -279,16 +258,16 @@ __global__ void __launch_bounds__(32 * KS, 2) traj_gauss_mma_kernel(DevModel m, 
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
             uint32_t ah[4], al[4];
-            gg_ldsm4(ah, ahb + 32 * ks);
-            if (X3) gg_ldsm4(al, ahb + a_mat + 32 * ks);
+            tc::ldsm4(ah, ahb + 32 * ks);
+            if (X3) tc::ldsm4(al, ahb + a_mat + 32 * ks);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (X3) {
-                    gg_mma(acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
-                    gg_mma(cor[u], al, bh[ks][u][0], bh[ks][u][1]);
-                    gg_mma(cor[u], ah, bl[ks][u][0], bl[ks][u][1]);
+                    tc::mma_bf16_16816(acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
+                    tc::mma_bf16_16816(cor[u], al, bh[ks][u][0], bh[ks][u][1]);
+                    tc::mma_bf16_16816(cor[u], ah, bl[ks][u][0], bl[ks][u][1]);
                 } else {
-                    gg_mma((ks & 1) ? cor[u] : acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
+                    tc::mma_bf16_16816((ks & 1) ? cor[u] : acc[u], ah, bh[ks][u][0], bh[ks][u][1]);
                 }
             }
         }

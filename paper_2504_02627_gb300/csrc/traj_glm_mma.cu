@@ -78,36 +78,6 @@ __device__ __forceinline__ uint32_t gm_xoff(int r, int c) {
     return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
-__device__ __forceinline__ void ldsm4(uint32_t (&v)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm4_t(uint32_t (&v)[4], uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr));
-}
-
-// D += A . B, A 16x16 (row), B 16x8 (col), BF16 in, FP32 accumulate
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// (a, b) -> packed BF16 pair (a in the low half), round to nearest even; the
-// residual pair (a - hi, b - hi) packed the same way
-__device__ __forceinline__ void gm_split(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 template <bool LOGIT, bool X3>
 __device__ __forceinline__ float gm_resid(float y, float eta, float inv_s2) {
     if (LOGIT) {
@@ -269,8 +239,8 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
             const uint32_t aoff = (uint32_t)(((8 * (mi & 1) + mr) * GM_AS + 16 * ks + 8 * (mi >> 1)) * 2);
-            ldsm4(ah[ks], at_base + aoff);
-            if (X3) ldsm4(al[ks], at_base + AT_LO + aoff);
+            tc::ldsm4(ah[ks], at_base + aoff);
+            if (X3) tc::ldsm4(al[ks], at_base + AT_LO + aoff);
         }
         float gacc[4][4];
 #pragma unroll
@@ -292,14 +262,14 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                 // matrices: (n-tile mi >> 1, dims 16 ks + 8 (mi & 1) .. + 7)
                 const uint32_t off = gm_xoff(r0 + 8 * (mi >> 1) + mr, 2 * ks + (mi & 1));
                 uint32_t bh[4], bl[4];
-                ldsm4(bh, xh_base + off);
-                if (X3) ldsm4(bl, xl_base + off);
+                tc::ldsm4(bh, xh_base + off);
+                if (X3) tc::ldsm4(bl, xl_base + off);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    mma_16816(eta[j], ah[ks], bh[2 * j], bh[2 * j + 1]);
+                    tc::mma_bf16_16816(eta[j], ah[ks], bh[2 * j], bh[2 * j + 1]);
                     if (X3) {
-                        mma_16816(cor[j], al[ks], bh[2 * j], bh[2 * j + 1]);
-                        mma_16816(cor[j], ah[ks], bl[2 * j], bl[2 * j + 1]);
+                        tc::mma_bf16_16816(cor[j], al[ks], bh[2 * j], bh[2 * j + 1]);
+                        tc::mma_bf16_16816(cor[j], ah[ks], bl[2 * j], bl[2 * j + 1]);
                     }
                 }
             }
@@ -327,8 +297,8 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                 const float q1 = gm_resid<LOGIT, X3>(yv.y, eta[j][1], inv_s2);
                 const float q2 = gm_resid<LOGIT, X3>(yv.x, eta[j][2], inv_s2);
                 const float q3 = gm_resid<LOGIT, X3>(yv.y, eta[j][3], inv_s2);
-                gm_split(q0, q1, rh[2 * j], rl[2 * j]);
-                gm_split(q2, q3, rh[2 * j + 1], rl[2 * j + 1]);
+                tc::split_bf16x2(q0, q1, rh[2 * j], rl[2 * j]);
+                tc::split_bf16x2(q2, q3, rh[2 * j + 1], rl[2 * j + 1]);
             }
             // GEMM2: G += r . X over these 16 observations (four n-tiles of 8 dims)
 #pragma unroll
@@ -336,15 +306,15 @@ __global__ void __launch_bounds__(GM_T, 1) traj_glm_mma_kernel(DevModel m, TrajA
                 // matrices (transposed): (dims 8 (2h + (mi >> 1)) .., observations 8 (mi & 1) ..)
                 const uint32_t off = gm_xoff(r0 + 8 * (mi & 1) + mr, 2 * h + (mi >> 1));
                 uint32_t bh[4], bl[4];
-                ldsm4_t(bh, xh_base + off);
-                if (X3) ldsm4_t(bl, xl_base + off);
+                tc::ldsm4_t(bh, xh_base + off);
+                if (X3) tc::ldsm4_t(bl, xl_base + off);
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int nt = 2 * h + u;
-                    mma_16816(gacc[nt], rh, bh[2 * u], bh[2 * u + 1]);
+                    tc::mma_bf16_16816(gacc[nt], rh, bh[2 * u], bh[2 * u + 1]);
                     if (X3) {
-                        mma_16816(gacc[nt], rl, bh[2 * u], bh[2 * u + 1]);
-                        mma_16816(gacc[nt], rh, bl[2 * u], bl[2 * u + 1]);
+                        tc::mma_bf16_16816(gacc[nt], rl, bh[2 * u], bh[2 * u + 1]);
+                        tc::mma_bf16_16816(gacc[nt], rh, bl[2 * u], bl[2 * u + 1]);
                     }
                 }
             }
