@@ -99,6 +99,9 @@ int32_t oracle_step_count(double h, double L, double eps, int32_t max_steps) {
 int64_t oracle_nth_prime(int64_t m) {
     static int32_t* table = 0;
     if (m < 1 || m > ORACLE_MAX_PRIME_INDEX) return 0;
+    /* the table is built once, on first use (under a lock when OpenMP threads
+     * may call in together) */
+#pragma omp critical(oracle_prime_table)
     if (!table) {
         /* sieve of Eratosthenes up to ORACLE_SIEVE_TOP */
         unsigned char* comp = (unsigned char*)calloc(ORACLE_SIEVE_TOP + 1, 1);
