@@ -521,6 +521,18 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
+    # the paper's Table 1 quantities for the last timed run (outside the events)
+    paper_q = None
+    s_last = smp.summary()
+    n_it = sum(x["iterations"] for x in s_last)
+    if n_it > 0:
+        n_part = sum(c.n_particles for c in smp._cfg)
+        grads_paper = sum(x["grad_evals"] for x in s_last) + n_part * (n_it // len(s_last))
+        paper_q = {"grad_evals_per_particle": grads_paper / (n_part * (n_it // len(s_last))),
+                   "ess_per_grad_eval": sum(x["ess_sum"] for x in s_last) / grads_paper,
+                   "note": "the paper's Table 1 quantities for the last timed run: gradient evaluations per "
+                           "particle per iteration counting S_j + 1 (the paper's convention), and J_eff per "
+                           "gradient evaluation (sums over the iterations)"}
     prof, prof_ge = _profiled_run(smp, K, 30_000 + rank, flush)
     dev_ms, ge_all, ess_all = aggregate_ranks(torch, dist, dev_ms, ge_total, ess_post, "cuda")
     value = ge_all / (dev_ms / 1e3)
@@ -703,6 +715,7 @@ def main():
         "ess_per_s": {"value": ess_all / (dev_ms / 1e3), "unit": "ESS/s",
                       "note": "sum of post-warm-up J_eff over iterations / device time"},
         "log_z": {"mean": float(np.mean(lz)), "sd": float(np.std(lz, ddof=1)) if len(lz) > 1 else None},
+        "paper_metrics": paper_q,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
