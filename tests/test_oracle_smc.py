@@ -194,3 +194,26 @@ def test_mcmc_mode_chains_reach_the_target():
     # different, weighted ensemble
     r2 = oracle.smc_run(t, oracle.SMCConfig(**{**cfg.__dict__, "mcmc": 0}))
     assert r2["log_z"] != 0.0
+
+
+def test_accept_reject_keeps_the_target_invariant():
+    """The Metropolis select (accept_reject = 1) makes each move leave the
+    target invariant: started exactly at N(0, I) (q_init = the target, so the
+    initial weights are uniform) with a step size large enough that many
+    proposals are rejected, the ensemble stays N(0, I): mean within 4 SE and
+    variance within 4 SE after every iteration."""
+    D, J = 3, 4096
+    t = oracle.TargetSpec.gauss_dense(np.zeros(D), np.eye(D))
+    cfg = oracle.SMCConfig(n_particles=J, n_iters=8, n_warmup=0, step_size=1.5, traj_len0=4.0, max_steps=50,
+                           init_scale=1.0, seed=17, accept_reject=1, adapt=0, jitter=1, ess_frac=0.0)
+    st = oracle.smc_init(t, cfg)
+    st["chees"] = oracle.initial_chees_state(cfg)
+    rejected = 0
+    for k in range(1, cfg.n_iters + 1):
+        out = oracle.smc_iteration(t, cfg, k, st)
+        assert out["status"] == 0
+        rejected += int(np.sum(out["alpha"] < 0.5))
+        th = st["theta"]
+        assert np.all(np.abs(th.mean(0)) <= 4 * np.sqrt(1.0 / J)), (k, th.mean(0))
+        assert np.all(np.abs(th.var(0, ddof=1) - 1.0) <= 4 * np.sqrt(2.0 / (J - 1))), (k, th.var(0, ddof=1))
+    assert rejected > J      # the step size really does reject proposals
