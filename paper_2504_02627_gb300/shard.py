@@ -1,0 +1,93 @@
+"""Particle-sharded resampling across ranks: the exchange step a multi-GPU
+SMC iteration would need (host logic, any torch.distributed backend).
+
+Ranks own contiguous slices of the particles (rank r: global indices
+[off_r, off_r + n_r)) and, after resampling, the same slices of the output
+slots.  Systematic resampling in fixed point (Sec. 3: the resampling step
+of Algorithm 3) needs only two scalars per rank to be exchanged -- its
+particle count and its total fixed-point weight T_r -- because output slot o
+takes the particle j whose inclusive prefix satisfies
+cnt(C_{j-1}) <= o < cnt(C_j), cnt(C) = min(N, ceil((N C - U) / T)),
+U = floor(r64 T / 2^64), and a rank's prefixes are its own cumulative sums
+plus the totals of the ranks before it.  Each rank emits (slot, ancestor)
+pairs for its own particles, the pairs go to the slots' owners, and the
+ancestors' rows are fetched from the ranks that hold them.  All arithmetic is
+on integers, so the ancestors are bit-identical to one device resampling all
+particles at once.
+
+On one GPU per box the library runs independent replicas instead; this
+module is the tested design of the exchange (all-gather of two integers, one
+all-to-all of pairs, one row exchange).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _count(C: int, N: int, T: int, U: int) -> int:
+    """Output slots i with i T + U < N C, clipped to [0, N]."""
+    v = N * C - U
+    if v <= 0:
+        return 0
+    return min(N, -(-v // T))
+
+
+def _layout(n_local: int, t_local: int, dist):
+    import torch
+    world = dist.get_world_size()
+    info = torch.tensor([n_local, t_local], dtype=torch.int64)
+    allinfo = [torch.zeros(2, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(allinfo, info)
+    ns = [int(a[0]) for a in allinfo]
+    ts = [int(a[1]) for a in allinfo]
+    return ns, ts
+
+
+def systematic_shard(q_local, r64: int, dist) -> np.ndarray:
+    """Global ancestor index of every output slot this rank owns, from its
+    slice of the fixed-point weights q (each < 2^62, their global sum T < 2^63)
+    and the iteration's 64-bit uniform r64."""
+    world, rank = dist.get_world_size(), dist.get_rank()
+    q_local = [int(x) for x in np.asarray(q_local, dtype=np.uint64)]
+    ns, ts = _layout(len(q_local), sum(q_local), dist)
+    N, T = sum(ns), sum(ts)
+    if T == 0:
+        raise ValueError("all weights are zero")
+    p_off, c_off = sum(ns[:rank]), sum(ts[:rank])
+    out_lo = np.cumsum([0] + ns)                       # rank r owns slots [out_lo[r], out_lo[r + 1])
+    U = (r64 * T) >> 64
+    pairs = [[] for _ in range(world)]
+    C = c_off
+    for j, qj in enumerate(q_local):
+        lo = _count(C, N, T, U)
+        C += qj
+        hi = _count(C, N, T, U)
+        for o in range(lo, hi):
+            r = int(np.searchsorted(out_lo, o, side="right") - 1)
+            pairs[r].append((o, p_off + j))
+    everyone = [None] * world
+    dist.all_gather_object(everyone, pairs)
+    mine = sorted(p for lists in everyone for p in lists[rank])
+    anc = np.array([a for _, a in mine], dtype=np.int64)
+    assert len(anc) == ns[rank] and all(o == out_lo[rank] + i for i, (o, _) in enumerate(mine))
+    return anc
+
+
+def gather_rows(rows_local: np.ndarray, anc: np.ndarray, dist) -> np.ndarray:
+    """rows_local [n_local, D] of this rank's particles; returns the rows of
+    the global indices `anc` (this rank's ancestors), fetched from the ranks
+    that own them."""
+    world, rank = dist.get_world_size(), dist.get_rank()
+    ns, _ = _layout(len(rows_local), 0, dist)
+    lo = np.cumsum([0] + ns)
+    owner = np.searchsorted(lo, anc, side="right") - 1
+    want = [sorted(set(int(a) for a in anc[owner == r])) for r in range(world)]
+    asks = [None] * world
+    dist.all_gather_object(asks, want)                 # asks[r][s]: what rank r needs from rank s
+    give = {r: {i: rows_local[i - lo[rank]] for i in asks[r][rank]} for r in range(world)}
+    got = [None] * world
+    dist.all_gather_object(got, give)                  # got[s][rank]: rows rank s sends to this rank
+    table = {}
+    for s in range(world):
+        table.update(got[s][rank])
+    return np.stack([table[int(a)] for a in anc]) if len(anc) else rows_local[:0]
