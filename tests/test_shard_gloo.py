@@ -54,7 +54,7 @@ def _rank(rank, world, port, out):
 def test_sharded_systematic_matches_single_device():
     world = len(SIZES)
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
