@@ -16,8 +16,8 @@ on integers, so the ancestors are bit-identical to one device resampling all
 particles at once.
 
 On one GPU per box the library runs independent replicas instead; this
-module is the tested design of the exchange (all-gather of two integers, one
-all-to-all of pairs, one row exchange).
+module is the tested design of the exchange (the normalisation partials,
+an all-gather of two integers, one all-to-all of pairs, one row exchange).
 """
 from __future__ import annotations
 
@@ -41,6 +41,37 @@ def _layout(n_local: int, t_local: int, dist):
     ns = [int(a[0]) for a in allinfo]
     ts = [int(a[1]) for a in allinfo]
     return ns, ts
+
+
+def normalise_shard(logw_local, dist):
+    """Global log-sum-exp and ESS (Eqs. for W and J_eff) of log-weights spread
+    over the ranks: each rank contributes (max, sum exp(lw - max),
+    sum exp(2 (lw - max))) of its slice; the partials are gathered and
+    combined in rank order, so every rank gets the same bits.  Returns
+    (lse, ess, W_local) with W_local = exp(lw - lse) for this rank's slice."""
+    import torch
+    world = dist.get_world_size()
+    lw = np.asarray(logw_local, dtype=np.float64)
+    m = lw.max() if lw.size and np.isfinite(lw.max()) else -np.inf
+    if np.isfinite(m):
+        e = np.exp(lw - m)
+        part = [m, float(e.sum()), float((e * e).sum())]
+    else:
+        part = [-np.inf, 0.0, 0.0]
+    t = torch.tensor(part, dtype=torch.float64)
+    parts = [torch.zeros(3, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, t)
+    M = max(float(p[0]) for p in parts)
+    if not np.isfinite(M):
+        raise ValueError("all weights are zero")
+    s1 = s2 = 0.0
+    for p in parts:                                     # rank order
+        if np.isfinite(float(p[0])):
+            f = np.exp(float(p[0]) - M)
+            s1 += float(p[1]) * f
+            s2 += float(p[2]) * f * f
+    lse = M + np.log(s1)
+    return lse, s1 * s1 / s2, np.exp(lw - lse)
 
 
 def systematic_shard(q_local, r64: int, dist) -> np.ndarray:

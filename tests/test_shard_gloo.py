@@ -1,8 +1,9 @@
 """The exchange step of particle-sharded resampling over gloo ranks on the
-CPU (3 ranks, uneven slices): the ancestors every rank computes for its
-output slots equal, bit for bit, those of one device resampling all
-particles (the oracle's fixed-point systematic rule), and the exchanged rows
-are those of the ancestors."""
+CPU (4 ranks, uneven slices, one empty): the ancestors every rank computes for
+its output slots equal, bit for bit, those of one device resampling all
+particles (the oracle's fixed-point systematic rule); the exchanged rows are
+those of the ancestors; and the normalisation partials give every rank the
+same log-sum-exp and ESS, equal to one device's to FP64 rounding."""
 import os
 import socket
 
@@ -45,7 +46,9 @@ def _rank(rank, world, port, out):
             sl = slice(lo, lo + SIZES[rank])
             anc = shard.systematic_shard(q[sl], r64, dist)
             rows = shard.gather_rows(theta[sl], anc, dist)
-            res.append((anc.tolist(), rows.tolist()))
+            lw = np.log(np.random.default_rng(seed + 100).gamma(0.3, size=sum(SIZES))) * 3.0
+            lse, ess, W = shard.normalise_shard(lw[sl], dist)
+            res.append((anc.tolist(), rows.tolist(), lse, ess, W.tolist()))
         out[rank] = res
     finally:
         dist.destroy_process_group()
@@ -65,3 +68,11 @@ def test_sharded_systematic_matches_single_device():
         np.testing.assert_array_equal(anc, anc_ref)
         rows = np.concatenate([np.array(res[r][i][1]).reshape(-1, 3) for r in range(world)])
         np.testing.assert_array_equal(rows, theta[anc_ref])
+        # the normalisation partials: every rank gets the same LSE and ESS, equal
+        # to one device's to FP64 rounding, and the slices of W
+        lw = np.log(np.random.default_rng(seed + 100).gamma(0.3, size=sum(SIZES))) * 3.0
+        lse_o, ess_o, W_o = oracle.normalise(lw)
+        assert len({res[r][i][2] for r in range(world)}) == 1 and len({res[r][i][3] for r in range(world)}) == 1
+        assert abs(res[0][i][2] - lse_o) <= 1e-12 * abs(lse_o) and abs(res[0][i][3] - ess_o) <= 1e-10 * ess_o
+        W = np.concatenate([np.array(res[r][i][4]) for r in range(world)])
+        np.testing.assert_allclose(W, W_o, rtol=1e-12, atol=0)
