@@ -91,10 +91,24 @@ typedef enum {
     SMC_PREC_BF16 = 2,      /* tensor cores, BF16 operands, FP32 accumulation (same
                                kernels; data that do not fit on chip are streamed,
                                see BF16X2)                                        */
-    SMC_PREC_BF16X2 = 3     /* tcgen05, streamed data (any n, dim <= 128): X rounded
+    SMC_PREC_BF16X2 = 3,    /* tcgen05, streamed data (any n, dim <= 128): X rounded
                                once to BF16, theta and the residuals r split into
                                BF16 hi + lo (two products per GEMM), FP32
                                accumulation                                      */
+    SMC_PREC_BF16C = 4      /* tcgen05, streamed data (any n, dim <= 128), centred:
+                               before each move every run's reference point
+                               theta_ref (the mean of its particles) and the
+                               reference quantities X theta_ref, sigmoid of it and
+                               X'(y - sigmoid) are evaluated with the FP32 data and
+                               FP64 sums; the trajectory's products then carry only
+                               the deviations theta - theta_ref and the residual
+                               changes, one BF16 product per GEMM with FP32
+                               accumulation.  The gradient at the start point is
+                               re-evaluated with the move's reference (so a move
+                               costs S_j + 1 gradients).  At most 16 runs per
+                               handle.  (Sec. 2 of the paper fixes no precision;
+                               the end-point energies in the weights stay FP32 data
+                               with FP64 sums, as for every precision.)          */
 } smc_precision;
 
 /* ------------------------------------------------------------------ config

@@ -17,7 +17,7 @@ from . import build as _build
 SMC_OK, SMC_E_INVAL, SMC_E_NOMEM, SMC_E_CUDA, SMC_E_DEGENERATE, SMC_E_TIMEOUT, SMC_E_STATE = \
     0, -1, -2, -3, -4, -5, -6
 GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
-PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2, PREC_BF16C = 0, 1, 2, 3, 4
 # trajectory-length jitter schemes (Sec. 3.2.1), smc_config.jitter
 (JITTER_NONE, JITTER_HALTON1, JITTER_UNIFORM, JITTER_HALTON_ND, JITTER_HALTON_ND_INV, JITTER_PRIMES,
  JITTER_PRIMES_INV, JITTER_GOLDEN, JITTER_EQUIDISTANT, JITTER_EQUIDISTANT_OFFSET, JITTER_SOBOL1) = range(11)

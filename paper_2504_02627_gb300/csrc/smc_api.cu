@@ -68,10 +68,40 @@ constexpr int64_t MAX_JITTER_PRIME_INDEX = 65536;   // P_m < 2^20: radical inver
 
 }  // namespace
 
+// Per-move reference arrays of the centred tensor-core path (TrajArgs::c_*).
+struct CentredScratch {
+    float* centre = nullptr;
+    float* gref = nullptr;
+    float2* refs = nullptr;
+    double* part = nullptr;
+    int32_t runs = 0;
+};
+
 struct smc_dev_model {
     DevModel m{};
     DevAlloc mem;
+    CentredScratch cs1;   // one run: the stage-level calls on caller buffers
 };
+
+namespace {
+CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs) {
+    CentredScratch c;
+    if (!traj_centred_supported(m)) return c;
+    c.centre = A.get<float>((size_t)(runs * m.dk));
+    c.gref = A.get<float>((size_t)(runs * m.dk));
+    c.refs = A.get<float2>((size_t)centred_refs_elems(m, runs));
+    c.part = A.get<double>((size_t)centred_part_elems(m, runs));
+    c.runs = (c.centre && c.gref && c.refs && c.part) ? runs : 0;
+    return c;
+}
+void set_centred(TrajArgs& a, const CentredScratch& c) {
+    a.c_centre = c.centre;
+    a.c_gref = c.gref;
+    a.c_refs = c.refs;
+    a.c_part = c.part;
+    a.c_runs = c.runs;
+}
+}  // namespace
 
 struct smc_handle {
     cudaStream_t stream = nullptr;
@@ -129,6 +159,7 @@ struct smc_handle {
     // launch plan chosen by the autotuner
     int32_t traj_tile = 0, n_traj_tiles = 1;
     std::vector<double> tile_ms;
+    CentredScratch cs;   // centred precision: reference arrays of every run
 };
 
 namespace {
@@ -251,7 +282,24 @@ std::string upload_model(smc_dev_model* dm, const smc_model* md, cudaStream_t s)
                 m.y_img = up(yi);
                 m.dk = (int32_t)dk;
                 m.n_chunks = (int32_t)nch;
+                // tiles of CENTRED_CHUNK observations for the centred path:
+                // [atoms][CENTRED_CHUNK rows][128 B], same swizzle
+                const int64_t CT = CENTRED_CHUNK, nt = (n + CT - 1) / CT, atoms = (dk + 63) / 64;
+                std::vector<uint16_t> xc((size_t)(nt * atoms * CT * 64), 0);
+                for (int64_t i = 0; i < n; ++i) {
+                    const int64_t c = i / CT, r = i % CT;
+                    for (int64_t d = 0; d < D; ++d) {
+                        const int64_t atom = d / 64, u = (d % 64) / 8, e = d % 8;
+                        const int64_t b = c * (atoms * CT * 128) + atom * (CT * 128) + r * 128 + ((u ^ (r & 7)) << 4) + 2 * e;
+                        xc[(size_t)(b / 2)] = Xh[(size_t)(i * Dp + d)];
+                    }
+                }
+                uint16_t* xcd = dm->mem.get<uint16_t>(xc.size());
+                if (xcd) cudaMemcpyAsync(xcd, xc.data(), xc.size() * 2, cudaMemcpyHostToDevice, s);
+                m.xc_img = xcd;
+                m.n_tiles128 = (int32_t)nt;
                 cudaStreamSynchronize(s);   // the staging vectors are pageable and local
+                dm->cs1 = alloc_centred(dm->mem, m, 1);
             }
             if (logit) {
                 m.lconst = -0.5 * (double)D * (LOG_2PI + 2.0 * std::log(tau));
@@ -312,7 +360,7 @@ std::string check_config(const smc_config& c) {
     if (c.mcmc != 0 && c.mcmc != 1) return "mcmc must be 0 or 1";
     if (c.step_adapt_rate > 0.0 && !(c.step_adapt_target > 0.0 && c.step_adapt_target < 1.0))
         return "step_adapt_target must be in (0, 1)";
-    if (c.precision < 0 || c.precision > 3) return "unknown precision";
+    if (c.precision < 0 || c.precision > 4) return "unknown precision";
     return "";
 }
 
@@ -403,6 +451,7 @@ cudaError_t initial_draw(smc_handle* h) {
         a.ld = h->ld;
         a.eval_only = 1;
         a.dev_err = h->dev_err;
+        set_centred(a, h->cs);
         ce = launch_traj(h->model.m, a, h->precision, s);
     }
     if (ce == cudaSuccess) ce = launch_init_finish(b, h->logpi[0], s);
@@ -451,6 +500,7 @@ cudaError_t autotune(smc_handle* h) {
     a.N = h->N;
     a.ld = h->ld;
     a.dev_err = h->dev_err;
+    set_centred(a, h->cs);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -523,6 +573,12 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         return SMC_E_INVAL;
     }
     h->precision = cfg[0].precision;
+    if (h->precision == SMC_PREC_BF16C && n_runs > CENTRED_MAX_RUNS) {
+        fprintf(stderr, "smc_init_batch: the centred precision serves at most %d runs per handle\n", CENTRED_MAX_RUNS);
+        h->model.mem.release();
+        delete h;
+        return SMC_E_INVAL;
+    }
     if (!traj_supported(h->model.m, h->precision)) {
         fprintf(stderr, "smc_init: no kernel for this model / dimension / precision\n");
         h->model.mem.release();
@@ -639,6 +695,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
     h->done = A.get<unsigned int>((size_t)n_runs);
     h->dev_err = A.get<int>(1);
+    if (h->precision == SMC_PREC_BF16C) h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs);
     if (A.err != cudaSuccess) {
         smc_status st = cuda_fail(h, A.err, "smc_init allocation");
         smc_destroy(h);
@@ -749,6 +806,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
         a.ld = h->ld;
         a.dev_err = h->dev_err;
         a.tile = h->traj_tile;
+        set_centred(a, h->cs);
         if (h->profiling) {
             const size_t i = 2 * h->n_event_pairs;
             while (h->events.size() < i + 2) {
@@ -1184,6 +1242,7 @@ smc_status smc_k_target(const smc_dev_model* m, const float* theta, int64_t N, i
     a.N = N;
     a.ld = ld;
     a.eval_only = 1;
+    set_centred(a, m->cs1);
     return kstatus(launch_traj(m->m, a, precision, static_cast<cudaStream_t>(stream)));
 }
 
@@ -1205,6 +1264,7 @@ smc_status smc_k_leapfrog(const smc_dev_model* m, float* theta, float* p, float*
     a.eps_fixed = eps;
     a.N = N;
     a.ld = ld;
+    set_centred(a, m->cs1);
     return kstatus(launch_traj(m->m, a, precision, static_cast<cudaStream_t>(stream)));
 }
 

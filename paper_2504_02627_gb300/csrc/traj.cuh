@@ -41,8 +41,16 @@ struct DevModel {
     const float* y_img;
     int32_t dk;           // D rounded up to 16 (MMA K of the first product, N of the second)
     int32_t n_chunks;
+    // Centred tensor-core path: X in BF16 as tiles of CENTRED_CHUNK
+    // observations, [ceil(dk / 64) atoms][CENTRED_CHUNK obs rows][128 B], an
+    // atom holding 64 dimensions in the 128-byte swizzle (16-byte unit u of
+    // row r at unit u ^ (r & 7)); zeros past n and past D.
+    const uint16_t* xc_img;
+    int32_t n_tiles128;
 };
 constexpr int STREAM_CHUNK = 64;
+constexpr int CENTRED_CHUNK = 128;
+constexpr int CENTRED_MAX_RUNS = 16;   // runs of one handle the centred path serves
 
 // What a trajectory launch reads and writes.  Slot t of the launch handles
 // particle j = perm ? perm[t] : t; it starts from source index src[j] (the
@@ -65,6 +73,13 @@ struct TrajArgs {
     int32_t eval_only;      // 1: compute log pi and grad at theta_in, no move
     int32_t tile;           // launch-configuration variant of the model's kernel (0: default)
     int* dev_err;           // set to 1 when a bounded device wait gives up (may be nullptr)
+    // centred tensor-core path only: per-move reference quantities of each
+    // run (written by the launcher before the trajectory kernel)
+    float* c_centre;        // [c_runs][dk] reference points theta_ref
+    float* c_gref;          // [c_runs][dk] reference gradients X'(y - s)
+    float2* c_refs;         // [n_tiles128][c_runs][CENTRED_CHUNK] (-log2(e) eta_ref, sigmoid(eta_ref))
+    double* c_part;         // [n_tiles128][c_runs][dk] per-tile parts of c_gref
+    int32_t c_runs;         // runs in these arrays (1 when runs == nullptr)
 };
 
 // Run of particle j: step size, Philox key, iteration and run-local index.
@@ -119,5 +134,11 @@ cudaError_t launch_traj_glm_mma(const DevModel& m, const TrajArgs& a, bool x3, c
 cudaError_t launch_traj_glm_stream(const DevModel& m, const TrajArgs& a, cudaStream_t s);
 bool traj_stream_supported(const DevModel& m);
 cudaError_t launch_traj_stream(const DevModel& m, const TrajArgs& a, int np, cudaStream_t s);
+// centred tensor-core path (traj_centred.cu): any n, D <= 128, precision 4;
+// the caller provides the TrajArgs::c_* arrays (sizes below)
+bool traj_centred_supported(const DevModel& m);
+int64_t centred_refs_elems(const DevModel& m, int n_runs);
+int64_t centred_part_elems(const DevModel& m, int n_runs);
+cudaError_t launch_traj_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s);
 
 }  // namespace smc

@@ -1,0 +1,715 @@
+// traj_centred.cu -- tensor-core (tcgen05) leapfrog trajectories for Bayesian
+// logistic and linear-Gaussian regression in the centred precision form.
+//
+// Centring.  Before each move, every run gets a reference point theta_ref
+// (the mean of its particles) and the per-observation reference quantities
+// eta_ref = X theta_ref, s = sigmoid(eta_ref) and the reference gradient
+// g_ref = X'(y - s) are evaluated once, with the FP32 data and FP64
+// accumulation.  During the trajectory only the deviations are products on
+// the tensor cores, in BF16 with FP32 accumulation:
+//
+//   GEMM1  d_eta^T [128 x 128 obs] = (theta - theta_ref)^T [128 x dk] . X_c^T
+//   GEMM2  G^T     [128 x dk]     += d_r^T [128 x 128 obs] . X_c
+//
+// with d_r = s - sigmoid(eta_ref + d_eta) (logistic) or -d_eta / sigma^2
+// (linear), and the gradient is g_ref + G - theta / tau^2.  Where particles
+// sit near each other -- the posterior, after the first iterations -- the
+// deviations are small, so one BF16 product per GEMM carries fewer rounding
+// errors in absolute terms than a hi + lo split of the full theta and
+// residual would.  The gradient is a fixed, deterministic function of theta
+// within a move (theta_ref changes only between moves, and the kernel
+// re-evaluates the gradient at the start point with the move's own
+// reference rather than reusing the cached one), so each trajectory is a
+// volume-preserving, reversible composition of shears; the end-point energy
+// that enters the importance weight is recomputed with the FP32 data and
+// FP64 accumulation, as in every other kernel.
+//
+// Layout.  One CTA holds 128 particles (MMA M = 128).  X streams through a
+// three-stage ring of 128-observation tiles: [atom][128 obs rows][128 B], an
+// atom being 64 dimensions in the 128-byte swizzle.  GEMM1 reads a tile as its
+// K-major B operand (rows = observations); GEMM2 reads the same bytes as an
+// MN-major B operand (N = dimensions, K = observations: leading byte offset =
+// the atom stride, stride byte offset = eight rows), so each observation is
+// staged once per step for both products.  TMEM columns: G [0, 128), two eta
+// buffers [128, 384), two d_r^T buffers (BF16 pairs) [384, 512); GEMM2 takes
+// its A operand from TMEM.
+//
+// Roles (352 threads): warp 8 lane 0 issues the bulk copies; warp 9 lane 0
+// issues GEMM1 and warp 10 lane 0 GEMM2, each from fully unrolled loops, so
+// neither product waits behind the other's dependencies; warps 0-7 form the
+// residuals from TMEM (warps 0-3 the even-numbered tiles of the step
+// sequence, 4-7 the odd ones) and hold the particle state: warp w owns TMEM
+// lanes 32 (w % 4) .. + 31 (one particle per lane) and dimensions
+// 64 (w / 4) .. + 63.  The sigmoid's exponential is the SFU's base-2
+// exponential; its reciprocal is the SFU's for five of every eight
+// observations and, for the other three, a bit-pattern seed refined by one
+// cubic and one Newton step on the FMA pipe (relative error below 1e-7), so
+// that the SFU and the issue slots share the load.  Every mbarrier wait is
+// bounded in wall time (2 s), after which *dev_err is set and the kernel runs
+// to its end without further waiting.
+#include <cuda_bf16.h>
+#include <math_constants.h>
+#include "tc_ptx.cuh"
+#include "traj.cuh"
+
+namespace smc {
+namespace {
+
+constexpr int CP = 128;                     // particles per CTA
+constexpr int CC = CENTRED_CHUNK;           // observations per tile
+constexpr int C_EPI_WARPS = 8;
+constexpr int C_PRODUCER_WARP = 8, C_MMA1_WARP = 9, C_MMA2_WARP = 10;
+constexpr int C_THREADS = 32 * 11;
+constexpr int C_NS = 3;                     // X tile stages
+constexpr int C_ATOM = CC * 128;            // one 64-dimension atom of a tile: 128 rows x 128 B
+constexpr int C_DATOM = CP * 128;           // one 64-dimension atom of the deviation operand
+constexpr uint32_t C_TMEM_COLS = 512;
+constexpr uint32_t C_COL_G = 0, C_COL_ETA = 128, C_COL_R = 384;
+constexpr int C_SMEM_MAX = 232448;
+constexpr int C_RCP_SFU_OF_8 = 5;           // observations (of every 8) whose reciprocal runs on the SFU
+
+struct CLayout {
+    int atoms, tile_bytes, ref_bytes, stage_bytes;
+    int off_d, off_stage, off_misc, off_bar, total;
+};
+
+// Byte layout of the dynamic shared memory (from a 1024-aligned base).  The
+// end-point pass reuses [0, off_misc) for theta^T, two FP32 X chunks and the
+// partial sums, so off_misc covers both uses.
+__host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
+    CLayout L;
+    L.atoms = (dk + 63) / 64;
+    L.tile_bytes = L.atoms * C_ATOM;
+    L.ref_bytes = n_ref * CC * 8;                         // (c, s) pairs per run, a multiple of 1024
+    L.stage_bytes = L.tile_bytes + L.ref_bytes;
+    L.off_d = 0;
+    L.off_stage = L.atoms * C_DATOM;
+    const int pipe = L.off_stage + C_NS * L.stage_bytes;
+    const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + 8 * CP * 8;
+    L.off_misc = ((pipe > endp ? pipe : endp) + 1023) & ~1023;
+    L.off_bar = L.off_misc + 6 * CP * 8;                  // kin, sq, ll: [2][128] f64 each
+    L.total = L.off_bar + 256 + 1024;                     // + alignment slack of the base
+    // more than half of the SM's shared memory, so that a second CTA, which
+    // would wait for the 512 TMEM columns, is never co-scheduled
+    if (L.total < 118 * 1024) L.total = 118 * 1024;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// 1 / d for d >= 1 on the FMA pipe: bit-pattern seed (relative error below
+// 0.051 for every normal d), one cubic step e -> e^3, one Newton step
+// e -> e^2, relative error below 1e-7.  The argument is clamped so that d is
+// finite (1 / d is then below 2^-64, i.e. zero at the precision it feeds).
+__device__ __forceinline__ float rcp_fma(float d) {
+    d = fminf(d, 1.8446744e19f);
+    float x = __int_as_float(0x7EF311C3 - __float_as_int(d));
+    float e = fmaf(-d, x, 1.0f);
+    x = fmaf(fmaf(e, e, e), x, x);
+    e = fmaf(-d, x, 1.0f);
+    return fmaf(e, x, x);
+}
+
+template <bool LOGIT>
+__global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, TrajArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const int n_ref = LOGIT ? a.c_runs : 0;
+    const CLayout L = c_layout(m.dk, m.Dp, n_ref);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int D = m.D, dk = m.dk, nch = m.n_tiles128;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [3] stage filled
+    uint64_t* empty = full + C_NS;                                   // [3] stage consumed by both GEMMs
+    uint64_t* eta_full = empty + C_NS;                               // [2] GEMM1 done
+    uint64_t* eta_empty = eta_full + 2;                              // [2] eta read by the epilogue
+    uint64_t* r_full = eta_empty + 2;                                // [2] d_r^T written
+    uint64_t* r_empty = r_full + 2;                                  // [2] GEMM2 done with d_r^T
+    uint64_t* g_full = r_empty + 2;                                  // pass's gradient complete
+    uint64_t* th_full = g_full + 1;                                  // next pass's deviation operand written
+    uint64_t* fin1 = th_full + 1;                                    // every GEMM1 issued has completed
+    uint64_t* fin2 = fin1 + 1;                                       // every GEMM2 issued has completed
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(fin2 + 1);
+    int* smax_s = reinterpret_cast<int*>(tmem_s + 1);
+    volatile int* abort_s = smax_s + 1;
+    double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [2][128] |p|^2 halves
+    double* sq_s = kin_s + 2 * CP;                                   // [2][128] |theta|^2 halves
+    double* ll_s = sq_s + 2 * CP;                                    // [128] log-likelihood
+    const uint32_t s_base = tc::smem_u32(sm);
+    int* err = a.dev_err;
+
+    if (tid == 0) {
+        for (int i = 0; i < C_NS; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&eta_full[i], 1);
+            tc::mbar_init(&eta_empty[i], 4);
+            tc::mbar_init(&r_full[i], 4);
+            tc::mbar_init(&r_empty[i], 1);
+        }
+        tc::mbar_init(g_full, 1);
+        tc::mbar_init(th_full, C_EPI_WARPS);
+        tc::mbar_init(fin1, 1);
+        tc::mbar_init(fin2, 1);
+        tc::fence_mbar_init();
+        *smax_s = 0;
+        *abort_s = 0;
+    }
+    if (wid == 0) {
+        tc::tmem_alloc(tmem_s, C_TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+
+    // ---------------------------------------------------------------- particle state (warps 0-7)
+    const bool epi = wid < C_EPI_WARPS;
+    const int quarter = wid & 3, dh = (wid >> 2) & 1;
+    const int prow = 32 * quarter + lane;
+    const int d0 = 64 * dh;
+    const float inv_tau2 = LOGIT ? (float)(1.0 / (m.h0 * m.h0)) : (float)(1.0 / (m.h1 * m.h1));
+    const double inv_tau2_d = LOGIT ? 1.0 / (m.h0 * m.h0) : 1.0 / (m.h1 * m.h1);
+    const float inv_s2 = LOGIT ? 0.0f : (float)(1.0 / (m.h0 * m.h0));
+    const float inv_s = LOGIT ? 0.0f : (float)(1.0 / m.h0);
+    float th[64];
+    int64_t j = -1, src = -1;
+    int S = 0, run = 0;
+    float ef = 0.0f;
+    {
+        const int64_t t = (int64_t)blockIdx.x * CP + prow;
+        if (epi && t < a.N) {
+            j = a.perm ? a.perm[t] : t;
+            src = a.src ? a.src[j] : j;
+            S = a.eval_only ? 0 : a.steps[j];
+            double eps;
+            uint64_t seed;
+            uint32_t kk, jl;
+            particle_run(a, j, run, eps, seed, kk, jl);
+            ef = (float)eps;
+            double kin = 0.0;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                const int d = d0 + i;
+                th[i] = d < D ? a.theta_in[(int64_t)d * a.ld + src] : 0.0f;
+            }
+            if (!a.eval_only) {
+                // momentum (given, or Philox + Box-Muller); the first half kick
+                // waits for the gradient of pass 0
+#pragma unroll
+                for (int i = 0; i < 64; i += 2) {
+                    const int d = d0 + i;
+                    if (d < D) {
+                        float pv[2];
+                        if (a.p_in) {
+                            pv[0] = a.p_in[(int64_t)d * a.ld + j];
+                            pv[1] = d + 1 < D ? a.p_in[(int64_t)(d + 1) * a.ld + j] : 0.0f;
+                        } else {
+                            double z0, z1;
+                            normal_pair(seed, (uint32_t)(d >> 1), jl, kk, TAG_MOM, z0, z1);
+                            pv[0] = (float)z0;
+                            pv[1] = d + 1 < D ? (float)z1 : 0.0f;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            if (d + e < D) {
+                                kin += (double)pv[e] * (double)pv[e];
+                                a.p_out[(int64_t)(d + e) * a.ld + j] = pv[e];
+                            }
+                        }
+                    }
+                }
+            }
+            kin_s[dh * CP + prow] = kin;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) th[i] = 0.0f;
+            if (epi) kin_s[dh * CP + prow] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (epi && S > 0) atomicMax(smax_s, S);
+    const float* cref = a.c_centre + (int64_t)run * dk;   // this particle's run reference point
+    // deviation operand rows of this thread (dims d0 .. d0 + 63), BF16, swizzled
+    auto write_dev = [&]() {
+        if (d0 >= dk) return;
+        unsigned char* row = sm + L.off_d + dh * C_DATOM + prow * 128;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int d = d0 + 8 * u + e;
+                v[e] = (j >= 0 && d < D) ? th[8 * u + e] - __ldg(cref + d) : 0.0f;
+            }
+            const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                       pack_bf16(v[6], v[7]));
+            *reinterpret_cast<uint4*>(row + ((u ^ (prow & 7)) << 4)) = w;
+        }
+    };
+    if (epi) write_dev();
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_s;
+    const int smax = *smax_s;
+    const int npass = a.eval_only ? 1 : smax + 1;   // pass 0: gradient at the start point
+    double H0 = 0.0;
+    if (epi && dh == 0 && j >= 0 && !a.eval_only) H0 = 0.5 * (kin_s[prow] + kin_s[CP + prow]) - a.logpi_in[src];
+
+    const int ksteps1 = dk / 16;
+    const int64_t total = (int64_t)npass * nch;
+
+    if (wid == C_PRODUCER_WARP) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(L.tile_bytes + L.ref_bytes);
+            int st = 0, c = 0;
+            uint32_t ph = 0;
+            for (int64_t it = 0; it < total; ++it) {
+                tc::mbar_wait_timed(&empty[st], ph ^ 1u, err, abort_s);
+                tc::mbar_arrive_expect_tx(&full[st], bytes);
+                unsigned char* dst = sm + L.off_stage + st * L.stage_bytes;
+                tc::bulk_g2s(dst, m.xc_img + (int64_t)c * (L.tile_bytes / 2), (uint32_t)L.tile_bytes, &full[st]);
+                if (L.ref_bytes > 0)
+                    tc::bulk_g2s(dst + L.tile_bytes, a.c_refs + (int64_t)c * n_ref * CC, (uint32_t)L.ref_bytes,
+                                 &full[st]);
+                if (++c == nch) c = 0;
+                if (++st == C_NS) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+            // every copy has landed before the stage memory is reused or the CTA exits
+            const int64_t first = total > C_NS ? total - C_NS : 0;
+            for (int64_t it = first; it < total; ++it)
+                tc::mbar_wait_timed(&full[(int)(it % C_NS)], (uint32_t)((it / C_NS) & 1), err, abort_s);
+        }
+    } else if (wid == C_MMA1_WARP) {
+        // ------------------------------------------------------------ GEMM1: d_eta = dev . X_c^T
+        if (lane == 0) {
+            const uint32_t IDESC1 = tc::idesc_bf16_f32(CP, CC);
+            int st = 0, b = 0;
+            uint32_t ph = 0, bph = 0;
+            for (int s = 0; s < npass; ++s) {
+                if (s >= 1) tc::mbar_wait_timed(th_full, (uint32_t)((s - 1) & 1), err, abort_s);
+                for (int c = 0; c < nch; ++c) {
+                    tc::mbar_wait_timed(&full[st], ph, err, abort_s);
+                    tc::mbar_wait_timed(&eta_empty[b], bph ^ 1u, err, abort_s);
+                    tc::fence_after_sync();
+                    const uint32_t xt = s_base + L.off_stage + st * L.stage_bytes;
+                    const uint32_t dcol = tmem + C_COL_ETA + (uint32_t)(b * CC);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        if (kk < ksteps1) {
+                            const int atom = kk >> 2, ko = (kk & 3) * 32;
+                            const uint64_t ad = tc::smem_desc(s_base + L.off_d + atom * C_DATOM + ko, 16, 1024,
+                                                              tc::SWZ_128B);
+                            const uint64_t bd = tc::smem_desc(xt + atom * C_ATOM + ko, 16, 1024, tc::SWZ_128B);
+                            tc::mma_bf16(dcol, ad, bd, IDESC1, kk > 0 ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&eta_full[b]);
+                    if (++st == C_NS) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (++b == 2) {
+                        b = 0;
+                        bph ^= 1u;
+                    }
+                }
+            }
+            tc::mma_commit(fin1);
+        }
+    } else if (wid == C_MMA2_WARP) {
+        // ------------------------------------------------------------ GEMM2: G += d_r^T . X_c
+        if (lane == 0) {
+            const uint32_t IDESC2 = tc::idesc_bf16_f32(CP, (uint32_t)dk) | (1u << 16);   // B MN-major
+            int st = 0, b = 0;
+            uint32_t ph = 0, bph = 0;
+            for (int s = 0; s < npass; ++s) {
+                for (int c = 0; c < nch; ++c) {
+                    tc::mbar_wait_timed(&full[st], ph, err, abort_s);
+                    tc::mbar_wait_timed(&r_full[b], bph, err, abort_s);
+                    tc::fence_after_sync();
+                    const uint32_t xt = s_base + L.off_stage + st * L.stage_bytes;
+                    const uint32_t acol = tmem + C_COL_R + (uint32_t)(b * (CC / 2));
+#pragma unroll
+                    for (int kk = 0; kk < CC / 16; ++kk) {
+                        const uint64_t bd = tc::smem_desc(xt + kk * 2048, C_ATOM, 1024, tc::SWZ_128B);
+                        tc::mma_bf16_ta(tmem + C_COL_G, acol + (uint32_t)(kk * 8), bd, IDESC2,
+                                        (c > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(&r_empty[b]);
+                    tc::mma_commit(&empty[st]);
+                    if (c == nch - 1) tc::mma_commit(g_full);
+                    if (++st == C_NS) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (++b == 2) {
+                        b = 0;
+                        bph ^= 1u;
+                    }
+                }
+            }
+            tc::mma_commit(fin2);
+        }
+    } else {
+        // ------------------------------------------------------------ residuals and state (warps 0-7)
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const float hf = 0.5f * ef;
+        const float kneg = -1.4426950408889634f;
+        const float* gref = a.c_gref + (int64_t)run * dk;
+        // tile `it` of the pass sequence uses buffer it % 2, taken by warp group it % 2
+        int st = 0;
+        uint32_t sph = 0, bph = 0;
+        int64_t it = 0;
+        for (int s = 0; s < npass; ++s) {
+            for (int c = 0; c < nch; ++c, ++it) {
+                if ((int)(it & 1) == dh) {
+                    if (lane == 0) {
+                        tc::mbar_wait_timed(&eta_full[dh], bph, err, abort_s);
+                        tc::mbar_wait_timed(&full[st], sph, err, abort_s);
+                        tc::mbar_wait_timed(&r_empty[dh], bph ^ 1u, err, abort_s);
+                    }
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    const uint32_t ecol = tmem + lane_base + C_COL_ETA + (uint32_t)(dh * CC);
+                    const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(dh * (CC / 2));
+                    const float4* refs = reinterpret_cast<const float4*>(sm + L.off_stage + st * L.stage_bytes +
+                                                                         L.tile_bytes + run * (CC * 8));
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        float v[32];
+                        tc::tmem_ld32(ecol + 32 * h, v);
+                        if (h == 3) {
+                            tc::fence_before_sync();
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&eta_empty[dh]);
+                        }
+                        uint32_t rr[16];
+#pragma unroll
+                        for (int e = 0; e < 32; e += 2) {
+                            float r0, r1;
+                            if (LOGIT) {
+                                const float4 cs = refs[(32 * h + e) / 2];   // (c, s) of two observations
+                                const float x0 = fmaf(kneg, v[e], cs.x);
+                                const float x1 = fmaf(kneg, v[e + 1], cs.z);
+                                const float q0 = 1.0f + tc::ex2_approx(x0);
+                                const float q1 = 1.0f + tc::ex2_approx(x1);
+                                // observation index within each group of 8: (e & 7) and (e & 7) + 1
+                                const float sg0 = ((e & 7) < C_RCP_SFU_OF_8) ? tc::rcp_approx(q0) : rcp_fma(q0);
+                                const float sg1 = ((e & 7) + 1 < C_RCP_SFU_OF_8) ? tc::rcp_approx(q1) : rcp_fma(q1);
+                                r0 = cs.y - sg0;
+                                r1 = cs.w - sg1;
+                            } else {
+                                r0 = -inv_s2 * v[e];
+                                r1 = -inv_s2 * v[e + 1];
+                            }
+                            rr[e / 2] = pack_bf16(r0, r1);
+                        }
+                        tc::tmem_st16(rcol + 16 * h, rr);
+                    }
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&r_full[dh]);
+                    bph ^= 1u;   // the next use of buffer dh is its next phase
+                }
+                if (++st == C_NS) {
+                    st = 0;
+                    sph ^= 1u;
+                }
+            }
+            // the pass's gradient g_ref + G - theta / tau^2, then the leapfrog update
+            tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
+            tc::fence_after_sync();
+            const bool live = j >= 0 && (a.eval_only || s <= S);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float gv[32];
+                if (d0 + 32 * h < dk) tc::tmem_ld32(tmem + lane_base + C_COL_G + d0 + 32 * h, gv);
+                if (live && d0 + 32 * h < dk) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int i = 32 * h + e, d = d0 + i;
+                        if (d < D) {
+                            const float g = __ldg(gref + d) + gv[e] - th[i] * inv_tau2;
+                            if (a.eval_only || s == S) a.grad_out[(int64_t)d * a.ld + j] = g;
+                            if (!a.eval_only) {
+                                float* pp = a.p_out + (int64_t)d * a.ld + j;
+                                float pv = *pp;
+                                if (s >= 1) pv = fmaf(hf, g, pv);
+                                if (s < S) {
+                                    pv = fmaf(hf, g, pv);
+                                    th[i] = fmaf(ef, pv, th[i]);
+                                }
+                                *pp = pv;
+                            }
+                        }
+                    }
+                }
+            }
+            if (s + 1 < npass) {
+                write_dev();
+                tc::fence_proxy_async_smem();
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (s + 1 < npass && lane == 0) tc::mbar_arrive(th_full);
+        }
+    }
+
+    // ---------------------------------------------------------------- end point energy
+    // eta = X theta in FP32 from the FP32 data (register tile of 8
+    // observations x 4 particles per thread, X chunks double-buffered in
+    // shared memory by cp.async), FP64 accumulation of the log-likelihood.
+    if (tid == 0) {
+        volatile int ignore_abort = 0;   // these drain waits run even after an abort
+        tc::mbar_wait_timed(fin1, 0u, err, &ignore_abort, 4000000000ull);
+        tc::mbar_wait_timed(fin2, 0u, err, &ignore_abort, 4000000000ull);
+    }
+    __syncthreads();
+    const int Dp = m.Dp, n = m.n, nch64 = m.n_chunks;
+    float* thT = reinterpret_cast<float*>(sm);                  // [dk][128]
+    float* xs = thT + dk * CP;                                  // [2][64][Dp]
+    double* llp = reinterpret_cast<double*>(xs + 2 * STREAM_CHUNK * Dp);   // [8][128]
+    if (epi) {
+        double sq = 0.0, kin = 0.0;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            const int d = d0 + i;
+            if (d < dk) thT[d * CP + prow] = th[i];
+            sq += (double)th[i] * (double)th[i];
+            if (j >= 0 && d < D && !a.eval_only) {
+                const double pv = a.p_out[(int64_t)d * a.ld + j];
+                kin += pv * pv;
+            }
+        }
+        sq_s[dh * CP + prow] = sq;
+        kin_s[dh * CP + prow] = kin;     // the initial halves were consumed by H0
+    }
+    auto issue_x = [&](int c, int buf) {
+        const int64_t row0 = (int64_t)c * STREAM_CHUNK;
+        const int64_t left = (int64_t)n - row0;
+        const int rows = left < STREAM_CHUNK ? (int)left : STREAM_CHUNK;
+        const int nvec = rows * Dp / 4;
+        float* dst = xs + buf * STREAM_CHUNK * Dp;
+        const float* srcx = m.X + row0 * Dp;
+        for (int v = tid; v < nvec; v += C_THREADS) tc::cp_async16(dst + 4 * v, srcx + 4 * v);
+        tc::cp_async_commit();
+    };
+    issue_x(0, 0);
+    {
+        const int pg = tid & 31, og = tid >> 5;     // warps 0-7 compute, 8-10 only copy
+        double ll[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < nch64; ++c) {
+            if (c + 1 < nch64) issue_x(c + 1, (c + 1) & 1);
+            else tc::cp_async_commit();
+            tc::cp_async_wait<1>();
+            __syncthreads();
+            if (og < 8) {
+                const float* xc = xs + (c & 1) * STREAM_CHUNK * Dp + og * 8 * Dp;
+                float acc[8][4];
+#pragma unroll
+                for (int o = 0; o < 8; ++o)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[o][q] = 0.0f;
+#pragma unroll 4
+                for (int d = 0; d < D; ++d) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(thT + d * CP + 4 * pg);
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const float x = xc[o * Dp + d];
+                        acc[o][0] = fmaf(x, t4.x, acc[o][0]);
+                        acc[o][1] = fmaf(x, t4.y, acc[o][1]);
+                        acc[o][2] = fmaf(x, t4.z, acc[o][2]);
+                        acc[o][3] = fmaf(x, t4.w, acc[o][3]);
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int64_t i = (int64_t)c * STREAM_CHUNK + og * 8 + o;
+                    if (i < n) {
+                        const float yv = __ldg(m.y + i);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float eta = acc[o][q];
+                            float term;
+                            if (LOGIT) {
+                                const float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
+                                term = yv * eta - sp;
+                            } else {
+                                const float z = (yv - eta) * inv_s;
+                                term = -0.5f * z * z;
+                            }
+                            ll[q] += (double)term;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (og < 8)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) llp[og * CP + 4 * pg + q] = ll[q];
+        __syncthreads();
+        if (tid < CP) {
+            double tot = 0.0;
+            for (int w = 0; w < 8; ++w) tot += llp[w * CP + tid];   // fixed order
+            ll_s[tid] = tot;
+        }
+    }
+    __syncthreads();
+    if (epi && j >= 0) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            const int d = d0 + i;
+            if (d < D && !a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th[i];
+        }
+        if (dh == 0) {
+            const double sq = sq_s[prow] + sq_s[CP + prow];
+            const double lp1 = ll_s[prow] - 0.5 * sq * inv_tau2_d + m.lconst;
+            a.logpi_out[j] = lp1;
+            if (!a.eval_only) {
+                const double kin = kin_s[prow] + kin_s[CP + prow];
+                double dH = (0.5 * kin - lp1) - H0;
+                if (!isfinite(dH)) dH = CUDART_INF;
+                if (a.dH) a.dH[j] = dH;
+                if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (wid == 0) tc::tmem_dealloc(tmem, C_TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- reference point and quantities
+// Run r of the launch: particles [off, off + n) (the whole launch when the
+// launch has no run table).
+__device__ __forceinline__ void run_range(const TrajArgs& a, int r, int64_t& off, int64_t& cnt) {
+    if (a.runs) {
+        off = a.runs[r].off;
+        cnt = a.runs[r].n;
+    } else {
+        off = 0;
+        cnt = a.N;
+    }
+}
+
+// theta_ref[r][d] = mean over the run's particles (after resampling: through
+// src) of theta[d]; zero for the padding dimensions D <= d < dk.
+__global__ void __launch_bounds__(256) k_centre_mean(TrajArgs a, int D, int dk) {
+    __shared__ double red[256];
+    const int r = blockIdx.x, d = blockIdx.y;
+    int64_t off, cnt;
+    run_range(a, r, off, cnt);
+    double sum = 0.0;
+    if (d < D)
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int64_t jj = off + i;
+            const int64_t sj = a.src ? a.src[jj] : jj;
+            sum += (double)a.theta_in[(int64_t)d * a.ld + sj];
+        }
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.c_centre[(int64_t)r * dk + d] = (d < D && cnt > 0) ? (float)(red[0] / (double)cnt) : 0.0f;
+}
+
+// Per 128-observation tile: eta_ref = X theta_ref (FP32 data, FP64 sums), the
+// tile's (c, s) pairs c = -log2(e) eta_ref, s = sigmoid(eta_ref) for the
+// logistic model, and the tile's part of g_ref = X'(y - s) (logistic, with the
+// FP32 s the kernel subtracts from) or X'(y - eta_ref) / sigma^2 (linear).
+template <bool LOGIT>
+__global__ void __launch_bounds__(128) k_centre_obs(DevModel m, TrajArgs a) {
+    __shared__ double rr[CC];
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int64_t i = (int64_t)c * CC + t;
+    const int D = m.D, dk = m.dk, Dp = m.Dp, R = a.c_runs;
+    for (int r = 0; r < R; ++r) {
+        const float* cr = a.c_centre + (int64_t)r * dk;
+        double res = 0.0;
+        float2 cs = make_float2(0.0f, 0.5f);
+        if (i < m.n) {
+            double eta = 0.0;
+            for (int d = 0; d < D; ++d) eta += (double)m.X[i * Dp + d] * (double)cr[d];
+            if (LOGIT) {
+                const float s = (float)(1.0 / (1.0 + exp(-eta)));
+                cs = make_float2((float)(-1.4426950408889634 * eta), s);
+                res = (double)m.y[i] - (double)s;
+            } else {
+                res = ((double)m.y[i] - eta) / (m.h0 * m.h0);
+            }
+        }
+        if (LOGIT) a.c_refs[((int64_t)c * R + r) * CC + t] = cs;
+        rr[t] = res;
+        __syncthreads();
+        if (t < dk) {
+            double g = 0.0;
+            if (t < D) {
+                const int rows = (int)((int64_t)m.n - (int64_t)c * CC < CC ? (int64_t)m.n - (int64_t)c * CC : CC);
+                for (int o = 0; o < rows; ++o) g += (double)m.X[((int64_t)c * CC + o) * Dp + t] * rr[o];
+            }
+            a.c_part[((int64_t)c * R + r) * dk + t] = g;
+        }
+        __syncthreads();
+    }
+}
+
+// g_ref[r][d] = sum over tiles of the partial sums, in tile order.
+__global__ void __launch_bounds__(128) k_centre_grad(TrajArgs a, int dk, int nch) {
+    const int r = blockIdx.x, d = threadIdx.x, R = a.c_runs;
+    if (d >= dk) return;
+    double g = 0.0;
+    for (int c = 0; c < nch; ++c) g += a.c_part[((int64_t)c * R + r) * dk + d];
+    a.c_gref[(int64_t)r * dk + d] = (float)g;
+}
+
+template <bool LOGIT>
+cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const int R = a.c_runs;
+    if (R < 1 || R > CENTRED_MAX_RUNS || !a.c_centre || !a.c_gref || !a.c_part || (LOGIT && !a.c_refs))
+        return cudaErrorInvalidValue;
+    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? R : 0);
+    if (L.total > C_SMEM_MAX) return cudaErrorInvalidValue;
+    k_centre_mean<<<dim3((unsigned)R, (unsigned)m.dk), 256, 0, s>>>(a, m.D, m.dk);
+    k_centre_obs<LOGIT><<<(unsigned)m.n_tiles128, 128, 0, s>>>(m, a);
+    k_centre_grad<<<(unsigned)R, 128, 0, s>>>(a, m.dk, m.n_tiles128);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int tiles = (int)((a.N + CP - 1) / CP);
+    auto kern = traj_centred_kernel<LOGIT>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)tiles, C_THREADS, (size_t)L.total, s>>>(m, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool traj_centred_supported(const DevModel& m) {
+    return (m.kind == LOGISTIC || m.kind == LINEAR_GAUSS) && m.D >= 1 && m.D <= 128 && m.xc_img &&
+           m.n_tiles128 >= 1 && m.n_chunks >= 1;
+}
+
+int64_t centred_refs_elems(const DevModel& m, int n_runs) { return (int64_t)m.n_tiles128 * n_runs * CC; }
+int64_t centred_part_elems(const DevModel& m, int n_runs) { return (int64_t)m.n_tiles128 * n_runs * m.dk; }
+
+cudaError_t launch_traj_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    if (!traj_centred_supported(m)) return cudaErrorInvalidValue;
+    if (!a.eval_only && !a.p_out) return cudaErrorInvalidValue;   // the momenta live in p_out
+    if (a.N <= 0) return cudaSuccess;
+    return m.kind == LOGISTIC ? launch_centred<true>(m, a, s) : launch_centred<false>(m, a, s);
+}
+
+}  // namespace smc

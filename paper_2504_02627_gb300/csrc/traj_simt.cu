@@ -600,6 +600,7 @@ bool traj_supported(const DevModel& m, int32_t precision) {
         return traj_glm_mma_supported(m, false) || traj_tc_supported(m) || traj_stream_supported(m);
     }
     if (precision == 3) return traj_stream_supported(m);
+    if (precision == 4) return traj_centred_supported(m);
     switch (m.kind) {
         case GAUSS_DENSE: return precision == 0 && m.D <= 128;
         case BANANA: return precision == 0 && m.D <= 64;
@@ -628,6 +629,7 @@ cudaError_t launch_traj(const DevModel& m, const TrajArgs& a, int32_t precision,
         return traj_tc_supported(m) ? launch_traj_tc(m, a, false, s) : launch_traj_stream(m, a, 1, s);
     }
     if (precision == 3) return launch_traj_stream(m, a, 2, s);
+    if (precision == 4) return launch_traj_centred(m, a, s);
     switch (m.kind) {
         case GAUSS_DENSE: return m.D <= 32 ? launch_traj_thread(m, a, s) : dispatch_dense(m, a, s);
         case BANANA:
