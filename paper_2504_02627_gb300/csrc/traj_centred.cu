@@ -57,16 +57,16 @@ namespace {
 
 constexpr int CP = 128;                     // particles per CTA
 constexpr int CC = CENTRED_CHUNK;           // observations per tile
-constexpr int C_EPI_WARPS = 8;
-constexpr int C_PRODUCER_WARP = 8, C_MMA1_WARP = 9, C_MMA2_WARP = 10;
-constexpr int C_THREADS = 32 * 11;
+constexpr int C_EPI_WARPS = 16;
+constexpr int C_PRODUCER_WARP = 16, C_MMA1_WARP = 17, C_MMA2_WARP = 18;
+constexpr int C_THREADS = 32 * 19;
 constexpr int C_NS = 3;                     // X tile stages
 constexpr int C_ATOM = CC * 128;            // one 64-dimension atom of a tile: 128 rows x 128 B
 constexpr int C_DATOM = CP * 128;           // one 64-dimension atom of the deviation operand
 constexpr uint32_t C_TMEM_COLS = 512;
 constexpr uint32_t C_COL_G = 0, C_COL_ETA = 128, C_COL_R = 384;
 constexpr int C_SMEM_MAX = 232448;
-constexpr int C_RCP_SFU_OF_8 = 5;           // observations (of every 8) whose reciprocal runs on the SFU
+constexpr int C_RCP_SFU_OF_8 = 8;           // observations (of every 8) whose reciprocal runs on the SFU
 
 struct CLayout {
     int atoms, tile_bytes, ref_bytes, stage_bytes;
@@ -85,9 +85,9 @@ __host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
     L.off_d = 0;
     L.off_stage = L.atoms * C_DATOM;
     const int pipe = L.off_stage + C_NS * L.stage_bytes;
-    const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + 8 * CP * 8;
+    const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + C_EPI_WARPS * CP * 8;
     L.off_misc = ((pipe > endp ? pipe : endp) + 1023) & ~1023;
-    L.off_bar = L.off_misc + 6 * CP * 8;                  // kin, sq, ll: [2][128] f64 each
+    L.off_bar = L.off_misc + 9 * CP * 8;                  // kin, sq: [4][128] f64; ll: [128] f64
     L.total = L.off_bar + 256 + 1024;                     // + alignment slack of the base
     // more than half of the SM's shared memory, so that a second CTA, which
     // would wait for the 512 TMEM columns, is never co-scheduled
@@ -115,13 +115,15 @@ __device__ __forceinline__ float rcp_fma(float d) {
 
 template <bool LOGIT>
 __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, TrajArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-aligned base by pointer arithmetic on the shared array, so that
+    // accesses through it stay shared-space loads and stores
+    unsigned char* sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int n_ref = LOGIT ? a.c_runs : 0;
     const CLayout L = c_layout(m.dk, m.Dp, n_ref);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int D = m.D, dk = m.dk, nch = m.n_tiles128;
+    const int64_t ld = a.ld;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [3] stage filled
     uint64_t* empty = full + C_NS;                                   // [3] stage consumed by both GEMMs
     uint64_t* eta_full = empty + C_NS;                               // [2] GEMM1 done
@@ -135,9 +137,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(fin2 + 1);
     int* smax_s = reinterpret_cast<int*>(tmem_s + 1);
     volatile int* abort_s = smax_s + 1;
-    double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [2][128] |p|^2 halves
-    double* sq_s = kin_s + 2 * CP;                                   // [2][128] |theta|^2 halves
-    double* ll_s = sq_s + 2 * CP;                                    // [128] log-likelihood
+    double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [4][128] |p|^2 parts
+    double* sq_s = kin_s + 4 * CP;                                   // [4][128] |theta|^2 parts
+    double* ll_s = sq_s + 4 * CP;                                    // [128] log-likelihood
     const uint32_t s_base = tc::smem_u32(sm);
     int* err = a.dev_err;
 
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&eta_full[i], 1);
-            tc::mbar_init(&eta_empty[i], 4);
-            tc::mbar_init(&r_full[i], 4);
+            tc::mbar_init(&eta_empty[i], 8);   // the two groups of four warps of the buffer
+            tc::mbar_init(&r_full[i], 8);
             tc::mbar_init(&r_empty[i], 1);
         }
         tc::mbar_init(g_full, 1);
@@ -165,47 +167,50 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         tc::tmem_relinquish();
     }
 
-    // ---------------------------------------------------------------- particle state (warps 0-7)
+    // ---------------------------------------------------------------- particle state (warps 0-15)
+    // warp w: TMEM lanes 32 (w % 4) .. + 31 (one particle per lane); group
+    // q = w / 4 owns dimensions 32 q .. 32 q + 31 of those particles and, in
+    // the tile loop, half (q % 2) of the observations of the tiles that use
+    // buffer q / 2.  theta and p live in theta_out / p_out during the move.
     const bool epi = wid < C_EPI_WARPS;
-    const int quarter = wid & 3, dh = (wid >> 2) & 1;
+    const int quarter = wid & 3, q = (wid >> 2) & 3;
     const int prow = 32 * quarter + lane;
-    const int d0 = 64 * dh;
+    const int ds = 32 * q;                             // first state dimension of this thread
+    const int bq = q >> 1, half = q & 1;
     const float inv_tau2 = LOGIT ? (float)(1.0 / (m.h0 * m.h0)) : (float)(1.0 / (m.h1 * m.h1));
     const double inv_tau2_d = LOGIT ? 1.0 / (m.h0 * m.h0) : 1.0 / (m.h1 * m.h1);
     const float inv_s2 = LOGIT ? 0.0f : (float)(1.0 / (m.h0 * m.h0));
     const float inv_s = LOGIT ? 0.0f : (float)(1.0 / m.h0);
-    float th[64];
+    const bool evalm = a.eval_only != 0;
     int64_t j = -1, src = -1;
     int S = 0, run = 0;
     float ef = 0.0f;
+    float th[32];
     {
         const int64_t t = (int64_t)blockIdx.x * CP + prow;
+        double kin = 0.0;
         if (epi && t < a.N) {
             j = a.perm ? a.perm[t] : t;
             src = a.src ? a.src[j] : j;
-            S = a.eval_only ? 0 : a.steps[j];
+            S = evalm ? 0 : a.steps[j];
             double eps;
             uint64_t seed;
             uint32_t kk, jl;
             particle_run(a, j, run, eps, seed, kk, jl);
             ef = (float)eps;
-            double kin = 0.0;
 #pragma unroll
-            for (int i = 0; i < 64; ++i) {
-                const int d = d0 + i;
-                th[i] = d < D ? a.theta_in[(int64_t)d * a.ld + src] : 0.0f;
-            }
-            if (!a.eval_only) {
-                // momentum (given, or Philox + Box-Muller); the first half kick
-                // waits for the gradient of pass 0
-#pragma unroll
-                for (int i = 0; i < 64; i += 2) {
-                    const int d = d0 + i;
-                    if (d < D) {
-                        float pv[2];
+            for (int i = 0; i < 32; i += 2) {
+                const int d = ds + i;
+                float tv[2] = {0.0f, 0.0f}, pv[2] = {0.0f, 0.0f};
+                if (d < D) {
+                    tv[0] = a.theta_in[(int64_t)d * ld + src];
+                    if (d + 1 < D) tv[1] = a.theta_in[(int64_t)(d + 1) * ld + src];
+                    if (!evalm) {
+                        // momentum (given, or Philox + Box-Muller); the first half
+                        // kick waits for the gradient of pass 0
                         if (a.p_in) {
-                            pv[0] = a.p_in[(int64_t)d * a.ld + j];
-                            pv[1] = d + 1 < D ? a.p_in[(int64_t)(d + 1) * a.ld + j] : 0.0f;
+                            pv[0] = a.p_in[(int64_t)d * ld + j];
+                            if (d + 1 < D) pv[1] = a.p_in[(int64_t)(d + 1) * ld + j];
                         } else {
                             double z0, z1;
                             normal_pair(seed, (uint32_t)(d >> 1), jl, kk, TAG_MOM, z0, z1);
@@ -213,52 +218,57 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             pv[1] = d + 1 < D ? (float)z1 : 0.0f;
                         }
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
+                        for (int e = 0; e < 2; ++e)
                             if (d + e < D) {
                                 kin += (double)pv[e] * (double)pv[e];
-                                a.p_out[(int64_t)(d + e) * a.ld + j] = pv[e];
+                                a.p_out[(int64_t)(d + e) * ld + j] = pv[e];
+                                a.theta_out[(int64_t)(d + e) * ld + j] = tv[e];
                             }
-                        }
                     }
                 }
+                th[i] = tv[0];
+                th[i + 1] = tv[1];
             }
-            kin_s[dh * CP + prow] = kin;
         } else {
 #pragma unroll
-            for (int i = 0; i < 64; ++i) th[i] = 0.0f;
-            if (epi) kin_s[dh * CP + prow] = 0.0;
+            for (int i = 0; i < 32; ++i) th[i] = 0.0f;
         }
+        if (epi) kin_s[q * CP + prow] = kin;
     }
-    __syncthreads();
-    if (epi && S > 0) atomicMax(smax_s, S);
     const float* cref = a.c_centre + (int64_t)run * dk;   // this particle's run reference point
-    // deviation operand rows of this thread (dims d0 .. d0 + 63), BF16, swizzled
-    auto write_dev = [&]() {
-        if (d0 >= dk) return;
-        unsigned char* row = sm + L.off_d + dh * C_DATOM + prow * 128;
+    // deviation operand: unit u (8 dimensions) of this thread's 32 dimensions
+    // of its particle row, BF16, swizzled
+    auto write_unit = [&](int u, const float* tv) {
+        unsigned char* row = sm + L.off_d + (q >> 1) * C_DATOM + prow * 128;
+        float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int d = d0 + 8 * u + e;
-                v[e] = (j >= 0 && d < D) ? th[8 * u + e] - __ldg(cref + d) : 0.0f;
-            }
-            const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                       pack_bf16(v[6], v[7]));
-            *reinterpret_cast<uint4*>(row + ((u ^ (prow & 7)) << 4)) = w;
+        for (int e = 0; e < 8; ++e) {
+            const int d = ds + 8 * u + e;
+            v[e] = (j >= 0 && d < D) ? tv[e] - __ldg(cref + d) : 0.0f;
         }
+        const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                   pack_bf16(v[6], v[7]));
+        const int unit = 4 * (q & 1) + u;
+        *reinterpret_cast<uint4*>(row + ((unit ^ (prow & 7)) << 4)) = w;
     };
-    if (epi) write_dev();
+    auto write_dev = [&](const float (&tv)[32]) {
+        if (ds >= dk) return;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) write_unit(u, tv + 8 * u);
+    };
+    if (epi) write_dev(th);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (epi && S > 0) atomicMax(smax_s, S);
+    double H0 = 0.0;
+    if (epi && q == 0 && j >= 0 && !evalm)
+        H0 = 0.5 * (kin_s[prow] + kin_s[CP + prow] + kin_s[2 * CP + prow] + kin_s[3 * CP + prow]) - a.logpi_in[src];
+    __syncthreads();
     const uint32_t tmem = *tmem_s;
     const int smax = *smax_s;
-    const int npass = a.eval_only ? 1 : smax + 1;   // pass 0: gradient at the start point
-    double H0 = 0.0;
-    if (epi && dh == 0 && j >= 0 && !a.eval_only) H0 = 0.5 * (kin_s[prow] + kin_s[CP + prow]) - a.logpi_in[src];
+    const int npass = evalm ? 1 : smax + 1;   // pass 0: gradient at the start point
 
     const int ksteps1 = dk / 16;
     const int64_t total = (int64_t)npass * nch;
@@ -360,65 +370,73 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             tc::mma_commit(fin2);
         }
     } else {
-        // ------------------------------------------------------------ residuals and state (warps 0-7)
+        // ------------------------------------------------------------ residuals and state (warps 0-15)
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const float hf = 0.5f * ef;
         const float kneg = -1.4426950408889634f;
         const float* gref = a.c_gref + (int64_t)run * dk;
-        // tile `it` of the pass sequence uses buffer it % 2, taken by warp group it % 2
         int st = 0;
         uint32_t sph = 0, bph = 0;
         int64_t it = 0;
         for (int s = 0; s < npass; ++s) {
             for (int c = 0; c < nch; ++c, ++it) {
-                if ((int)(it & 1) == dh) {
+                if ((int)(it & 1) == bq) {
                     if (lane == 0) {
-                        tc::mbar_wait_timed(&eta_full[dh], bph, err, abort_s);
+                        tc::mbar_wait_timed(&eta_full[bq], bph, err, abort_s);
                         tc::mbar_wait_timed(&full[st], sph, err, abort_s);
-                        tc::mbar_wait_timed(&r_empty[dh], bph ^ 1u, err, abort_s);
                     }
                     __syncwarp();
                     tc::fence_after_sync();
-                    const uint32_t ecol = tmem + lane_base + C_COL_ETA + (uint32_t)(dh * CC);
-                    const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(dh * (CC / 2));
-                    const float4* refs = reinterpret_cast<const float4*>(sm + L.off_stage + st * L.stage_bytes +
-                                                                         L.tile_bytes + run * (CC * 8));
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        float v[32];
-                        tc::tmem_ld32(ecol + 32 * h, v);
-                        if (h == 3) {
-                            tc::fence_before_sync();
-                            __syncwarp();
-                            if (lane == 0) tc::mbar_arrive(&eta_empty[dh]);
-                        }
-                        uint32_t rr[16];
+                    const uint32_t ecol = tmem + lane_base + C_COL_ETA + (uint32_t)(bq * CC + 64 * half);
+                    const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(bq * (CC / 2) + 32 * half);
+                    const float4* refs = reinterpret_cast<const float4*>(
+                        sm + L.off_stage + st * L.stage_bytes + L.tile_bytes + run * (CC * 8) + half * (64 * 8));
+                    // both halves of this warp's 64 eta columns are loaded up
+                    // front; the second arrives while the first is formed
+                    uint32_t v0[32], v1[32];
+                    tc::tmem_ld32_nowait(ecol, v0);
+                    tc::tmem_ld32_nowait(ecol + 32, v1);
+                    tc::tmem_wait_ld();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&eta_empty[bq]);
+                    // each pair's packed BF16 residuals overwrite the pair's first
+                    // (already consumed) slot, so v[0..15] ends up holding the row
+                    auto residuals = [&](uint32_t (&v)[32], int h) {
 #pragma unroll
                         for (int e = 0; e < 32; e += 2) {
                             float r0, r1;
+                            const float v0f = __uint_as_float(v[e]), v1f = __uint_as_float(v[e + 1]);
                             if (LOGIT) {
                                 const float4 cs = refs[(32 * h + e) / 2];   // (c, s) of two observations
-                                const float x0 = fmaf(kneg, v[e], cs.x);
-                                const float x1 = fmaf(kneg, v[e + 1], cs.z);
+                                const float x0 = fmaf(kneg, v0f, cs.x);
+                                const float x1 = fmaf(kneg, v1f, cs.z);
                                 const float q0 = 1.0f + tc::ex2_approx(x0);
                                 const float q1 = 1.0f + tc::ex2_approx(x1);
-                                // observation index within each group of 8: (e & 7) and (e & 7) + 1
                                 const float sg0 = ((e & 7) < C_RCP_SFU_OF_8) ? tc::rcp_approx(q0) : rcp_fma(q0);
                                 const float sg1 = ((e & 7) + 1 < C_RCP_SFU_OF_8) ? tc::rcp_approx(q1) : rcp_fma(q1);
                                 r0 = cs.y - sg0;
                                 r1 = cs.w - sg1;
                             } else {
-                                r0 = -inv_s2 * v[e];
-                                r1 = -inv_s2 * v[e + 1];
+                                r0 = -inv_s2 * v0f;
+                                r1 = -inv_s2 * v1f;
                             }
-                            rr[e / 2] = pack_bf16(r0, r1);
+                            v[e / 2] = pack_bf16(r0, r1);
                         }
-                        tc::tmem_st16(rcol + 16 * h, rr);
-                    }
+                    };
+                    residuals(v0, 0);
+                    // the buffer's previous residuals have been read by GEMM2
+                    if (lane == 0) tc::mbar_wait_timed(&r_empty[bq], bph ^ 1u, err, abort_s);
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    tc::tmem_st16_nowait(rcol, v0);
+                    residuals(v1, 1);
+                    tc::tmem_st16_nowait(rcol + 16, v1);
+                    tc::tmem_wait_st();
                     tc::fence_before_sync();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&r_full[dh]);
-                    bph ^= 1u;   // the next use of buffer dh is its next phase
+                    if (lane == 0) tc::mbar_arrive(&r_full[bq]);
+                    bph ^= 1u;   // the next use of buffer bq is its next phase
                 }
                 if (++st == C_NS) {
                     st = 0;
@@ -428,36 +446,42 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             // the pass's gradient g_ref + G - theta / tau^2, then the leapfrog update
             tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
             tc::fence_after_sync();
-            const bool live = j >= 0 && (a.eval_only || s <= S);
+            const bool live = j >= 0 && (evalm || s <= S);
+            const bool more = s + 1 < npass;
+            if (ds < dk) {
+                uint32_t gv[32];
+                tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
+                tc::tmem_wait_ld();
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float gv[32];
-                if (d0 + 32 * h < dk) tc::tmem_ld32(tmem + lane_base + C_COL_G + d0 + 32 * h, gv);
-                if (live && d0 + 32 * h < dk) {
+                for (int u = 0; u < 4; ++u) {
+                    float tv[8];
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int i = 32 * h + e, d = d0 + i;
-                        if (d < D) {
-                            const float g = __ldg(gref + d) + gv[e] - th[i] * inv_tau2;
-                            if (a.eval_only || s == S) a.grad_out[(int64_t)d * a.ld + j] = g;
-                            if (!a.eval_only) {
-                                float* pp = a.p_out + (int64_t)d * a.ld + j;
+                    for (int e8 = 0; e8 < 8; ++e8) {
+                        const int e = 8 * u + e8, d = ds + e;
+                        float tnew = 0.0f;
+                        if (live && d < D) {
+                            float tcur = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
+                            const float g = __ldg(gref + d) + __uint_as_float(gv[e]) - tcur * inv_tau2;
+                            if (evalm || s == S) a.grad_out[(int64_t)d * ld + j] = g;
+                            if (!evalm) {
+                                float* pp = a.p_out + (int64_t)d * ld + j;
                                 float pv = *pp;
                                 if (s >= 1) pv = fmaf(hf, g, pv);
                                 if (s < S) {
                                     pv = fmaf(hf, g, pv);
-                                    th[i] = fmaf(ef, pv, th[i]);
+                                    tcur = fmaf(ef, pv, tcur);
+                                    a.theta_out[(int64_t)d * ld + j] = tcur;
                                 }
                                 *pp = pv;
                             }
+                            tnew = tcur;
                         }
+                        tv[e8] = tnew;
                     }
+                    if (more) write_unit(u, tv);
                 }
             }
-            if (s + 1 < npass) {
-                write_dev();
-                tc::fence_proxy_async_smem();
-            }
+            if (more) tc::fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncwarp();
             if (s + 1 < npass && lane == 0) tc::mbar_arrive(th_full);
@@ -465,9 +489,10 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     }
 
     // ---------------------------------------------------------------- end point energy
-    // eta = X theta in FP32 from the FP32 data (register tile of 8
+    // eta = X theta in FP32 from the FP32 data (register tile of 4
     // observations x 4 particles per thread, X chunks double-buffered in
-    // shared memory by cp.async), FP64 accumulation of the log-likelihood.
+    // shared memory by cp.async), a thread's four terms of a particle summed in
+    // FP32, then FP64 accumulation of the log-likelihood.
     if (tid == 0) {
         volatile int ignore_abort = 0;   // these drain waits run even after an abort
         tc::mbar_wait_timed(fin1, 0u, err, &ignore_abort, 4000000000ull);
@@ -477,21 +502,25 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     const int Dp = m.Dp, n = m.n, nch64 = m.n_chunks;
     float* thT = reinterpret_cast<float*>(sm);                  // [dk][128]
     float* xs = thT + dk * CP;                                  // [2][64][Dp]
-    double* llp = reinterpret_cast<double*>(xs + 2 * STREAM_CHUNK * Dp);   // [8][128]
+    double* llp = reinterpret_cast<double*>(xs + 2 * STREAM_CHUNK * Dp);   // [16][128]
     if (epi) {
         double sq = 0.0, kin = 0.0;
 #pragma unroll
-        for (int i = 0; i < 64; ++i) {
-            const int d = d0 + i;
-            if (d < dk) thT[d * CP + prow] = th[i];
-            sq += (double)th[i] * (double)th[i];
-            if (j >= 0 && d < D && !a.eval_only) {
-                const double pv = a.p_out[(int64_t)d * a.ld + j];
-                kin += pv * pv;
+        for (int e = 0; e < 32; ++e) {
+            const int d = ds + e;
+            float tvv = 0.0f;
+            if (j >= 0 && d < D) {
+                tvv = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
+                if (!evalm) {
+                    const double pv = a.p_out[(int64_t)d * ld + j];
+                    kin += pv * pv;
+                }
             }
+            if (d < dk) thT[d * CP + prow] = tvv;
+            sq += (double)tvv * (double)tvv;
         }
-        sq_s[dh * CP + prow] = sq;
-        kin_s[dh * CP + prow] = kin;     // the initial halves were consumed by H0
+        sq_s[q * CP + prow] = sq;
+        kin_s[q * CP + prow] = kin;     // the initial parts were consumed by H0
     }
     auto issue_x = [&](int c, int buf) {
         const int64_t row0 = (int64_t)c * STREAM_CHUNK;
@@ -505,40 +534,49 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     };
     issue_x(0, 0);
     {
-        const int pg = tid & 31, og = tid >> 5;     // warps 0-7 compute, 8-10 only copy
+        const int pg = lane, og = wid;     // warps 0-15 compute 4 observations each, 16-18 only copy
         double ll[4] = {0.0, 0.0, 0.0, 0.0};
         for (int c = 0; c < nch64; ++c) {
             if (c + 1 < nch64) issue_x(c + 1, (c + 1) & 1);
             else tc::cp_async_commit();
             tc::cp_async_wait<1>();
             __syncthreads();
-            if (og < 8) {
-                const float* xc = xs + (c & 1) * STREAM_CHUNK * Dp + og * 8 * Dp;
-                float acc[8][4];
+            if (og < C_EPI_WARPS) {
+                const float* xc = xs + (c & 1) * STREAM_CHUNK * Dp + og * 4 * Dp;
+                float acc[4][4];
 #pragma unroll
-                for (int o = 0; o < 8; ++o)
+                for (int o = 0; o < 4; ++o)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[o][q] = 0.0f;
-#pragma unroll 4
-                for (int d = 0; d < D; ++d) {
-                    const float4 t4 = *reinterpret_cast<const float4*>(thT + d * CP + 4 * pg);
+                    for (int k = 0; k < 4; ++k) acc[o][k] = 0.0f;
+                // four dimensions per iteration: X rows as float4 (Dp is a
+                // multiple of 4 and zero-padded; theta^T rows past D are zero)
+                const float* tcol = thT + 4 * pg;
+                for (int d = 0; d < Dp; d += 4) {
+                    float4 xv[4];
 #pragma unroll
-                    for (int o = 0; o < 8; ++o) {
-                        const float x = xc[o * Dp + d];
-                        acc[o][0] = fmaf(x, t4.x, acc[o][0]);
-                        acc[o][1] = fmaf(x, t4.y, acc[o][1]);
-                        acc[o][2] = fmaf(x, t4.z, acc[o][2]);
-                        acc[o][3] = fmaf(x, t4.w, acc[o][3]);
+                    for (int o = 0; o < 4; ++o) xv[o] = *reinterpret_cast<const float4*>(xc + o * Dp + d);
+#pragma unroll
+                    for (int dd = 0; dd < 4; ++dd) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tcol + (d + dd) * CP);
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            const float x = dd == 0 ? xv[o].x : dd == 1 ? xv[o].y : dd == 2 ? xv[o].z : xv[o].w;
+                            acc[o][0] = fmaf(x, t4.x, acc[o][0]);
+                            acc[o][1] = fmaf(x, t4.y, acc[o][1]);
+                            acc[o][2] = fmaf(x, t4.z, acc[o][2]);
+                            acc[o][3] = fmaf(x, t4.w, acc[o][3]);
+                        }
                     }
                 }
+                float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int o = 0; o < 8; ++o) {
-                    const int64_t i = (int64_t)c * STREAM_CHUNK + og * 8 + o;
+                for (int o = 0; o < 4; ++o) {
+                    const int64_t i = (int64_t)c * STREAM_CHUNK + og * 4 + o;
                     if (i < n) {
                         const float yv = __ldg(m.y + i);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float eta = acc[o][q];
+                        for (int k = 0; k < 4; ++k) {
+                            const float eta = acc[o][k];
                             float term;
                             if (LOGIT) {
                                 const float sp = eta > 0.0f ? eta + log1pf(expf(-eta)) : log1pf(expf(eta));
@@ -547,41 +585,36 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                                 const float z = (yv - eta) * inv_s;
                                 term = -0.5f * z * z;
                             }
-                            ll[q] += (double)term;
+                            part[k] += term;
                         }
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ll[k] += (double)part[k];
             }
             __syncthreads();
         }
-        if (og < 8)
+        if (og < C_EPI_WARPS)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) llp[og * CP + 4 * pg + q] = ll[q];
+            for (int k = 0; k < 4; ++k) llp[og * CP + 4 * pg + k] = ll[k];
         __syncthreads();
         if (tid < CP) {
             double tot = 0.0;
-            for (int w = 0; w < 8; ++w) tot += llp[w * CP + tid];   // fixed order
+            for (int w = 0; w < C_EPI_WARPS; ++w) tot += llp[w * CP + tid];   // fixed order
             ll_s[tid] = tot;
         }
     }
     __syncthreads();
-    if (epi && j >= 0) {
-#pragma unroll
-        for (int i = 0; i < 64; ++i) {
-            const int d = d0 + i;
-            if (d < D && !a.eval_only) a.theta_out[(int64_t)d * a.ld + j] = th[i];
-        }
-        if (dh == 0) {
-            const double sq = sq_s[prow] + sq_s[CP + prow];
-            const double lp1 = ll_s[prow] - 0.5 * sq * inv_tau2_d + m.lconst;
-            a.logpi_out[j] = lp1;
-            if (!a.eval_only) {
-                const double kin = kin_s[prow] + kin_s[CP + prow];
-                double dH = (0.5 * kin - lp1) - H0;
-                if (!isfinite(dH)) dH = CUDART_INF;
-                if (a.dH) a.dH[j] = dH;
-                if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
-            }
+    if (epi && q == 0 && j >= 0) {
+        const double sq = sq_s[prow] + sq_s[CP + prow] + sq_s[2 * CP + prow] + sq_s[3 * CP + prow];
+        const double lp1 = ll_s[prow] - 0.5 * sq * inv_tau2_d + m.lconst;
+        a.logpi_out[j] = lp1;
+        if (!evalm) {
+            const double kin = kin_s[prow] + kin_s[CP + prow] + kin_s[2 * CP + prow] + kin_s[3 * CP + prow];
+            double dH = (0.5 * kin - lp1) - H0;
+            if (!isfinite(dH)) dH = CUDART_INF;
+            if (a.dH) a.dH[j] = dH;
+            if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
         }
     }
     tc::fence_before_sync();

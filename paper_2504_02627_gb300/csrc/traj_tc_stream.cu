@@ -22,9 +22,9 @@
 // lane) and dimensions 64 (w / 4) .. + 63.
 // TMEM columns: eta [0, 192), G [192, 192 + dk), R^T [320, 512).  Every wait on
 // an mbarrier is bounded (then *dev_err is set and the kernel still runs to
-// its end) in wall time (2 s of %globaltimer per wait), and a waiting thread
-// sleeps in hardware (try_wait suspend hint) instead of spinning on issue
-// slots the epilogue warps need.
+// its end) in wall time (2 s of %globaltimer per wait); a waiting thread polls
+// with try_wait, which suspends it in hardware between polls, and reads the
+// clock once per 64 polls, so it takes few issue slots from the epilogue.
 //
 // Precision: X is rounded once to BF16 (a fixed perturbation of the data the
 // integrator sees); with np = 2 the state operands Theta and r are split into
