@@ -80,6 +80,7 @@ struct TrajArgs {
     float2* c_refs;         // [n_tiles128][c_runs][CENTRED_CHUNK] (-log2(e) eta_ref, sigmoid(eta_ref))
     double* c_part;         // [n_tiles128][c_runs][dk] per-tile parts of c_gref
     int32_t c_runs;         // runs in these arrays (1 when runs == nullptr)
+    int32_t c_split;        // CTAs per particle tile (observation split), set by the launcher
 };
 
 // Run of particle j: step size, Philox key, iteration and run-local index.

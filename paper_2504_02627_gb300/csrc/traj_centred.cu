@@ -34,19 +34,29 @@
 // buffers [128, 384), two d_r^T buffers (BF16 pairs) [384, 512); GEMM2 takes
 // its A operand from TMEM.
 //
-// Roles (352 threads): warp 8 lane 0 issues the bulk copies; warp 9 lane 0
-// issues GEMM1 and warp 10 lane 0 GEMM2, each from fully unrolled loops, so
-// neither product waits behind the other's dependencies; warps 0-7 form the
-// residuals from TMEM (warps 0-3 the even-numbered tiles of the step
-// sequence, 4-7 the odd ones) and hold the particle state: warp w owns TMEM
-// lanes 32 (w % 4) .. + 31 (one particle per lane) and dimensions
-// 64 (w / 4) .. + 63.  The sigmoid's exponential is the SFU's base-2
-// exponential; its reciprocal is the SFU's for five of every eight
-// observations and, for the other three, a bit-pattern seed refined by one
-// cubic and one Newton step on the FMA pipe (relative error below 1e-7), so
-// that the SFU and the issue slots share the load.  Every mbarrier wait is
-// bounded in wall time (2 s), after which *dev_err is set and the kernel runs
-// to its end without further waiting.
+// Roles (608 threads): warp 16 lane 0 issues the bulk copies; warp 17 lane 0
+// issues GEMM1 and warp 18 lane 0 GEMM2, each from fully unrolled loops, so
+// neither product waits behind the other's dependencies; warps 0-15 form the
+// residuals from TMEM (warps 0-7 the even-numbered tiles of the pass
+// sequence, 8-15 the odd ones, each group of four half of a tile's
+// observations) and update the particle state, which lives in theta_out /
+// p_out during the move.  The sigmoid's exponential is the SFU's base-2
+// exponential; one SFU reciprocal of the product (1 + 2^x0)(1 + 2^x1) serves
+// a pair of observations.
+//
+// Clusters.  A tile's observations may be split over a cluster of k CTAs
+// (k = 1, 2, 4 or 8, fixed by the tile count and the SM count, so that the
+// long trajectories of a move, which sorting by step count gathers in the
+// first tiles, spread over several SMs).  Every CTA of the cluster holds the
+// same 128 particles and accumulates the partial gradient of its share of
+// the observation tiles; each pass the partials are published in shared
+// memory, and the CTA that owns a 16-dimension slot of the state sums the k
+// partials of that slot in rank order (the same sum in every CTA), updates
+// theta and p for the slot, and writes the slot's BF16 deviations into the
+// GEMM1 operand of every CTA of the cluster through distributed shared
+// memory.  The split changes only the FP32 summation order of the gradient.
+// Every mbarrier wait is bounded in wall time (2 s), after which *dev_err is
+// set and the kernel runs to its end without further waiting.
 #include <cuda_bf16.h>
 #include <math_constants.h>
 #include "tc_ptx.cuh"
@@ -60,31 +70,33 @@ constexpr int CC = CENTRED_CHUNK;           // observations per tile
 constexpr int C_EPI_WARPS = 16;
 constexpr int C_PRODUCER_WARP = 16, C_MMA1_WARP = 17, C_MMA2_WARP = 18;
 constexpr int C_THREADS = 32 * 19;
-constexpr int C_NS = 3;                     // X tile stages
+constexpr int C_NS_MAX = 4;                 // X tile stages (4 when shared memory allows, else 3)
 constexpr int C_ATOM = CC * 128;            // one 64-dimension atom of a tile: 128 rows x 128 B
 constexpr int C_DATOM = CP * 128;           // one 64-dimension atom of the deviation operand
 constexpr uint32_t C_TMEM_COLS = 512;
 constexpr uint32_t C_COL_G = 0, C_COL_ETA = 128, C_COL_R = 384;
 constexpr int C_SMEM_MAX = 232448;
-constexpr int C_RCP_SFU_OF_8 = 8;           // observations (of every 8) whose reciprocal runs on the SFU
+constexpr float C_X_MAX = 60.0f;           // clamp of the exponent: two factors 1 + 2^x multiply without overflow
 
 struct CLayout {
-    int atoms, tile_bytes, ref_bytes, stage_bytes;
-    int off_d, off_stage, off_misc, off_bar, total;
+    int atoms, tile_bytes, ref_bytes, stage_bytes, stages;
+    int off_d, off_stage, off_gx, off_misc, off_bar, total;
 };
 
-// Byte layout of the dynamic shared memory (from a 1024-aligned base).  The
-// end-point pass reuses [0, off_misc) for theta^T, two FP32 X chunks and the
-// partial sums, so off_misc covers both uses.
-__host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
+// Byte layout of the dynamic shared memory (from a 1024-aligned base) with
+// `stages` X tile stages.  The end-point pass reuses [0, off_misc) for
+// theta^T, two FP32 X chunks and the partial sums, so off_misc covers both uses.
+__host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int stages) {
     CLayout L;
     L.atoms = (dk + 63) / 64;
     L.tile_bytes = L.atoms * C_ATOM;
     L.ref_bytes = n_ref * CC * 8;                         // (c, s) pairs per run, a multiple of 1024
     L.stage_bytes = L.tile_bytes + L.ref_bytes;
+    L.stages = stages;
     L.off_d = 0;
     L.off_stage = L.atoms * C_DATOM;
-    const int pipe = L.off_stage + C_NS * L.stage_bytes;
+    L.off_gx = L.off_stage + stages * L.stage_bytes;     // [dk][128] f32 partial gradient of this CTA
+    const int pipe = L.off_gx + dk * CP * 4;
     const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + C_EPI_WARPS * CP * 8;
     L.off_misc = ((pipe > endp ? pipe : endp) + 1023) & ~1023;
     L.off_bar = L.off_misc + 9 * CP * 8;                  // kin, sq: [4][128] f64; ll: [128] f64
@@ -94,23 +106,20 @@ __host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
     if (L.total < 118 * 1024) L.total = 118 * 1024;
     return L;
 }
+__host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
+    CLayout L = c_layout_n(dk, Dp, n_ref, C_NS_MAX);
+    for (int st = C_NS_MAX - 1; st >= 2 && L.total > C_SMEM_MAX; --st) L = c_layout_n(dk, Dp, n_ref, st);
+    return L;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// 1 / d for d >= 1 on the FMA pipe: bit-pattern seed (relative error below
-// 0.051 for every normal d), one cubic step e -> e^3, one Newton step
-// e -> e^2, relative error below 1e-7.  The argument is clamped so that d is
-// finite (1 / d is then below 2^-64, i.e. zero at the precision it feeds).
-__device__ __forceinline__ float rcp_fma(float d) {
-    d = fminf(d, 1.8446744e19f);
-    float x = __int_as_float(0x7EF311C3 - __float_as_int(d));
-    float e = fmaf(-d, x, 1.0f);
-    x = fmaf(fmaf(e, e, e), x, x);
-    e = fmaf(-d, x, 1.0f);
-    return fmaf(e, x, x);
+// Named hardware barrier of `count` threads (ids 1.. are free: 0 is __syncthreads).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 template <bool LOGIT>
@@ -122,11 +131,18 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     const int n_ref = LOGIT ? a.c_runs : 0;
     const CLayout L = c_layout(m.dk, m.Dp, n_ref);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int D = m.D, dk = m.dk, nch = m.n_tiles128;
+    const int D = m.D, dk = m.dk, nch_all = m.n_tiles128;
     const int64_t ld = a.ld;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [3] stage filled
-    uint64_t* empty = full + C_NS;                                   // [3] stage consumed by both GEMMs
-    uint64_t* eta_full = empty + C_NS;                               // [2] GEMM1 done
+    // cluster split of the observation tiles: this CTA takes [c_lo, c_hi)
+    const int kc = (int)a.c_split, rank = (int)tc::cluster_rank();
+    const int64_t tile = blockIdx.x / kc;
+    const int c_lo = (int)((int64_t)rank * nch_all / kc), c_hi = (int)((int64_t)(rank + 1) * nch_all / kc);
+    const int nch = c_hi - c_lo;
+    const int nslot = dk / 16, slot_lo = rank * nslot / kc, slot_hi = (rank + 1) * nslot / kc;
+    const int NS = L.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [NS] stage filled
+    uint64_t* empty = full + C_NS_MAX;                               // [NS] stage consumed by both GEMMs
+    uint64_t* eta_full = empty + C_NS_MAX;                           // [2] GEMM1 done
     uint64_t* eta_empty = eta_full + 2;                              // [2] eta read by the epilogue
     uint64_t* r_full = eta_empty + 2;                                // [2] d_r^T written
     uint64_t* r_empty = r_full + 2;                                  // [2] GEMM2 done with d_r^T
@@ -134,17 +150,21 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     uint64_t* th_full = g_full + 1;                                  // next pass's deviation operand written
     uint64_t* fin1 = th_full + 1;                                    // every GEMM1 issued has completed
     uint64_t* fin2 = fin1 + 1;                                       // every GEMM2 issued has completed
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(fin2 + 1);
+    uint64_t* gx_full = fin2 + 1;                                    // every CTA's partial gradient published
+    uint64_t* gx_free = gx_full + 1;                                 // every CTA done reading this CTA's partial
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(gx_free + 1);
     int* smax_s = reinterpret_cast<int*>(tmem_s + 1);
     volatile int* abort_s = smax_s + 1;
     double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [4][128] |p|^2 parts
     double* sq_s = kin_s + 4 * CP;                                   // [4][128] |theta|^2 parts
     double* ll_s = sq_s + 4 * CP;                                    // [128] log-likelihood
     const uint32_t s_base = tc::smem_u32(sm);
+    float* gx = reinterpret_cast<float*>(sm + L.off_gx);             // [dk][128] this CTA's partial gradient
+    const uint32_t gx_base = s_base + (uint32_t)L.off_gx, dev_base = s_base + (uint32_t)L.off_d;
     int* err = a.dev_err;
 
     if (tid == 0) {
-        for (int i = 0; i < C_NS; ++i) {
+        for (int i = 0; i < NS; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
@@ -155,9 +175,11 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             tc::mbar_init(&r_empty[i], 1);
         }
         tc::mbar_init(g_full, 1);
-        tc::mbar_init(th_full, C_EPI_WARPS);
+        tc::mbar_init(th_full, C_EPI_WARPS * kc);   // every epilogue warp of the cluster
         tc::mbar_init(fin1, 1);
         tc::mbar_init(fin2, 1);
+        tc::mbar_init(gx_full, C_EPI_WARPS * kc);
+        tc::mbar_init(gx_free, C_EPI_WARPS * kc);
         tc::fence_mbar_init();
         *smax_s = 0;
         *abort_s = 0;
@@ -187,7 +209,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     float ef = 0.0f;
     float th[32];
     {
-        const int64_t t = (int64_t)blockIdx.x * CP + prow;
+        const int64_t t = tile * CP + prow;
         double kin = 0.0;
         if (epi && t < a.N) {
             j = a.perm ? a.perm[t] : t;
@@ -217,12 +239,15 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             pv[0] = (float)z0;
                             pv[1] = d + 1 < D ? (float)z1 : 0.0f;
                         }
+                        const bool own = (d >> 4) >= slot_lo && (d >> 4) < slot_hi;
 #pragma unroll
                         for (int e = 0; e < 2; ++e)
                             if (d + e < D) {
                                 kin += (double)pv[e] * (double)pv[e];
-                                a.p_out[(int64_t)(d + e) * ld + j] = pv[e];
-                                a.theta_out[(int64_t)(d + e) * ld + j] = tv[e];
+                                if (own) {
+                                    a.p_out[(int64_t)(d + e) * ld + j] = pv[e];
+                                    a.theta_out[(int64_t)(d + e) * ld + j] = tv[e];
+                                }
                             }
                     }
                 }
@@ -262,6 +287,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     __syncthreads();
     tc::fence_after_sync();
     if (epi && S > 0) atomicMax(smax_s, S);
+    tc::cluster_sync();   // barriers of every CTA of the cluster initialised before any remote arrive
     double H0 = 0.0;
     if (epi && q == 0 && j >= 0 && !evalm)
         H0 = 0.5 * (kin_s[prow] + kin_s[CP + prow] + kin_s[2 * CP + prow] + kin_s[3 * CP + prow]) - a.logpi_in[src];
@@ -277,7 +303,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             const uint32_t bytes = (uint32_t)(L.tile_bytes + L.ref_bytes);
-            int st = 0, c = 0;
+            int st = 0, c = c_lo;
             uint32_t ph = 0;
             for (int64_t it = 0; it < total; ++it) {
                 tc::mbar_wait_timed(&empty[st], ph ^ 1u, err, abort_s);
@@ -287,16 +313,16 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 if (L.ref_bytes > 0)
                     tc::bulk_g2s(dst + L.tile_bytes, a.c_refs + (int64_t)c * n_ref * CC, (uint32_t)L.ref_bytes,
                                  &full[st]);
-                if (++c == nch) c = 0;
-                if (++st == C_NS) {
+                if (++c == c_hi) c = c_lo;
+                if (++st == NS) {
                     st = 0;
                     ph ^= 1u;
                 }
             }
             // every copy has landed before the stage memory is reused or the CTA exits
-            const int64_t first = total > C_NS ? total - C_NS : 0;
+            const int64_t first = total > NS ? total - NS : 0;
             for (int64_t it = first; it < total; ++it)
-                tc::mbar_wait_timed(&full[(int)(it % C_NS)], (uint32_t)((it / C_NS) & 1), err, abort_s);
+                tc::mbar_wait_timed(&full[(int)(it % NS)], (uint32_t)((it / NS) & 1), err, abort_s);
         }
     } else if (wid == C_MMA1_WARP) {
         // ------------------------------------------------------------ GEMM1: d_eta = dev . X_c^T
@@ -305,8 +331,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             int st = 0, b = 0;
             uint32_t ph = 0, bph = 0;
             for (int s = 0; s < npass; ++s) {
-                if (s >= 1) tc::mbar_wait_timed(th_full, (uint32_t)((s - 1) & 1), err, abort_s);
-                for (int c = 0; c < nch; ++c) {
+                if (s >= 1) tc::mbar_wait_cluster_timed(th_full, (uint32_t)((s - 1) & 1), err, abort_s);
+                for (int c = c_lo; c < c_hi; ++c) {
                     tc::mbar_wait_timed(&full[st], ph, err, abort_s);
                     tc::mbar_wait_timed(&eta_empty[b], bph ^ 1u, err, abort_s);
                     tc::fence_after_sync();
@@ -323,7 +349,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                         }
                     }
                     tc::mma_commit(&eta_full[b]);
-                    if (++st == C_NS) {
+                    if (++st == NS) {
                         st = 0;
                         ph ^= 1u;
                     }
@@ -342,7 +368,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             int st = 0, b = 0;
             uint32_t ph = 0, bph = 0;
             for (int s = 0; s < npass; ++s) {
-                for (int c = 0; c < nch; ++c) {
+                for (int c = c_lo; c < c_hi; ++c) {
                     tc::mbar_wait_timed(&full[st], ph, err, abort_s);
                     tc::mbar_wait_timed(&r_full[b], bph, err, abort_s);
                     tc::fence_after_sync();
@@ -352,12 +378,12 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     for (int kk = 0; kk < CC / 16; ++kk) {
                         const uint64_t bd = tc::smem_desc(xt + kk * 2048, C_ATOM, 1024, tc::SWZ_128B);
                         tc::mma_bf16_ta(tmem + C_COL_G, acol + (uint32_t)(kk * 8), bd, IDESC2,
-                                        (c > 0 || kk > 0) ? 1u : 0u);
+                                        (c > c_lo || kk > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(&r_empty[b]);
                     tc::mma_commit(&empty[st]);
-                    if (c == nch - 1) tc::mma_commit(g_full);
-                    if (++st == C_NS) {
+                    if (c == c_hi - 1) tc::mma_commit(g_full);
+                    if (++st == NS) {
                         st = 0;
                         ph ^= 1u;
                     }
@@ -379,13 +405,15 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         uint32_t sph = 0, bph = 0;
         int64_t it = 0;
         for (int s = 0; s < npass; ++s) {
-            for (int c = 0; c < nch; ++c, ++it) {
+            for (int c = c_lo; c < c_hi; ++c, ++it) {
                 if ((int)(it & 1) == bq) {
-                    if (lane == 0) {
+                    // one thread of the buffer's eight warps waits for the tile;
+                    // the others sleep on a hardware barrier instead of polling
+                    if (lane == 0 && (wid & 7) == 0) {
                         tc::mbar_wait_timed(&eta_full[bq], bph, err, abort_s);
                         tc::mbar_wait_timed(&full[st], sph, err, abort_s);
                     }
-                    __syncwarp();
+                    named_sync(1u + (uint32_t)bq, 256u);
                     tc::fence_after_sync();
                     const uint32_t ecol = tmem + lane_base + C_COL_ETA + (uint32_t)(bq * CC + 64 * half);
                     const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(bq * (CC / 2) + 32 * half);
@@ -401,7 +429,11 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&eta_empty[bq]);
                     // each pair's packed BF16 residuals overwrite the pair's first
-                    // (already consumed) slot, so v[0..15] ends up holding the row
+                    // (already consumed) slot, so v[0..15] ends up holding the row.
+                    // One SFU reciprocal serves both observations of a pair:
+                    // 1 / q0 = q1 / (q0 q1), 1 / q1 = q0 / (q0 q1), with the
+                    // exponents clamped so that q0 q1 < 2^121 (a sigmoid below
+                    // 2^-60 is then taken as 2^-60, i.e. zero here).
                     auto residuals = [&](uint32_t (&v)[32], int h) {
 #pragma unroll
                         for (int e = 0; e < 32; e += 2) {
@@ -409,14 +441,13 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             const float v0f = __uint_as_float(v[e]), v1f = __uint_as_float(v[e + 1]);
                             if (LOGIT) {
                                 const float4 cs = refs[(32 * h + e) / 2];   // (c, s) of two observations
-                                const float x0 = fmaf(kneg, v0f, cs.x);
-                                const float x1 = fmaf(kneg, v1f, cs.z);
+                                const float x0 = fminf(fmaf(kneg, v0f, cs.x), C_X_MAX);
+                                const float x1 = fminf(fmaf(kneg, v1f, cs.z), C_X_MAX);
                                 const float q0 = 1.0f + tc::ex2_approx(x0);
                                 const float q1 = 1.0f + tc::ex2_approx(x1);
-                                const float sg0 = ((e & 7) < C_RCP_SFU_OF_8) ? tc::rcp_approx(q0) : rcp_fma(q0);
-                                const float sg1 = ((e & 7) + 1 < C_RCP_SFU_OF_8) ? tc::rcp_approx(q1) : rcp_fma(q1);
-                                r0 = cs.y - sg0;
-                                r1 = cs.w - sg1;
+                                const float rp = tc::rcp_approx(q0 * q1);
+                                r0 = fmaf(-q1, rp, cs.y);
+                                r1 = fmaf(-q0, rp, cs.w);
                             } else {
                                 r0 = -inv_s2 * v0f;
                                 r1 = -inv_s2 * v1f;
@@ -438,53 +469,93 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     if (lane == 0) tc::mbar_arrive(&r_full[bq]);
                     bph ^= 1u;   // the next use of buffer bq is its next phase
                 }
-                if (++st == C_NS) {
+                if (++st == NS) {
                     st = 0;
                     sph ^= 1u;
                 }
             }
-            // the pass's gradient g_ref + G - theta / tau^2, then the leapfrog update
+            // the pass's gradient g_ref + (sum of the cluster's partial G) -
+            // theta / tau^2, then the leapfrog update of the slots this CTA owns
             tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
             tc::fence_after_sync();
-            const bool live = j >= 0 && (evalm || s <= S);
-            const bool more = s + 1 < npass;
+            // publish this CTA's partial gradient (dims ds .. ds + 31) once every
+            // CTA has read the previous pass's
+            if (s >= 1) tc::mbar_wait_cluster_timed(gx_free, (uint32_t)((s - 1) & 1), err, abort_s);
             if (ds < dk) {
                 uint32_t gv[32];
                 tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float tv[8];
-#pragma unroll
-                    for (int e8 = 0; e8 < 8; ++e8) {
-                        const int e = 8 * u + e8, d = ds + e;
-                        float tnew = 0.0f;
-                        if (live && d < D) {
-                            float tcur = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
-                            const float g = __ldg(gref + d) + __uint_as_float(gv[e]) - tcur * inv_tau2;
-                            if (evalm || s == S) a.grad_out[(int64_t)d * ld + j] = g;
-                            if (!evalm) {
-                                float* pp = a.p_out + (int64_t)d * ld + j;
-                                float pv = *pp;
-                                if (s >= 1) pv = fmaf(hf, g, pv);
-                                if (s < S) {
-                                    pv = fmaf(hf, g, pv);
-                                    tcur = fmaf(ef, pv, tcur);
-                                    a.theta_out[(int64_t)d * ld + j] = tcur;
-                                }
-                                *pp = pv;
-                            }
-                            tnew = tcur;
-                        }
-                        tv[e8] = tnew;
-                    }
-                    if (more) write_unit(u, tv);
-                }
+                for (int e = 0; e < 32; ++e) gx[(ds + e) * CP + prow] = __uint_as_float(gv[e]);
             }
-            if (more) tc::fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncwarp();
-            if (s + 1 < npass && lane == 0) tc::mbar_arrive(th_full);
+            if (lane == 0)
+                for (int r = 0; r < kc; ++r) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_full), (uint32_t)r));
+            tc::mbar_wait_cluster_timed(gx_full, (uint32_t)(s & 1), err, abort_s);
+            const bool live = j >= 0 && (evalm || s <= S);
+            const bool more = s + 1 < npass;
+#pragma unroll
+            for (int hs = 0; hs < 2; ++hs) {
+                const int slot = 2 * q + hs;
+                if (slot >= nslot || slot < slot_lo || slot >= slot_hi) continue;
+                float tv[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int d = 16 * slot + e;
+                    // the cluster's partials of this dimension, summed in rank order
+                    const uint32_t ga = gx_base + (uint32_t)((d * CP + prow) * 4);
+                    float gsum = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
+                    for (int r = 1; r < kc; ++r) gsum += tc::ld_cluster_f32(tc::map_to_rank(ga, (uint32_t)r));
+                    float tnew = 0.0f;
+                    if (live && d < D) {
+                        float tcur = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
+                        const float g = __ldg(gref + d) + gsum - tcur * inv_tau2;
+                        if (evalm || s == S) a.grad_out[(int64_t)d * ld + j] = g;
+                        if (!evalm) {
+                            float* pp = a.p_out + (int64_t)d * ld + j;
+                            float pv = *pp;
+                            if (s >= 1) pv = fmaf(hf, g, pv);
+                            if (s < S) {
+                                pv = fmaf(hf, g, pv);
+                                tcur = fmaf(ef, pv, tcur);
+                                a.theta_out[(int64_t)d * ld + j] = tcur;
+                            }
+                            *pp = pv;
+                        }
+                        tnew = tcur;
+                    }
+                    tv[e] = tnew;
+                }
+                if (more) {
+                    // the slot's two 16-byte units of the deviation row, into the
+                    // GEMM1 operand of every CTA of the cluster
+                    const uint32_t row = dev_base + (uint32_t)((slot >> 2) * C_DATOM + prow * 128);
+#pragma unroll
+                    for (int u2 = 0; u2 < 2; ++u2) {
+                        float v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int d = 16 * slot + 8 * u2 + e;
+                            v[e] = (j >= 0 && d < D) ? tv[8 * u2 + e] - __ldg(cref + d) : 0.0f;
+                        }
+                        const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                                   pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+                        const int unit = 2 * (slot & 3) + u2;
+                        const uint32_t ua = row + (uint32_t)((unit ^ (prow & 7)) << 4);
+                        for (int r = 0; r < kc; ++r) tc::st_cluster_u4(tc::map_to_rank(ua, (uint32_t)r), w);
+                    }
+                }
+            }
+            // the deviations reach the other CTAs' tensor cores, and this CTA
+            // is done with the cluster's partials
+            tc::fence_proxy_async_cluster();
+            __syncwarp();
+            if (lane == 0)
+                for (int r = 0; r < kc; ++r) {
+                    if (more) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(th_full), (uint32_t)r));
+                    tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_free), (uint32_t)r));
+                }
         }
     }
 
@@ -499,7 +570,10 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         tc::mbar_wait_timed(fin2, 0u, err, &ignore_abort, 4000000000ull);
     }
     __syncthreads();
-    const int Dp = m.Dp, n = m.n, nch64 = m.n_chunks;
+    tc::cluster_sync();   // every CTA of the cluster has written its slots of the final state
+    const int Dp = m.Dp, n = m.n;
+    // this CTA's share of the 64-observation chunks of the end point
+    const int e_lo = (int)((int64_t)rank * m.n_chunks / kc), e_hi = (int)((int64_t)(rank + 1) * m.n_chunks / kc);
     float* thT = reinterpret_cast<float*>(sm);                  // [dk][128]
     float* xs = thT + dk * CP;                                  // [2][64][Dp]
     double* llp = reinterpret_cast<double*>(xs + 2 * STREAM_CHUNK * Dp);   // [16][128]
@@ -532,17 +606,17 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         for (int v = tid; v < nvec; v += C_THREADS) tc::cp_async16(dst + 4 * v, srcx + 4 * v);
         tc::cp_async_commit();
     };
-    issue_x(0, 0);
+    if (e_lo < e_hi) issue_x(e_lo, 0);
     {
         const int pg = lane, og = wid;     // warps 0-15 compute 4 observations each, 16-18 only copy
         double ll[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int c = 0; c < nch64; ++c) {
-            if (c + 1 < nch64) issue_x(c + 1, (c + 1) & 1);
+        for (int c = e_lo; c < e_hi; ++c) {
+            if (c + 1 < e_hi) issue_x(c + 1, (c + 1 - e_lo) & 1);
             else tc::cp_async_commit();
             tc::cp_async_wait<1>();
             __syncthreads();
             if (og < C_EPI_WARPS) {
-                const float* xc = xs + (c & 1) * STREAM_CHUNK * Dp + og * 4 * Dp;
+                const float* xc = xs + ((c - e_lo) & 1) * STREAM_CHUNK * Dp + og * 4 * Dp;
                 float acc[4][4];
 #pragma unroll
                 for (int o = 0; o < 4; ++o)
@@ -605,9 +679,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         }
     }
     __syncthreads();
-    if (epi && q == 0 && j >= 0) {
+    tc::cluster_sync();   // every CTA's log-likelihood part is in its shared memory
+    if (rank == 0 && epi && q == 0 && j >= 0) {
+        // the cluster's parts, summed in rank order
+        const uint32_t la = tc::smem_u32(ll_s + prow);
+        double llsum = tc::ld_cluster_f64(tc::map_to_rank(la, 0u));
+        for (int r = 1; r < kc; ++r) llsum += tc::ld_cluster_f64(tc::map_to_rank(la, (uint32_t)r));
         const double sq = sq_s[prow] + sq_s[CP + prow] + sq_s[2 * CP + prow] + sq_s[3 * CP + prow];
-        const double lp1 = ll_s[prow] - 0.5 * sq * inv_tau2_d + m.lconst;
+        const double lp1 = llsum - 0.5 * sq * inv_tau2_d + m.lconst;
         a.logpi_out[j] = lp1;
         if (!evalm) {
             const double kin = kin_s[prow] + kin_s[CP + prow] + kin_s[2 * CP + prow] + kin_s[3 * CP + prow];
@@ -618,7 +697,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         }
     }
     tc::fence_before_sync();
-    __syncthreads();
+    tc::cluster_sync();   // no CTA leaves while another may still read its shared memory
     tc::fence_after_sync();
     if (wid == 0) tc::tmem_dealloc(tmem, C_TMEM_COLS);
 }
@@ -708,6 +787,24 @@ __global__ void __launch_bounds__(128) k_centre_grad(TrajArgs a, int dk, int nch
     a.c_gref[(int64_t)r * dk + d] = (float)g;
 }
 
+// CTAs per particle tile: the largest k in {1, 2, 4, 8} with at most two CTAs
+// per SM over the launch and at least one observation tile per CTA.  It
+// depends only on the particle count, the data and the device, so a result
+// never depends on a timing.
+int centred_split(const DevModel& m, int64_t N) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    const int64_t tiles = (N + CP - 1) / CP;
+    int k = 8;
+    while (k > 1 && (tiles * k > 2 * (int64_t)sms || k > m.n_tiles128)) k >>= 1;
+    return k;
+}
+
 template <bool LOGIT>
 cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     const int R = a.c_runs;
@@ -720,11 +817,26 @@ cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s)
     k_centre_grad<<<(unsigned)R, 128, 0, s>>>(a, m.dk, m.n_tiles128);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int tiles = (int)((a.N + CP - 1) / CP);
+    const int64_t tiles = (a.N + CP - 1) / CP;
+    TrajArgs a2 = a;
+    a2.c_split = centred_split(m, a.N);
     auto kern = traj_centred_kernel<LOGIT>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)tiles, C_THREADS, (size_t)L.total, s>>>(m, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(tiles * a2.c_split), 1, 1);
+    cfg.blockDim = dim3(C_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)L.total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a2.c_split;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, m, a2);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
