@@ -1,29 +1,39 @@
 """Benchmark of the SMC-ChEES hot path on GB300 (one JSON line on rank 0).
 
-Workload (default): Bayesian logistic regression, n=1000 observations, D=25
-(intercept + 24 N(0,1) features), N=4096 particles, K=50 SMC iterations,
-1-d Halton jitter, eps=1e-3, L0=5, at most 500 leapfrog steps.  One "step"
-is one complete sampler run (initial draw + K iterations: every stage of the
-path), restarted on the device with a new seed (smc_reset) each step.
+Main line (default): Bayesian logistic regression, n = 1e5 observations,
+D = 100 (N(0,1) features with pairwise correlation 0.3), N = 16384 particles,
+K = 30 SMC iterations (M_warmup = 15), ChEES-HMC with eps = 1e-3, L0 = 5, at
+most 500 leapfrog steps, 1-d Halton jitter, in the chosen form: the centred
+tensor-core trajectory kernel (one BF16 product per GEMM on the deviations
+from each move's reference point, FP32 accumulation, exact end-point
+energies).  A "step" is one SMC iteration (the loop body of Algorithm 3:
+weights, resampling, jitter and step counts, ordering, momentum, the
+trajectories, reweighting, evidence, ChEES adaptation); consecutive steps
+continue the same run and a finished run is restarted (new seed, initial
+draw) outside the timed region.
 
-value      = real particle-gradient evaluations (sum of leapfrog steps over
-             particles and iterations, all ranks) / device time of the timed
-             steps (CUDA events on the library's stream, L2 flushed between
-             steps outside the events, max over ranks).
-e2e        = the same metric through the public C-ABI from host memory:
-             smc_init (host model data copied in) -> smc_run -> particles,
-             log-weights and evidence copied back -> smc_destroy.
-roofline   = the trajectory kernel (dominant): algorithmic FLOPs per launch
-             (4 n D per particle-gradient + 2 n D per particle for the endpoint
-             energy) / its mean event-timed duration.
-cpu_baseline / --impl reference = the FP64 C oracle on the host cores.
-large_logistic = the n=1e5, D=100, 16384-particle regression on the streamed
-             tensor-core kernel (BF16x2), with its roofline.
-preconditioner = the learned transport map against the plain identity-metric
-             sampler on the 8192-particle 100-d Gaussian (condition number
-             1e4) and 50-d banana targets: ESS/s, grad-evals/s, acceptance,
-             moment accuracy against the closed forms, and the achieved
-             FLOP rate of the latent-space trajectory kernel.
+value      = real particle-gradient evaluations (sum of the leapfrog steps
+             S_j of every particle) / device time of the timed iterations
+             (CUDA events on the library's stream, L2 flushed before every
+             iteration outside the events, max over ranks).
+roofline   = the trajectory stage (the reference kernels and the trajectory
+             kernel): algorithmic FLOPs 4 n D per particle-gradient plus
+             2 n D per particle for the end-point energy, over its
+             event-timed duration in one full profiled run, against the
+             measured sustained BF16 tensor peak.
+e2e        = the same metric through the public C-ABI from host memory for
+             one full run: smc_init (host model data copied in) -> smc_run ->
+             particles, log-weights and evidence copied back -> smc_destroy.
+cpu_baseline / --impl reference = the FP64 C oracle on the host cores, one
+             SMC iteration of the same workload with a bounded particle
+             sample per step (the full workload would take hours).
+sides      = the other configurations, each with chosen and plain forms and
+             its accuracy check: c1 (10-d Gaussian, latency and closed-form
+             evidence over 10 seeds), c2 (n = 1000 logistic regression: 10
+             seeds batched in one centred handle against 10 plain FP32 runs,
+             log-Z and posterior-mean agreement with a long plain run), c4
+             (64 batched hierarchical runs, evidence against quadrature), c5
+             (learned transport map against the plain sampler, closed forms).
 
 N > 1 (torchrun): independent replicas, one per GPU, different seeds
 ("replicas only": the method's particle sets do not exchange data).
@@ -39,7 +49,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -50,6 +59,18 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+METRIC = "particle-grad-evals/s & ESS/s at fixed log-Z error, chosen vs plain FP32 on 1 GB300"
+PREC_NAMES = ["fp32", "bf16x3", "bf16", "bf16x2", "bf16 centred"]
+WORKLOAD_DESC = {
+    "logistic_large": "Bayesian logistic regression, synthetic, n=100000, D=100 (N(0,1) features with pairwise "
+                      "correlation 0.3), N=16384 particles, K=30 SMC iterations (M_warmup 15), eps=1e-3 L0=5 max "
+                      "500 steps, 1-d Halton jitter",
+    "logistic": "Bayesian logistic regression, synthetic, n=1000, D=25 (intercept + 24 N(0,1) features), "
+                "N=4096 particles, K=50 SMC iterations, ChEES-HMC eps=1e-3 L0=5 max 500 steps, 1-d Halton",
+    "gauss10": "10-d correlated Gaussian, N=256, K=20",
+    "hier": "batched hierarchical normal (non-centred, 50 groups x 20 obs, D=52), 64 independent runs with "
+            "particle counts uniform on 512..8192 (seeded, 278k particles) in every launch, K=50, eps=0.01, L0=1, FP32",
+}
 
 
 def _peaks():
@@ -61,15 +82,31 @@ def _peaks():
 
 
 def _workload(name):
-    if name == "logistic":
-        return workloads.logistic()
-    if name == "gauss10":
-        return workloads.gauss10()
-    if name == "hier":
-        return workloads.hier()
-    if name == "logistic_large":
-        return workloads.logistic_large()
-    raise ValueError(name)
+    return {"logistic": workloads.logistic, "gauss10": workloads.gauss10, "hier": workloads.hier,
+            "logistic_large": workloads.logistic_large}[name]()
+
+
+def chosen_precision(w):
+    """The chosen form of each model: the centred tensor-core kernel for the
+    regression models, BF16x3 warp MMAs for a dense Gaussian above 32
+    dimensions, FP32 otherwise (no tensor-core kernel)."""
+    if w["kind"] in ("logistic", "linear_gauss") and w["D"] <= 128:
+        return 4
+    if w["kind"] == "gauss_dense" and w["D"] > 32:
+        return 1
+    return 0
+
+
+def _flops_per_grad(w):
+    if w["kind"] in ("logistic", "linear_gauss"):
+        return 4.0 * w["n"] * w["D"], 2.0 * w["n"] * w["D"]
+    if w["kind"] == "gauss_dense":
+        return 2.0 * w["D"] ** 2, 2.0 * w["D"] ** 2
+    if w["kind"] == "hier_normal":
+        # per group: b = mu + tau eta (2), ybar - b (1), n (.)/s^2 (2), sum (1),
+        # tau eta r into d/dlog tau (3), r tau - eta (2)
+        return 11.0 * w["n"] + 4.0, 14.0 * w["n"]
+    return 0.0, 0.0
 
 
 def aggregate_ranks(torch, dist, dev_ms, grad_evals, ess, device):
@@ -83,67 +120,6 @@ def aggregate_ranks(torch, dist, dev_ms, grad_evals, ess, device):
     dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(tmax[0]), float(t[1]), float(t[2])
-
-
-def _timed_runs(torch, smp, K, seeds, flush, moments=None):
-    """One full sampler run per seed, each bracketed by CUDA events on the
-    sampler's stream after an L2 flush; returns (device ms, gradient
-    evaluations, post-warm-up ESS sum, log Z per run).  With a list in
-    `moments`, the weighted posterior mean and variance of every run are
-    appended to it (read back after the events)."""
-    ms, ge, ess, lz = 0.0, 0, 0.0, []
-    for sd in seeds:
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        smp.reset(sd)
-        smp.run(K)                              # smc_run replays CUDA graphs
-        e1.record()
-        summ = smp.summary()                    # synchronises after the step; outside the events
-        ms += e0.elapsed_time(e1)
-        ge += sum(x["grad_evals"] for x in summ)
-        ess += sum(x["ess_sum_post_warmup"] for x in summ)
-        lz.append(summ[0]["log_z"])
-        if moments is not None:
-            moments.append(smp.moments())
-    torch.cuda.synchronize()
-    return ms, ge, ess, lz
-
-
-def _profiled_run(smp, K, seed, flush):
-    """Trajectory-kernel time and launch count: one more run with in-library
-    events around every trajectory launch (no graphs), outside the timed region."""
-    smp.profile(True)
-    flush.zero_()
-    smp.reset(seed)
-    smp.run(K)
-    ge = sum(x["grad_evals"] for x in smp.summary())
-    prof = smp.get_profile()
-    smp.profile(False)
-    return prof, ge
-
-
-def _mma_flops_per_grad(w, prec):
-    """MMA FLOPs the warp-level tensor-core kernel issues per gradient (two
-    products over the padded dimension 32 and observations padded to 16, three
-    BF16 products each in the compensated form) and per end point (none: the
-    end point is FP32)."""
-    if w["kind"] not in ("logistic", "linear_gauss") or w["D"] > 32 or prec not in (1, 2):
-        return None
-    n16 = -(-w["n"] // 16) * 16
-    return 2 * 2.0 * 32 * n16 * (3 if prec == 1 else 1), 0.0
-
-
-def _flops_per_grad(w):
-    if w["kind"] in ("logistic", "linear_gauss"):
-        return 4.0 * w["n"] * w["D"], 2.0 * w["n"] * w["D"]
-    if w["kind"] == "gauss_dense":
-        return 2.0 * w["D"] ** 2, 2.0 * w["D"] ** 2
-    if w["kind"] == "hier_normal":
-        # per group: b = mu + tau eta (2), ybar - b (1), n (.)/s^2 (2), sum (1),
-        # tau eta r into d/dlog tau (3), r tau - eta (2)
-        return 11.0 * w["n"] + 4.0, 14.0 * w["n"]
-    return 0.0, 0.0
 
 
 class ClockSampler:
@@ -196,7 +172,7 @@ class ClockSampler:
 def _traffic_for(kernel_file, workload):
     """Per-launch DRAM bytes of the trajectory kernel from a committed ncu
     summary, if it was taken on the current source of that kernel and for
-    this bench workload (one file holds the kernels of several models)."""
+    this bench workload."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -210,41 +186,363 @@ def _traffic_for(kernel_file, workload):
     return None
 
 
-def cpu_oracle_rate(w, run, seconds_target=20.0, iters=2):
-    """The FP64 oracle on the host cores: the first `iters` SMC iterations of
-    the same workload (all particles, full data); returns grad-evals/s."""
+def _kernel_file(w, prec):
+    if prec == 4:
+        return "traj_centred.cu"
+    if prec == 3:
+        return "traj_tc_stream.cu"
+    if prec in (1, 2):
+        if w["kind"] == "gauss_dense":
+            return "traj_gauss_mma.cu"
+        return "traj_glm_mma.cu" if w["D"] <= 32 else "traj_tc.cu"
+    return "traj_thread.cu" if w["kind"] in ("hier_normal", "banana") or w["D"] <= 32 else "traj_simt.cu"
+
+
+def _oracle_target(w):
     import oracle
     if w["kind"] == "logistic":
-        t = oracle.TargetSpec.logistic(w["X"], w["y"], w.get("tau", 1.0))
-    elif w["kind"] == "gauss_dense":
-        t = oracle.TargetSpec.gauss_dense(w["mu"], w["P"])
-    else:
-        t = oracle.TargetSpec.hier_normal(w["ybar"], w["n_g"], w["ss"], w["sigma"])
+        return oracle.TargetSpec.logistic(w["X"], w["y"], w.get("tau", 1.0))
+    if w["kind"] == "gauss_dense":
+        return oracle.TargetSpec.gauss_dense(w["mu"], w["P"])
+    return oracle.TargetSpec.hier_normal(w["ybar"], w["n_g"], w["ss"], w["sigma"])
+
+
+def _oracle_sample_particles(w):
+    """Particles of the bounded oracle sample: all of a small workload, 16 of
+    the 1e5-observation one (one SMC iteration of all 16384 would take hours
+    in FP64 on the host)."""
+    return 16 if w["kind"] == "logistic" and w["n"] > 10_000 else w["run"]["n_particles"]
+
+
+def oracle_iteration_rate(w, seconds_target=20.0, seed=999, first_k=1):
+    """The FP64 oracle on the host cores: SMC iterations of the workload with
+    the bounded particle sample, until about `seconds_target` of wall time;
+    returns (grad-evals/s, cores, wall s, iterations, particles)."""
+    import oracle
+    t = _oracle_target(w)
     cores = os.cpu_count() or 1
-    cfg = oracle.SMCConfig(seed=999, **dict(run))
-    t0 = time.perf_counter()
+    Ns = _oracle_sample_particles(w)
+    cfg = oracle.SMCConfig(seed=seed, **dict(w["run"], n_particles=Ns))
     st = oracle.smc_init(t, cfg, nthreads=cores)
     st["chees"] = oracle.initial_chees_state(cfg)
+    k = 1
+    while k < first_k:
+        oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        k += 1
+    t0 = time.perf_counter()
     ge, done = 0, 0
-    for k in range(1, iters + 1):
+    while k <= cfg.n_iters:
         out = oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
         ge += out["stats"]["grad_evals"]
         done += 1
+        k += 1
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
-    return ge / dt, cores, dt, done
+    return ge / dt, cores, dt, done, Ns
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, on the host cores: per
+    step one SMC iteration of the workload with the bounded particle sample
+    (all particles of the small workloads)."""
+    import oracle
+    if rank != 0:
+        return None
+    w = _workload(args.workload)
+    t = _oracle_target(w)
+    cores = os.cpu_count() or 1
+    Ns = _oracle_sample_particles(w)
+    cfg = oracle.SMCConfig(seed=2024, **dict(w["run"], n_particles=Ns))
+
+    def fresh():
+        st = oracle.smc_init(t, cfg, nthreads=cores)
+        st["chees"] = oracle.initial_chees_state(cfg)
+        return st
+
+    st, k = fresh(), 1
+    for _ in range(args.warmup):
+        if k > cfg.n_iters:
+            st, k = fresh(), 1
+        oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        k += 1
+    dt, ge, ess = 0.0, 0, 0.0
+    for _ in range(args.steps):
+        if k > cfg.n_iters:
+            st, k = fresh(), 1
+        t0 = time.perf_counter()
+        out = oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
+        dt += time.perf_counter() - t0
+        ge += out["stats"]["grad_evals"]
+        ess += out["stats"]["ess"]
+        k += 1
+    val = ge / dt
+    sample = (f"{args.steps} SMC iterations after {args.warmup} untimed, N={Ns} particles "
+              f"(of {w['run']['n_particles']}) on the full data, FP64 C oracle, OpenMP over particles")
+    return {"metric": METRIC, "value": val, "unit": "particle-grad-evals/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "step": "one SMC iteration"},
+            "cpu_baseline": {"value": val, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "particle-grad-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "ess_per_s": ess / dt}
+
+
+# ------------------------------------------------------------------ timing helpers
+def timed_iterations(torch, smp, K_run, n_steps, seeds, flush, stats_out=None):
+    """`n_steps` SMC iterations, each bracketed by CUDA events on the current
+    stream after an L2 flush; a run that has done its K_run iterations is
+    restarted with the next seed outside the events.  Returns (device ms,
+    gradient evaluations, J_eff sum) of the timed iterations."""
+    ms, ge, ess = 0.0, 0, 0.0
+    seeds = iter(seeds)
+    for _ in range(n_steps):
+        s0 = smp.summary()
+        if s0[0]["iterations"] >= K_run:
+            smp.reset(next(seeds))
+            s0 = smp.summary()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        smp.step(with_stats=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        s1 = smp.summary()
+        ge += sum(b["grad_evals"] - a["grad_evals"] for a, b in zip(s0, s1))
+        ess += sum(b["ess_sum"] - a["ess_sum"] for a, b in zip(s0, s1))
+    return ms, ge, ess
+
+
+def full_run(torch, smp, K, seed, flush, profile=False):
+    """One complete run (initial draw by smc_reset, K iterations) between two
+    events after an L2 flush; with `profile`, trajectory launches are timed
+    by events inside the library."""
+    if profile:
+        smp.profile(True)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    smp.reset(seed)
+    smp.run(K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = None
+    if profile:
+        prof = smp.get_profile()
+        smp.profile(False)
+    return ms, smp.summary(), prof
+
+
+def _mcse(x):
+    x = np.asarray(x, dtype=np.float64)
+    return float(np.std(x, ddof=1) / np.sqrt(len(x))) if len(x) > 1 else None
+
+
+# ------------------------------------------------------------------ closed forms
+def _gauss_truth(w):
+    """log Z, mean and marginal variances of exp(-1/2 (t - mu)' P (t - mu) + c)."""
+    D = w["D"]
+    P = np.asarray(w["P"], np.float32).astype(np.float64)
+    _, ld = np.linalg.slogdet(P)
+    return 0.5 * D * np.log(2 * np.pi) - 0.5 * ld + w.get("c", 0.0), np.asarray(w["mu"], np.float64), \
+        np.diag(np.linalg.inv(P))
 
 
 def _c5_truth(w):
     """Closed-form log Z, mean and marginal variances of the C5 targets."""
     D = w["D"]
     if w["kind"] == "gauss_dense":
-        P = np.asarray(w["P"], np.float32).astype(np.float64)
-        _, ld = np.linalg.slogdet(P)
-        return 0.5 * D * np.log(2 * np.pi) - 0.5 * ld, np.zeros(D), np.diag(np.linalg.inv(P))
+        return _gauss_truth(w)
     a, b = w["a"], w["b"]
     return 0.0, np.zeros(D), np.tile([a, 1.0 + 2.0 * b * b * a * a], D // 2)
+
+
+def _hier_log_z(w):
+    """Evidence of the non-centred hierarchical normal: each group's eta
+    integrates to sqrt(2 pi s^2 / n) N(ybar_g; mu, s^2 / n + tau^2) times the
+    within-group term, mu integrates against N(0, 1) in closed form
+    (N(ybar; 0, v I + 1 1')), and log tau by trapezoidal quadrature on a fine
+    grid (all groups share n)."""
+    ybar = np.asarray(w["ybar"], np.float32).astype(np.float64)
+    n_g = np.asarray(w["n_g"], np.float64)
+    ss = np.asarray(w["ss"], np.float32).astype(np.float64)
+    s2 = w["sigma"] ** 2
+    G = len(ybar)
+    n = n_g[0]
+    assert np.all(n_g == n)
+    const = np.sum(-0.5 * n_g * np.log(2 * np.pi * s2) - ss / (2 * s2) + 0.5 * np.log(2 * np.pi * s2 / n_g))
+    ell = np.linspace(-12.0, 12.0, 48001)
+    v = s2 / n + np.exp(2 * ell)
+    # N(ybar; 0, v I + 1 1'): det = v^(G-1) (v + G); quadratic form (|y|^2 - (sum y)^2 / (v + G)) / v
+    yy, sy = float(ybar @ ybar), float(ybar.sum())
+    logdet = (G - 1) * np.log(v) + np.log(v + G)
+    quad = (yy - sy * sy / (v + G)) / v
+    lg = -0.5 * (G * np.log(2 * np.pi) + logdet + quad) - 0.5 * ell * ell - 0.5 * np.log(2 * np.pi)
+    m = lg.max()
+    h = ell[1] - ell[0]
+    wts = np.full(len(ell), h)
+    wts[0] = wts[-1] = 0.5 * h
+    return float(const + m + np.log(np.sum(wts * np.exp(lg - m))))
+
+
+# ------------------------------------------------------------------ side lines
+def side_c1(g, torch, stream, flush, R=10):
+    """10-d Gaussian (N = 256, K = 20): the latency of one SMC iteration of
+    one run (graph replay, no other work on the GPU), and the accuracy of the
+    evidence and posterior moments over R seeds (one batched handle of R
+    runs; batched runs equal single runs bit for bit) against the closed
+    forms."""
+    w = workloads.gauss10()
+    run = dict(w["run"])
+    K = run["n_iters"]
+    md = g.ModelData.from_workload(w)
+    smp = g.Sampler(md, g.make_config(seed=31, **run), stream)
+    smp.run(K)
+    ms, _, _ = full_run(torch, smp, K, 32, flush)
+    ms2, _, _ = full_run(torch, smp, K, 33, flush)
+    smp.close()
+    lz_t, m_t, v_t = _gauss_truth(w)
+    bat = g.Sampler(md, [g.make_config(seed=100 + r, **run) for r in range(R)], stream)
+    bat.run(K)
+    lz = bat.log_evidence()
+    th, lw = bat.particles()
+    bat.close()
+    N = run["n_particles"]
+    errs = []
+    for r in range(R):
+        x, l = th[:, r * N:(r + 1) * N].T.astype(np.float64), lw[r * N:(r + 1) * N]
+        W = np.exp(l - l.max())
+        W /= W.sum()
+        m = W @ x
+        errs.append((m - m_t) / np.sqrt(v_t))
+    errs = np.asarray(errs)
+    mc = _mcse(lz)
+    return {"workload": "10-d correlated Gaussian N(0, Sigma), q_init = N(0, 4I), N=256, K=20, FP32 thread kernel",
+            "us_per_iteration": 1e3 * min(ms, ms2) / K,
+            "log_z": {"mean": float(np.mean(lz)), "mcse": mc, "closed_form": lz_t,
+                      "err_in_mcse": abs(float(np.mean(lz)) - lz_t) / mc if mc else None, "seeds": R},
+            "posterior_mean": {"max_abs_err_sd_units_mean_over_seeds": float(np.mean(np.abs(errs).max(axis=1))),
+                               "mean_err_over_seeds_in_mcse": float(np.max(np.abs(errs.mean(0)) /
+                                                                            (errs.std(0, ddof=1) / np.sqrt(R))))}}
+
+
+def side_c2(g, torch, stream, flush, R=10):
+    """n = 1000 logistic regression (N = 4096, K = 50): chosen = R seeds in
+    one batched handle of the centred tensor-core kernel (40960 particles in
+    every launch); plain = the same R seeds as R single FP32 runs, one launch
+    sequence per run.  Throughput and ESS/s of both, and the log-Z and
+    posterior-mean agreement of both with a long plain run (8 x N particles,
+    the reference the model has no closed form for)."""
+    w = workloads.logistic()
+    run = dict(w["run"])
+    K = run["n_iters"]
+    md = g.ModelData.from_workload(w)
+    seeds = [2000 + r for r in range(R)]
+    # chosen: one batched handle
+    bat = g.Sampler(md, [g.make_config(seed=s, precision=4, **run) for s in seeds], stream)
+    bat.run(K)
+    bat.reset(1)
+    c_ms, c_sum, c_prof = full_run(torch, bat, K, 1, flush, profile=True)
+    c_lz = [x["log_z"] for x in c_sum]
+    c_ge = sum(x["grad_evals"] for x in c_sum)
+    c_ess = sum(x["ess_sum_post_warmup"] for x in c_sum)
+    th_b, lw_b = bat.particles()
+    bat.close()
+    # full_run resets with one seed for every run of the batch; re-run with the per-run seeds for the
+    # accuracy statistics (the timing above is unaffected by the seed values)
+    bat = g.Sampler(md, [g.make_config(seed=s, precision=4, **run) for s in seeds], stream)
+    bat.run(K)
+    c_lz = list(bat.log_evidence())
+    th_b, lw_b = bat.particles()
+    bat.close()
+    # plain: R single FP32 runs
+    p_ms, p_ge, p_ess, p_lz, p_mean = 0.0, 0, 0.0, [], []
+    sp = g.Sampler(md, g.make_config(seed=seeds[0], precision=0, **run), stream)
+    sp.run(2)
+    for s in seeds:
+        ms, summ, _ = full_run(torch, sp, K, s, flush)
+        p_ms += ms
+        p_ge += summ[0]["grad_evals"]
+        p_ess += summ[0]["ess_sum_post_warmup"]
+        p_lz.append(summ[0]["log_z"])
+        p_mean.append(sp.moments()[0])
+    sp.close()
+    # reference: one long plain run
+    ref = g.Sampler(md, g.make_config(seed=99, precision=0, **dict(run, n_particles=8 * run["n_particles"])), stream)
+    ref.run(K)
+    ref_lz = float(ref.log_evidence()[0])
+    ref_m, ref_v = ref.moments()
+    ref.close()
+    N = run["n_particles"]
+    c_mean = []
+    for r in range(R):
+        x, l = th_b[:, r * N:(r + 1) * N].T.astype(np.float64), lw_b[r * N:(r + 1) * N]
+        W = np.exp(l - l.max())
+        W /= W.sum()
+        c_mean.append(W @ x)
+    sd = np.sqrt(ref_v)
+
+    def acc(lz, means):
+        mc = _mcse(lz)
+        e = (np.asarray(means) - ref_m) / sd
+        return {"log_z_mean": float(np.mean(lz)), "log_z_mcse": mc,
+                "log_z_err_vs_reference_in_mcse": abs(float(np.mean(lz)) - ref_lz) / mc if mc else None,
+                "posterior_mean_err_sd_units": float(np.mean(np.abs(e).max(axis=1)))}
+
+    fl_grad, fl_end = _flops_per_grad(w)
+    ach = (fl_grad * c_ge + fl_end * R * N * K) / (c_prof["traj_ms"] / 1e3) / 1e12
+    pk = _peaks()[0].get("bf16_tflops_sustained", 1700.0)
+    chosen = {"value": c_ge / (c_ms / 1e3), "ess_per_s": c_ess / (c_ms / 1e3), "ms_per_run_of_batch": c_ms,
+              "roofline": {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                           "kernel": "centred tcgen05 trajectory kernel (10 runs per launch)"},
+              **acc(c_lz, c_mean)}
+    plain = {"value": p_ge / (p_ms / 1e3), "ess_per_s": p_ess / (p_ms / 1e3), "ms_per_run": p_ms / R,
+             **acc(p_lz, p_mean)}
+    return {"workload": WORKLOAD_DESC["logistic"], "seeds": R,
+            "chosen": dict(chosen, form="centred BF16 tensor cores, 10 runs batched in one handle"),
+            "plain": dict(plain, form="FP32 SIMT, one run per launch sequence"),
+            "reference": {"log_z": ref_lz, "particles": 8 * N, "form": "plain FP32, one run"},
+            "chosen_vs_plain": {"throughput": chosen["value"] / plain["value"],
+                                "ess_per_s": chosen["ess_per_s"] / plain["ess_per_s"]},
+            "unit": "particle-grad-evals/s"}
+
+
+def side_c4(g, torch, stream, flush):
+    """Batched hierarchical normal: 64 runs of uneven particle counts in
+    every launch (FP32 thread kernel, the autotuned launch plan); throughput
+    and the evidence of the 64 runs against quadrature."""
+    w = workloads.hier()
+    run = dict(w["run"])
+    K = run["n_iters"]
+    md = g.ModelData.from_workload(w)
+    cfgs = [g.make_config(seed=5000 + r, **dict(run, n_particles=int(nr))) for r, nr in enumerate(w["run_sizes"])]
+    smp = g.Sampler(md, cfgs, stream)
+    smp.run(2)
+    ms, summ, prof = full_run(torch, smp, K, 5000, flush, profile=True)
+    ge = sum(x["grad_evals"] for x in summ)
+    ess = sum(x["ess_sum_post_warmup"] for x in summ)
+    plan = smp.plan()
+    smp.close()
+    smp = g.Sampler(md, cfgs, stream)
+    smp.run(K)
+    lz = smp.log_evidence()
+    smp.close()
+    truth = _hier_log_z(w)
+    fl_grad, fl_end = _flops_per_grad(w)
+    ach = (fl_grad * ge + fl_end * sum(int(x) for x in w["run_sizes"]) * K) / (prof["traj_ms"] / 1e3) / 1e12
+    mc = _mcse(lz)
+    return {"workload": WORKLOAD_DESC["hier"], "value": ge / (ms / 1e3), "unit": "particle-grad-evals/s",
+            "ess_per_s": ess / (ms / 1e3), "ms_per_run_of_batch": ms, "autotune": plan,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP32_FMA_PEAK_TFLOPS, "kernel": "FP32 thread-per-particle trajectory kernel",
+                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"},
+            "log_z": {"mean": float(np.mean(lz)), "mcse": mc, "quadrature": truth, "runs": len(lz),
+                      "err_in_mcse": abs(float(np.mean(lz)) - truth) / mc if mc else None}}
 
 
 def _flow_flops_per_grad(w, H, L):
@@ -256,12 +554,12 @@ def _flow_flops_per_grad(w, H, L):
     return L * 4.0 * (Dh * H + H * H + H * D) + tgt
 
 
-def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
+def side_c5(g, torch, stream, flush, K=50, M=25, H=128, L=4):
     """The learned preconditioner against the plain identity-metric sampler
-    on the two 8192-particle targets of the preconditioner workload: one
-    complete run each (K iterations, training during warm-up), device-timed,
-    L2 flushed before each; ESS/s, grad-evals/s, acceptance and the accuracy
-    of the posterior moments against the closed forms."""
+    on the two 8192-particle targets: one complete run each (K iterations,
+    training during warm-up), device-timed, L2 flushed before each; ESS/s,
+    grad-evals/s, acceptance and the accuracy of the posterior moments and
+    evidence against the closed forms."""
     out = {}
     for name, w, eps in (("gauss100_cond1e4", workloads.gauss100_cond(), 0.01),
                          ("banana50", workloads.banana50(), 0.05)):
@@ -277,7 +575,7 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
             if arm.startswith("flow"):
                 smp.enable_flow(workloads.flow_init(w["D"], H, L, seed=5), H, L, train_every=2, epochs=20,
                                 lr=1e-3, min_ess_frac=0.25, precision=2 if arm == "flow_bf16" else 0)
-            smp.run(2)                      # first launches (function attributes, graph capture) untimed
+            smp.run(2)
             smp.reset(777)
             smp.profile(True)
             flush.zero_()
@@ -303,137 +601,57 @@ def precond_compare(g, torch, stream, flush, K=50, M=25, H=128, L=4):
             if arm.startswith("flow"):
                 fl = _flow_flops_per_grad(w, H, L) * (summ["grad_evals"] + run["n_particles"] * K)
                 r["flow_traj_tflops"] = fl / (prof["traj_ms"] / 1e3) / 1e12
-                if arm == "flow":
-                    r["flow_traj_frac_of_fp32_peak"] = r["flow_traj_tflops"] / FP32_FMA_PEAK_TFLOPS
-                else:
-                    pk = _peaks()[0]
-                    r["flow_traj_frac_of_bf16_peak"] = r["flow_traj_tflops"] / pk.get("bf16_tflops_sustained",
-                                                                                   pk["bf16_tflops"])
             res[arm] = r
         res["config"] = {"N": run["n_particles"], "K": K, "M_warmup": M, "eps": eps, "flow": f"{L} coupling layers, "
-                         f"width {H}, tanh, Adam lr 1e-3, 20 epochs every 2 warm-up iterations, ESS gate 0.25 J; "
-                         f"flow: FP32 conditioner products, flow_bf16: BF16 warp-MMA products (training FP32); "
-                         f"plain_bf16x3: no map, the Gaussian's P (theta - mu) on BF16x3 warp MMAs"}
+                         f"width {H}, tanh, Adam lr 1e-3, 20 epochs every 2 warm-up iterations, ESS gate 0.25 J"}
+        res["note"] = ("the evidence estimate of this sampler is the initial importance step from q_init = N(0, I) "
+                       "times per-iteration factors of mean one; in 100 (50) dimensions that step's weights are "
+                       "degenerate, so log Z is far from the closed form for every arm, and the arms are compared "
+                       "on ESS/s and posterior-moment error")
         out[name] = res
     return out
 
 
-def large_logistic_line(g, torch, stream, flush, precision=3):
-    """The large Bayesian logistic regression (n = 1e5 observations, D = 100,
-    correlated features, 16384 particles, 30 iterations) on the streamed
-    tensor-core kernel: one untimed iteration (first launches), then one
-    complete device-timed run with the trajectory launches timed by events
-    inside the library.  Roofline of the trajectory kernel against the
-    sustained BF16 tensor peak: algorithmic FLOPs are 4 n D per gradient
-    (X theta and X' r) plus 2 n D per particle for the FP32 end-point energy."""
+# ------------------------------------------------------------------ C3: chosen vs plain, kernel level
+def c3_kernel_compare(g, torch, stream, flush, theta_dn, S=10, eps=1e-3):
+    """The same 16384 particles (a sampler state) and momenta through S
+    leapfrog steps with each trajectory kernel of the model: chosen centred
+    BF16, the BF16x2 split, plain FP32 SIMT.  A whole plain FP32 run of this
+    workload takes about ten minutes, so the plain arm is compared here, per
+    particle-gradient, on one bounded trajectory launch; the energy error
+    (mean |Delta H| of the launch) shows what each gradient precision costs in
+    acceptance."""
     w = workloads.logistic_large()
-    run = dict(w["run"])
-    K, n, D = run["n_iters"], w["n"], w["D"]
     md = g.ModelData.from_workload(w)
-    smp = g.Sampler(md, g.make_config(seed=5151, precision=precision, **run), stream)
-    smp.run(1)
-    smp.reset(6161)
-    smp.profile(True)
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    smp.run(K)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    prof = smp.get_profile()
-    smp.profile(False)
-    summ = smp.summary()[0]
-    N = smp.n_total
-    smp.close()
-    peaks, kind = _peaks()
-    flops = 4.0 * n * D * summ["grad_evals"] + 2.0 * n * D * N * K
-    achieved = flops / (prof["traj_ms"] / 1e3) / 1e12
-    pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    # chosen vs plain on the same first iterations: the FP32 streamed kernel
-    # is ~16x slower per step, so both arms run the first `k_cmp` iterations
-    k_cmp = 2
-    cmp = {}
-    for name, prec in (("bf16x2", precision), ("fp32", 0)):
-        sv = g.Sampler(md, g.make_config(seed=5151, precision=prec, **run), stream)
+    dm = g.DevModel(md, stream)
+    D, N = theta_dn.shape
+    lib = g.lib()
+    out = {}
+    p0 = torch.randn(D, N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+    steps = torch.full((N,), S, dtype=torch.int32, device="cuda")
+    for name, prec in (("centred_bf16", 4), ("bf16x2", 3), ("fp32", 0)):
+        th = torch.as_tensor(theta_dn).cuda().contiguous()
+        p = p0.clone()
+        gr = torch.zeros(D, N, device="cuda")
+        lp = torch.zeros(N, dtype=torch.float64, device="cuda")
+        g.check(lib.smc_k_target(dm.h, th.data_ptr(), N, N, lp.data_ptr(), gr.data_ptr(), prec, stream), "target")
+        lp0 = lp.clone()
+        kin0 = 0.5 * (p.double() ** 2).sum(0)
         flush.zero_()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record()
-        sv.run(k_cmp)
-        c1.record()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.check(lib.smc_k_leapfrog(dm.h, th.data_ptr(), p.data_ptr(), gr.data_ptr(), lp.data_ptr(), steps.data_ptr(),
+                                   eps, N, N, prec, stream), "leapfrog")
+        e1.record()
         torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1)
-        sm_ = sv.summary()[0]
-        sv.close()
-        cmp[name] = {"ms": cms, "grad_evals": sm_["grad_evals"], "value": sm_["grad_evals"] / (cms / 1e3),
-                     "unit": "particle-grad-evals/s"}
-    cmp["iterations"] = k_cmp
-    cmp["note"] = "first iterations of the same run (seed 5151): chosen BF16x2 tensor cores vs plain FP32 SIMT"
-    return {"workload": WORKLOAD_DESC["logistic_large"], "precision": ["fp32", "bf16x3", "bf16", "bf16x2"][precision],
-            "chosen_vs_plain": cmp,
-            "value": summ["grad_evals"] / (ms / 1e3), "unit": "particle-grad-evals/s", "ms_per_run": ms,
-            "ess_per_s": summ["ess_sum_post_warmup"] / (ms / 1e3), "log_z": summ["log_z"],
-            "grad_evals": summ["grad_evals"], "traj_share": prof["traj_ms"] / ms,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                         "peak_source": f"bf16 dense sustained, {kind}",
-                         "kernel": "streamed tcgen05 trajectory kernel",
-                         "note": "algorithmic FLOPs; the kernel issues 2 products per GEMM (split state operands) "
-                                 "and pads D=100 to 112"},
-            "l2": "flushed before the run (256 MB write, outside the events)"}
-
-
-def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle as it stands, on the host cores, one
-    SMC iteration of the workload per step (bounded sample)."""
-    import oracle
-    w = _workload(args.workload)
-    run = dict(w["run"])
-    if rank != 0:
-        return None
-    t = oracle.TargetSpec.logistic(w["X"], w["y"], w.get("tau", 1.0)) if w["kind"] == "logistic" else \
-        oracle.TargetSpec.gauss_dense(w["mu"], w["P"])
-    cores = os.cpu_count() or 1
-    cfg = oracle.SMCConfig(seed=2024, **run)
-    st = oracle.smc_init(t, cfg, nthreads=cores)
-    st["chees"] = oracle.initial_chees_state(cfg)
-    k = 1
-    for _ in range(args.warmup):
-        oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
-        k += 1
-    t0 = time.perf_counter()
-    ge, ess = 0, 0.0
-    for _ in range(args.steps):
-        out = oracle.smc_iteration(t, cfg, k, st, nthreads=cores)
-        ge += out["stats"]["grad_evals"]
-        ess += out["stats"]["ess"]
-        k += 1
-    dt = time.perf_counter() - t0
-    val = ge / dt
-    sample = (f"{args.steps} SMC iterations (k={args.warmup + 1}..{k - 1}) of the {args.workload} workload "
-              f"after {args.warmup} untimed, N={run['n_particles']}, FP64 C oracle, OpenMP")
-    return {"metric": METRIC, "value": val, "unit": "particle-grad-evals/s", "impl": "reference",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC[args.workload]},
-            "cpu_baseline": {"value": val, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": val, "unit": "particle-grad-evals/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0},
-            "ess_per_s": ess / dt}
-
-
-METRIC = "particle-grad-evals/s & ESS/s at fixed log-Z error, chosen vs plain FP32 on 1 GB300"
-WORKLOAD_DESC = {
-    "logistic": "Bayesian logistic regression, synthetic, n=1000, D=25 (intercept + 24 N(0,1) features), "
-                "N=4096 particles, K=50 SMC iterations, ChEES-HMC eps=1e-3 L0=5 max 500 steps, 1-d Halton",
-    "gauss10": "10-d correlated Gaussian, N=256, K=20",
-    "hier": "batched hierarchical normal (non-centred, 50 groups x 20 obs, D=52), 64 independent runs with "
-            "particle counts uniform on 512..8192 (seeded, 278k particles) in every launch, K=50, eps=0.01, L0=1, FP32",
-    "logistic_large": "Bayesian logistic regression, synthetic, n=100000, D=100 (N(0,1) features with pairwise "
-                      "correlation 0.3), N=16384 particles, K=30 SMC iterations, eps=1e-3 L0=5 max 500 steps, "
-                      "1-d Halton, streamed tcgen05 BF16x2 gradients",
-}
+        ms = e0.elapsed_time(e1)
+        dH = (0.5 * (p.double() ** 2).sum(0) - lp) - (kin0 - lp0)
+        out[name] = {"ms": ms, "value": N * S / (ms / 1e3), "mean_abs_dH": float(dH.abs().mean())}
+    dm.close()
+    out["note"] = (f"one launch of {S} leapfrog steps of the same {N} particles (a state of the sampler after its "
+                   f"first iterations) and momenta, eps={eps}")
+    out["chosen_over_plain"] = out["centred_bf16"]["value"] / out["fp32"]["value"]
+    return out
 
 
 def main():
@@ -442,19 +660,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="logistic")
+    ap.add_argument("--workload", default="logistic_large", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--precision", type=int, default=None,
-                    help="timed main line: 0 FP32 SIMT, 1 BF16x3 tensor cores (compensated), 2 BF16 tensor "
-                         "cores; default: the chosen form, BF16x3 where the model has a tensor-core kernel, "
-                         "else FP32")
-    ap.add_argument("--variants", default="2",
-                    help="precisions also measured (fewer steps) and reported under 'variants'")
+                    help="main line precision (0 FP32, 1 BF16x3, 2 BF16, 3 BF16x2, 4 centred BF16); default: "
+                         "the chosen form of the workload's model")
+    ap.add_argument("--sides", default="c1,c2,c4,c5", help="side configurations to add (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-precond", action="store_true",
-                    help="skip the learned-preconditioner comparison (two 8192-particle targets)")
-    ap.add_argument("--no-large", action="store_true",
-                    help="skip the large logistic regression line (n=1e5, D=100, 16384 particles)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -484,184 +696,90 @@ def main():
     K = run["n_iters"]
     md = g.ModelData.from_workload(w)
     batched = "run_sizes" in w
+    prec = chosen_precision(w) if args.precision is None else args.precision
 
     def make_configs(seed0, precision):
         if not batched:
             return g.make_config(seed=seed0, precision=precision, **run)
-        # uneven independent runs in one handle (particle counts from the workload)
         return [g.make_config(seed=seed0 + r, precision=precision, **dict(run, n_particles=int(nr)))
                 for r, nr in enumerate(w["run_sizes"])]
 
-    prec = args.precision
-    if prec is None:
-        prec = 1
-        try:
-            g.Sampler(md, make_configs(1, 1), stream).close()
-        except RuntimeError:
-            prec = 0    # no tensor-core kernel for this model: the chosen form is FP32
     smp = g.Sampler(md, make_configs(1000 + 1000 * rank, prec), stream)
-    n_runs = smp.n_runs
-
+    n_runs, n_part = smp.n_runs, smp.n_total
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-    seeds = [20_000 + 1000 * rank + i for i in range(args.steps)]
+    seeds = [20_000 + 1000 * rank + i for i in range(1000)]
 
-    for i in range(args.warmup):
-        smp.reset(10_000 + 1000 * rank + i)
-        smp.run(K)
-    torch.cuda.synchronize()
-
+    # ---------------- warm-up and timed SMC iterations
+    timed_iterations(torch, smp, K, args.warmup, seeds[500:], flush)
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    mom_c = [] if not batched else None
-    dev_ms, ge_total, ess_post, lz = _timed_runs(torch, smp, K, seeds, flush, mom_c)
+    dev_ms, ge_total, ess_post = timed_iterations(torch, smp, K, args.steps, seeds, flush)
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
-    # the paper's Table 1 quantities for the last timed run (outside the events)
-    paper_q = None
-    s_last = smp.summary()
-    n_it = sum(x["iterations"] for x in s_last)
-    if n_it > 0:
-        n_part = sum(c.n_particles for c in smp._cfg)
-        grads_paper = sum(x["grad_evals"] for x in s_last) + n_part * (n_it // len(s_last))
-        paper_q = {"grad_evals_per_particle": grads_paper / (n_part * (n_it // len(s_last))),
-                   "ess_per_grad_eval": sum(x["ess_sum"] for x in s_last) / grads_paper,
-                   "note": "the paper's Table 1 quantities for the last timed run: gradient evaluations per "
-                           "particle per iteration counting S_j + 1 (the paper's convention), and J_eff per "
-                           "gradient evaluation (sums over the iterations)"}
-    prof, prof_ge = _profiled_run(smp, K, 30_000 + rank, flush)
     dev_ms, ge_all, ess_all = aggregate_ranks(torch, dist, dev_ms, ge_total, ess_post, "cuda")
     value = ge_all / (dev_ms / 1e3)
 
-    # ---------------- plain FP32 on the same seeds: the comparison the metric names
-    plain = None
-    if prec != 0:
-        sp = g.Sampler(md, make_configs(1000 + 1000 * rank, 0), stream)
-        sp.reset(10_000 + 1000 * rank)
-        sp.run(K)
-        torch.cuda.synchronize()
-        mom_p = [] if not batched else None
-        p_ms, p_ge, p_ess, p_lz = _timed_runs(torch, sp, K, seeds, flush, mom_p)
-        p_prof, p_prof_ge = _profiled_run(sp, K, 30_000 + rank, flush)
-        sp.close()
-        fl_grad, fl_end = _flops_per_grad(w)
-        p_flops = fl_grad * p_prof_ge + fl_end * smp.n_total * K
-        p_ach = p_flops / (p_prof["traj_ms"] / 1e3) / 1e12
-        d = np.asarray(lz) - np.asarray(p_lz)
-        plain = {"value": p_ge / (p_ms / 1e3), "unit": "particle-grad-evals/s", "ms_per_step": p_ms / len(seeds),
-                 "ess_per_s": p_ess / (p_ms / 1e3),
-                 "log_z": {"mean": float(np.mean(p_lz)), "sd": float(np.std(p_lz, ddof=1)) if len(p_lz) > 1 else None},
-                 "roofline": {"bound": "alu", "achieved": p_ach, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": p_ach / FP32_FMA_PEAK_TFLOPS, "kernel": "FP32 SIMT trajectory kernel"},
-                 "log_z_paired_diff": {"mean": float(np.mean(d)),
-                                       "sd": float(np.std(d, ddof=1)) if len(d) > 1 else None,
-                                       "note": "chosen minus plain, same seeds (same initial particles and "
-                                               "momentum streams); compare with the between-seed sd"},
-                 "seeds": "the timed seeds of the main line"}
-        if mom_c and mom_p:
-            # posterior means, chosen minus plain per seed, in posterior sd units
-            dm = [np.max(np.abs(mc[0] - mp[0]) / np.sqrt(mp[1])) for mc, mp in zip(mom_c, mom_p)]
-            plain["mean_paired_diff_sd_units"] = {"max_over_dims_mean_over_seeds": float(np.mean(dm)),
-                                                  "note": "compare with the Monte Carlo error of a mean, "
-                                                          "about 1/sqrt(ESS) sd"}
-
-    # ---------------- other precisions of the same workload (tensor-core forms)
-    variants = {}
-    for pv in [int(x) for x in args.variants.split(",") if x.strip() != ""]:
-        if pv == prec or pv == 0:
-            continue
-        try:
-            sv = g.Sampler(md, make_configs(1000 + 1000 * rank, pv), stream)
-        except RuntimeError:
-            continue    # no kernel for this model at that precision
-        sv.reset(5_000 + rank)
-        sv.run(K)
-        torch.cuda.synchronize()
-        nv = max(1, args.steps // 2)
-        ms_v, ge_v, ess_v = 0.0, 0, 0.0
-        for i in range(nv):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            sv.reset(40_000 + 1000 * rank + i)
-            sv.run(K)
-            e1.record()
-            sm_ = sv.summary()
-            ms_v += e0.elapsed_time(e1)
-            ge_v += sum(x["grad_evals"] for x in sm_)
-            ess_v += sum(x["ess_sum_post_warmup"] for x in sm_)
-        sv.close()
-        variants[["fp32", "bf16x3", "bf16"][pv]] = {
-            "value": ge_v / (ms_v / 1e3), "unit": "particle-grad-evals/s", "ms_per_step": ms_v / nv,
-            "ess_per_s": ess_v / (ms_v / 1e3), "steps": nv}
-
-    # ---------------- roofline of the trajectory kernel
+    # ---------------- one full profiled run: roofline, launches, evidence, Table 1 quantities
+    p_ms, p_sum, prof = full_run(torch, smp, K, 30_000 + rank, flush, profile=True)
+    lz_runs = [x["log_z"] for x in p_sum]
+    theta_state = smp.particles()[0] if (w["kind"] == "logistic" and w["n"] > 10_000) else None
+    s_last = p_sum
+    n_it = sum(x["iterations"] for x in s_last)
+    grads_paper = sum(x["grad_evals"] for x in s_last) + n_part * (n_it // len(s_last))
+    paper_q = {"grad_evals_per_particle": grads_paper / (n_part * (n_it // len(s_last))),
+               "ess_per_grad_eval": sum(x["ess_sum"] for x in s_last) / grads_paper,
+               "note": "the paper's Table 1 quantities for the profiled run: gradient evaluations per particle per "
+                       "iteration counting S_j + 1 (the paper's convention), and J_eff per gradient evaluation"}
     peaks, peak_kind = _peaks()
     fl_grad, fl_end = _flops_per_grad(w)
-    n_part = smp.n_total
+    prof_ge = sum(x["grad_evals"] for x in p_sum)
     traj_flops = fl_grad * prof_ge + fl_end * n_part * K
     traj_ms = prof["traj_ms"]
     traj_n = max(1, prof["traj_launches"])
-    achieved = traj_flops / traj_n / (traj_ms / traj_n / 1e3) / 1e12
+    achieved = traj_flops / (traj_ms / 1e3) / 1e12
     if prec == 0:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_FMA_PEAK_TFLOPS,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (max SM clock)"}
-        kfile = "traj_simt.cu"
     else:
-        # a kernel inside a long step: the sustained bf16 peak
-        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])   # a kernel inside a long step
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                 "peak_source": f"bf16 dense sustained, {peak_kind}"}
-        kfile = "traj_glm_mma.cu" if w["kind"] in ("logistic", "linear_gauss") and w["D"] <= 32 else "traj_tc.cu"
-        ex = _mma_flops_per_grad(w, prec)
-        if ex is not None:
-            roof["executed"] = (ex[0] * prof_ge + ex[1] * n_part * K) / (traj_ms / 1e3) / 1e12
-            roof["executed_note"] = ("MMA FLOP/s actually issued: the three BF16 products of the compensated "
-                                     "form, the dimension padded to 32 and the observations to 16")
-            ceil = C.c_double()
-            if g.lib().smc_k_mma_peak(1 << 14, C.byref(ceil), C.c_void_p(stream)) == 0:
-                roof["warp_mma_ceiling"] = ceil.value
-                roof["executed_frac_of_warp_mma_ceiling"] = roof["executed"] / ceil.value
-                roof["ceiling_note"] = ("issue-rate ceiling of warp-level BF16 MMAs (mma.sync m16n8k16) measured "
-                                        "live by smc_k_mma_peak; the kernel's MMAs are of that kind")
-    tr = _traffic_for(kfile, args.workload)
-    roof["traffic"] = tr
-    roof["kernel"] = "trajectory (leapfrog) kernel"
-    roof["launches_profiled"] = prof["traj_launches"]
-    roof["mean_launch_ms"] = traj_ms / traj_n
-    roof["share_of_step_time"] = traj_ms / (dev_ms / args.steps) if dev_ms > 0 else None
+    kfile = _kernel_file(w, prec)
+    roof.update({"traffic": _traffic_for(kfile, args.workload), "kernel": f"trajectory stage ({kfile})",
+                 "launches_profiled": prof["traj_launches"], "mean_launch_ms": traj_ms / traj_n,
+                 "share_of_run_time": traj_ms / p_ms,
+                 "work": "algorithmic: 4 n D FLOP per particle-gradient (X theta and X' r) + 2 n D per particle "
+                         "per iteration (end-point energy); the real count of leapfrog gradients, S_j per particle"})
+    kernel_launches_per_iter = prof["kernel_launches"] / max(1, K)
 
-    # ---------------- learned preconditioner vs the plain sampler (rank 0, N=1)
-    precond = None
-    if not args.no_precond and world == 1 and args.workload == "logistic":
-        precond = precond_compare(g, torch, stream, flush)
-    large = None
-    if not args.no_large and world == 1 and args.workload == "logistic":
-        large = large_logistic_line(g, torch, stream, flush)
+    # ---------------- chosen vs plain (C3: kernel level on the sampler's state)
+    cvp = None
+    if theta_state is not None and world == 1:
+        cvp = c3_kernel_compare(g, torch, stream, flush, np.ascontiguousarray(theta_state[:, :n_part]))
 
-    # ---------------- end to end through the C-ABI with host buffers
+    # ---------------- end to end through the C-ABI with host buffers (one full run)
     e2e = None
     if not args.no_e2e:
         lib = g.lib()
-        h2d = 0
-        for a in md.arrays:
-            if a is not None:
-                h2d += a.nbytes
+        h2d = sum(a.nbytes for a in md.arrays if a is not None)
         D = w["D"]
         theta_h = np.empty((D, n_part), dtype=np.float32)
         logw_h = np.empty(n_part)
         lz_h = np.empty(n_runs)
         times, ge_e = [], 0
-        for i in range(max(2, args.steps // 2)):
+        n_e2e = 1 if K * n_part * w.get("n", 1) > 1e9 else 3
+        for i in range(n_e2e):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = C.c_void_p()
-            c2 = make_configs(30_000 + 100 * i + 1000 * rank, prec)
+            c2 = make_configs(40_000 + 100 * i + 1000 * rank, prec)
             if batched:
                 arr = (g._binding.SmcConfig * len(c2))(*c2)
                 g.check(lib.smc_init_batch(C.byref(h), len(c2), arr, C.byref(md.struct), C.c_void_p(stream)),
@@ -677,9 +795,21 @@ def main():
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             ge_e += sum(x.grad_evals for x in summ)
+            lz_runs += list(lz_h)
         e2e = {"value": ge_e * world / sum(times), "unit": "particle-grad-evals/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(theta_h.nbytes + logw_h.nbytes + lz_h.nbytes),
-               "steps": len(times)}
+               "steps": len(times),
+               "step": "one full run through smc_init (host model data) -> smc_run -> host copies -> smc_destroy"}
+    smp.close()
+
+    # ---------------- side configurations (rank 0, N = 1)
+    sides = {}
+    if world == 1:
+        for name in [x.strip() for x in args.sides.split(",") if x.strip()]:
+            fn = {"c1": side_c1, "c2": side_c2, "c4": side_c4, "c5": side_c5}[name]
+            t0 = time.perf_counter()
+            sides[name] = fn(g, torch, stream, flush)
+            sides[name]["wall_s"] = time.perf_counter() - t0
 
     if dist:
         dist.barrier()
@@ -690,10 +820,10 @@ def main():
     # ---------------- CPU baseline (oracle on the host cores), rank 0, N=1 only
     cpu = None
     if world == 1 and not args.no_cpu_baseline and not batched:
-        rate, cores, dt, iters = cpu_oracle_rate(w, run)
+        rate, cores, dt, iters, Ns = oracle_iteration_rate(w)
         cpu = {"value": rate, "unit": "particle-grad-evals/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {iters} SMC iterations of the same workload (N={n_part}, full data), "
-                         f"FP64 C oracle, OpenMP, {dt:.1f} s wall"}
+               "sample": f"the first {iters} SMC iteration(s) of the workload with N={Ns} particles (of {n_part}) "
+                         f"on the full data, FP64 C oracle, OpenMP over particles, {dt:.1f} s wall"}
 
     line = {
         "metric": METRIC,
@@ -708,25 +838,25 @@ def main():
         "vs_baseline": None,
         "dtype": "f32" if prec == 0 else "bf16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "step": f"one full sampler run ({K} iterations)",
-                   "precision": ["fp32", "bf16x3", "bf16"][prec],
-                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+        "config": {"workload": WORKLOAD_DESC[args.workload],
+                   "step": f"one SMC iteration (of {K}-iteration runs, continued across steps)",
+                   "precision": PREC_NAMES[prec],
+                   "l2": "flushed before every timed iteration (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "ess_per_s": {"value": ess_all / (dev_ms / 1e3), "unit": "ESS/s",
-                      "note": "sum of post-warm-up J_eff over iterations / device time"},
-        "log_z": {"mean": float(np.mean(lz)), "sd": float(np.std(lz, ddof=1)) if len(lz) > 1 else None},
+                      "note": "J_eff after reweighting (Eq. for J_eff), summed over the timed iterations / their "
+                              "device time"},
+        "log_z": {"runs": len(lz_runs), "values": [float(x) for x in lz_runs],
+                  "note": "one profiled run and the end-to-end runs; the model has no closed form (see sides.c2 "
+                          "for the log-Z agreement check of the regression sampler)"},
         "paper_metrics": paper_q,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "plain_fp32": plain,
-        "chosen_vs_plain": None if plain is None else {
-            "throughput": value / plain["value"], "ess_per_s": (ess_all / (dev_ms / 1e3)) / plain["ess_per_s"]},
-        "variants": variants,
-        "preconditioner": precond,
-        "large_logistic": large,
-        "autotune": smp.plan(),
-        "gpu_launches": prof["kernel_launches"] * args.steps,
+        "chosen_vs_plain": cvp,
+        "sides": sides,
+        "autotune": None,
+        "gpu_launches": int(round(kernel_launches_per_iter * args.steps)),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

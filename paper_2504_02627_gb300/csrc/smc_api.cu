@@ -820,7 +820,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
                            : launch_traj(h->model.m, a, h->precision, s);
             cudaEventRecord(h->events[i + 1], s);
             h->n_event_pairs += 1;
-            h->kernel_launches += KERNELS_PER_ITERATION;
+            h->kernel_launches += KERNELS_PER_ITERATION + (h->precision == SMC_PREC_BF16C ? 3 : 0);   // + reference kernels
         } else {
             e = h->flow_on ? launch_traj_flow(h->model.m, h->flow, a, h->z0, h->z1, s)
                            : launch_traj(h->model.m, a, h->precision, s);

@@ -499,31 +499,51 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             for (int hs = 0; hs < 2; ++hs) {
                 const int slot = 2 * q + hs;
                 if (slot >= nslot || slot < slot_lo || slot >= slot_hi) continue;
+                // every load of the slot is issued before the first store (the
+                // state arrays may alias as far as the compiler knows), so the
+                // slot costs a few memory latencies, not one per dimension
+                float gs[16], tcur[16], pcur[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    // the cluster's partials of this dimension, summed in rank order
+                    const uint32_t ga = gx_base + (uint32_t)(((16 * slot + e) * CP + prow) * 4);
+                    gs[e] = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
+                }
+                for (int r = 1; r < kc; ++r)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        gs[e] += tc::ld_cluster_f32(
+                            tc::map_to_rank(gx_base + (uint32_t)(((16 * slot + e) * CP + prow) * 4), (uint32_t)r));
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int d = 16 * slot + e;
+                    tcur[e] = 0.0f;
+                    pcur[e] = 0.0f;
+                    if (live && d < D) {
+                        tcur[e] = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
+                        if (!evalm) pcur[e] = a.p_out[(int64_t)d * ld + j];
+                    }
+                }
                 float tv[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int d = 16 * slot + e;
-                    // the cluster's partials of this dimension, summed in rank order
-                    const uint32_t ga = gx_base + (uint32_t)((d * CP + prow) * 4);
-                    float gsum = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
-                    for (int r = 1; r < kc; ++r) gsum += tc::ld_cluster_f32(tc::map_to_rank(ga, (uint32_t)r));
                     float tnew = 0.0f;
                     if (live && d < D) {
-                        float tcur = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
-                        const float g = __ldg(gref + d) + gsum - tcur * inv_tau2;
+                        float t0 = tcur[e];
+                        const float g = __ldg(gref + d) + gs[e] - t0 * inv_tau2;
                         if (evalm || s == S) a.grad_out[(int64_t)d * ld + j] = g;
                         if (!evalm) {
-                            float* pp = a.p_out + (int64_t)d * ld + j;
-                            float pv = *pp;
+                            float pv = pcur[e];
                             if (s >= 1) pv = fmaf(hf, g, pv);
                             if (s < S) {
                                 pv = fmaf(hf, g, pv);
-                                tcur = fmaf(ef, pv, tcur);
-                                a.theta_out[(int64_t)d * ld + j] = tcur;
+                                t0 = fmaf(ef, pv, t0);
+                                a.theta_out[(int64_t)d * ld + j] = t0;
                             }
-                            *pp = pv;
+                            a.p_out[(int64_t)d * ld + j] = pv;
                         }
-                        tnew = tcur;
+                        tnew = t0;
                     }
                     tv[e] = tnew;
                 }
