@@ -50,9 +50,9 @@
 // first tiles, spread over several SMs).  Every CTA of the cluster holds the
 // same 128 particles and accumulates the partial gradient of its share of
 // the observation tiles; each pass the partials are published in shared
-// memory, and the CTA that owns a 16-dimension slot of the state sums the k
-// partials of that slot in rank order (the same sum in every CTA), updates
-// theta and p for the slot, and writes the slot's BF16 deviations into the
+// memory, and the CTA that owns an 8-dimension unit of the state sums the k
+// partials of that unit in rank order (the same sum in every CTA), updates
+// theta and p for the unit, and writes the unit's BF16 deviations into the
 // GEMM1 operand of every CTA of the cluster through distributed shared
 // memory.  The split changes only the FP32 summation order of the gradient.
 // Every mbarrier wait is bounded in wall time (2 s), after which *dev_err is
@@ -80,13 +80,13 @@ constexpr float C_X_MAX = 60.0f;           // clamp of the exponent: two factors
 
 struct CLayout {
     int atoms, tile_bytes, ref_bytes, stage_bytes, stages;
-    int off_d, off_stage, off_gx, off_misc, off_bar, total;
+    int off_d, off_stage, off_gx, off_misc, off_cref, off_bar, total;
 };
 
 // Byte layout of the dynamic shared memory (from a 1024-aligned base) with
 // `stages` X tile stages.  The end-point pass reuses [0, off_misc) for
 // theta^T, two FP32 X chunks and the partial sums, so off_misc covers both uses.
-__host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int stages) {
+__host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_run, int stages) {
     CLayout L;
     L.atoms = (dk + 63) / 64;
     L.tile_bytes = L.atoms * C_ATOM;
@@ -99,16 +99,17 @@ __host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int sta
     const int pipe = L.off_gx + dk * CP * 4;
     const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + C_EPI_WARPS * CP * 8;
     L.off_misc = ((pipe > endp ? pipe : endp) + 1023) & ~1023;
-    L.off_bar = L.off_misc + 9 * CP * 8;                  // kin, sq: [4][128] f64; ll: [128] f64
+    L.off_cref = L.off_misc + 9 * CP * 8;                 // kin, sq: [4][128] f64; ll: [128] f64
+    L.off_bar = L.off_cref + 2 * n_run * dk * 4;          // reference points, reference gradients [runs][dk]
     L.total = L.off_bar + 256 + 1024;                     // + alignment slack of the base
     // more than half of the SM's shared memory, so that a second CTA, which
     // would wait for the 512 TMEM columns, is never co-scheduled
     if (L.total < 118 * 1024) L.total = 118 * 1024;
     return L;
 }
-__host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref) {
-    CLayout L = c_layout_n(dk, Dp, n_ref, C_NS_MAX);
-    for (int st = C_NS_MAX - 1; st >= 2 && L.total > C_SMEM_MAX; --st) L = c_layout_n(dk, Dp, n_ref, st);
+__host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref, int n_run) {
+    CLayout L = c_layout_n(dk, Dp, n_ref, n_run, C_NS_MAX);
+    for (int st = C_NS_MAX - 1; st >= 2 && L.total > C_SMEM_MAX; --st) L = c_layout_n(dk, Dp, n_ref, n_run, st);
     return L;
 }
 
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     // accesses through it stay shared-space loads and stores
     unsigned char* sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int n_ref = LOGIT ? a.c_runs : 0;
-    const CLayout L = c_layout(m.dk, m.Dp, n_ref);
+    const CLayout L = c_layout(m.dk, m.Dp, n_ref, a.c_runs);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int D = m.D, dk = m.dk, nch_all = m.n_tiles128;
     const int64_t ld = a.ld;
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     const int64_t tile = blockIdx.x / kc;
     const int c_lo = (int)((int64_t)rank * nch_all / kc), c_hi = (int)((int64_t)(rank + 1) * nch_all / kc);
     const int nch = c_hi - c_lo;
-    const int nslot = dk / 16, slot_lo = rank * nslot / kc, slot_hi = (rank + 1) * nslot / kc;
+    // ownership of the state for the update: 8-dimension units, a contiguous share per rank
+    const int nunit = dk / 8, u_lo = rank * nunit / kc, u_hi = (rank + 1) * nunit / kc;
     const int NS = L.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.off_bar);   // [NS] stage filled
     uint64_t* empty = full + C_NS_MAX;                               // [NS] stage consumed by both GEMMs
@@ -188,6 +190,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         tc::tmem_alloc(tmem_s, C_TMEM_COLS);
         tc::tmem_relinquish();
     }
+    // the runs' reference points and reference gradients, read every pass
+    float* cref_s = reinterpret_cast<float*>(sm + L.off_cref);       // [runs][dk]
+    float* gref_s = cref_s + a.c_runs * dk;                          // [runs][dk]
+    for (int i = tid; i < a.c_runs * dk; i += C_THREADS) {
+        cref_s[i] = a.c_centre[i];
+        gref_s[i] = a.c_gref[i];
+    }
+    __syncthreads();
 
     // ---------------------------------------------------------------- particle state (warps 0-15)
     // warp w: TMEM lanes 32 (w % 4) .. + 31 (one particle per lane); group
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             pv[0] = (float)z0;
                             pv[1] = d + 1 < D ? (float)z1 : 0.0f;
                         }
-                        const bool own = (d >> 4) >= slot_lo && (d >> 4) < slot_hi;
+                        const bool own = (d >> 3) >= u_lo && (d >> 3) < u_hi;
 #pragma unroll
                         for (int e = 0; e < 2; ++e)
                             if (d + e < D) {
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         }
         if (epi) kin_s[q * CP + prow] = kin;
     }
-    const float* cref = a.c_centre + (int64_t)run * dk;   // this particle's run reference point
+    const float* cref = cref_s + run * dk;                // this particle's run reference point
     // deviation operand: unit u (8 dimensions) of this thread's 32 dimensions
     // of its particle row, BF16, swizzled
     auto write_unit = [&](int u, const float* tv) {
@@ -269,7 +279,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int d = ds + 8 * u + e;
-            v[e] = (j >= 0 && d < D) ? tv[e] - __ldg(cref + d) : 0.0f;
+            v[e] = (j >= 0 && d < D) ? tv[e] - cref[d] : 0.0f;
         }
         const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                    pack_bf16(v[6], v[7]));
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const float hf = 0.5f * ef;
         const float kneg = -1.4426950408889634f;
-        const float* gref = a.c_gref + (int64_t)run * dk;
+        const float* gref = gref_s + run * dk;
         int st = 0;
         uint32_t sph = 0, bph = 0;
         int64_t it = 0;
@@ -475,12 +485,17 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 }
             }
             // the pass's gradient g_ref + (sum of the cluster's partial G) -
-            // theta / tau^2, then the leapfrog update of the slots this CTA owns
-            tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
+            // theta / tau^2, then the leapfrog update of the units this CTA owns
+            // one thread waits for the pass's gradient (and for every CTA to be
+            // done with the previous pass's partials); the other epilogue
+            // warps sleep on a hardware barrier instead of polling
+            if (tid == 0) {
+                tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
+                if (s >= 1) tc::mbar_wait_cluster_timed(gx_free, (uint32_t)((s - 1) & 1), err, abort_s);
+            }
+            named_sync(3u, 32u * C_EPI_WARPS);
             tc::fence_after_sync();
-            // publish this CTA's partial gradient (dims ds .. ds + 31) once every
-            // CTA has read the previous pass's
-            if (s >= 1) tc::mbar_wait_cluster_timed(gx_free, (uint32_t)((s - 1) & 1), err, abort_s);
+            // publish this CTA's partial gradient (dims ds .. ds + 31)
             if (ds < dk) {
                 uint32_t gv[32];
                 tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
@@ -492,31 +507,38 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             __syncwarp();
             if (lane == 0)
                 for (int r = 0; r < kc; ++r) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_full), (uint32_t)r));
-            tc::mbar_wait_cluster_timed(gx_full, (uint32_t)(s & 1), err, abort_s);
+            if (tid == 0) tc::mbar_wait_cluster_timed(gx_full, (uint32_t)(s & 1), err, abort_s);
+            named_sync(3u, 32u * C_EPI_WARPS);
             const bool live = j >= 0 && (evalm || s <= S);
             const bool more = s + 1 < npass;
+            // the update of the units this CTA owns, spread over all sixteen
+            // warps: group q takes units q, q + 4, q + 8, q + 12 of its particle
 #pragma unroll
-            for (int hs = 0; hs < 2; ++hs) {
-                const int slot = 2 * q + hs;
-                if (slot >= nslot || slot < slot_lo || slot >= slot_hi) continue;
-                // every load of the slot is issued before the first store (the
-                // state arrays may alias as far as the compiler knows), so the
-                // slot costs a few memory latencies, not one per dimension
-                float gs[16], tcur[16], pcur[16];
+            for (int uu = 0; uu < 4; ++uu) {
+                const int unit = q + 4 * uu;
+                if (unit >= nunit || unit < u_lo || unit >= u_hi) continue;
+                // every load of the unit is issued before its first store (the
+                // state arrays may alias as far as the compiler knows)
+                float gs[8], tcur[8], pcur[8];
+                if (kc == 1) {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    // the cluster's partials of this dimension, summed in rank order
-                    const uint32_t ga = gx_base + (uint32_t)(((16 * slot + e) * CP + prow) * 4);
-                    gs[e] = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
+                    for (int e = 0; e < 8; ++e) gs[e] = gx[(8 * unit + e) * CP + prow];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        // the cluster's partials of this dimension, summed in rank order
+                        const uint32_t ga = gx_base + (uint32_t)(((8 * unit + e) * CP + prow) * 4);
+                        gs[e] = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
+                    }
+                    for (int r = 1; r < kc; ++r)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            gs[e] += tc::ld_cluster_f32(
+                                tc::map_to_rank(gx_base + (uint32_t)(((8 * unit + e) * CP + prow) * 4), (uint32_t)r));
                 }
-                for (int r = 1; r < kc; ++r)
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        gs[e] += tc::ld_cluster_f32(
-                            tc::map_to_rank(gx_base + (uint32_t)(((16 * slot + e) * CP + prow) * 4), (uint32_t)r));
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int d = 16 * slot + e;
+                for (int e = 0; e < 8; ++e) {
+                    const int d = 8 * unit + e;
                     tcur[e] = 0.0f;
                     pcur[e] = 0.0f;
                     if (live && d < D) {
@@ -524,14 +546,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                         if (!evalm) pcur[e] = a.p_out[(int64_t)d * ld + j];
                     }
                 }
-                float tv[16];
+                float tv[8];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int d = 16 * slot + e;
+                for (int e = 0; e < 8; ++e) {
+                    const int d = 8 * unit + e;
                     float tnew = 0.0f;
                     if (live && d < D) {
                         float t0 = tcur[e];
-                        const float g = __ldg(gref + d) + gs[e] - t0 * inv_tau2;
+                        const float g = gref[d] + gs[e] - t0 * inv_tau2;
                         if (evalm || s == S) a.grad_out[(int64_t)d * ld + j] = g;
                         if (!evalm) {
                             float pv = pcur[e];
@@ -548,28 +570,29 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     tv[e] = tnew;
                 }
                 if (more) {
-                    // the slot's two 16-byte units of the deviation row, into the
-                    // GEMM1 operand of every CTA of the cluster
-                    const uint32_t row = dev_base + (uint32_t)((slot >> 2) * C_DATOM + prow * 128);
+                    // the unit's 16 bytes of the deviation row, into the GEMM1
+                    // operand of every CTA of the cluster
+                    float v[8];
 #pragma unroll
-                    for (int u2 = 0; u2 < 2; ++u2) {
-                        float v[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int d = 16 * slot + 8 * u2 + e;
-                            v[e] = (j >= 0 && d < D) ? tv[8 * u2 + e] - __ldg(cref + d) : 0.0f;
-                        }
-                        const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                                   pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                        const int unit = 2 * (slot & 3) + u2;
-                        const uint32_t ua = row + (uint32_t)((unit ^ (prow & 7)) << 4);
-                        for (int r = 0; r < kc; ++r) tc::st_cluster_u4(tc::map_to_rank(ua, (uint32_t)r), w);
+                    for (int e = 0; e < 8; ++e) {
+                        const int d = 8 * unit + e;
+                        v[e] = (j >= 0 && d < D) ? tv[e] - cref[d] : 0.0f;
+                    }
+                    const uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                               pack_bf16(v[6], v[7]));
+                    const uint32_t uoff =
+                        (uint32_t)((unit >> 3) * C_DATOM + prow * 128 + (((unit & 7) ^ (prow & 7)) << 4));
+                    if (kc == 1) {
+                        *reinterpret_cast<uint4*>(sm + L.off_d + uoff) = w;
+                    } else {
+                        for (int r = 0; r < kc; ++r) tc::st_cluster_u4(tc::map_to_rank(dev_base + uoff, (uint32_t)r), w);
                     }
                 }
             }
             // the deviations reach the other CTAs' tensor cores, and this CTA
             // is done with the cluster's partials
-            tc::fence_proxy_async_cluster();
+            if (kc == 1) tc::fence_proxy_async_smem();
+            else tc::fence_proxy_async_cluster();
             __syncwarp();
             if (lane == 0)
                 for (int r = 0; r < kc; ++r) {
@@ -590,7 +613,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         tc::mbar_wait_timed(fin2, 0u, err, &ignore_abort, 4000000000ull);
     }
     __syncthreads();
-    tc::cluster_sync();   // every CTA of the cluster has written its slots of the final state
+    tc::cluster_sync();   // every CTA of the cluster has written its units of the final state
     const int Dp = m.Dp, n = m.n;
     // this CTA's share of the 64-observation chunks of the end point
     const int e_lo = (int)((int64_t)rank * m.n_chunks / kc), e_hi = (int)((int64_t)(rank + 1) * m.n_chunks / kc);
@@ -830,7 +853,7 @@ cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s)
     const int R = a.c_runs;
     if (R < 1 || R > CENTRED_MAX_RUNS || !a.c_centre || !a.c_gref || !a.c_part || (LOGIT && !a.c_refs))
         return cudaErrorInvalidValue;
-    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? R : 0);
+    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? R : 0, R);
     if (L.total > C_SMEM_MAX) return cudaErrorInvalidValue;
     k_centre_mean<<<dim3((unsigned)R, (unsigned)m.dk), 256, 0, s>>>(a, m.D, m.dk);
     k_centre_obs<LOGIT><<<(unsigned)m.n_tiles128, 128, 0, s>>>(m, a);
