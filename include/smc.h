@@ -128,8 +128,10 @@ typedef struct {
                                0 none (h = 1); 1 1-d Halton of n = j*K + k; 2
                                uniform; 3 N-d Halton; 4 N-d inverse Halton; 5 N-d
                                primes; 6 N-d inverse primes; 7 1-d golden ratio;
-                               8 equidistant; 9 offset equidistant; 10 1-d Sobol.
-                               3-6 need n_iters <= 65536                       */
+                               8 equidistant; 9 offset equidistant; 10 1-d Sobol;
+                               11 1-d Halton of n = (k-1)*J + j + 1 (the J x K
+                               matrix read iteration-major).  3-6 need
+                               n_iters <= 65536                                */
     double ess_frac;        /* resample when ESS < ess_frac * J                   */
     uint64_t seed;          /* Philox4x32-10 key                                  */
     int32_t accept_reject;  /* 0: the paper's SMC-ChEES (every particle moves, log w
@@ -281,15 +283,6 @@ smc_status smc_get_plan(const smc_handle* h, int32_t* traj_tile, int32_t* n_tile
  * on (the captured graph is dropped).  Errors: SMC_E_INVAL. */
 smc_status smc_set_plan(smc_handle* h, int32_t traj_tile);
 
-/* Measurement: the issue-rate ceiling of warp-level BF16 tensor-core MMAs
- * (mma.sync m16n8k16, FP32 accumulation) on the current device, in TFLOP/s:
- * one launch of `iters` iterations of eight independent MMA chains per warp,
- * two 256-thread CTAs per SM, event-timed on `stream` after a warm-up launch.
- * The denominator for the issued MMA rate of the warp-MMA trajectory kernels.
- * Allocates and frees (stream-ordered) a small output buffer.  Errors:
- * SMC_E_INVAL (iters outside [1, 2^24]), SMC_E_CUDA. */
-smc_status smc_k_mma_peak(int64_t iters, double* tflops, void* stream);
-
 /* Copies the last error text (NUL-terminated, truncated to len). */
 smc_status smc_last_error(const smc_handle* h, char* buf, int64_t len);
 
@@ -404,7 +397,9 @@ smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps,
  *     word 0 of Philox block (x, r, k, 6) (masked to half the bits) into the
  *     other half, applied until the value is below J;
  *   9 offset equidistant: that + 0.1 u, u the uniform of block (1, j, k, 5);
- *   10 1-d Sobol: radical inverse base 2 of g = n ^ (n >> 1), n = j*K + k.
+ *   10 1-d Sobol: radical inverse base 2 of g = n ^ (n >> 1), n = j*K + k;
+ *   11 1-d Halton of n = (k-1)*J + j + 1 (the J x K index matrix of 1 read
+ *      iteration-major).
  * Every FP64 operation rounds once, in the order written.  Errors:
  * SMC_E_INVAL (scheme, sizes, J*K + k >= 2^32, K > 65536 for 3-6). */
 smc_status smc_k_jitter(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k, double* out_h,
@@ -466,6 +461,18 @@ smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
                           int32_t* ancestors, int32_t* status_out, void* scratch,
                           void* stream);
 
+/* Failure detection of the resampling scan's bounded wait (the paper has no
+ * counterpart: it concerns this library's look-back scan for the resampling
+ * step of Algorithm 3).  Runs the scan's look-back for tile 1 of a two-tile
+ * run whose tile 0 never publishes its prefix, giving up after poll_limit
+ * polls without progress (about 64 ns each; the sampler uses 2^22).  Writes
+ * *status_out (device i32): -5 when the wait gave up, as the sampler reports
+ * SMC_E_TIMEOUT for a run.  scratch: device, at least 64 bytes, 16-byte
+ * aligned, overwritten.  Returns SMC_E_INVAL for poll_limit outside
+ * [1, 2^40] or null pointers, SMC_E_CUDA if the launch fails; the GPU
+ * context stays usable. */
+smc_status smc_k_lookback_wait_check(int64_t poll_limit, int32_t* status_out, void* scratch, void* stream);
+
 /* Systematic resampling exactly as smc_k_resample, for callers that cannot
  * allocate device memory where they resample (a host framework that owns the
  * whole device memory budget, or a latency-critical loop that cannot afford
@@ -477,6 +484,9 @@ smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
  * SMC_E_INVAL with a message on stderr.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device
  * current) and caches it; make that first call before any stream capture.
+ * The cached address belongs to the device's primary context: after
+ * cudaDeviceReset, or anything else that destroys that context, the library
+ * must be unloaded and loaded again before the next call.
  * Every call shares the one array, and each call clears the part it uses
  * before reading it; calls whose work overlaps on the GPU (other streams,
  * other host threads) race on it and must be serialised by the caller.

@@ -1,10 +1,10 @@
 """Single-launch kernel timings through the kernel-level entry points (a
 micro-benchmark and the profiling driver for one trajectory kernel at a time).
 
-    python -m paper_2504_02627_gb300.kernel_bench stream --n 20000 --particles 16384 --steps 40
-    python -m paper_2504_02627_gb300.kernel_bench flow --particles 8192 --steps 8
-    python -m paper_2504_02627_gb300.kernel_bench glm --particles 4096 --steps 20
-    python -m paper_2504_02627_gb300.kernel_bench gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
+    python kernel_bench.py stream --n 20000 --particles 16384 --steps 40
+    python kernel_bench.py flow --particles 8192 --steps 8
+    python kernel_bench.py glm --particles 4096 --steps 20
+    python kernel_bench.py gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
 
 Each run makes seeded synthetic inputs (the workloads of this repository),
 launches one target evaluation, then leapfrog trajectories of `--steps` steps
@@ -24,12 +24,12 @@ import numpy as np
 
 
 def _setup():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    root = os.path.dirname(os.path.abspath(__file__))
     if root not in sys.path:
         sys.path.insert(0, root)
     import torch
     import workloads
-    from . import _binding as B
+    from paper_2504_02627_gb300 import _binding as B
     return torch, workloads, B
 
 
@@ -144,7 +144,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--precision", type=int, default=None,
-                    help="stream: 2 (BF16) or 3 (BF16x2, default); glm: 0 (FP32, default), 1 (BF16x3) or 2 (BF16); "
+                    help="stream: 2 (BF16), 3 (BF16x2, default) or 4 (centred BF16); glm: 0 (FP32, default), "
+                         "1 (BF16x3), 2 (BF16) or 4 (centred BF16); "
                          "flow: 0 (FP32, default) or 2 (BF16 conditioner products)")
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)

@@ -275,7 +275,8 @@ def multinomial_u64(seed, k, i):
 
 # jitter schemes (Sec. 3.2.1): names of the `jitter` values
 JITTER = {"none": 0, "halton1": 1, "uniform": 2, "halton_nd": 3, "halton_nd_inv": 4, "primes": 5,
-          "primes_inv": 6, "golden": 7, "equidistant": 8, "equidistant_offset": 9, "sobol1": 10}
+          "primes_inv": 6, "golden": 7, "equidistant": 8, "equidistant_offset": 9, "sobol1": 10,
+          "halton1_iter": 11}
 
 
 def jitter(scheme, seed, j, k, J, K):

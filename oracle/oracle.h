@@ -71,7 +71,8 @@ double oracle_halton2(uint32_t n);
  *   9 offset equidistant: that plus 0.1 u, u the FP64 uniform of Philox block
  *   (1, j, k, JITTER);  10 1-d Sobol: radical inverse base 2 of the Gray
  *   code g = n ^ (n >> 1) of n = jK + k (the first Sobol dimension in Gray-
- *   code order).
+ *   code order);  11 1-d Halton, base 2, of n = (k - 1) J + j + 1 (the J x K
+ *   matrix of scheme 1 read iteration-major).
  * Schemes 3-6 reuse their K dimensions cyclically past iteration K.
  * Every value is a correctly rounded FP64 operation sequence: radical
  * inverses as one division of two exact integers, sqrt, products and frac

@@ -182,6 +182,9 @@ double oracle_jitter(int32_t scheme, uint64_t seed, int64_t j, int64_t k, int64_
             const uint32_t n = (uint32_t)(j * K + k);
             return oracle_halton2(n ^ (n >> 1));
         }
+        /* 1-d Halton with the J x K matrix read iteration-major: iteration k
+         * takes the J consecutive indices (k - 1) J + 1 .. k J (Sec. 3.2) */
+        case 11: return oracle_halton2((uint32_t)((k - 1) * J + j + 1));
         default: return 1.0;
     }
 }

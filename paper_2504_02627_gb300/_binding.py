@@ -20,7 +20,8 @@ GAUSS_DENSE, LOGISTIC, HIER_NORMAL, BANANA, LINEAR_GAUSS = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2, PREC_BF16C = 0, 1, 2, 3, 4
 # trajectory-length jitter schemes (Sec. 3.2.1), smc_config.jitter
 (JITTER_NONE, JITTER_HALTON1, JITTER_UNIFORM, JITTER_HALTON_ND, JITTER_HALTON_ND_INV, JITTER_PRIMES,
- JITTER_PRIMES_INV, JITTER_GOLDEN, JITTER_EQUIDISTANT, JITTER_EQUIDISTANT_OFFSET, JITTER_SOBOL1) = range(11)
+ JITTER_PRIMES_INV, JITTER_GOLDEN, JITTER_EQUIDISTANT, JITTER_EQUIDISTANT_OFFSET, JITTER_SOBOL1,
+ JITTER_HALTON1_ITER) = range(12)
 (BUF_THETA, BUF_GRAD, BUF_LOGPI, BUF_LOGW, BUF_W, BUF_ANCESTORS, BUF_STEPS, BUF_P_FINAL,
  BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1) = range(14)
 
@@ -81,7 +82,6 @@ EXPORTS = {
     "smc_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "smc_get_plan": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP]),
     "smc_set_plan": (C.c_int, [C.c_void_p, C.c_int32]),
-    "smc_k_mma_peak": (C.c_int, [C.c_int64, _DP, C.c_void_p]),
     "smc_get_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
     "smc_destroy": (None, [C.c_void_p]),
@@ -101,6 +101,7 @@ EXPORTS = {
     "smc_k_normalise": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     "smc_k_resample_scratch_bytes": (C.c_int64, [C.c_int64]),
+    "smc_k_lookback_wait_check": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_k_resample": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
     "smc_k_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,

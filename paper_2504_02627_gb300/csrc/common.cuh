@@ -199,7 +199,8 @@ __device__ __forceinline__ double frac_rn(double x) { return __dsub_rn(x, floor(
 // frac((i + 1) sqrt(P_k)) / P_{K+1-k}; 7 golden ratio frac((iK + k)(sqrt 5 -
 // 1)/2); 8 equidistant (shuffle_k(i) + 1) / J; 9 offset equidistant: that +
 // 0.1 u (Philox block (1, i, k, JITTER)); 10 1-d Sobol: radical inverse base
-// 2 of the Gray code of iK + k.  primes[m - 1] is the m-th prime (schemes
+// 2 of the Gray code of iK + k; 11 1-d Halton in iteration-major order, base 2
+// radical inverse of (k - 1) J + i + 1.  primes[m - 1] is the m-th prime (schemes
 // 3-6, which reuse their K dimensions cyclically past iteration K).  Every
 // FP64 operation is rounded once, in the order written.
 __device__ __forceinline__ double jitter_h(int32_t scheme, uint64_t seed, int64_t i, int64_t k, int64_t J,
@@ -236,6 +237,7 @@ __device__ __forceinline__ double jitter_h(int32_t scheme, uint64_t seed, int64_
             const uint32_t n = (uint32_t)(i * K + k);
             return halton2(n ^ (n >> 1));
         }
+        case 11: return halton2((uint32_t)((k - 1) * J + i + 1));
         default: return 1.0;
     }
 }

@@ -349,7 +349,7 @@ std::string check_config(const smc_config& c) {
     if (!(c.step_size > 0.0) || !std::isfinite(c.step_size)) return "step_size must be > 0";
     if (!(c.traj_len0 > 0.0)) return "traj_len0 must be > 0";
     if (c.max_steps < 1 || c.max_steps > 65536) return "max_steps must be in [1, 65536]";
-    if (c.jitter < 0 || c.jitter > 10) return "jitter must be in [0, 10]";
+    if (c.jitter < 0 || c.jitter > 11) return "jitter must be in [0, 11]";
     if (jitter_needs_primes(c.jitter) && c.n_iters > MAX_JITTER_PRIME_INDEX)
         return "the N-d jitter schemes need n_iters <= 65536";
     if (c.accept_reject != 0 && c.accept_reject != 1) return "accept_reject must be 0 or 1";
@@ -1208,7 +1208,7 @@ smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps, in
 
 smc_status smc_k_jitter(int32_t scheme, uint64_t seed, int64_t J, int64_t K, int64_t k, double* out_h,
                         void* stream) {
-    if (scheme < 0 || scheme > 10 || J < 0 || J > (1ll << 30) || K < 1 || k < 1 || k > K) return SMC_E_INVAL;
+    if (scheme < 0 || scheme > 11 || J < 0 || J > (1ll << 30) || K < 1 || k < 1 || k > K) return SMC_E_INVAL;
     if (J > 0 && !out_h) return SMC_E_INVAL;
     if (J * K + k >= (1ll << 32)) return SMC_E_INVAL;
     if (jitter_needs_primes(scheme) && K > MAX_JITTER_PRIME_INDEX) return SMC_E_INVAL;
@@ -1280,6 +1280,12 @@ smc_status smc_k_resample(const double* W, int64_t N, uint64_t r64, uint64_t* q,
     if (N < 1 || N > (1ll << 30) || !W || !q || !ancestors || !status_out || !scratch) return SMC_E_INVAL;
     return kstatus(launch_resample_flat(W, N, r64, reinterpret_cast<unsigned long long*>(q), ancestors, status_out,
                                         scratch, static_cast<cudaStream_t>(stream)));
+}
+
+smc_status smc_k_lookback_wait_check(int64_t poll_limit, int32_t* status_out, void* scratch, void* stream) {
+    if (poll_limit < 1 || poll_limit > (1ll << 40) || !status_out || !scratch) return SMC_E_INVAL;
+    return kstatus(launch_lookback_wait_check((long long)poll_limit, reinterpret_cast<TileDesc*>(scratch),
+                                              status_out, static_cast<cudaStream_t>(stream)));
 }
 
 // ------------------------------------------------------------------ transport map

@@ -167,10 +167,64 @@ __device__ __forceinline__ unsigned long long systematic_count(unsigned long lon
     return c < N ? c : N;
 }
 
+// Decoupled look-back of tile g (thread 0 only): publishes the tile's
+// aggregate, walks back over the predecessors of its run (tiles first .. g-1)
+// summing aggregates until an inclusive prefix, and publishes its own
+// inclusive prefix.  Every wait on a predecessor is bounded: after `limit`
+// polls without progress it gives up, sets *failed (the caller has already
+// stored the run's error status, which is ordered before the publication) and
+// returns the partial sum; the tile still publishes, so no successor waits
+// forever.  Returns the exclusive prefix of the tile.
+__device__ unsigned long long lookback_prefix(TileDesc* tiles, int64_t g, int64_t first, unsigned int epoch,
+                                              unsigned long long tile_agg, long long limit, int* status,
+                                              bool& failed) {
+    TileDesc* me = tiles + g;
+    unsigned long long excl = 0ull;
+    failed = false;
+    if (g == first) {
+        me->incl = tile_agg;
+        __threadfence();
+        atomicExch(&me->flag, (epoch << 2) | 2u);
+        return 0ull;
+    }
+    me->agg = tile_agg;
+    __threadfence();
+    atomicExch(&me->flag, (epoch << 2) | 1u);
+    int64_t pred = g - 1;
+    long long spins = 0;
+    while (true) {
+        const volatile TileDesc* pd = tiles + pred;
+        const unsigned int f = pd->flag;
+        if ((f >> 2) == epoch && (f & 3u) != 0u) {
+            __threadfence();
+            if ((f & 3u) == 2u) {
+                excl += pd->incl;
+                break;
+            }
+            excl += pd->agg;
+            --pred;
+            spins = 0;
+            continue;
+        }
+        if (++spins > limit) {   // bounded wait: report, never hang
+            *(volatile int*)status = -5;
+            __threadfence();
+            failed = true;
+            break;
+        }
+        __nanosleep(64);
+    }
+    me->incl = excl + tile_agg;
+    __threadfence();
+    atomicExch(&me->flag, (epoch << 2) | 2u);
+    return excl;
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
     __shared__ unsigned int tile_s;
     __shared__ unsigned long long wsum[SCAN_THREADS / 32];
     __shared__ unsigned long long excl_s;
+    __shared__ int failed_s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) tile_s = atomicAdd(b.counter, 1u);
     __syncthreads();
@@ -231,45 +285,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample_scan(StepBufs b) {
 
     // look-back over predecessor tiles of the same run
     if (tid == 0) {
-        TileDesc* me = b.tiles + g;
-        unsigned long long excl = 0ull;
-        if (t_in_run == 0) {
-            me->incl = tile_agg;
-            __threadfence();
-            atomicExch(&me->flag, (epoch << 2) | 2u);
-        } else {
-            me->agg = tile_agg;
-            __threadfence();
-            atomicExch(&me->flag, (epoch << 2) | 1u);
-            int64_t pred = g - 1;
-            long long spins = 0;
-            while (true) {
-                const volatile TileDesc* pd = b.tiles + pred;
-                const unsigned int f = pd->flag;
-                if ((f >> 2) == epoch && (f & 3u) != 0u) {
-                    __threadfence();
-                    if ((f & 3u) == 2u) {
-                        excl += pd->incl;
-                        break;
-                    }
-                    excl += pd->agg;
-                    --pred;
-                    spins = 0;
-                    continue;
-                }
-                if (++spins > LOOKBACK_SPIN_LIMIT) {   // bounded wait: report, never hang
-                    st.status = -5;
-                    break;
-                }
-                __nanosleep(64);
-            }
-            me->incl = excl + tile_agg;
-            __threadfence();
-            atomicExch(&me->flag, (epoch << 2) | 2u);
-        }
-        excl_s = excl;
+        bool failed;
+        excl_s = lookback_prefix(b.tiles, g, rp.tile0, epoch, tile_agg, LOOKBACK_SPIN_LIMIT, &st.status, failed);
+        // a run whose look-back gave up anywhere (here or in a predecessor,
+        // whose status store precedes its publication) gets no resampling from
+        // this tile on: identity source indices for the tile's own slots
+        failed_s = failed || *(volatile int*)&st.status != 0;
     }
     __syncthreads();
+    if (failed_s) {
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const int64_t i = base + (int64_t)k * SCAN_THREADS + tid;
+            if (i < rp.n) {
+                b.anc[rp.off + i] = (int32_t)i;
+                if (b.src) b.src[rp.off + i] = (int32_t)(rp.off + i);
+            }
+        }
+        return;
+    }
     const unsigned long long off = excl_s + thread_excl;
     // systematic: particle i of the run owns output slots [cnt(C_{i-1}),
     // cnt(C_i)); multinomial: the prefix is kept for k_multinomial_search
@@ -864,6 +897,25 @@ __global__ void __launch_bounds__(RUN_THREADS) k_quantise_flat(const double* W, 
 }
 
 __global__ void k_copy_status(const FlatScratch* fs, int32_t* status) { *status = fs->st.status; }
+
+// The look-back wait of the resampling scan against a predecessor that never
+// publishes: tile 1 of a two-tile run whose tile 0 descriptor holds no flag
+// of the current epoch, with the caller's poll limit; the wait must give up
+// and report -5 in *status (device), never hang.
+__global__ void k_lookback_wait_check(TileDesc* tiles, long long limit, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    tiles[0].flag = 0u;   // epoch 0, not ready: nothing will ever publish it
+    tiles[0].agg = tiles[0].incl = 0ull;
+    *status = 0;
+    __threadfence();
+    bool failed;
+    (void)lookback_prefix(tiles, 1, 0, 1u, 1ull, limit, status, failed);
+    if (!failed) *status = 1;   // cannot happen: the predecessor never publishes
+}
+cudaError_t launch_lookback_wait_check(long long limit, TileDesc* tiles, int* status, cudaStream_t s) {
+    k_lookback_wait_check<<<1, 32, 0, s>>>(tiles, limit, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_resample_flat(const double* W, int64_t N, uint64_t r64, unsigned long long* q,
                                  int32_t* anc, int32_t* status, void* scratch, cudaStream_t s) {

@@ -80,6 +80,7 @@ cudaError_t launch_init_draw(const StepBufs& b, float* theta, cudaStream_t s);
 cudaError_t launch_init_finish(const StepBufs& b, const double* logpi, cudaStream_t s);
 cudaError_t launch_weights_steps(const StepBufs& b, cudaStream_t s);
 cudaError_t launch_resample_scan(const StepBufs& b, cudaStream_t s);
+cudaError_t launch_lookback_wait_check(long long limit, TileDesc* tiles, int* status, cudaStream_t s);
 cudaError_t launch_sort(const StepBufs& b, cudaStream_t s);
 cudaError_t launch_move_stats(const StepBufs& b, cudaStream_t s);
 constexpr int KERNELS_PER_ITERATION = 7;   // kernels launched by one smc_step

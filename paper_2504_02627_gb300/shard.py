@@ -17,7 +17,8 @@ particles at once.
 
 On one GPU per box the library runs independent replicas instead; this
 module is the tested design of the exchange (the normalisation partials,
-an all-gather of two integers, one all-to-all of pairs, one row exchange).
+an all-gather of two integers, one all-to-all of pairs, one all-to-all of
+row requests and one of rows: a rank receives only what is addressed to it).
 """
 from __future__ import annotations
 
@@ -96,12 +97,30 @@ def systematic_shard(q_local, r64: int, dist) -> np.ndarray:
         for o in range(lo, hi):
             r = int(np.searchsorted(out_lo, o, side="right") - 1)
             pairs[r].append((o, p_off + j))
-    everyone = [None] * world
-    dist.all_gather_object(everyone, pairs)
-    mine = sorted(p for lists in everyone for p in lists[rank])
-    anc = np.array([a for _, a in mine], dtype=np.int64)
-    assert len(anc) == ns[rank] and all(o == out_lo[rank] + i for i, (o, _) in enumerate(mine))
+    flat = [np.asarray(pr, dtype=np.int64).reshape(-1, 2) for pr in pairs]
+    got = _all_to_all(flat, 2, np.int64, dist)          # the pairs of the slots this rank owns
+    mine = got[np.argsort(got[:, 0], kind="stable")]
+    anc = mine[:, 1].copy()
+    assert len(anc) == ns[rank] and np.array_equal(mine[:, 0], out_lo[rank] + np.arange(ns[rank]))
     return anc
+
+
+def _all_to_all(blocks, width, dtype, dist):
+    """Point-to-point exchange: blocks[r] ([k_r, width] rows) goes to rank r;
+    returns the rows every rank sent to this one, in sender order.  One
+    all-to-all of the row counts, then one of the rows themselves, so a rank
+    receives only what is addressed to it."""
+    import torch
+    world = dist.get_world_size()
+    send_counts = torch.tensor([len(b) for b in blocks], dtype=torch.int64)
+    recv_counts = torch.empty(world, dtype=torch.int64)
+    dist.all_to_all_single(recv_counts, send_counts)
+    rc = [int(x) for x in recv_counts]
+    send = torch.from_numpy(np.concatenate([np.asarray(b, dtype=dtype).reshape(-1, width) for b in blocks])
+                            .reshape(-1).copy())
+    recv = torch.empty(sum(rc) * width, dtype=send.dtype)
+    dist.all_to_all_single(recv, send, [c * width for c in rc], [len(b) * width for b in blocks])
+    return recv.numpy().reshape(-1, width)
 
 
 def gather_rows(rows_local: np.ndarray, anc: np.ndarray, dist) -> np.ndarray:
@@ -112,13 +131,28 @@ def gather_rows(rows_local: np.ndarray, anc: np.ndarray, dist) -> np.ndarray:
     ns, _ = _layout(len(rows_local), 0, dist)
     lo = np.cumsum([0] + ns)
     owner = np.searchsorted(lo, anc, side="right") - 1
-    want = [sorted(set(int(a) for a in anc[owner == r])) for r in range(world)]
-    asks = [None] * world
-    dist.all_gather_object(asks, want)                 # asks[r][s]: what rank r needs from rank s
-    give = {r: {i: rows_local[i - lo[rank]] for i in asks[r][rank]} for r in range(world)}
-    got = [None] * world
-    dist.all_gather_object(got, give)                  # got[s][rank]: rows rank s sends to this rank
+    want = [np.unique(anc[owner == r]).astype(np.int64) for r in range(world)]
+    asks = _all_to_all([w.reshape(-1, 1) for w in want], 1, np.int64, dist)[:, 0]   # indices others need from me
+    # the asked rows, in the order the asks arrived (sender by sender)
+    recv_counts = _ask_counts(want, dist)
+    off = np.cumsum([0] + recv_counts)
+    D = rows_local.shape[1] if rows_local.ndim == 2 else 0
+    give = [rows_local[asks[off[r]:off[r + 1]] - lo[rank]] for r in range(world)]
+    rows = _all_to_all(give, D, rows_local.dtype, dist)   # sender order = owner order, each sorted as asked
     table = {}
-    for s in range(world):
-        table.update(got[s][rank])
+    k = 0
+    for r in range(world):
+        for i in want[r]:
+            table[int(i)] = rows[k]
+            k += 1
     return np.stack([table[int(a)] for a in anc]) if len(anc) else rows_local[:0]
+
+
+def _ask_counts(want, dist):
+    """How many rows each rank asked this one for (the counts of the ask exchange)."""
+    import torch
+    world = dist.get_world_size()
+    send = torch.tensor([len(w) for w in want], dtype=torch.int64)
+    recv = torch.empty(world, dtype=torch.int64)
+    dist.all_to_all_single(recv, send)
+    return [int(x) for x in recv]

@@ -46,7 +46,7 @@ def test_normals_match_oracle(D):
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("scheme", range(11))
+@pytest.mark.parametrize("scheme", range(12))
 @pytest.mark.parametrize("J,K", [(1000, 50), (37, 9)])
 def test_jitter_schemes_bit_exact(scheme, J, K):
     """The jitter schemes of Sec. 3.2.1 (smc_k_jitter): every h bit-exact
@@ -154,7 +154,10 @@ def _summand_scale(w, th):
         mu, logtau, eta = th[:, :1], th[:, 1:2], th[:, 2:]
         tau = np.exp(logtau)
         # the residual ybar - (mu + tau eta) cancels near the posterior: bound
-        # its FP32 error by the magnitudes of its operands
+        # its FP32 error by the magnitudes of its operands, each counted once
+        # per rounding it goes through -- ybar and mu enter the two sums once,
+        # tau eta carries the error of expf (within 2 ulp in CUDA's
+        # documentation) plus the rounding of the product: 3 units
         dev_ops = np.abs(w["ybar"][None, :]) + np.abs(mu) + 3.0 * np.abs(tau * eta)
         r = w["n_g"][None, :] * dev_ops / w["sigma"] ** 2
         gs = np.concatenate([r.sum(1, keepdims=True) + np.abs(mu),
@@ -415,17 +418,6 @@ def test_tc_one_leapfrog_step(name, eps, N, precision):
     # the end-point energy is exact to FP32 accuracy at the GPU's own end point
     lp_at_g, _ = oracle.logpi(t, th_g)
     assert np.all(np.abs(lp_g - lp_at_g) <= 1e-5 * ls1)
-
-
-def test_warp_mma_ceiling_probe():
-    """smc_k_mma_peak measures the warp-level BF16 MMA rate the warp-MMA
-    trajectory kernels are held against: finite, and between a tenth of and
-    the full dense BF16 rate of the part."""
-    import ctypes as C
-    v = C.c_double()
-    assert g.lib().smc_k_mma_peak(1 << 12, C.byref(v), stream()) == 0
-    assert np.isfinite(v.value) and 100.0 < v.value < 2500.0, v.value
-    assert g.lib().smc_k_mma_peak(0, C.byref(v), stream()) != 0
 
 
 @pytest.mark.parametrize("name,N,eps", [("banana50", 8192, 0.05), ("hier", 278_000, 0.01)])

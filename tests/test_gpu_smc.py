@@ -411,7 +411,7 @@ def test_multinomial_resampling_bit_exact(N):
     smp.close()
 
 
-@pytest.mark.parametrize("scheme", [2, 3, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("scheme", [2, 3, 6, 7, 8, 9, 10, 11])
 def test_sampler_jitter_schemes_step_counts(scheme):
     """The sampler's step counts under each jitter scheme (Sec. 3.2.1) are
     bit-exact against the oracle's h with the GPU's L (gauss10, a ragged

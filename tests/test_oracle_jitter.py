@@ -8,6 +8,9 @@ other than itself:
 * N-d primes and the golden-ratio sequence against a 50-digit evaluation of
   frac(n x) within the rounding bound of the FP64 evaluation;
 * 1-d Sobol against scipy's unscrambled one-dimensional Sobol sequence;
+* 1-d Halton in both orders of its J x K index matrix (particle-major, scheme
+  1, and iteration-major, scheme 11) against scipy's unscrambled
+  one-dimensional Halton sequence reshaped the two ways;
 * uniform: a chi-square test; equidistant: every column a permutation of
   {1..J}/J, different per iteration; offset equidistant: within [0, 0.1) of
   it;
@@ -49,6 +52,18 @@ def test_halton_nd_matches_scipy_and_inverse_reverses():
     np.testing.assert_allclose(H, ref, rtol=0, atol=1e-15)
     Hi = oracle.jitter_matrix(oracle.JITTER["halton_nd_inv"], 5, J, K)
     np.testing.assert_array_equal(Hi, H[:, ::-1])
+
+
+def test_halton1_both_index_orders_match_scipy():
+    J, K = 48, 10
+    ref = stats.qmc.Halton(d=1, scramble=False).random(J * K + 1)[1:, 0]   # points n = 1 .. J K
+    H1 = oracle.jitter_matrix(oracle.JITTER["halton1"], 5, J, K)
+    np.testing.assert_array_equal(H1, ref.reshape(J, K))                # n = j K + k
+    H11 = oracle.jitter_matrix(oracle.JITTER["halton1_iter"], 5, J, K)
+    np.testing.assert_array_equal(H11, ref.reshape(K, J).T)             # n = (k - 1) J + j + 1
+    # iteration-major: each iteration's J values are a stratified sample of (0, 1)
+    for k in range(K):
+        assert np.all(np.histogram(H11[:, k], bins=16, range=(0, 1))[0] == J // 16)
 
 
 def _frac_hp(n, x_dec):
@@ -104,7 +119,7 @@ def test_uniform_and_equidistant():
                                       np.arange(J2))
 
 
-@pytest.mark.parametrize("scheme", range(11))
+@pytest.mark.parametrize("scheme", range(12))
 def test_sampler_step_counts_follow_the_scheme(scheme):
     t = oracle.TargetSpec.gauss_dense(np.zeros(3), np.eye(3))
     cfg = oracle.SMCConfig(n_particles=64, n_iters=4, n_warmup=2, step_size=0.1, traj_len0=1.0,

@@ -45,8 +45,10 @@ def _run(entry, W, r64):
 def test_noalloc_matches_allocating_entry_on_two_calls_in_a_row():
     need_gpu()
     # the second call is smaller than the first, so stale descriptors of the
-    # first call remain in the fixed scratch when it runs
-    for N, seed, r64 in ((70001, 1, 0x9E3779B97F4A7C15), (5000, 2, 12345)):
+    # first call remain in the fixed scratch when it runs; the third is larger
+    # than the second, and the last one uses the whole advertised maximum
+    for N, seed, r64 in ((70001, 1, 0x9E3779B97F4A7C15), (5000, 2, 12345), (300007, 3, 2**63 + 7),
+                         (B.NOALLOC_MAX_N, 4, 987654321)):
         W = _weights(N, seed)
         q0, a0, s0 = _run("alloc", W, r64)
         q1, a1, s1 = _run("noalloc", W, r64)
@@ -61,3 +63,11 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     one = ctypes.c_void_p(8)
     assert lib.smc_k_resample_noalloc(one, B.NOALLOC_MAX_N + 1, 1, one, one, one, None) == -1
     assert lib.smc_k_resample_noalloc(one, 0, 1, one, one, one, None) == -1
+
+
+def test_noalloc_scratch_holds_the_advertised_maximum():
+    # the fixed array is 64 KiB; the layout the scan uses must fit it for every
+    # N up to the maximum (a host-side size query, no GPU needed)
+    lib = g.lib()
+    assert lib.smc_k_resample_scratch_bytes(B.NOALLOC_MAX_N) <= 65536
+    assert lib.smc_k_resample_scratch_bytes(B.NOALLOC_MAX_N + 1) >= lib.smc_k_resample_scratch_bytes(B.NOALLOC_MAX_N)
