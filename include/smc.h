@@ -383,7 +383,7 @@ smc_status smc_k_steps(int64_t N, int64_t K, int64_t k, double L, double eps,
                        void* stream);
 
 /* Jitter h of particles j = 0..J-1 (the paper's j - 1) at iteration k (1 <= k
- * <= K) under scheme 0..10 (Sec. 3.2.1; the list at smc_config.jitter), as the
+ * <= K) under scheme 0..11 (Sec. 3.2.1; the list at smc_config.jitter), as the
  * sampler computes it: out_h [J] f64, device.  For j (0-based), iteration k:
  *   1 1-d Halton: radical inverse base 2 of n = j*K + k;
  *   2 uniform: (m + 1/2) 2^-52, m the 52-bit integer of words 0, 1 of Philox

@@ -115,9 +115,13 @@ def test_degenerate_target_reports_status():
 
 def test_table1_shape_gaussian_1d_halton():
     """Sec. 4 'Gaussian' with 1-d Halton: the paper prints 8.01 gradient
-    evaluations per particle and J_eff per evaluation 0.125 (Table 1).  With
-    this project's Adam constants the adapted trajectory is longer; the check
-    only bounds the ratio (statistical, parity unpinned for the constants)."""
+    evaluations per particle and J_eff per evaluation 0.125 (Table 1).  The
+    Adam constants are not given by the paper; over Adam rates 0.025 to 0.25,
+    both readings of the J x K Halton index order, Adam descent and the
+    printed initial momentum in the ChEES estimate, none brings the adapted
+    trajectory down to the paper's (this oracle gives about 19 gradients per
+    particle at the default rate 0.025), so the check only bounds the ratio
+    (statistical; parity unpinned for the constants)."""
     with open(os.path.join(os.path.dirname(__file__), "golden", "table1_1d_halton.json")) as f:
         gold = json.load(f)
     ge_paper = gold["grad_evals_per_particle"]["gaussian_5d"]
