@@ -15,6 +15,7 @@ import ctypes as C
 import os
 import subprocess
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -63,7 +64,8 @@ class Config(C.Structure):
                 ("init_scale", C.c_double), ("flow_train_every", C.c_int32), ("flow_epochs", C.c_int32),
                 ("flow_lr", C.c_double), ("flow_min_ess", C.c_double),
                 ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double),
-                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32)]
+                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32),
+                ("init_mean", C.POINTER(C.c_double)), ("init_chol", C.POINTER(C.c_double))]
 
 
 class Stats(C.Structure):
@@ -409,14 +411,25 @@ class SMCConfig:
     step_adapt_target: float = 0.651
     resample_scheme: int = 0          # 0 systematic, 1 multinomial (the paper's choice)
     mcmc: int = 0                     # 1: Algorithm 2 as independent chains (no weights)
+    init_mean: Optional[np.ndarray] = None   # q_init = N(init_mean, init_chol init_chol^T)
+    init_chol: Optional[np.ndarray] = None   # lower-triangular [D, D]; None: init_scale * I
 
     def struct(self):
-        return Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
-                      self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
-                      self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
-                      self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
-                      self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess,
-                      self.step_adapt_rate, self.step_adapt_target, self.resample_scheme, self.mcmc)
+        cs = Config(self.n_particles, self.n_iters, self.n_warmup, self.step_size,
+                    self.traj_len0, self.max_steps, self.ess_frac, self.seed & (2**64 - 1),
+                    self.jitter, self.accept_reject, self.adapt, self.chees_initial_p,
+                    self.adam_lr, self.adam_b1, self.adam_b2, self.adam_eps, self.init_scale,
+                    self.flow_train_every, self.flow_epochs, self.flow_lr, self.flow_min_ess,
+                    self.step_adapt_rate, self.step_adapt_target, self.resample_scheme, self.mcmc)
+        keep = []
+        for name in ("init_mean", "init_chol"):
+            a = getattr(self, name)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                setattr(cs, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+        cs._keep = keep          # the arrays live as long as the struct
+        return cs
 
 
 def stats_to_dicts(arr):

@@ -218,6 +218,16 @@ typedef struct {
                                  importance weights (log w = 0 from the start,
                                  so J_eff = J and nothing resamples), the
                                  Metropolis select of accept_reject, log Z = 0 */
+    /* A general Gaussian initial distribution q_init = N(m, L L^T) (the paper
+     * leaves q_init to the user; its experiments use N(0, I), Sec. 4).  Either
+     * pointer may be NULL: m = 0, L = init_scale * I.  With either given,
+     * theta_0 = m + L z with z the same standard normals as the isotropic
+     * draw, each component summed in the order m_d + L_d0 z_0 + ... + L_dd z_d,
+     * and log q_init = -|z|^2 / 2 - (D/2 log 2 pi + sum_d log L_dd), the
+     * log-determinant summed over d in order. */
+    const double* init_mean;  /* [D], or NULL                                   */
+    const double* init_chol;  /* [D x D] row-major, lower-triangular, positive
+                                 diagonal (the upper triangle is not read), or NULL */
 } oracle_config;
 
 typedef struct {

@@ -37,20 +37,42 @@ static double lse(const double* a, int64_t N) {
 
 double oracle_smc_init(const oracle_target* t, const oracle_config* c, double* theta,
                        double* grad, double* logpi, double* logw, int32_t nthreads) {
-    /* theta_0^j ~ q_init = N(0, s^2 I); w_1^j = pi(theta_0^j) / q_init(theta_0^j). */
+    /* theta_0^j ~ q_init = N(0, s^2 I), or N(m, L L^T) when the config gives
+     * a mean or a Cholesky factor; w_1^j = pi(theta_0^j) / q_init(theta_0^j). */
     const int64_t N = c->n_particles, D = t->D;
     const double s = c->init_scale;
+    const int general = c->init_mean != 0 || c->init_chol != 0;
+    double logdet = 0.0;     /* log |det L| = sum_d log L_dd */
+    if (general) {
+        if (c->init_chol)
+            for (int64_t d = 0; d < D; ++d) logdet += log(c->init_chol[d * D + d]);
+        else
+            logdet = (double)D * log(s);
+    }
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t j = 0; j < N; ++j) {
         double* th = theta + j * D;
         oracle_normals(c->seed, ORACLE_TAG_INIT, 0u, (uint32_t)j, D, th);
         double zz = 0.0;
-        for (int64_t d = 0; d < D; ++d) {
-            zz += th[d] * th[d];
-            th[d] *= s;
+        for (int64_t d = 0; d < D; ++d) zz += th[d] * th[d];
+        double logq;
+        if (!general) {
+            for (int64_t d = 0; d < D; ++d) th[d] *= s;
+            logq = -0.5 * zz - 0.5 * (double)D * (LOG_2PI + 2.0 * log(s));
+        } else {
+            /* theta = m + L z, component d from the highest index down so
+             * that z_e (e <= d) is still unmodified when it is read */
+            for (int64_t d = D - 1; d >= 0; --d) {
+                double acc = c->init_mean ? c->init_mean[d] : 0.0;
+                for (int64_t e = 0; e <= d; ++e) {
+                    const double l = c->init_chol ? c->init_chol[d * D + e] : (e == d ? s : 0.0);
+                    acc += l * th[e];
+                }
+                th[d] = acc;
+            }
+            logq = -0.5 * zz - (0.5 * (double)D * LOG_2PI + logdet);
         }
-        double logq = -0.5 * zz - 0.5 * (double)D * (LOG_2PI + 2.0 * log(s));
         double lp = oracle_logpi(t, th, grad + j * D);
         logpi[j] = lp;
         logw[j] = c->mcmc ? 0.0 : (isfinite(lp) ? lp - logq : -INFINITY);
