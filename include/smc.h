@@ -163,6 +163,19 @@ typedef struct {
                                    weight (log w = 0, J_eff = J, nothing resamples),
                                    every move takes the Metropolis select of
                                    accept_reject, log Z stays 0               */
+    /* Optional Gaussian initial distribution q_init = N(m, L L') (Algorithm 3
+     * weights the first population by w_1 = pi / q_init; the paper's
+     * experiments use N(0, I), Sec. 4).  Host pointers, read and copied by
+     * smc_init / smc_init_batch only (the caller keeps ownership; later calls,
+     * smc_reset included, use the copies).  NULL: m = 0, L = init_scale * I.
+     * With either given, theta_0 = m + L z (z the same standard normals as the
+     * isotropic draw; component d summed as m_d + L_d0 z_0 + ... + L_dd z_d in
+     * FP64, then rounded to FP32) and log q_init = -|z|^2/2 - (dim/2 log 2 pi
+     * + sum_d log L_dd).  Errors (SMC_E_INVAL): a non-finite mean, or a factor
+     * whose diagonal is not positive and finite or whose lower triangle is
+     * not finite.  The upper triangle is not read. */
+    const double* init_mean;    /* [dim] f64, or NULL                              */
+    const double* init_chol;    /* [dim x dim] f64 row-major lower-triangular, or NULL */
 } smc_config;
 
 typedef struct {

@@ -42,7 +42,8 @@ class SmcConfig(C.Structure):
                 ("adam_b1", C.c_double), ("adam_b2", C.c_double), ("adam_eps", C.c_double),
                 ("init_scale", C.c_double), ("precision", C.c_int32), ("pad", C.c_int32),
                 ("step_adapt_rate", C.c_double), ("step_adapt_target", C.c_double),
-                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32)]
+                ("resample_scheme", C.c_int32), ("mcmc", C.c_int32),
+                ("init_mean", _DP), ("init_chol", _DP)]
 
 
 class SmcFlowConfig(C.Structure):
@@ -188,13 +189,25 @@ class ModelData:
 def make_config(n_particles, n_iters, n_warmup, step_size, traj_len0=5.0, max_steps=500, jitter=1,
                 ess_frac=0.5, seed=1000, adapt=1, adam_lr=0.025, adam_b1=0.9, adam_b2=0.999,
                 adam_eps=1e-8, init_scale=1.0, precision=PREC_FP32, accept_reject=0,
-                step_adapt_rate=0.0, step_adapt_target=0.651, resample_scheme=0, mcmc=0) -> SmcConfig:
-    return SmcConfig(int(n_particles), int(n_iters), int(n_warmup), float(step_size), float(traj_len0),
-                     int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), int(accept_reject),
-                     int(adapt),
-                     float(adam_lr), float(adam_b1), float(adam_b2), float(adam_eps), float(init_scale),
-                     int(precision), 0, float(step_adapt_rate), float(step_adapt_target),
-                     int(resample_scheme), int(mcmc))
+                step_adapt_rate=0.0, step_adapt_target=0.651, resample_scheme=0, mcmc=0,
+                init_mean=None, init_chol=None) -> SmcConfig:
+    """An smc_config.  init_mean [D] / init_chol [D, D] (lower-triangular)
+    give q_init = N(init_mean, init_chol init_chol^T); the arrays are kept
+    alive with the struct and copied by smc_init."""
+    c = SmcConfig(int(n_particles), int(n_iters), int(n_warmup), float(step_size), float(traj_len0),
+                  int(max_steps), int(jitter), float(ess_frac), int(seed) & (2**64 - 1), int(accept_reject),
+                  int(adapt),
+                  float(adam_lr), float(adam_b1), float(adam_b2), float(adam_eps), float(init_scale),
+                  int(precision), 0, float(step_adapt_rate), float(step_adapt_target),
+                  int(resample_scheme), int(mcmc))
+    keep = []
+    for name, a in (("init_mean", init_mean), ("init_chol", init_chol)):
+        if a is not None:
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            setattr(c, name, a.ctypes.data_as(_DP))
+    c._keep = keep
+    return c
 
 
 def stats_dicts(arr):
@@ -209,6 +222,7 @@ class Sampler:
         cfgs = configs if isinstance(configs, (list, tuple)) else [configs]
         self.n_runs = len(cfgs)
         self._cfg = (SmcConfig * self.n_runs)(*cfgs)
+        self._cfg_keep = [getattr(c, "_keep", None) for c in cfgs]   # initial-distribution arrays
         h = C.c_void_p()
         if self.n_runs == 1:
             st = lib().smc_init(C.byref(h), self._cfg, C.byref(model.struct), C.c_void_p(stream))

@@ -34,7 +34,10 @@ struct RunParams {
     double step_rate;       // optional warm-up step-size rule: log eps += step_rate (a_h - step_target)
     double step_target;
     int32_t mcmc;           // 1: Algorithm 2 as independent chains (no importance weights)
-    int32_t pad;
+    int32_t init_general;   // 1: q_init = N(init_mean, init_chol init_chol') (either may be null)
+    const double* init_mean;    // [D] device copy, or null (0)
+    const double* init_chol;    // [D x D] device copy, row-major lower-triangular, or null (init_scale I)
+    double init_logdet;     // sum_d log L_dd (D log init_scale without a factor)
 };
 
 constexpr int SLICE = 128;  // particles per CTA in the weight / statistics kernels (four warps:

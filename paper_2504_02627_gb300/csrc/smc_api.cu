@@ -137,7 +137,8 @@ struct smc_handle {
     int64_t iters_done = 0;
     int sticky = 0;
     std::string err;
-    std::vector<smc_config> cfg;
+    std::vector<smc_config> cfg;       // init_mean / init_chol cleared: they were the caller's
+    std::vector<std::vector<double>> init_host;   // staged copies of the initial distributions
     // profiling: events around trajectory launches, launch counter
     bool profiling = false;
     // CUDA graph of two consecutive iterations (buffer parity 0 -> 1 -> 0)
@@ -361,6 +362,21 @@ std::string check_config(const smc_config& c) {
     if (c.step_adapt_rate > 0.0 && !(c.step_adapt_target > 0.0 && c.step_adapt_target < 1.0))
         return "step_adapt_target must be in (0, 1)";
     if (c.precision < 0 || c.precision > 4) return "unknown precision";
+    return "";
+}
+
+// The optional Gaussian initial distribution N(m, L L') of one run.
+std::string check_init_dist(const smc_config& c, int64_t D) {
+    if (c.init_mean)
+        for (int64_t d = 0; d < D; ++d)
+            if (!std::isfinite(c.init_mean[d])) return "init_mean must be finite";
+    if (c.init_chol)
+        for (int64_t d = 0; d < D; ++d) {
+            const double l = c.init_chol[d * D + d];
+            if (!(l > 0.0) || !std::isfinite(l)) return "init_chol needs a positive, finite diagonal";
+            for (int64_t e = 0; e < d; ++e)
+                if (!std::isfinite(c.init_chol[d * D + e])) return "init_chol must be finite";
+        }
     return "";
 }
 
@@ -591,6 +607,15 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         delete h;
         return SMC_E_INVAL;
     }
+    for (int64_t r = 0; r < n_runs; ++r) {
+        const std::string ei = check_init_dist(cfg[r], model->dim);
+        if (!ei.empty()) {
+            fprintf(stderr, "smc_init: run %lld: %s\n", (long long)r, ei.c_str());
+            h->model.mem.release();
+            delete h;
+            return SMC_E_INVAL;
+        }
+    }
     h->n_runs = n_runs;
     h->D = model->dim;
     h->K = cfg[0].n_iters;
@@ -625,6 +650,16 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         rp.step_rate = cfg[r].step_adapt_rate;
         rp.resample_scheme = cfg[r].resample_scheme;
         rp.step_target = cfg[r].step_adapt_target;
+        if (cfg[r].init_mean || cfg[r].init_chol) {
+            // log |det L| summed over d in order (D log s without a factor)
+            rp.init_general = 1;
+            double ldet = 0.0;
+            if (cfg[r].init_chol)
+                for (int64_t d = 0; d < model->dim; ++d) ldet += std::log(cfg[r].init_chol[d * model->dim + d]);
+            else
+                ldet = (double)model->dim * std::log(cfg[r].init_scale);
+            rp.init_logdet = ldet;
+        }
         rp.slice0 = (int32_t)slices;
         rp.n_slices = (int32_t)((rp.n + SLICE - 1) / SLICE);
         slices += rp.n_slices;
@@ -696,12 +731,41 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->done = A.get<unsigned int>((size_t)n_runs);
     h->dev_err = A.get<int>(1);
     if (h->precision == SMC_PREC_BF16C) h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs);
+    for (int64_t r = 0; r < n_runs; ++r) {
+        RunParams& rp = h->h_runs[(size_t)r];
+        const int64_t D = h->D;
+        if (cfg[r].init_mean) {
+            h->init_host.emplace_back(cfg[r].init_mean, cfg[r].init_mean + D);
+            rp.init_mean = A.get<double>((size_t)D);
+        }
+        if (cfg[r].init_chol) {
+            h->init_host.emplace_back(cfg[r].init_chol, cfg[r].init_chol + D * D);
+            rp.init_chol = A.get<double>((size_t)(D * D));
+        }
+    }
     if (A.err != cudaSuccess) {
         smc_status st = cuda_fail(h, A.err, "smc_init allocation");
         smc_destroy(h);
         return st;
     }
     cudaStream_t s = h->stream;
+    {
+        // the staged initial distributions, in the order they were staged
+        size_t k = 0;
+        for (int64_t r = 0; r < n_runs; ++r) {
+            const RunParams& rp = h->h_runs[(size_t)r];
+            if (cfg[r].init_mean) {
+                cudaMemcpyAsync(const_cast<double*>(rp.init_mean), h->init_host[k].data(),
+                                sizeof(double) * h->init_host[k].size(), cudaMemcpyHostToDevice, s);
+                ++k;
+            }
+            if (cfg[r].init_chol) {
+                cudaMemcpyAsync(const_cast<double*>(rp.init_chol), h->init_host[k].data(),
+                                sizeof(double) * h->init_host[k].size(), cudaMemcpyHostToDevice, s);
+                ++k;
+            }
+        }
+    }
     cudaMemcpyAsync(h->d_runs, h->h_runs.data(), sizeof(RunParams) * (size_t)n_runs, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(h->d_rstate, h_state.data(), sizeof(RunState) * (size_t)n_runs, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(h->d_run_of, run_of.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
@@ -719,6 +783,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     cudaMemsetAsync(h->p_final, 0, nd * sizeof(float), s);
 
     h->cfg.assign(cfg, cfg + n_runs);
+    for (smc_config& c : h->cfg) c.init_mean = c.init_chol = nullptr;   // the caller's memory
     cudaError_t ce = initial_draw(h);
     if (ce == cudaSuccess) ce = autotune(h);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);

@@ -12,7 +12,8 @@ constexpr int RUN_THREADS = 1024;
 constexpr double LOG_2PI = 1.8378770664093454835606594728112;
 
 // ============================================================ initial draw
-// theta_0 ~ q_init = N(0, s^2 I) (Eq. for theta_0), and log q_init(theta_0)
+// theta_0 ~ q_init = N(0, s^2 I) (Eq. for theta_0), or N(m, L L') when the
+// run has a general Gaussian initial distribution, and log q_init(theta_0)
 // parked in logw until the target has been evaluated.
 __global__ void k_init_draw(StepBufs b, float* theta) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -20,6 +21,32 @@ __global__ void k_init_draw(StepBufs b, float* theta) {
     const int r = b.run_of[j];
     const RunParams rp = b.runs[r];
     const uint32_t jl = (uint32_t)(j - rp.off);
+    if (rp.init_general) {
+        // theta_d = m_d + L_d0 z_0 + ... + L_dd z_d in FP64, added column by
+        // column (the same order for every d), every product and sum rounded
+        // on its own (no contraction), so the result is that of the plain
+        // sum written in this order
+        double acc[MAX_CHEES_DIM];
+        const int64_t D = b.D;
+        for (int64_t d = 0; d < D; ++d) acc[d] = rp.init_mean ? rp.init_mean[d] : 0.0;
+        double zz = 0.0;
+        for (int64_t e = 0; e < D; e += 2) {
+            double z[2];
+            normal_pair(rp.seed, (uint32_t)(e >> 1), jl, 0u, TAG_INIT, z[0], z[1]);
+            for (int u = 0; u < 2 && e + u < D; ++u) {
+                const int64_t c = e + u;
+                zz = __dadd_rn(zz, __dmul_rn(z[u], z[u]));
+                if (rp.init_chol) {
+                    for (int64_t d = c; d < D; ++d) acc[d] = __dadd_rn(acc[d], __dmul_rn(rp.init_chol[d * D + c], z[u]));
+                } else {
+                    acc[c] = __dadd_rn(acc[c], __dmul_rn(rp.init_scale, z[u]));
+                }
+            }
+        }
+        for (int64_t d = 0; d < D; ++d) theta[d * b.ld + j] = (float)acc[d];
+        b.logw[j] = __dsub_rn(-0.5 * zz, __dadd_rn(__dmul_rn(0.5 * (double)D, LOG_2PI), rp.init_logdet));
+        return;
+    }
     double zz = 0.0;
     for (int64_t d = 0; d < b.D; d += 2) {
         double z0, z1;

@@ -25,7 +25,9 @@
 // FP64 accumulation, as in every other kernel.
 //
 // Layout.  One CTA holds 128 particles (MMA M = 128).  X streams through a
-// three-stage ring of 128-observation tiles: [atom][128 obs rows][128 B], an
+// ring of up to four stages (as many as fit in shared memory next to the
+// deviations and the partial gradients) of 128-observation tiles:
+// [atom][128 obs rows][128 B], an
 // atom being 64 dimensions in the 128-byte swizzle.  GEMM1 reads a tile as its
 // K-major B operand (rows = observations); GEMM2 reads the same bytes as an
 // MN-major B operand (N = dimensions, K = observations: leading byte offset =
@@ -40,7 +42,11 @@
 // residuals from TMEM (warps 0-7 the even-numbered tiles of the pass
 // sequence, 8-15 the odd ones, each group of four half of a tile's
 // observations) and update the particle state, which lives in theta_out /
-// p_out during the move.  The sigmoid's exponential is the SFU's base-2
+// p_out during the move.  A residual thread reads eta in the 16-lane shape
+// (two observations of two particles per access) and writes the packed BF16
+// residuals in the matching 16x128b shape, which is GEMM2's K order; so one
+// shared-memory load of an observation pair's reference values serves four
+// particles.  The sigmoid's exponential is the SFU's base-2
 // exponential; one SFU reciprocal of the product (1 + 2^x0)(1 + 2^x1) serves
 // a pair of observations.
 //
@@ -123,7 +129,10 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <bool LOGIT>
+// MULTI: the handle has several runs, so a warp's particles may belong to
+// different runs (each with its own reference values); without it every
+// particle uses run 0's.
+template <bool LOGIT, bool MULTI>
 __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, TrajArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned base by pointer arithmetic on the shared array, so that
@@ -411,6 +420,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         const float hf = 0.5f * ef;
         const float kneg = -1.4426950408889634f;
         const float* gref = gref_s + run * dk;
+        // the runs of the four particles whose residuals this thread forms
+        // (quarter lanes g4, g4 + 8, g4 + 16, g4 + 24), and whether the
+        // warp's 32 particles all belong to one run
+        const int g4 = lane >> 2, tig = lane & 3;
+        int runq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) runq[k] = __shfl_sync(0xffffffffu, run, g4 + 8 * k);
+        const bool run_uni = __all_sync(0xffffffffu, run == __shfl_sync(0xffffffffu, run, 0)) != 0;
         int st = 0;
         uint32_t sph = 0, bph = 0;
         int64_t it = 0;
@@ -427,52 +444,84 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     tc::fence_after_sync();
                     const uint32_t ecol = tmem + lane_base + C_COL_ETA + (uint32_t)(bq * CC + 64 * half);
                     const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(bq * (CC / 2) + 32 * half);
-                    const float4* refs = reinterpret_cast<const float4*>(
-                        sm + L.off_stage + st * L.stage_bytes + L.tile_bytes + run * (CC * 8) + half * (64 * 8));
-                    // both halves of this warp's 64 eta columns are loaded up
-                    // front; the second arrives while the first is formed
-                    uint32_t v0[32], v1[32];
-                    tc::tmem_ld32_nowait(ecol, v0);
-                    tc::tmem_ld32_nowait(ecol + 32, v1);
+                    const unsigned char* refs0 =
+                        sm + L.off_stage + st * L.stage_bytes + L.tile_bytes + half * (64 * 8);
+                    // this thread forms the residuals of the quarter's lanes
+                    // g4, g4 + 8 (va) and g4 + 16, g4 + 24 (vb) for the
+                    // observation pairs 8 mm + 2 tig (+1), mm = 0..7, of the
+                    // half: one (c, s) load serves two observations of four
+                    // particles when they belong to one run
+                    uint32_t va[32], vb[32];
+                    tc::tmem_ld16x256_x8_nowait(ecol, va);
+                    tc::tmem_ld16x256_x8_nowait(ecol + (16u << 16), vb);
                     tc::tmem_wait_ld();
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&eta_empty[bq]);
-                    // each pair's packed BF16 residuals overwrite the pair's first
-                    // (already consumed) slot, so v[0..15] ends up holding the row.
                     // One SFU reciprocal serves both observations of a pair:
                     // 1 / q0 = q1 / (q0 q1), 1 / q1 = q0 / (q0 q1), with the
                     // exponents clamped so that q0 q1 < 2^121 (a sigmoid below
                     // 2^-60 is then taken as 2^-60, i.e. zero here).
-                    auto residuals = [&](uint32_t (&v)[32], int h) {
-#pragma unroll
-                        for (int e = 0; e < 32; e += 2) {
-                            float r0, r1;
-                            const float v0f = __uint_as_float(v[e]), v1f = __uint_as_float(v[e + 1]);
-                            if (LOGIT) {
-                                const float4 cs = refs[(32 * h + e) / 2];   // (c, s) of two observations
-                                const float x0 = fminf(fmaf(kneg, v0f, cs.x), C_X_MAX);
-                                const float x1 = fminf(fmaf(kneg, v1f, cs.z), C_X_MAX);
-                                const float q0 = 1.0f + tc::ex2_approx(x0);
-                                const float q1 = 1.0f + tc::ex2_approx(x1);
-                                const float rp = tc::rcp_approx(q0 * q1);
-                                r0 = fmaf(-q1, rp, cs.y);
-                                r1 = fmaf(-q0, rp, cs.w);
-                            } else {
-                                r0 = -inv_s2 * v0f;
-                                r1 = -inv_s2 * v1f;
-                            }
-                            v[e / 2] = pack_bf16(r0, r1);
+                    auto res_pair = [&](uint32_t e0, uint32_t e1, const float4& cs) -> uint32_t {
+                        const float v0f = __uint_as_float(e0), v1f = __uint_as_float(e1);
+                        float r0, r1;
+                        if (LOGIT) {
+                            const float x0 = fminf(fmaf(kneg, v0f, cs.x), C_X_MAX);
+                            const float x1 = fminf(fmaf(kneg, v1f, cs.z), C_X_MAX);
+                            const float q0 = 1.0f + tc::ex2_approx(x0);
+                            const float q1 = 1.0f + tc::ex2_approx(x1);
+                            const float rp = tc::rcp_approx(q0 * q1);
+                            r0 = fmaf(-q1, rp, cs.y);
+                            r1 = fmaf(-q0, rp, cs.w);
+                        } else {
+                            r0 = -inv_s2 * v0f;
+                            r1 = -inv_s2 * v1f;
                         }
+                        return pack_bf16(r0, r1);
                     };
-                    residuals(v0, 0);
+                    // each observation pair's packed residuals overwrite
+                    // already consumed registers: v[2 mm] (lane g4 or g4 + 16)
+                    // and v[2 mm + 1] (lane + 8), the order of the 16x128b store
+                    if (!MULTI || run_uni) {
+                        const float4* f = reinterpret_cast<const float4*>(refs0 + runq[0] * (CC * 8));
+#pragma unroll
+                        for (int mm = 0; mm < 8; ++mm) {
+                            const float4 cs = LOGIT ? f[4 * mm + tig] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            const uint32_t a0 = res_pair(va[4 * mm], va[4 * mm + 1], cs);
+                            const uint32_t a1 = res_pair(va[4 * mm + 2], va[4 * mm + 3], cs);
+                            const uint32_t b0 = res_pair(vb[4 * mm], vb[4 * mm + 1], cs);
+                            const uint32_t b1 = res_pair(vb[4 * mm + 2], vb[4 * mm + 3], cs);
+                            va[2 * mm] = a0;
+                            va[2 * mm + 1] = a1;
+                            vb[2 * mm] = b0;
+                            vb[2 * mm + 1] = b1;
+                        }
+                    } else {
+                        // particles of several runs: each lane pair its own (c, s)
+                        auto mixed = [&](uint32_t (&v)[32], int r0, int r1) {
+#pragma unroll
+                            for (int mm = 0; mm < 8; ++mm) {
+                                const int o = 4 * mm + tig;
+                                const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                                const float4 c0 =
+                                    LOGIT ? reinterpret_cast<const float4*>(refs0 + r0 * (CC * 8))[o] : z4;
+                                const float4 c1 =
+                                    LOGIT ? reinterpret_cast<const float4*>(refs0 + r1 * (CC * 8))[o] : z4;
+                                const uint32_t p0 = res_pair(v[4 * mm], v[4 * mm + 1], c0);
+                                const uint32_t p1 = res_pair(v[4 * mm + 2], v[4 * mm + 3], c1);
+                                v[2 * mm] = p0;
+                                v[2 * mm + 1] = p1;
+                            }
+                        };
+                        mixed(va, runq[0], runq[1]);
+                        mixed(vb, runq[2], runq[3]);
+                    }
                     // the buffer's previous residuals have been read by GEMM2
                     if (lane == 0) tc::mbar_wait_timed(&r_empty[bq], bph ^ 1u, err, abort_s);
                     __syncwarp();
                     tc::fence_after_sync();
-                    tc::tmem_st16_nowait(rcol, v0);
-                    residuals(v1, 1);
-                    tc::tmem_st16_nowait(rcol + 16, v1);
+                    tc::tmem_st16x128_x8_nowait(rcol, va);
+                    tc::tmem_st16x128_x8_nowait(rcol + (16u << 16), vb);
                     tc::tmem_wait_st();
                     tc::fence_before_sync();
                     __syncwarp();
@@ -863,7 +912,7 @@ cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s)
     const int64_t tiles = (a.N + CP - 1) / CP;
     TrajArgs a2 = a;
     a2.c_split = centred_split(m, a.N);
-    auto kern = traj_centred_kernel<LOGIT>;
+    auto kern = R > 1 ? traj_centred_kernel<LOGIT, true> : traj_centred_kernel<LOGIT, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
