@@ -52,7 +52,7 @@ def run_glm_like(args, streamed):
     torch, workloads, B = _setup()
     s = torch.cuda.current_stream().cuda_stream
     if streamed:
-        w = workloads.logistic_large(n=args.n)
+        w = workloads.logistic_large(n=args.n, D=args.dim)
         prec = B.PREC_BF16X2 if args.precision is None else args.precision
     else:
         w = workloads.logistic()
@@ -140,6 +140,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("which", choices=["stream", "flow", "glm", "gauss"])
     ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
+    ap.add_argument("--dim", type=int, default=100, help="coefficients of the streamed regression")
     ap.add_argument("--particles", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--eps", type=float, default=1e-4)

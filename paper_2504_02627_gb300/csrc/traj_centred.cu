@@ -76,7 +76,7 @@ constexpr int CC = CENTRED_CHUNK;           // observations per tile
 constexpr int C_EPI_WARPS = 16;
 constexpr int C_PRODUCER_WARP = 16, C_MMA1_WARP = 17, C_MMA2_WARP = 18;
 constexpr int C_THREADS = 32 * 19;
-constexpr int C_NS_MAX = 4;                 // X tile stages (4 when shared memory allows, else 3)
+constexpr int C_NS_MAX = 4;                 // X tile stages (4 when shared memory allows, else 3 or 2)
 constexpr int C_ATOM = CC * 128;            // one 64-dimension atom of a tile: 128 rows x 128 B
 constexpr int C_DATOM = CP * 128;           // one 64-dimension atom of the deviation operand
 constexpr uint32_t C_TMEM_COLS = 512;
@@ -86,12 +86,13 @@ constexpr float C_X_MAX = 60.0f;           // clamp of the exponent: two factors
 
 struct CLayout {
     int atoms, tile_bytes, ref_bytes, stage_bytes, stages;
-    int off_d, off_stage, off_gx, off_misc, off_cref, off_bar, total;
+    int off_d, off_stage, off_gx, off_emisc, off_cref, off_bar, total;
 };
 
 // Byte layout of the dynamic shared memory (from a 1024-aligned base) with
-// `stages` X tile stages.  The end-point pass reuses [0, off_misc) for
-// theta^T, two FP32 X chunks and the partial sums, so off_misc covers both uses.
+// `stages` X tile stages.  The end-point pass reuses [0, off_cref), the
+// pipeline's memory, for theta^T, two FP32 X chunks, the partial sums and
+// its kinetic / prior / likelihood parts, so off_cref covers both uses.
 __host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_run, int stages) {
     CLayout L;
     L.atoms = (dk + 63) / 64;
@@ -103,9 +104,14 @@ __host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_r
     L.off_stage = L.atoms * C_DATOM;
     L.off_gx = L.off_stage + stages * L.stage_bytes;     // [dk][128] f32 partial gradient of this CTA
     const int pipe = L.off_gx + dk * CP * 4;
+    // the end point reuses the pipeline's memory: theta^T, two X chunks and
+    // per-warp parts, then its kin, sq: [4][128] f64 and ll: [128] f64 (the
+    // prologue keeps its kinetic parts in the first stage, idle until the
+    // copies start)
     const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + C_EPI_WARPS * CP * 8;
-    L.off_misc = ((pipe > endp ? pipe : endp) + 1023) & ~1023;
-    L.off_cref = L.off_misc + 9 * CP * 8;                 // kin, sq: [4][128] f64; ll: [128] f64
+    L.off_emisc = (endp + 1023) & ~1023;
+    const int endx = L.off_emisc + 9 * CP * 8;
+    L.off_cref = ((pipe > endx ? pipe : endx) + 1023) & ~1023;
     L.off_bar = L.off_cref + 2 * n_run * dk * 4;          // reference points, reference gradients [runs][dk]
     L.total = L.off_bar + 256 + 1024;                     // + alignment slack of the base
     // more than half of the SM's shared memory, so that a second CTA, which
@@ -166,7 +172,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(gx_free + 1);
     int* smax_s = reinterpret_cast<int*>(tmem_s + 1);
     volatile int* abort_s = smax_s + 1;
-    double* kin_s = reinterpret_cast<double*>(sm + L.off_misc);      // [4][128] |p|^2 parts
+    double* kin0_s = reinterpret_cast<double*>(sm + L.off_stage);    // prologue: [4][128] |p_0|^2 parts
+    double* kin_s = reinterpret_cast<double*>(sm + L.off_emisc);     // end point: [4][128] |p|^2 parts
     double* sq_s = kin_s + 4 * CP;                                   // [4][128] |theta|^2 parts
     double* ll_s = sq_s + 4 * CP;                                    // [128] log-likelihood
     const uint32_t s_base = tc::smem_u32(sm);
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
 #pragma unroll
             for (int i = 0; i < 32; ++i) th[i] = 0.0f;
         }
-        if (epi) kin_s[q * CP + prow] = kin;
+        if (epi) kin0_s[q * CP + prow] = kin;
     }
     const float* cref = cref_s + run * dk;                // this particle's run reference point
     // deviation operand: unit u (8 dimensions) of this thread's 32 dimensions
@@ -309,7 +316,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     tc::cluster_sync();   // barriers of every CTA of the cluster initialised before any remote arrive
     double H0 = 0.0;
     if (epi && q == 0 && j >= 0 && !evalm)
-        H0 = 0.5 * (kin_s[prow] + kin_s[CP + prow] + kin_s[2 * CP + prow] + kin_s[3 * CP + prow]) - a.logpi_in[src];
+        H0 = 0.5 * (kin0_s[prow] + kin0_s[CP + prow] + kin0_s[2 * CP + prow] + kin0_s[3 * CP + prow]) -
+             a.logpi_in[src];
     __syncthreads();
     const uint32_t tmem = *tmem_s;
     const int smax = *smax_s;
@@ -544,13 +552,15 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             }
             named_sync(3u, 32u * C_EPI_WARPS);
             tc::fence_after_sync();
-            // publish this CTA's partial gradient (dims ds .. ds + 31)
+            // publish this CTA's partial gradient (dims ds .. ds + 31 below
+            // dk: with dk = 112 the last group holds only 16 rows of gx)
             if (ds < dk) {
                 uint32_t gv[32];
                 tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 32; ++e) gx[(ds + e) * CP + prow] = __uint_as_float(gv[e]);
+                for (int e = 0; e < 32; ++e)
+                    if (ds + e < dk) gx[(ds + e) * CP + prow] = __uint_as_float(gv[e]);
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -686,7 +696,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             sq += (double)tvv * (double)tvv;
         }
         sq_s[q * CP + prow] = sq;
-        kin_s[q * CP + prow] = kin;     // the initial parts were consumed by H0
+        kin_s[q * CP + prow] = kin;
     }
     auto issue_x = [&](int c, int buf) {
         const int64_t row0 = (int64_t)c * STREAM_CHUNK;
