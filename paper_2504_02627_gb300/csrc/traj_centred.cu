@@ -85,7 +85,7 @@ constexpr int C_SMEM_MAX = 232448;
 constexpr float C_X_MAX = 60.0f;           // clamp of the exponent: two factors 1 + 2^x multiply without overflow
 
 struct CLayout {
-    int atoms, tile_bytes, ref_bytes, stage_bytes, stages;
+    int atoms, tile_bytes, ref_bytes, stage_bytes, stages, xbufs;
     int off_d, off_stage, off_gx, off_emisc, off_cref, off_bar, total;
 };
 
@@ -93,8 +93,9 @@ struct CLayout {
 // `stages` X tile stages.  The end-point pass reuses [0, off_cref), the
 // pipeline's memory, for theta^T, two FP32 X chunks, the partial sums and
 // its kinetic / prior / likelihood parts, so off_cref covers both uses.
-__host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_run, int stages) {
+__host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_run, int stages, int xbufs) {
     CLayout L;
+    L.xbufs = xbufs;
     L.atoms = (dk + 63) / 64;
     L.tile_bytes = L.atoms * C_ATOM;
     L.ref_bytes = n_ref * CC * 8;                         // (c, s) pairs per run, a multiple of 1024
@@ -104,11 +105,11 @@ __host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_r
     L.off_stage = L.atoms * C_DATOM;
     L.off_gx = L.off_stage + stages * L.stage_bytes;     // [dk][128] f32 partial gradient of this CTA
     const int pipe = L.off_gx + dk * CP * 4;
-    // the end point reuses the pipeline's memory: theta^T, two X chunks and
-    // per-warp parts, then its kin, sq: [4][128] f64 and ll: [128] f64 (the
-    // prologue keeps its kinetic parts in the first stage, idle until the
-    // copies start)
-    const int endp = dk * CP * 4 + 2 * STREAM_CHUNK * Dp * 4 + C_EPI_WARPS * CP * 8;
+    // the end point reuses the pipeline's memory: theta^T, one or two FP32
+    // X chunks of CC observations and per-warp parts, then its kin, sq:
+    // [4][128] f64 and ll: [128] f64 (the prologue keeps its kinetic parts in
+    // the first stage, idle until the copies start)
+    const int endp = dk * CP * 4 + xbufs * CC * Dp * 4 + C_EPI_WARPS * CP * 8;
     L.off_emisc = (endp + 1023) & ~1023;
     const int endx = L.off_emisc + 9 * CP * 8;
     L.off_cref = ((pipe > endx ? pipe : endx) + 1023) & ~1023;
@@ -119,9 +120,12 @@ __host__ __device__ inline CLayout c_layout_n(int dk, int Dp, int n_ref, int n_r
     if (L.total < 118 * 1024) L.total = 118 * 1024;
     return L;
 }
+// The most X stages that fit (4, 3 or 2) with a double-buffered end point,
+// else two stages with a single end-point buffer.
 __host__ __device__ inline CLayout c_layout(int dk, int Dp, int n_ref, int n_run) {
-    CLayout L = c_layout_n(dk, Dp, n_ref, n_run, C_NS_MAX);
-    for (int st = C_NS_MAX - 1; st >= 2 && L.total > C_SMEM_MAX; --st) L = c_layout_n(dk, Dp, n_ref, n_run, st);
+    CLayout L = c_layout_n(dk, Dp, n_ref, n_run, C_NS_MAX, 2);
+    for (int st = C_NS_MAX - 1; st >= 2 && L.total > C_SMEM_MAX; --st) L = c_layout_n(dk, Dp, n_ref, n_run, st, 2);
+    if (L.total > C_SMEM_MAX) L = c_layout_n(dk, Dp, n_ref, n_run, 2, 1);
     return L;
 }
 
@@ -674,11 +678,13 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     __syncthreads();
     tc::cluster_sync();   // every CTA of the cluster has written its units of the final state
     const int Dp = m.Dp, n = m.n;
-    // this CTA's share of the 64-observation chunks of the end point
-    const int e_lo = (int)((int64_t)rank * m.n_chunks / kc), e_hi = (int)((int64_t)(rank + 1) * m.n_chunks / kc);
+    // this CTA's share of the CC-observation chunks of the end point (the
+    // same split as its X tiles)
+    const int e_lo = c_lo, e_hi = c_hi;
+    const int XB = L.xbufs;
     float* thT = reinterpret_cast<float*>(sm);                  // [dk][128]
-    float* xs = thT + dk * CP;                                  // [2][64][Dp]
-    double* llp = reinterpret_cast<double*>(xs + 2 * STREAM_CHUNK * Dp);   // [16][128]
+    float* xs = thT + dk * CP;                                  // [XB][CC][Dp]
+    double* llp = reinterpret_cast<double*>(xs + XB * CC * Dp);   // [16][128]
     if (epi) {
         double sq = 0.0, kin = 0.0;
 #pragma unroll
@@ -699,43 +705,51 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         kin_s[q * CP + prow] = kin;
     }
     auto issue_x = [&](int c, int buf) {
-        const int64_t row0 = (int64_t)c * STREAM_CHUNK;
+        const int64_t row0 = (int64_t)c * CC;
         const int64_t left = (int64_t)n - row0;
-        const int rows = left < STREAM_CHUNK ? (int)left : STREAM_CHUNK;
+        const int rows = left < CC ? (int)left : CC;
         const int nvec = rows * Dp / 4;
-        float* dst = xs + buf * STREAM_CHUNK * Dp;
+        float* dst = xs + buf * CC * Dp;
         const float* srcx = m.X + row0 * Dp;
         for (int v = tid; v < nvec; v += C_THREADS) tc::cp_async16(dst + 4 * v, srcx + 4 * v);
         tc::cp_async_commit();
     };
     if (e_lo < e_hi) issue_x(e_lo, 0);
     {
-        const int pg = lane, og = wid;     // warps 0-15 compute 4 observations each, 16-18 only copy
+        // warps 0-15 compute 8 observations each for 4 particles per lane
+        // (a register tile of 8 x 4: every theta^T load serves 8
+        // observations), warps 16-18 only copy
+        const int pg = lane, og = wid;
         double ll[4] = {0.0, 0.0, 0.0, 0.0};
         for (int c = e_lo; c < e_hi; ++c) {
-            if (c + 1 < e_hi) issue_x(c + 1, (c + 1 - e_lo) & 1);
-            else tc::cp_async_commit();
-            tc::cp_async_wait<1>();
+            const int buf = (c - e_lo) % XB;
+            if (XB == 2) {
+                if (c + 1 < e_hi) issue_x(c + 1, buf ^ 1);
+                else tc::cp_async_commit();
+                tc::cp_async_wait<1>();
+            } else {
+                tc::cp_async_wait<0>();
+            }
             __syncthreads();
             if (og < C_EPI_WARPS) {
-                const float* xc = xs + ((c - e_lo) & 1) * STREAM_CHUNK * Dp + og * 4 * Dp;
-                float acc[4][4];
+                const float* xc = xs + buf * CC * Dp + og * 8 * Dp;
+                float acc[8][4];
 #pragma unroll
-                for (int o = 0; o < 4; ++o)
+                for (int o = 0; o < 8; ++o)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) acc[o][k] = 0.0f;
                 // four dimensions per iteration: X rows as float4 (Dp is a
                 // multiple of 4 and zero-padded; theta^T rows past D are zero)
                 const float* tcol = thT + 4 * pg;
                 for (int d = 0; d < Dp; d += 4) {
-                    float4 xv[4];
+                    float4 xv[8];
 #pragma unroll
-                    for (int o = 0; o < 4; ++o) xv[o] = *reinterpret_cast<const float4*>(xc + o * Dp + d);
+                    for (int o = 0; o < 8; ++o) xv[o] = *reinterpret_cast<const float4*>(xc + o * Dp + d);
 #pragma unroll
                     for (int dd = 0; dd < 4; ++dd) {
                         const float4 t4 = *reinterpret_cast<const float4*>(tcol + (d + dd) * CP);
 #pragma unroll
-                        for (int o = 0; o < 4; ++o) {
+                        for (int o = 0; o < 8; ++o) {
                             const float x = dd == 0 ? xv[o].x : dd == 1 ? xv[o].y : dd == 2 ? xv[o].z : xv[o].w;
                             acc[o][0] = fmaf(x, t4.x, acc[o][0]);
                             acc[o][1] = fmaf(x, t4.y, acc[o][1]);
@@ -746,8 +760,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 }
                 float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    const int64_t i = (int64_t)c * STREAM_CHUNK + og * 4 + o;
+                for (int o = 0; o < 8; ++o) {
+                    const int64_t i = (int64_t)c * CC + og * 8 + o;
                     if (i < n) {
                         const float yv = __ldg(m.y + i);
 #pragma unroll
@@ -769,6 +783,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 for (int k = 0; k < 4; ++k) ll[k] += (double)part[k];
             }
             __syncthreads();
+            if (XB == 1 && c + 1 < e_hi) issue_x(c + 1, 0);
         }
         if (og < C_EPI_WARPS)
 #pragma unroll
