@@ -75,6 +75,9 @@ struct CentredScratch {
     float2* refs = nullptr;
     double* part = nullptr;
     int32_t runs = 0;
+    float* sth = nullptr;     // the move's theta and p in slot order, [D x s_ld] (handles only)
+    float* sp = nullptr;
+    int64_t s_ld = 0;
 };
 
 struct smc_dev_model {
@@ -84,7 +87,8 @@ struct smc_dev_model {
 };
 
 namespace {
-CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs) {
+// ld > 0 (a handle's particle stride) adds the slot-ordered state buffers.
+CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs, int64_t ld = 0) {
     CentredScratch c;
     if (!traj_centred_supported(m)) return c;
     c.centre = A.get<float>((size_t)(runs * m.dk));
@@ -92,14 +96,24 @@ CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs) {
     c.refs = A.get<float2>((size_t)centred_refs_elems(m, runs));
     c.part = A.get<double>((size_t)centred_part_elems(m, runs));
     c.runs = (c.centre && c.gref && c.refs && c.part) ? runs : 0;
+    if (ld > 0) {
+        c.sth = A.get<float>((size_t)(m.D * ld));
+        c.sp = A.get<float>((size_t)(m.D * ld));
+        c.s_ld = (c.sth && c.sp) ? ld : 0;
+    }
     return c;
 }
+// Call after a.ld is set: the slot-ordered buffers serve only launches with
+// the stride they were sized for.
 void set_centred(TrajArgs& a, const CentredScratch& c) {
     a.c_centre = c.centre;
     a.c_gref = c.gref;
     a.c_refs = c.refs;
     a.c_part = c.part;
     a.c_runs = c.runs;
+    const bool slots = c.s_ld > 0 && c.s_ld == a.ld;
+    a.c_sth = slots ? c.sth : nullptr;
+    a.c_sp = slots ? c.sp : nullptr;
 }
 }  // namespace
 
@@ -730,7 +744,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
     h->done = A.get<unsigned int>((size_t)n_runs);
     h->dev_err = A.get<int>(1);
-    if (h->precision == SMC_PREC_BF16C) h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs);
+    if (h->precision == SMC_PREC_BF16C) h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs, h->ld);
     for (int64_t r = 0; r < n_runs; ++r) {
         RunParams& rp = h->h_runs[(size_t)r];
         const int64_t D = h->D;

@@ -81,6 +81,11 @@ struct TrajArgs {
     double* c_part;         // [n_tiles128][c_runs][dk] per-tile parts of c_gref
     int32_t c_runs;         // runs in these arrays (1 when runs == nullptr)
     int32_t c_split;        // CTAs per particle tile (observation split), set by the launcher
+    // optional [D x ld] f32 buffers for the move's theta and p in slot order
+    // (so the per-pass update reads and writes them coalesced); nullptr: the
+    // move keeps its state in theta_out / p_out at the particles' indices
+    float* c_sth;
+    float* c_sp;
 };
 
 // Run of particle j: step size, Philox key, iteration and run-local index.

@@ -223,7 +223,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     // warp w: TMEM lanes 32 (w % 4) .. + 31 (one particle per lane); group
     // q = w / 4 owns dimensions 32 q .. 32 q + 31 of those particles and, in
     // the tile loop, half (q % 2) of the observations of the tiles that use
-    // buffer q / 2.  theta and p live in theta_out / p_out during the move.
+    // buffer q / 2.  theta and p live in the slot-ordered buffers c_sth /
+    // c_sp during the move (index: the slot), else in theta_out / p_out
+    // (index: the particle).
     const bool epi = wid < C_EPI_WARPS;
     const int quarter = wid & 3, q = (wid >> 2) & 3;
     const int prow = 32 * quarter + lane;
@@ -234,6 +236,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     const float inv_s2 = LOGIT ? 0.0f : (float)(1.0 / (m.h0 * m.h0));
     const float inv_s = LOGIT ? 0.0f : (float)(1.0 / m.h0);
     const bool evalm = a.eval_only != 0;
+    const bool slotst = a.c_sth != nullptr && a.c_sp != nullptr && !evalm;
+    float* const thb = slotst ? a.c_sth : a.theta_out;
+    float* const pb = slotst ? a.c_sp : a.p_out;
     int64_t j = -1, src = -1;
     int S = 0, run = 0;
     float ef = 0.0f;
@@ -275,8 +280,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             if (d + e < D) {
                                 kin += (double)pv[e] * (double)pv[e];
                                 if (own) {
-                                    a.p_out[(int64_t)(d + e) * ld + j] = pv[e];
-                                    a.theta_out[(int64_t)(d + e) * ld + j] = tv[e];
+                                    pb[(int64_t)(d + e) * ld + (slotst ? t : j)] = pv[e];
+                                    thb[(int64_t)(d + e) * ld + (slotst ? t : j)] = tv[e];
                                 }
                             }
                     }
@@ -291,6 +296,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         if (epi) kin0_s[q * CP + prow] = kin;
     }
     const float* cref = cref_s + run * dk;                // this particle's run reference point
+    const int64_t si = slotst ? tile * CP + prow : j;     // index of this thread's state in thb / pb
     // deviation operand: unit u (8 dimensions) of this thread's 32 dimensions
     // of its particle row, BF16, swizzled
     auto write_unit = [&](int u, const float* tv) {
@@ -605,8 +611,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     tcur[e] = 0.0f;
                     pcur[e] = 0.0f;
                     if (live && d < D) {
-                        tcur[e] = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
-                        if (!evalm) pcur[e] = a.p_out[(int64_t)d * ld + j];
+                        tcur[e] = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * ld + si];
+                        if (!evalm) pcur[e] = pb[(int64_t)d * ld + si];
                     }
                 }
                 float tv[8];
@@ -624,9 +630,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             if (s < S) {
                                 pv = fmaf(hf, g, pv);
                                 t0 = fmaf(ef, pv, t0);
-                                a.theta_out[(int64_t)d * ld + j] = t0;
+                                thb[(int64_t)d * ld + si] = t0;
                             }
-                            a.p_out[(int64_t)d * ld + j] = pv;
+                            pb[(int64_t)d * ld + si] = pv;
                         }
                         tnew = t0;
                     }
@@ -692,10 +698,17 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             const int d = ds + e;
             float tvv = 0.0f;
             if (j >= 0 && d < D) {
-                tvv = evalm ? a.theta_in[(int64_t)d * ld + src] : a.theta_out[(int64_t)d * ld + j];
+                tvv = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * ld + si];
                 if (!evalm) {
-                    const double pv = a.p_out[(int64_t)d * ld + j];
+                    const float pvf = pb[(int64_t)d * ld + si];
+                    const double pv = pvf;
                     kin += pv * pv;
+                    // the final state from the slot-ordered buffers to the
+                    // particle's outputs, by the CTA that owns the unit
+                    if (slotst && (d >> 3) >= u_lo && (d >> 3) < u_hi) {
+                        a.theta_out[(int64_t)d * ld + j] = tvv;
+                        a.p_out[(int64_t)d * ld + j] = pvf;
+                    }
                 }
             }
             if (d < dk) thT[d * CP + prow] = tvv;
