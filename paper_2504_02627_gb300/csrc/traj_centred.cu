@@ -558,26 +558,30 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             // warps sleep on a hardware barrier instead of polling
             if (tid == 0) {
                 tc::mbar_wait_timed(g_full, (uint32_t)(s & 1), err, abort_s);
-                if (s >= 1) tc::mbar_wait_cluster_timed(gx_free, (uint32_t)((s - 1) & 1), err, abort_s);
+                if (kc > 1 && s >= 1) tc::mbar_wait_cluster_timed(gx_free, (uint32_t)((s - 1) & 1), err, abort_s);
             }
             named_sync(3u, 32u * C_EPI_WARPS);
             tc::fence_after_sync();
-            // publish this CTA's partial gradient (dims ds .. ds + 31 below
-            // dk: with dk = 112 the last group holds only 16 rows of gx)
-            if (ds < dk) {
-                uint32_t gv[32];
-                tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
-                tc::tmem_wait_ld();
+            if (kc > 1) {
+                // publish this CTA's partial gradient (dims ds .. ds + 31 below
+                // dk: with dk = 112 the last group holds only 16 rows of gx);
+                // a CTA alone reads its own units from TMEM instead
+                if (ds < dk) {
+                    uint32_t gv[32];
+                    tc::tmem_ld32_nowait(tmem + lane_base + C_COL_G + ds, gv);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    if (ds + e < dk) gx[(ds + e) * CP + prow] = __uint_as_float(gv[e]);
+                    for (int e = 0; e < 32; ++e)
+                        if (ds + e < dk) gx[(ds + e) * CP + prow] = __uint_as_float(gv[e]);
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0)
+                    for (int r = 0; r < kc; ++r)
+                        tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_full), (uint32_t)r));
+                if (tid == 0) tc::mbar_wait_cluster_timed(gx_full, (uint32_t)(s & 1), err, abort_s);
+                named_sync(3u, 32u * C_EPI_WARPS);
             }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0)
-                for (int r = 0; r < kc; ++r) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_full), (uint32_t)r));
-            if (tid == 0) tc::mbar_wait_cluster_timed(gx_full, (uint32_t)(s & 1), err, abort_s);
-            named_sync(3u, 32u * C_EPI_WARPS);
             const bool live = j >= 0 && (evalm || s <= S);
             const bool more = s + 1 < npass;
             // the update of the units this CTA owns, spread over all sixteen
@@ -590,8 +594,13 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 // state arrays may alias as far as the compiler knows)
                 float gs[8], tcur[8], pcur[8];
                 if (kc == 1) {
+                    // the unit's eight gradient columns of this thread's
+                    // particle (its warp's TMEM lane quarter)
+                    uint32_t gv[8];
+                    tc::tmem_ld8_nowait(tmem + lane_base + C_COL_G + (uint32_t)(8 * unit), gv);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) gs[e] = gx[(8 * unit + e) * CP + prow];
+                    for (int e = 0; e < 8; ++e) gs[e] = __uint_as_float(gv[e]);
                 } else {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
@@ -599,11 +608,17 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                         const uint32_t ga = gx_base + (uint32_t)(((8 * unit + e) * CP + prow) * 4);
                         gs[e] = tc::ld_cluster_f32(tc::map_to_rank(ga, 0u));
                     }
-                    for (int r = 1; r < kc; ++r)
+                    // each rank's eight values are all requested before the
+                    // first is added, so a rank costs one round trip
+                    for (int r = 1; r < kc; ++r) {
+                        float v[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            gs[e] += tc::ld_cluster_f32(
+                            v[e] = tc::ld_cluster_f32(
                                 tc::map_to_rank(gx_base + (uint32_t)(((8 * unit + e) * CP + prow) * 4), (uint32_t)r));
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) gs[e] += v[e];
+                    }
                 }
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -666,7 +681,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             if (lane == 0)
                 for (int r = 0; r < kc; ++r) {
                     if (more) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(th_full), (uint32_t)r));
-                    tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_free), (uint32_t)r));
+                    if (kc > 1) tc::mbar_arrive_cluster(tc::map_to_rank(tc::smem_u32(gx_free), (uint32_t)r));
                 }
         }
     }
