@@ -78,6 +78,14 @@ struct CentredScratch {
     float* sth = nullptr;     // the move's theta and p in slot order, [D x s_ld] (handles only)
     float* sp = nullptr;
     int64_t s_ld = 0;
+    // several runs (handles only): run-uniform particle tiles (TrajArgs::c_tiles)
+    int2* tiles = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* padoff = nullptr;
+    int32_t* pcnt = nullptr;
+    int64_t ntiles = 0;
+    std::vector<int2> h_tiles;        // host copies, uploaded once on the handle's stream
+    std::vector<int32_t> h_padoff;
 };
 
 struct smc_dev_model {
@@ -87,8 +95,13 @@ struct smc_dev_model {
 };
 
 namespace {
-// ld > 0 (a handle's particle stride) adds the slot-ordered state buffers.
-CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs, int64_t ld = 0) {
+// sizes (a handle's particles per run) adds the slot-ordered state buffers
+// and, with several runs, the run-uniform tile layout: run r's slots start at
+// a multiple of 128, and the tiles are listed by their relative rank within
+// their run (then by run), so that every run's longest trajectories start
+// first.
+CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs,
+                             const std::vector<int64_t>* sizes = nullptr) {
     CentredScratch c;
     if (!traj_centred_supported(m)) return c;
     c.centre = A.get<float>((size_t)(runs * m.dk));
@@ -96,12 +109,44 @@ CentredScratch alloc_centred(DevAlloc& A, const DevModel& m, int32_t runs, int64
     c.refs = A.get<float2>((size_t)centred_refs_elems(m, runs));
     c.part = A.get<double>((size_t)centred_part_elems(m, runs));
     c.runs = (c.centre && c.gref && c.refs && c.part) ? runs : 0;
-    if (ld > 0) {
-        c.sth = A.get<float>((size_t)(m.D * ld));
-        c.sp = A.get<float>((size_t)(m.D * ld));
-        c.s_ld = (c.sth && c.sp) ? ld : 0;
+    if (!sizes) return c;
+    int64_t N = 0;
+    for (int64_t n : *sizes) N += n;
+    int64_t slots = round_up(N, 32);
+    if (runs > 1) {
+        struct T { double key; int32_t r; int64_t i; };
+        std::vector<T> tl;
+        int64_t P = 0;
+        c.h_padoff.resize((size_t)runs);
+        for (int32_t r = 0; r < runs; ++r) {
+            c.h_padoff[(size_t)r] = (int32_t)P;
+            const int64_t nt = ((*sizes)[(size_t)r] + 127) / 128;
+            for (int64_t i = 0; i < nt; ++i) tl.push_back({((double)i + 0.5) / (double)nt, r, i});
+            P += nt * 128;
+        }
+        std::stable_sort(tl.begin(), tl.end(), [](const T& x, const T& y) {
+            return x.key < y.key || (x.key == y.key && x.r < y.r);
+        });
+        for (const T& t : tl) c.h_tiles.push_back(make_int2(t.r, c.h_padoff[(size_t)t.r] + (int32_t)(128 * t.i)));
+        c.ntiles = (int64_t)tl.size();
+        slots = P;
+        const int64_t nblk = (N + 1023) / 1024;
+        c.tiles = A.get<int2>((size_t)c.ntiles);
+        c.perm = A.get<int32_t>((size_t)P);
+        c.padoff = A.get<int32_t>((size_t)runs);
+        c.pcnt = A.get<int32_t>((size_t)(2 * nblk * runs));
     }
+    c.sth = A.get<float>((size_t)(m.D * slots));
+    c.sp = A.get<float>((size_t)(m.D * slots));
+    c.s_ld = (c.sth && c.sp) ? slots : 0;
     return c;
+}
+// The tile table and run offsets, and -1 in every slot (the pads stay -1).
+void upload_centred(const CentredScratch& c, cudaStream_t s) {
+    if (!c.tiles) return;
+    cudaMemcpyAsync(c.tiles, c.h_tiles.data(), sizeof(int2) * c.h_tiles.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c.padoff, c.h_padoff.data(), sizeof(int32_t) * c.h_padoff.size(), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c.perm, 0xff, sizeof(int32_t) * (size_t)c.s_ld, s);
 }
 // Call after a.ld is set: the slot-ordered buffers serve only launches with
 // the stride they were sized for.
@@ -111,9 +156,14 @@ void set_centred(TrajArgs& a, const CentredScratch& c) {
     a.c_refs = c.refs;
     a.c_part = c.part;
     a.c_runs = c.runs;
-    const bool slots = c.s_ld > 0 && c.s_ld == a.ld;
-    a.c_sth = slots ? c.sth : nullptr;
-    a.c_sp = slots ? c.sp : nullptr;
+    a.c_sth = c.s_ld > 0 ? c.sth : nullptr;
+    a.c_sp = c.s_ld > 0 ? c.sp : nullptr;
+    a.c_sld = c.s_ld;
+    a.c_tiles = c.tiles;
+    a.c_perm = c.perm;
+    a.c_padoff = c.padoff;
+    a.c_pcnt = c.pcnt;
+    a.c_ntiles = c.ntiles;
 }
 }  // namespace
 
@@ -744,7 +794,11 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
     h->done = A.get<unsigned int>((size_t)n_runs);
     h->dev_err = A.get<int>(1);
-    if (h->precision == SMC_PREC_BF16C) h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs, h->ld);
+    if (h->precision == SMC_PREC_BF16C) {
+        std::vector<int64_t> sizes((size_t)n_runs);
+        for (int64_t r = 0; r < n_runs; ++r) sizes[(size_t)r] = cfg[r].n_particles;
+        h->cs = alloc_centred(A, h->model.m, (int32_t)n_runs, &sizes);
+    }
     for (int64_t r = 0; r < n_runs; ++r) {
         RunParams& rp = h->h_runs[(size_t)r];
         const int64_t D = h->D;
@@ -763,6 +817,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
         return st;
     }
     cudaStream_t s = h->stream;
+    upload_centred(h->cs, s);
     {
         // the staged initial distributions, in the order they were staged
         size_t k = 0;
@@ -899,7 +954,9 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
                            : launch_traj(h->model.m, a, h->precision, s);
             cudaEventRecord(h->events[i + 1], s);
             h->n_event_pairs += 1;
-            h->kernel_launches += KERNELS_PER_ITERATION + (h->precision == SMC_PREC_BF16C ? 3 : 0);   // + reference kernels
+            // + the centred form's reference kernels, and its run partition with several runs
+            h->kernel_launches += KERNELS_PER_ITERATION +
+                                  (h->precision == SMC_PREC_BF16C ? (h->n_runs > 1 ? 6 : 3) : 0);
         } else {
             e = h->flow_on ? launch_traj_flow(h->model.m, h->flow, a, h->z0, h->z1, s)
                            : launch_traj(h->model.m, a, h->precision, s);

@@ -81,11 +81,24 @@ struct TrajArgs {
     double* c_part;         // [n_tiles128][c_runs][dk] per-tile parts of c_gref
     int32_t c_runs;         // runs in these arrays (1 when runs == nullptr)
     int32_t c_split;        // CTAs per particle tile (observation split), set by the launcher
-    // optional [D x ld] f32 buffers for the move's theta and p in slot order
-    // (so the per-pass update reads and writes them coalesced); nullptr: the
-    // move keeps its state in theta_out / p_out at the particles' indices
+    // optional [D x c_sld] f32 buffers for the move's theta and p in slot
+    // order (so the per-pass update reads and writes them coalesced);
+    // nullptr: the move keeps its state in theta_out / p_out at the
+    // particles' indices
     float* c_sth;
     float* c_sp;
+    int64_t c_sld;
+    // several runs: every particle tile holds one run's particles.  Run r's
+    // particles take the slots [c_padoff[r], c_padoff[r] + n_r) in the order
+    // of perm (a stable partition of it, written into c_perm by the
+    // launcher; the slots up to the next multiple of 128 hold -1), and tile b
+    // covers the 128 slots from c_tiles[b].y, all of run c_tiles[b].x.
+    // nullptr: tiles are the slots of perm in order (one run).
+    const int2* c_tiles;
+    int32_t* c_perm;
+    const int32_t* c_padoff;
+    int32_t* c_pcnt;        // partition scratch: [ceil(N / 1024)][c_runs] counts, then bases
+    int64_t c_ntiles;       // tiles of the launch when c_tiles is set
 };
 
 // Run of particle j: step size, Philox key, iteration and run-local index.

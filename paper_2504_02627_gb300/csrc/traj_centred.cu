@@ -139,23 +139,27 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// MULTI: the handle has several runs, so a warp's particles may belong to
-// different runs (each with its own reference values); without it every
-// particle uses run 0's.
-template <bool LOGIT, bool MULTI>
+template <bool LOGIT>
 __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, TrajArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned base by pointer arithmetic on the shared array, so that
     // accesses through it stay shared-space loads and stores
     unsigned char* sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int n_ref = LOGIT ? a.c_runs : 0;
-    const CLayout L = c_layout(m.dk, m.Dp, n_ref, a.c_runs);
+    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? 1 : 0, a.c_runs);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int D = m.D, dk = m.dk, nch_all = m.n_tiles128;
     const int64_t ld = a.ld;
     // cluster split of the observation tiles: this CTA takes [c_lo, c_hi)
     const int kc = (int)a.c_split, rank = (int)tc::cluster_rank();
     const int64_t tile = blockIdx.x / kc;
+    // the tile's run and first slot (run-uniform tiles), else the slots of perm in order
+    int trun = 0;
+    int64_t slot0 = tile * CP;
+    if (a.c_tiles) {
+        const int2 tt = a.c_tiles[tile];
+        trun = tt.x;
+        slot0 = tt.y;
+    }
     const int c_lo = (int)((int64_t)rank * nch_all / kc), c_hi = (int)((int64_t)(rank + 1) * nch_all / kc);
     const int nch = c_hi - c_lo;
     // ownership of the state for the update: 8-dimension units, a contiguous share per rank
@@ -239,15 +243,19 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
     const bool slotst = a.c_sth != nullptr && a.c_sp != nullptr && !evalm;
     float* const thb = slotst ? a.c_sth : a.theta_out;
     float* const pb = slotst ? a.c_sp : a.p_out;
+    const int64_t sld = slotst ? a.c_sld : ld;           // stride of thb / pb
     int64_t j = -1, src = -1;
     int S = 0, run = 0;
     float ef = 0.0f;
     float th[32];
     {
-        const int64_t t = tile * CP + prow;
+        const int64_t t = slot0 + prow;
         double kin = 0.0;
-        if (epi && t < a.N) {
-            j = a.perm ? a.perm[t] : t;
+        int64_t jt = -1;
+        if (a.c_tiles) jt = a.c_perm[t];                     // -1 in a pad slot
+        else if (t < a.N) jt = a.perm ? a.perm[t] : t;
+        if (epi && jt >= 0) {
+            j = jt;
             src = a.src ? a.src[j] : j;
             S = evalm ? 0 : a.steps[j];
             double eps;
@@ -280,8 +288,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             if (d + e < D) {
                                 kin += (double)pv[e] * (double)pv[e];
                                 if (own) {
-                                    pb[(int64_t)(d + e) * ld + (slotst ? t : j)] = pv[e];
-                                    thb[(int64_t)(d + e) * ld + (slotst ? t : j)] = tv[e];
+                                    pb[(int64_t)(d + e) * sld + (slotst ? t : j)] = pv[e];
+                                    thb[(int64_t)(d + e) * sld + (slotst ? t : j)] = tv[e];
                                 }
                             }
                     }
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         if (epi) kin0_s[q * CP + prow] = kin;
     }
     const float* cref = cref_s + run * dk;                // this particle's run reference point
-    const int64_t si = slotst ? tile * CP + prow : j;     // index of this thread's state in thb / pb
+    const int64_t si = slotst ? slot0 + prow : j;         // index of this thread's state in thb / pb
     // deviation operand: unit u (8 dimensions) of this thread's 32 dimensions
     // of its particle row, BF16, swizzled
     auto write_unit = [&](int u, const float* tv) {
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                 unsigned char* dst = sm + L.off_stage + st * L.stage_bytes;
                 tc::bulk_g2s(dst, m.xc_img + (int64_t)c * (L.tile_bytes / 2), (uint32_t)L.tile_bytes, &full[st]);
                 if (L.ref_bytes > 0)
-                    tc::bulk_g2s(dst + L.tile_bytes, a.c_refs + (int64_t)c * n_ref * CC, (uint32_t)L.ref_bytes,
+                    tc::bulk_g2s(dst + L.tile_bytes, a.c_refs + ((int64_t)c * a.c_runs + trun) * CC, (uint32_t)L.ref_bytes,
                                  &full[st]);
                 if (++c == c_hi) c = c_lo;
                 if (++st == NS) {
@@ -438,14 +446,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
         const float hf = 0.5f * ef;
         const float kneg = -1.4426950408889634f;
         const float* gref = gref_s + run * dk;
-        // the runs of the four particles whose residuals this thread forms
-        // (quarter lanes g4, g4 + 8, g4 + 16, g4 + 24), and whether the
-        // warp's 32 particles all belong to one run
-        const int g4 = lane >> 2, tig = lane & 3;
-        int runq[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) runq[k] = __shfl_sync(0xffffffffu, run, g4 + 8 * k);
-        const bool run_uni = __all_sync(0xffffffffu, run == __shfl_sync(0xffffffffu, run, 0)) != 0;
+        // a residual thread's observation pairs: 8 mm + 2 tig (+1)
+        const int tig = lane & 3;
         int st = 0;
         uint32_t sph = 0, bph = 0;
         int64_t it = 0;
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     // g4, g4 + 8 (va) and g4 + 16, g4 + 24 (vb) for the
                     // observation pairs 8 mm + 2 tig (+1), mm = 0..7, of the
                     // half: one (c, s) load serves two observations of four
-                    // particles when they belong to one run
+                    // particles
                     uint32_t va[32], vb[32];
                     tc::tmem_ld16x256_x8_nowait(ecol, va);
                     tc::tmem_ld16x256_x8_nowait(ecol + (16u << 16), vb);
@@ -500,8 +502,10 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     // each observation pair's packed residuals overwrite
                     // already consumed registers: v[2 mm] (lane g4 or g4 + 16)
                     // and v[2 mm + 1] (lane + 8), the order of the 16x128b store
-                    if (!MULTI || run_uni) {
-                        const float4* f = reinterpret_cast<const float4*>(refs0 + runq[0] * (CC * 8));
+                    {
+                        // every particle of the tile belongs to the tile's run,
+                        // whose (c, s) pairs are the stage's only ones
+                        const float4* f = reinterpret_cast<const float4*>(refs0);
 #pragma unroll
                         for (int mm = 0; mm < 8; ++mm) {
                             const float4 cs = LOGIT ? f[4 * mm + tig] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -514,25 +518,6 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             vb[2 * mm] = b0;
                             vb[2 * mm + 1] = b1;
                         }
-                    } else {
-                        // particles of several runs: each lane pair its own (c, s)
-                        auto mixed = [&](uint32_t (&v)[32], int r0, int r1) {
-#pragma unroll
-                            for (int mm = 0; mm < 8; ++mm) {
-                                const int o = 4 * mm + tig;
-                                const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                                const float4 c0 =
-                                    LOGIT ? reinterpret_cast<const float4*>(refs0 + r0 * (CC * 8))[o] : z4;
-                                const float4 c1 =
-                                    LOGIT ? reinterpret_cast<const float4*>(refs0 + r1 * (CC * 8))[o] : z4;
-                                const uint32_t p0 = res_pair(v[4 * mm], v[4 * mm + 1], c0);
-                                const uint32_t p1 = res_pair(v[4 * mm + 2], v[4 * mm + 3], c1);
-                                v[2 * mm] = p0;
-                                v[2 * mm + 1] = p1;
-                            }
-                        };
-                        mixed(va, runq[0], runq[1]);
-                        mixed(vb, runq[2], runq[3]);
                     }
                     // the buffer's previous residuals have been read by GEMM2
                     if (lane == 0) tc::mbar_wait_timed(&r_empty[bq], bph ^ 1u, err, abort_s);
@@ -626,8 +611,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     tcur[e] = 0.0f;
                     pcur[e] = 0.0f;
                     if (live && d < D) {
-                        tcur[e] = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * ld + si];
-                        if (!evalm) pcur[e] = pb[(int64_t)d * ld + si];
+                        tcur[e] = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * sld + si];
+                        if (!evalm) pcur[e] = pb[(int64_t)d * sld + si];
                     }
                 }
                 float tv[8];
@@ -645,9 +630,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                             if (s < S) {
                                 pv = fmaf(hf, g, pv);
                                 t0 = fmaf(ef, pv, t0);
-                                thb[(int64_t)d * ld + si] = t0;
+                                thb[(int64_t)d * sld + si] = t0;
                             }
-                            pb[(int64_t)d * ld + si] = pv;
+                            pb[(int64_t)d * sld + si] = pv;
                         }
                         tnew = t0;
                     }
@@ -713,9 +698,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
             const int d = ds + e;
             float tvv = 0.0f;
             if (j >= 0 && d < D) {
-                tvv = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * ld + si];
+                tvv = evalm ? a.theta_in[(int64_t)d * ld + src] : thb[(int64_t)d * sld + si];
                 if (!evalm) {
-                    const float pvf = pb[(int64_t)d * ld + si];
+                    const float pvf = pb[(int64_t)d * sld + si];
                     const double pv = pvf;
                     kin += pv * pv;
                     // the final state from the slot-ordered buffers to the
@@ -923,6 +908,65 @@ __global__ void __launch_bounds__(128) k_centre_obs(DevModel m, TrajArgs a) {
     }
 }
 
+// Run-uniform tiles (several runs): a stable partition of the launch's
+// particles, in the order of perm, by run.  Counts per 1024-slot block, their
+// exclusive scan over the blocks for every run (from the run's first slot),
+// then each particle's slot: its block's base + the counts of its run in the
+// earlier warps of the block + its rank among the warp's lanes of that run.
+__global__ void __launch_bounds__(1024) k_part_count(TrajArgs a) {
+    __shared__ int cnt[CENTRED_MAX_RUNS];
+    const int R = a.c_runs;
+    if ((int)threadIdx.x < R) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (t < a.N) {
+        const int64_t j = a.perm ? a.perm[t] : t;
+        atomicAdd(&cnt[a.run_of ? a.run_of[j] : 0], 1);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < R) a.c_pcnt[(int64_t)blockIdx.x * R + threadIdx.x] = cnt[threadIdx.x];
+}
+__global__ void __launch_bounds__(32 * CENTRED_MAX_RUNS) k_part_scan(TrajArgs a, int64_t nblk) {
+    const int R = a.c_runs, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= R) return;
+    int32_t* base = a.c_pcnt + nblk * R;
+    int carry = a.c_padoff[w];
+    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+        const int64_t b = b0 + lane;
+        const int v = b < nblk ? a.c_pcnt[b * R + w] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b < nblk) base[b * R + w] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+}
+__global__ void __launch_bounds__(1024) k_part_scatter(TrajArgs a, int64_t nblk) {
+    __shared__ int wc[32][CENTRED_MAX_RUNS];   // per warp: particles of each run
+    const int R = a.c_runs, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    int64_t j = -1;
+    int r = -1;
+    if (t < a.N) {
+        j = a.perm ? a.perm[t] : t;
+        r = a.run_of ? a.run_of[j] : 0;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, r);
+    const int lower = __popc(peers & ((1u << lane) - 1u));
+    if (lane < R) wc[w][lane] = 0;
+    __syncwarp();
+    if (r >= 0 && lower == 0) wc[w][r] = __popc(peers);
+    __syncthreads();
+    if (r >= 0) {
+        int pos = a.c_pcnt[nblk * R + (int64_t)blockIdx.x * R + r] + lower;
+        for (int v = 0; v < w; ++v) pos += wc[v][r];
+        a.c_perm[pos] = (int32_t)j;
+    }
+}
+
 // g_ref[r][d] = sum over tiles of the partial sums, in tile order.
 __global__ void __launch_bounds__(128) k_centre_grad(TrajArgs a, int dk, int nch) {
     const int r = blockIdx.x, d = threadIdx.x, R = a.c_runs;
@@ -936,7 +980,7 @@ __global__ void __launch_bounds__(128) k_centre_grad(TrajArgs a, int dk, int nch
 // per SM over the launch and at least one observation tile per CTA.  It
 // depends only on the particle count, the data and the device, so a result
 // never depends on a timing.
-int centred_split(const DevModel& m, int64_t N) {
+int centred_split(const DevModel& m, int64_t tiles) {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
@@ -944,7 +988,6 @@ int centred_split(const DevModel& m, int64_t N) {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 1;
     }
-    const int64_t tiles = (N + CP - 1) / CP;
     int k = 8;
     while (k > 1 && (tiles * k > 2 * (int64_t)sms || k > m.n_tiles128)) k >>= 1;
     return k;
@@ -955,17 +998,27 @@ cudaError_t launch_centred(const DevModel& m, const TrajArgs& a, cudaStream_t s)
     const int R = a.c_runs;
     if (R < 1 || R > CENTRED_MAX_RUNS || !a.c_centre || !a.c_gref || !a.c_part || (LOGIT && !a.c_refs))
         return cudaErrorInvalidValue;
-    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? R : 0, R);
+    // several runs need the run-uniform tile layout (a handle's); a tile's
+    // stage then carries the reference pairs of its own run only
+    if (R > 1 && (!a.c_tiles || !a.c_perm || !a.c_padoff || !a.c_pcnt || a.c_ntiles < 1))
+        return cudaErrorInvalidValue;
+    const CLayout L = c_layout(m.dk, m.Dp, LOGIT ? 1 : 0, R);
     if (L.total > C_SMEM_MAX) return cudaErrorInvalidValue;
+    if (a.c_tiles) {
+        const int64_t nblk = (a.N + 1023) / 1024;
+        k_part_count<<<(unsigned)nblk, 1024, 0, s>>>(a);
+        k_part_scan<<<1, 32 * R, 0, s>>>(a, nblk);
+        k_part_scatter<<<(unsigned)nblk, 1024, 0, s>>>(a, nblk);
+    }
     k_centre_mean<<<dim3((unsigned)R, (unsigned)m.dk), 256, 0, s>>>(a, m.D, m.dk);
     k_centre_obs<LOGIT><<<(unsigned)m.n_tiles128, 128, 0, s>>>(m, a);
     k_centre_grad<<<(unsigned)R, 128, 0, s>>>(a, m.dk, m.n_tiles128);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (a.N + CP - 1) / CP;
+    const int64_t tiles = a.c_tiles ? a.c_ntiles : (a.N + CP - 1) / CP;
     TrajArgs a2 = a;
-    a2.c_split = centred_split(m, a.N);
-    auto kern = R > 1 ? traj_centred_kernel<LOGIT, true> : traj_centred_kernel<LOGIT, false>;
+    a2.c_split = centred_split(m, tiles);
+    auto kern = traj_centred_kernel<LOGIT>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
