@@ -136,9 +136,36 @@ def run_flow(args):
             "steps": args.steps, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
+def run_sampler(args):
+    """SMC iterations of the centred sampler on a handle (the path the bench
+    runs: slot-ordered state, and with --runs > 1 the run-uniform tiles):
+    the logistic regression with n observations and --dim coefficients,
+    --runs runs of --particles particles each, --iters iterations after one
+    untimed iteration; the trajectory stage timed by the library's events."""
+    torch, workloads, B = _setup()
+    import paper_2504_02627_gb300 as g
+    s = torch.cuda.current_stream().cuda_stream
+    w = workloads.logistic_large(n=args.n, D=args.dim) if args.dim != 25 else workloads.logistic(n=args.n)
+    run = dict(w["run"], n_particles=args.particles, n_iters=args.iters + 1, n_warmup=max(1, args.iters // 2))
+    cfgs = [g.make_config(seed=3000 + r, precision=4, **run) for r in range(args.runs)]
+    smp = g.Sampler(g.ModelData.from_workload(w), cfgs if args.runs > 1 else cfgs[0], s)
+    smp.step(with_stats=False)
+    ge0 = sum(x["grad_evals"] for x in smp.summary())
+    smp.profile(True)
+    for _ in range(args.iters):
+        smp.step(with_stats=False)
+    torch.cuda.synchronize()
+    prof = smp.get_profile()
+    ge = sum(x["grad_evals"] for x in smp.summary()) - ge0
+    smp.close()
+    return {"kernel": "centred sampler", "n": w["n"], "D": w["D"], "runs": args.runs, "particles": args.particles,
+            "iters": args.iters, "traj_ms": prof["traj_ms"], "grad_evals": ge,
+            "grad_evals_per_traj_s": ge / (prof["traj_ms"] / 1e3)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["stream", "flow", "glm", "gauss"])
+    ap.add_argument("which", choices=["stream", "flow", "glm", "gauss", "sampler"])
     ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
     ap.add_argument("--dim", type=int, default=100, help="coefficients of the streamed regression")
     ap.add_argument("--particles", type=int, default=16384)
@@ -150,8 +177,12 @@ def main(argv=None):
                          "flow: 0 (FP32, default) or 2 (BF16 conditioner products)")
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--runs", type=int, default=1, help="sampler: runs in the handle")
+    ap.add_argument("--iters", type=int, default=3, help="sampler: timed SMC iterations")
     args = ap.parse_args(argv)
-    if args.which == "flow":
+    if args.which == "sampler":
+        out = run_sampler(args)
+    elif args.which == "flow":
         out = run_flow(args)
     elif args.which == "gauss":
         out = run_gauss(args)
