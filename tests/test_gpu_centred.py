@@ -320,6 +320,33 @@ def test_centred_batched_runs_equal_single_runs_bit_for_bit():
     batch.close()
 
 
+def test_centred_sixteen_ragged_runs_equal_single_runs_bit_for_bit():
+    """Sixteen runs of sizes around the 128-particle tile (1, 127, 128, 129,
+    ...): the run partition gives every tile one run's particles (padded run
+    blocks), and each run's particles, weights and evidence are the same bits
+    as when the run is alone."""
+    w = _sampler_case()
+    run = dict(w["run"], n_iters=4, n_warmup=2)
+    sizes = [1, 127, 128, 129, 255, 256, 257, 3, 64, 200, 130, 2, 384, 99, 128, 31]
+    cfgs = [g.make_config(seed=800 + i, precision=PREC, **dict(run, n_particles=n)) for i, n in enumerate(sizes)]
+    md = g.ModelData.from_workload(w)
+    batch = g.Sampler(md, cfgs, stream())
+    batch.run(run["n_iters"])
+    th_b, lw_b = batch.particles()
+    lz_b = batch.log_evidence()
+    batch.close()
+    off = 0
+    for i, n in enumerate(sizes):
+        one = g.Sampler(md, cfgs[i], stream())
+        one.run(run["n_iters"])
+        th1, lw1 = one.particles()
+        np.testing.assert_array_equal(th_b[:, off:off + n], th1)
+        np.testing.assert_array_equal(lw_b[off:off + n], lw1)
+        assert lz_b[i] == one.log_evidence()[0]
+        off += n
+        one.close()
+
+
 def test_centred_handle_rejects_more_than_16_runs():
     w = _sampler_case()
     run = dict(w["run"], n_particles=64)
