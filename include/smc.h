@@ -282,8 +282,10 @@ smc_status smc_get_profile(smc_handle* h, double* traj_ms, int64_t* traj_launche
 
 /* Launch plan of the trajectory kernel.  smc_init / smc_init_batch run an
  * autotuner once, after the initial draw: every launch-configuration variant
- * of the model's trajectory kernel (CTA size, register cap of the
- * thread-per-particle kernels) runs a 16-step trajectory of the handle's own
+ * of the model's trajectory kernel (CTA size, register cap, one-shot or
+ * persistent launch of the thread-per-particle kernels: the persistent form
+ * runs as many CTAs as fit at once, each taking tiles of length-sorted
+ * particles from a device counter) runs a 16-step trajectory of the handle's own
  * initial particles into the scratch half of the state, timed with CUDA
  * events (best of three), and the fastest is kept.  Variants run the same
  * arithmetic in the same order, so the choice changes speed only, never a

@@ -196,6 +196,7 @@ struct smc_handle {
     double* colsum = nullptr;
     unsigned int* done = nullptr;
     int* dev_err = nullptr;     // set by a bounded device wait that gave up
+    unsigned int* work = nullptr;   // tile counter of persistent trajectory launches
     int64_t n_tiles = 0;
     int32_t max_steps_all = 0;
     int64_t iters_done = 0;
@@ -531,6 +532,7 @@ cudaError_t initial_draw(smc_handle* h) {
         a.ld = h->ld;
         a.eval_only = 1;
         a.dev_err = h->dev_err;
+        a.work = h->work;
         set_centred(a, h->cs);
         ce = launch_traj(h->model.m, a, h->precision, s);
     }
@@ -580,6 +582,7 @@ cudaError_t autotune(smc_handle* h) {
     a.N = h->N;
     a.ld = h->ld;
     a.dev_err = h->dev_err;
+    a.work = h->work;
     set_centred(a, h->cs);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -794,6 +797,7 @@ smc_status create(smc_handle** out, int64_t n_runs, const smc_config* cfg, const
     h->colsum = A.get<double>((size_t)(slices * 2 * h->D));
     h->done = A.get<unsigned int>((size_t)n_runs);
     h->dev_err = A.get<int>(1);
+    h->work = A.get<unsigned int>(1);
     if (h->precision == SMC_PREC_BF16C) {
         std::vector<int64_t> sizes((size_t)n_runs);
         for (int64_t r = 0; r < n_runs; ++r) sizes[(size_t)r] = cfg[r].n_particles;
@@ -939,6 +943,7 @@ smc_status smc_step(smc_handle* h, smc_stats* stats) {
         a.N = h->N;
         a.ld = h->ld;
         a.dev_err = h->dev_err;
+        a.work = h->work;
         a.tile = h->traj_tile;
         set_centred(a, h->cs);
         if (h->profiling) {

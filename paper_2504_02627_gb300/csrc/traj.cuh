@@ -73,6 +73,7 @@ struct TrajArgs {
     int32_t eval_only;      // 1: compute log pi and grad at theta_in, no move
     int32_t tile;           // launch-configuration variant of the model's kernel (0: default)
     int* dev_err;           // set to 1 when a bounded device wait gives up (may be nullptr)
+    unsigned int* work;     // tile counter of the persistent launch variants (may be nullptr)
     // centred tensor-core path only: per-move reference quantities of each
     // run (written by the launcher before the trajectory kernel)
     float* c_centre;        // [c_runs][dk] reference points theta_ref

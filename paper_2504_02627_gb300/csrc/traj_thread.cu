@@ -4,6 +4,7 @@
 // carries theta, p and grad of its particle in registers for the whole
 // trajectory, draws its momentum from the (seed, i, j, k, MOM) Philox stream
 // and returns the end-point energy error Delta H and min(1, exp(-Delta H)).
+#include <algorithm>
 #include <cstdio>
 #include <math_constants.h>
 #include "traj.cuh"
@@ -145,14 +146,11 @@ struct HierM {
     }
 };
 
-template <template <int> class MT, int DM, int NT = 128, int MINB = 1>
-__global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajArgs a) {
+// The move of the particle in slot t (Algorithm 1 for its S_j steps, the
+// end-point energy and Delta H), the model's data already in shared memory.
+template <template <int> class MT, int DM>
+__device__ __forceinline__ void particle_move(const DevModel& m, const TrajArgs& a, const float* sm, int64_t t) {
     using M = MT<DM>;
-    extern __shared__ __align__(16) float sm[];
-    M::load(m, sm);
-    __syncthreads();
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.N) return;
     const int64_t j = a.perm ? a.perm[t] : t;
     const int64_t src = a.src ? a.src[j] : j;
     const int D = m.D;
@@ -173,7 +171,7 @@ __global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajA
         for (int d = 0; d < DM; ++d)
             if (d < D) a.grad_out[(int64_t)d * a.ld + j] = g[d];
         a.logpi_out[j] = lp;
-        return;
+        return;   // from the particle's move
     }
 
 #pragma unroll
@@ -226,6 +224,36 @@ __global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajA
     if (a.alpha) a.alpha[j] = dH <= 0.0 ? 1.0 : exp(-dH);
 }
 
+// One particle per thread, one CTA per NT slots.
+template <template <int> class MT, int DM, int NT = 128, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) traj_thread_kernel(DevModel m, TrajArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    MT<DM>::load(m, sm);
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.N) particle_move<MT, DM>(m, a, sm, t);
+}
+
+// Persistent form: as many CTAs as fit on the GPU at once, each loading the
+// model's data once and then taking tiles of NT slots from a device counter
+// (zeroed by the launcher) in slot order, i.e. longest trajectories first.
+// Every particle's arithmetic is that of traj_thread_kernel.
+template <template <int> class MT, int DM, int NT = 128, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) traj_thread_persist_kernel(DevModel m, TrajArgs a, int64_t ntiles) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ unsigned int tile_s;
+    MT<DM>::load(m, sm);
+    for (;;) {
+        if (threadIdx.x == 0) tile_s = atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int64_t tile = tile_s;
+        __syncthreads();   // every thread has the tile before the next one is taken
+        if (tile >= ntiles) break;
+        const int64_t t = tile * NT + threadIdx.x;
+        if (t < a.N) particle_move<MT, DM>(m, a, sm, t);
+    }
+}
+
 
 namespace {
 
@@ -243,19 +271,53 @@ cudaError_t launch_thread_v(const DevModel& m, const TrajArgs& a, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <template <int> class MT, int DM, int NT, int MINB>
+cudaError_t launch_thread_persist(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
+    const size_t sm = MT<DM>::smem_bytes(m);
+    auto kern = traj_thread_persist_kernel<MT, DM, NT, MINB>;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t ntiles = (a.N + NT - 1) / NT;
+    if (ntiles == 0) return cudaSuccess;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+    e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, NT, sm, s>>>(m, a, ntiles);
+    return cudaGetLastError();
+}
+
 // Variants of the thread-per-particle kernel for the autotuner: CTA size
-// (the granularity with which length-sorted slots are dealt to the SMs) and
-// a register cap that trades spills for a third resident CTA.  Same code,
-// same arithmetic.
-// Small particles (DM < 16) have only the default.
-constexpr int32_t THREAD_TILES = 4;
+// (the granularity with which length-sorted slots are dealt to the SMs), a
+// register cap that trades spills for a third resident CTA, and for each of
+// these the persistent form (4-7: tiles from a device counter; they need
+// TrajArgs::work, else the launch falls back to the one-shot form).  Same
+// code, same arithmetic.  Small particles (DM < 16) have only the default.
+constexpr int32_t THREAD_TILES = 8;
 template <template <int> class MT, int DM>
 cudaError_t launch_thread(const DevModel& m, const TrajArgs& a, cudaStream_t s) {
     if constexpr (DM >= 16) {
-        switch (a.tile) {
+        const int v = (a.tile >= 4 && !a.work) ? a.tile - 4 : a.tile;
+        switch (v) {
             case 1: return launch_thread_v<MT, DM, 64, 1>(m, a, s);
             case 2: return launch_thread_v<MT, DM, 256, 1>(m, a, s);
             case 3: return launch_thread_v<MT, DM, 128, 3>(m, a, s);
+            case 4: return launch_thread_persist<MT, DM, 128, 1>(m, a, s);
+            case 5: return launch_thread_persist<MT, DM, 64, 1>(m, a, s);
+            case 6: return launch_thread_persist<MT, DM, 256, 1>(m, a, s);
+            case 7: return launch_thread_persist<MT, DM, 128, 3>(m, a, s);
             default: break;
         }
     }

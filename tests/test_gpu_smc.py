@@ -301,7 +301,7 @@ def test_metropolis_variant_matches_oracle(mode):
 
 
 # ------------------------------------------------------------- autotuned launch plan
-@pytest.mark.parametrize("name,n_tiles", [("hier", 4), ("banana50", 4), ("gauss10", 1), ("logistic", 1)])
+@pytest.mark.parametrize("name,n_tiles", [("hier", 8), ("banana50", 8), ("gauss10", 1), ("logistic", 1)])
 def test_autotuner_plan(name, n_tiles):
     """smc_init times every launch variant of the model's trajectory kernel on
     the handle's own particles and keeps the fastest."""
@@ -320,20 +320,21 @@ def test_autotuner_plan(name, n_tiles):
 @pytest.mark.parametrize("name", ["hier", "banana50"])
 def test_autotuner_variants_give_identical_results(name):
     """The variants differ only in launch configuration (CTA size, register
-    cap): forcing each one reproduces the same particles, weights and evidence
-    bit for bit, so the autotuner can never change a result."""
+    cap, one-shot or persistent with tiles from a device counter): forcing
+    each one reproduces the same particles, weights and evidence bit for
+    bit, so the autotuner can never change a result."""
     w = rounded_workload(workloads.hier() if name == "hier" else _cases()[name])
     run = dict(w["run"], n_particles=1500, n_iters=6, n_warmup=3)
     md = g.ModelData.from_workload(w)
     outs = []
-    for v in range(4):
+    for v in range(8):
         smp = g.Sampler(md, g.make_config(seed=77, **run), stream())
         smp.set_plan(v)
         smp.run(run["n_iters"])                # graph replay with variant v
         th, lw = smp.particles()
         outs.append((th.copy(), lw.copy(), smp.log_evidence().copy()))
         with pytest.raises(RuntimeError):
-            smp.set_plan(4)
+            smp.set_plan(8)
         smp.close()
     for th, lw, lz in outs[1:]:
         np.testing.assert_array_equal(th, outs[0][0])
