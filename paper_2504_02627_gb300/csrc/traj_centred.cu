@@ -44,9 +44,10 @@
 // observations) and update the particle state, which lives in theta_out /
 // p_out during the move.  A residual thread reads eta in the 16-lane shape
 // (two observations of two particles per access) and writes the packed BF16
-// residuals in the matching 16x128b shape, which is GEMM2's K order; so one
-// shared-memory load of an observation pair's reference values serves four
-// particles.  The sigmoid's exponential is the SFU's base-2
+// residuals in the matching 16x128b shape, which is GEMM2's K order; it forms
+// its two 16-lane groups one after the other (one group's eta live at a time),
+// so one shared-memory load of an observation pair's reference values serves
+// two particles.  The sigmoid's exponential is the SFU's base-2
 // exponential; one SFU reciprocal of the product (1 + 2^x0)(1 + 2^x1) serves
 // a pair of observations.
 //
@@ -466,18 +467,6 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     const uint32_t rcol = tmem + lane_base + C_COL_R + (uint32_t)(bq * (CC / 2) + 32 * half);
                     const unsigned char* refs0 =
                         sm + L.off_stage + st * L.stage_bytes + L.tile_bytes + half * (64 * 8);
-                    // this thread forms the residuals of the quarter's lanes
-                    // g4, g4 + 8 (va) and g4 + 16, g4 + 24 (vb) for the
-                    // observation pairs 8 mm + 2 tig (+1), mm = 0..7, of the
-                    // half: one (c, s) load serves two observations of four
-                    // particles
-                    uint32_t va[32], vb[32];
-                    tc::tmem_ld16x256_x8_nowait(ecol, va);
-                    tc::tmem_ld16x256_x8_nowait(ecol + (16u << 16), vb);
-                    tc::tmem_wait_ld();
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&eta_empty[bq]);
                     // One SFU reciprocal serves both observations of a pair:
                     // 1 / q0 = q1 / (q0 q1), 1 / q1 = q0 / (q0 q1), with the
                     // exponents clamped so that q0 q1 < 2^121 (a sigmoid below
@@ -499,31 +488,46 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                         }
                         return pack_bf16(r0, r1);
                     };
-                    // each observation pair's packed residuals overwrite
-                    // already consumed registers: v[2 mm] (lane g4 or g4 + 16)
-                    // and v[2 mm + 1] (lane + 8), the order of the 16x128b store
-                    {
-                        // every particle of the tile belongs to the tile's run,
-                        // whose (c, s) pairs are the stage's only ones
-                        const float4* f = reinterpret_cast<const float4*>(refs0);
+                    // this thread forms the residuals of the quarter's lanes
+                    // g4, g4 + 8 (first group) and g4 + 16, g4 + 24 (second)
+                    // for the observation pairs 8 mm + 2 tig (+1), mm = 0..7,
+                    // of the half: one (c, s) load serves two observations of
+                    // two particles.  Each observation pair's packed residuals
+                    // overwrite already consumed registers: v[2 mm] (lane g4 or
+                    // g4 + 16) and v[2 mm + 1] (lane + 8), the order of the
+                    // 16x128b store.
+                    // every particle of the tile belongs to the tile's run,
+                    // whose (c, s) pairs are the stage's only ones
+                    const float4* f = reinterpret_cast<const float4*>(refs0);
+                    auto form = [&](uint32_t (&v)[32]) {
 #pragma unroll
                         for (int mm = 0; mm < 8; ++mm) {
                             const float4 cs = LOGIT ? f[4 * mm + tig] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                            const uint32_t a0 = res_pair(va[4 * mm], va[4 * mm + 1], cs);
-                            const uint32_t a1 = res_pair(va[4 * mm + 2], va[4 * mm + 3], cs);
-                            const uint32_t b0 = res_pair(vb[4 * mm], vb[4 * mm + 1], cs);
-                            const uint32_t b1 = res_pair(vb[4 * mm + 2], vb[4 * mm + 3], cs);
-                            va[2 * mm] = a0;
-                            va[2 * mm + 1] = a1;
-                            vb[2 * mm] = b0;
-                            vb[2 * mm + 1] = b1;
+                            const uint32_t a0 = res_pair(v[4 * mm], v[4 * mm + 1], cs);
+                            const uint32_t a1 = res_pair(v[4 * mm + 2], v[4 * mm + 3], cs);
+                            v[2 * mm] = a0;
+                            v[2 * mm + 1] = a1;
                         }
-                    }
+                    };
+                    // The two groups go one after the other, so that only one
+                    // group's eta is live at a time (no register spills); the
+                    // second group's load overlaps the first group's store,
+                    // and the eta buffer is released once both are read.
+                    uint32_t va[32], vb[32];
+                    tc::tmem_ld16x256_x8_nowait(ecol, va);
+                    tc::tmem_wait_ld();
+                    form(va);
                     // the buffer's previous residuals have been read by GEMM2
                     if (lane == 0) tc::mbar_wait_timed(&r_empty[bq], bph ^ 1u, err, abort_s);
                     __syncwarp();
                     tc::fence_after_sync();
                     tc::tmem_st16x128_x8_nowait(rcol, va);
+                    tc::tmem_ld16x256_x8_nowait(ecol + (16u << 16), vb);
+                    tc::tmem_wait_ld();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&eta_empty[bq]);
+                    form(vb);
                     tc::tmem_st16x128_x8_nowait(rcol + (16u << 16), vb);
                     tc::tmem_wait_st();
                     tc::fence_before_sync();
