@@ -33,7 +33,8 @@ sides      = the other configurations, each with chosen and plain forms and
              seeds batched in one centred handle against 10 plain FP32 runs,
              log-Z and posterior-mean agreement with a long plain run), c4
              (64 batched hierarchical runs, evidence against quadrature), c5
-             (learned transport map against the plain sampler, closed forms).
+             (learned transport map against the plain sampler, closed forms;
+             the map's trajectories and its training in FP32 or BF16).
 
 N > 1 (torchrun): independent replicas, one per GPU, different seeds
 ("replicas only": the method's particle sets do not exchange data).
@@ -635,14 +636,15 @@ def side_c5(g, torch, stream, flush, K=50, M=25, H=128, L=4):
         md = g.ModelData.from_workload(w)
         qm, qL = pilot_q_init(g, md, run, stream)
         res = {}
-        arms = ("plain", "plain_bf16x3", "flow", "flow_bf16") if w["kind"] == "gauss_dense" else \
-            ("plain", "flow", "flow_bf16")
+        arms = ("plain", "plain_bf16x3", "flow", "flow_bf16", "flow_bf16_train") if w["kind"] == "gauss_dense" \
+            else ("plain", "flow", "flow_bf16", "flow_bf16_train")
         for arm in arms:
             prec = 1 if arm == "plain_bf16x3" else 0
             smp = g.Sampler(md, g.make_config(seed=4242, precision=prec, init_mean=qm, init_chol=qL, **run), stream)
             if arm.startswith("flow"):
                 smp.enable_flow(workloads.flow_init(w["D"], H, L, seed=5), H, L, train_every=2, epochs=20,
-                                lr=1e-3, min_ess_frac=0.25, precision=2 if arm == "flow_bf16" else 0)
+                                lr=1e-3, min_ess_frac=0.25, precision=0 if arm == "flow" else 2,
+                                train_precision=2 if arm == "flow_bf16_train" else 0)
             smp.run(2)
             smp.reset(777)
             smp.profile(True)

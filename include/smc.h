@@ -347,7 +347,14 @@ typedef struct {
                                SMC_PREC_FP32 (0), or SMC_PREC_BF16 (2): BF16
                                weights and activations on warp-level tensor-core
                                MMAs with FP32 accumulation (hidden a multiple of
-                               16); training stays FP32                           */
+                               16)                                                */
+    int32_t train_precision;/* products of the training gradient: SMC_PREC_FP32
+                               (0), or SMC_PREC_BF16 (2): the conditioner, its
+                               transposed products and the weight gradients
+                               (sums over particles) on BF16 warp MMAs with FP32
+                               accumulation (hidden a multiple of 16); the
+                               master weights, bias gradients, the coupling
+                               arithmetic and Adam stay FP32                      */
 } smc_flow_config;
 
 /* Number of parameters of the flow (0 for an invalid shape). */
@@ -451,12 +458,15 @@ smc_status smc_k_flow_leapfrog(const smc_dev_model* m, int32_t hidden, int32_t l
 /* Gradient of the weighted training loss of smc_flow_enable with respect to
  * every parameter: grad (device f32, smc_flow_num_params values) from params
  * (device f32), theta f32 [dim x ld] and W f64 [N] (used as given, not
- * normalised).  Per-CTA partial gradients are summed in a fixed order, so the
- * result is deterministic.  Allocates (stream-ordered) and frees the work
- * copies and the partials (ceil(N / 32) x n_params floats). */
+ * normalised).  precision: SMC_PREC_FP32, or SMC_PREC_BF16 (the products on
+ * BF16 warp MMAs, as smc_flow_config.train_precision).  Per-CTA partial
+ * gradients are summed in a fixed order, so the result is deterministic.
+ * Allocates (stream-ordered) and frees the work copies, the BF16 fragments
+ * and the partials (ceil(N / 32) x n_params floats).  Errors: SMC_E_INVAL
+ * (shape, precision, null pointers, ld < N), SMC_E_NOMEM, SMC_E_CUDA. */
 smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, const float* params,
                                 const float* theta, const double* W, int64_t N, int64_t ld,
-                                float* grad, void* stream);
+                                float* grad, int32_t precision, void* stream);
 
 /* Normalised weights (Sec. 3): lse, ess (device scalars, f64) and W [N] f64
  * from logw [N] f64. */

@@ -3,6 +3,7 @@ micro-benchmark and the profiling driver for one trajectory kernel at a time).
 
     python kernel_bench.py stream --n 20000 --particles 16384 --steps 40
     python kernel_bench.py flow --particles 8192 --steps 8
+    python kernel_bench.py flow_train --particles 8192 --precision 2
     python kernel_bench.py glm --particles 4096 --steps 20
     python kernel_bench.py gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
 
@@ -136,6 +137,37 @@ def run_flow(args):
             "steps": args.steps, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
+def run_flow_train(args):
+    """The training gradient of the coupling flow (smc_k_flow_loss_grad: the
+    work copies and fragments, the per-CTA gradient kernel, the fixed-order
+    reduction) on --particles particles near the 100-d Gaussian's scale, with
+    FP32 (--precision 0) or BF16 (2) products."""
+    torch, workloads, B = _setup()
+    s = torch.cuda.current_stream().cuda_stream
+    D, H, L, N = args.dim, args.hidden, args.layers, args.particles
+    rng = np.random.default_rng(3)
+    params = workloads.flow_init(D, H, L, seed=5)
+    Dh = D // 2
+    lsz = H * Dh + H + H * H + H + D * H + D
+    for l in range(L):
+        o = l * lsz + H * Dh + H + H * H + H
+        params[o:o + D * H + D] = 0.1 * rng.standard_normal(D * H + D) / np.sqrt(H)
+    par = torch.tensor(params.astype(np.float32)).cuda()
+    th = torch.tensor(rng.standard_normal((D, N)).astype(np.float32)).cuda()
+    W = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    gr = torch.empty(par.numel(), dtype=torch.float32, device="cuda")
+    prec = B.PREC_FP32 if args.precision is None else args.precision
+    lib = B.lib()
+    ms = _time(torch, lambda: B.check(lib.smc_k_flow_loss_grad(D, H, L, par.data_ptr(), th.data_ptr(), W.data_ptr(),
+                                                               N, N, gr.data_ptr(), prec, s), "smc_k_flow_loss_grad"))
+    # per particle and layer: the conditioner twice (inverse pass, backward
+    # recompute), the transposed products and the weight gradients
+    flops = 8.0 * L * (Dh * H + H * H + H * D) * N
+    return {"kernel": "flow training gradient (" + ("BF16 warp MMA" if prec == B.PREC_BF16 else "FP32 SIMT") + ")",
+            "D": D, "hidden": H, "layers": L, "particles": N, "ms": ms,
+            "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
+
+
 def run_sampler(args):
     """SMC iterations of the centred sampler on a handle (the path the bench
     runs: slot-ordered state, and with --runs > 1 the run-uniform tiles):
@@ -165,7 +197,7 @@ def run_sampler(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["stream", "flow", "glm", "gauss", "sampler"])
+    ap.add_argument("which", choices=["stream", "flow", "flow_train", "glm", "gauss", "sampler"])
     ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
     ap.add_argument("--dim", type=int, default=100, help="coefficients of the streamed regression")
     ap.add_argument("--particles", type=int, default=16384)
@@ -174,7 +206,7 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=None,
                     help="stream: 2 (BF16), 3 (BF16x2, default) or 4 (centred BF16); glm: 0 (FP32, default), "
                          "1 (BF16x3), 2 (BF16) or 4 (centred BF16); "
-                         "flow: 0 (FP32, default) or 2 (BF16 conditioner products)")
+                         "flow, flow_train: 0 (FP32, default) or 2 (BF16 products)")
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--runs", type=int, default=1, help="sampler: runs in the handle")
@@ -184,6 +216,8 @@ def main(argv=None):
         out = run_sampler(args)
     elif args.which == "flow":
         out = run_flow(args)
+    elif args.which == "flow_train":
+        out = run_flow_train(args)
     elif args.which == "gauss":
         out = run_gauss(args)
     else:

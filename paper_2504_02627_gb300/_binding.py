@@ -49,7 +49,7 @@ class SmcConfig(C.Structure):
 class SmcFlowConfig(C.Structure):
     _fields_ = [("hidden", C.c_int32), ("layers", C.c_int32), ("train_every", C.c_int32),
                 ("epochs", C.c_int32), ("lr", C.c_double), ("min_ess_frac", C.c_double),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("train_precision", C.c_int32)]
 
 
 class SmcStats(C.Structure):
@@ -114,7 +114,7 @@ EXPORTS = {
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_int64,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "smc_k_flow_loss_grad": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
-                                       C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
+                                       C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]),
 }
 NOALLOC_MAX_N = 4194304     # SMC_NOALLOC_MAX_N in include/smc.h
 
@@ -317,14 +317,16 @@ class Sampler:
         return out
 
     def enable_flow(self, params, hidden: int, layers: int, train_every: int = 2, epochs: int = 10,
-                    lr: float = 1e-3, min_ess_frac: float = 0.25, precision: int = 0):
+                    lr: float = 1e-3, min_ess_frac: float = 0.25, precision: int = 0, train_precision: int = 0):
         """smc_flow_enable: the affine-coupling transport map (FP64 host params);
-        precision PREC_FP32 or PREC_BF16 (conditioner products on BF16 warp MMAs)."""
+        precision PREC_FP32 or PREC_BF16 (conditioner products of the
+        trajectories on BF16 warp MMAs), train_precision the same for the
+        training gradient's products."""
         p = np.ascontiguousarray(params, dtype=np.float64)
         n = lib().smc_flow_num_params(self.dim, hidden, layers)
         if p.size != n:
             raise ValueError(f"flow needs {n} parameters, got {p.size}")
-        fc = SmcFlowConfig(hidden, layers, train_every, epochs, lr, min_ess_frac, precision)
+        fc = SmcFlowConfig(hidden, layers, train_every, epochs, lr, min_ess_frac, precision, train_precision)
         check(lib().smc_flow_enable(self.h, C.byref(fc), _dp(p)), "smc_flow_enable", self.h)
         self.flow_shape = (hidden, layers)
 

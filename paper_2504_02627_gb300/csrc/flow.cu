@@ -9,7 +9,11 @@
 // activations [rows x 32] stay in shared memory and the weights stream from
 // L2 as 16-byte rows of padded work copies (a transposed copy serves the
 // backward products), each thread accumulating a 4 x 4 tile.  FP32 with the
-// trajectory end-point energy accumulated in FP64.
+// trajectory end-point energy accumulated in FP64.  The BF16 forms run the
+// same products on m16n8k16 warp MMAs (BF16 operands, FP32 accumulation):
+// the trajectories' conditioner and transposed products from pre-arranged
+// weight fragments, and in training also the weight gradients, which are
+// products over the CTA's 32 particles.
 #include <cuda_bf16.h>
 #include <math_constants.h>
 #include "flow.cuh"
@@ -825,6 +829,235 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
     }
 }
 
+// -------------------------------------------------------------- BF16 training
+// The training step with every conditioner product on BF16 warp MMAs (FP32
+// accumulation; master weights, bias sums, Adam and the coupling arithmetic
+// stay FP32): the conditioner of the inverse pass and of the backward pass
+// (as in the BF16 trajectories), the transposed products W3^T c_o, W2^T c_h2,
+// W1^T c_h1 from the transposed fragments, and the weight gradients, which
+// are products over the CTA's 32 particles, c [rows x 32] . act^T [32 x cols].
+constexpr int WLD = FG + 8;      // row stride (BF16) of the weight-gradient operands
+
+// FP32 rows X [R x 32] -> BF16 rows Y [Rpad][WLD] (particles contiguous),
+// zero for R <= r < Rpad.  A thread converts eight particles of one row.
+__device__ __noinline__ void to_rows(const float* X, int R, int Rpad, __nv_bfloat16* Y) {
+    for (int e = threadIdx.x; e < Rpad * 4; e += FT) {
+        const int r = e >> 2, p0 = 8 * (e & 3);
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (r < R) {
+            const float4 a = *reinterpret_cast<const float4*>(X + r * FG + p0);
+            const float4 b = *reinterpret_cast<const float4*>(X + r * FG + p0 + 4);
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(a.z, a.w);
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(b.x, b.y), h3 = __floats2bfloat162_rn(b.z, b.w);
+            w[0] = *reinterpret_cast<const uint32_t*>(&h0);
+            w[1] = *reinterpret_cast<const uint32_t*>(&h1);
+            w[2] = *reinterpret_cast<const uint32_t*>(&h2);
+            w[3] = *reinterpret_cast<const uint32_t*>(&h3);
+        }
+        *reinterpret_cast<uint4*>(Y + r * WLD + p0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// out[row(m) * ldo + n] = sum over the CTA's 32 particles p of A[m][p] B[n][p]
+// for m < 16 MT, n < min(16 NP, Nvalid); A, B BF16 rows [.][WLD] in shared
+// memory (K = the particles: two k-steps of m16n8k16).  A warp takes one
+// m-tile and four n-tiles.  CMAP: A's rows are the conditioner's padded
+// output rows (s rows from 0, t rows from Dh4), stored at the canonical rows
+// of W3 (s then t, Dh each); otherwise rows m < Mvalid are stored as they are.
+template <bool CMAP>
+__device__ __noinline__ void cta_wgrad(const __nv_bfloat16* A, int MT, const __nv_bfloat16* B, int NP, float* out,
+                                       int ldo, int Mvalid, int Nvalid, int Dh, int Dh4) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int mi = lane >> 3, mr = lane & 7;
+    const int NQ = (NP + 1) >> 1;
+    const uint32_t abase = tc::smem_u32(A), bbase = tc::smem_u32(B);
+    auto row_of = [&](int m) -> int {
+        if (!CMAP) return m < Mvalid ? m : -1;
+        return m < Dh ? m : (m >= Dh4 && m < Dh4 + Dh ? Dh + (m - Dh4) : -1);
+    };
+    for (int it = wid; it < MT * NQ; it += FT / 32) {
+        const int mt = it / NQ, q = it % NQ;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            // A fragment: lanes 0-15 address rows 0-15 at k 0-7, lanes 16-31 the same rows at k 8-15
+            uint32_t a[4];
+            tc::ldsm4(a, abase + (uint32_t)(((16 * mt + (lane & 15)) * WLD + 16 * ks + 8 * (lane >> 4)) * 2));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int np = 2 * q + h;     // n-tiles 2 np and 2 np + 1
+                if (np < NP) {
+                    const int nrow = 16 * np + 8 * (mi >> 1) + mr;
+                    const int kcol = 16 * ks + 8 * (mi & 1);
+                    uint32_t b[4];
+                    tc::ldsm4(b, bbase + (uint32_t)((nrow * WLD + kcol) * 2));
+                    tc::mma_bf16_16816(acc[2 * h], a, b[0], b[1]);
+                    tc::mma_bf16_16816(acc[2 * h + 1], a, b[2], b[3]);
+                }
+            }
+        }
+        const int r0 = row_of(16 * mt + g), r1 = row_of(16 * mt + g + 8);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (2 * q + (u >> 1) < NP) {
+                const int c0 = 8 * (4 * q + u) + 2 * t;
+                if (r0 >= 0) {
+                    if (c0 < Nvalid) out[(int64_t)r0 * ldo + c0] = acc[u][0];
+                    if (c0 + 1 < Nvalid) out[(int64_t)r0 * ldo + c0 + 1] = acc[u][1];
+                }
+                if (r1 >= 0) {
+                    if (c0 < Nvalid) out[(int64_t)r1 * ldo + c0] = acc[u][2];
+                    if (c0 + 1 < Nvalid) out[(int64_t)r1 * ldo + c0 + 1] = acc[u][3];
+                }
+            }
+        }
+    }
+}
+
+// Shared memory of the BF16 training kernel: FP32 x, c [D x 32], the layer
+// inputs zl [L x D x 32], h1, h2 [H x 32], o [O4 x 32], ch [H x 32]; then the
+// particle-major BF16 operand [32][<= 136] and the two row-major BF16
+// operands of the weight-gradient products [128][WLD].
+__device__ __forceinline__ FlowSmem flow_train_smem(unsigned char* base, int D, int H, int L, int O4,
+                                                    __nv_bfloat16*& A16, __nv_bfloat16*& B16) {
+    FlowSmem s{};
+    float* f = reinterpret_cast<float*>(base);
+    s.x = f;
+    s.c = s.x + D * FG;
+    s.zl = s.c + D * FG;
+    s.h1 = s.zl + L * D * FG;
+    s.h2 = s.h1 + H * FG;
+    s.o = s.h2 + H * FG;
+    s.ch = s.o + O4 * FG;
+    s.pm = reinterpret_cast<__nv_bfloat16*>(s.ch + H * FG);
+    A16 = s.pm + FG * (128 + 8);
+    B16 = A16 + 128 * WLD;
+    return s;
+}
+
+// The weighted-NLL gradient of k_flow_train with BF16 products; the same
+// partials layout (canonical parameter order, one row per CTA).
+__global__ void __launch_bounds__(FT, 1) k_flow_train_mma(DevFlow f, const float* theta, int64_t ld,
+                                                          const int32_t* src, const double* W, FlowGate gate,
+                                                          int64_t N, float* partials) {
+    if (!gate.open()) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *A16, *B16;
+    FlowSmem s = flow_train_smem(smem_raw, f.D, f.H, f.L, f.O4, A16, B16);
+    __shared__ float w_s[FG];
+    const int t = threadIdx.x, D = f.D, H = f.H, Dh = f.Dh, Dh4 = f.Dh4;
+    const int64_t slot0 = (int64_t)blockIdx.x * FG;
+    if (t < FG) {
+        const int64_t j = slot0 + t;
+        float wv = 0.0f;
+        if (j < N) {
+            wv = (gate.rs && gate.rs->resample) ? (float)(1.0 / (double)gate.rp->n) : (float)W[j];
+        }
+        w_s[t] = wv;
+    }
+    __syncthreads();
+    for (int e = t; e < D * FG; e += FT) {
+        const int d = e / FG, q = e % FG;
+        const int64_t j = slot0 + q;
+        s.x[e] = (j < N && w_s[q] != 0.0f) ? theta[(int64_t)d * ld + (src ? src[j] : j)] : 0.0f;
+    }
+    __syncthreads();
+    for (int l = f.L - 1; l >= 0; --l) {
+        for (int e = t; e < D * FG; e += FT) s.zl[l * D * FG + e] = s.x[e];
+        __syncthreads();
+        conditioner<true>(f, l, s.x, s);
+        const int boff = (l & 1) ? 0 : Dh;
+        for (int e = t; e < Dh * FG; e += FT) {
+            const int k = e / FG, q = e % FG;
+            const float sv = 2.0f * tanhf(s.o[k * FG + q]);
+            const float tv = s.o[(Dh4 + k) * FG + q];
+            s.x[(boff + k) * FG + q] = (s.x[(boff + k) * FG + q] - tv) * expf(-sv);
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < D * FG; e += FT) s.c[e] = w_s[e % FG] * s.x[e];
+    __syncthreads();
+    const int64_t lsz = (int64_t)H * Dh + H + (int64_t)H * H + H + (int64_t)D * H + D;
+    const FlowFragOff fo = flow_frag_off(H, f.kp1, f.o4p);
+    float* part = partials + (int64_t)blockIdx.x * f.n_params;
+    for (int l = 0; l < f.L; ++l) {
+        const float* in = s.zl + l * D * FG;
+        const uint4* fr = f.frag + (int64_t)l * f.layer_frag;
+        float* gl = part + l * lsz;
+        float *gW1 = gl, *gb1 = gW1 + (int64_t)H * Dh, *gW2 = gb1 + H, *gb2 = gW2 + (int64_t)H * H, *gW3 = gb2 + H,
+              *gb3 = gW3 + (int64_t)D * H;
+        conditioner<true>(f, l, in, s);
+        const int boff = (l & 1) ? 0 : Dh, aoff = (l & 1) ? Dh : 0;
+        for (int e = t; e < Dh4 * FG; e += FT) {
+            const int k = e / FG, q = e % FG;
+            float cs_raw = 0.0f, ct = 0.0f;
+            if (k < Dh) {
+                const float th = tanhf(s.o[k * FG + q]);
+                const float ems = expf(-2.0f * th);
+                const float b = (in[(boff + k) * FG + q] - s.o[(Dh4 + k) * FG + q]) * ems;
+                const float cb = s.c[(boff + k) * FG + q];
+                const float cs = fmaf(-cb, b, w_s[q]);
+                cs_raw = cs * 2.0f * (1.0f - th * th);
+                ct = -cb * ems;
+                s.c[(boff + k) * FG + q] = cb * ems;
+            }
+            s.o[k * FG + q] = cs_raw;
+            s.o[(Dh4 + k) * FG + q] = ct;
+        }
+        __syncthreads();
+        // c_o: dW3 = c_o h2^T, db3 = row sums, c_h2 = (W3^T c_o) (1 - h2^2)
+        to_rows(s.o, f.O4, f.o4p, A16);
+        to_rows(s.h2, H, H, B16);
+        to_pm(s.o, f.O4, f.o4p, s.pm, f.o4p + 8);
+        __syncthreads();
+        cta_wgrad<true>(A16, f.o4p / 16, B16, H / 16, gW3, H, 0, H, Dh, Dh4);
+        for (int r = t; r < D; r += FT) {
+            const int rp = r < Dh ? r : Dh4 + (r - Dh);
+            float acc = 0.0f;
+            for (int q = 0; q < FG; ++q) acc += s.o[rp * FG + q];
+            gb3[r] = acc;
+        }
+        cta_mma<false, false>(fr + fo.W3t, H / 16, f.o4p / 16, s.pm, f.o4p + 8, s.ch, nullptr, H);
+        __syncthreads();
+        for (int e = t; e < H * FG; e += FT) s.ch[e] *= 1.0f - s.h2[e] * s.h2[e];
+        __syncthreads();
+        // c_h2: dW2 = c_h2 h1^T, db2, c_h1 = (W2^T c_h2) (1 - h1^2)
+        to_rows(s.ch, H, H, A16);
+        to_rows(s.h1, H, H, B16);
+        to_pm(s.ch, H, H, s.pm, H + 8);
+        __syncthreads();
+        cta_wgrad<false>(A16, H / 16, B16, H / 16, gW2, H, H, H, Dh, Dh4);
+        for (int r = t; r < H; r += FT) {
+            float acc = 0.0f;
+            for (int q = 0; q < FG; ++q) acc += s.ch[r * FG + q];
+            gb2[r] = acc;
+        }
+        cta_mma<false, false>(fr + fo.W2t, H / 16, H / 16, s.pm, H + 8, s.h2, nullptr, H);   // h2 no longer needed
+        __syncthreads();
+        for (int e = t; e < H * FG; e += FT) s.h2[e] *= 1.0f - s.h1[e] * s.h1[e];
+        __syncthreads();
+        // c_h1: dW1 = c_h1 a^T, db1, c_a += W1^T c_h1
+        to_rows(s.h2, H, H, A16);
+        to_rows(in + aoff * FG, Dh, f.kp1, B16);
+        to_pm(s.h2, H, H, s.pm, H + 8);
+        __syncthreads();
+        cta_wgrad<false>(A16, H / 16, B16, f.kp1 / 16, gW1, Dh, H, Dh, Dh, Dh4);
+        for (int r = t; r < H; r += FT) {
+            float acc = 0.0f;
+            for (int q = 0; q < FG; ++q) acc += s.h2[r * FG + q];
+            gb1[r] = acc;
+        }
+        cta_mma<false, false>(fr + fo.W1t, f.kp1 / 16, H / 16, s.pm, H + 8, s.ch, nullptr, Dh4);
+        __syncthreads();
+        for (int e = t; e < Dh * FG; e += FT) s.c[aoff * FG + e] += s.ch[e];
+        __syncthreads();
+    }
+}
+
 // grad[i] = sum over CTAs of partials[c][i], in CTA order.
 __global__ void k_flow_reduce(const float* partials, int64_t n_blocks, int64_t n_params, float* grad,
                               FlowGate gate) {
@@ -868,6 +1101,17 @@ bool flow_bf16_supported(int64_t D, int H, int L) {
     if (!flow_shape_ok(D, H, L) || !flow_bf16_ok(H)) return false;
     const int Dh4 = (int)(((D / 2) + 3) & ~3ll);
     return flow_smem_bytes((int)D, H, L, 2 * Dh4) + flow_pm_bytes() <= 226 * 1024;
+}
+
+static size_t flow_train_mma_smem_bytes(int D, int H, int L, int O4) {
+    return sizeof(float) * (size_t)FG * (2 * D + L * D + 3 * H + O4) + flow_pm_bytes() +
+           sizeof(uint16_t) * 2 * 128 * WLD;
+}
+
+bool flow_train_bf16_supported(int64_t D, int H, int L) {
+    if (!flow_shape_ok(D, H, L) || !flow_bf16_ok(H)) return false;
+    const int Dh4 = (int)(((D / 2) + 3) & ~3ll);
+    return flow_train_mma_smem_bytes((int)D, H, L, 2 * Dh4) <= 226 * 1024;
 }
 
 DevFlow flow_shape(int D, int H, int L) {
@@ -926,10 +1170,19 @@ cudaError_t flow_loss_grad(const DevFlow& f, const float* theta, int64_t ld, con
                            FlowGate gate, int64_t N, float* partials, cudaStream_t s) {
     const int64_t grid = (N + FG - 1) / FG;
     if (grid == 0) return cudaSuccess;
-    const size_t sm = flow_smem_bytes(f.D, f.H, f.L, f.O4);
-    cudaError_t e = cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_flow_train<<<(unsigned)grid, FT, sm, s>>>(f, theta, ld, src, W, gate, N, partials);
+    cudaError_t e;
+    if (f.train_bf16) {
+        if (!f.frag || f.layer_frag <= 0) return cudaErrorInvalidValue;
+        const size_t sm = flow_train_mma_smem_bytes(f.D, f.H, f.L, f.O4);
+        e = cudaFuncSetAttribute(k_flow_train_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_flow_train_mma<<<(unsigned)grid, FT, sm, s>>>(f, theta, ld, src, W, gate, N, partials);
+    } else {
+        const size_t sm = flow_smem_bytes(f.D, f.H, f.L, f.O4);
+        e = cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_flow_train<<<(unsigned)grid, FT, sm, s>>>(f, theta, ld, src, W, gate, N, partials);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_flow_reduce<<<(unsigned)((f.n_params + 255) / 256), 256, 0, s>>>(partials, grid, f.n_params, f.grad, gate);

@@ -22,6 +22,7 @@ struct DevFlow {
     int32_t D, H, L, Dh, Dh4, O4;
     int32_t kp1, o4p;            // Dh, O4 rounded up to 16
     int32_t bf16;                // 1: conditioner products on warp-level BF16 MMAs
+    int32_t train_bf16;          // 1: the training gradient's products on warp-level BF16 MMAs
     int64_t n_params;            // canonical parameter count
     int64_t layer_work;          // floats per layer of the work copies
     int64_t layer_frag;          // 16-byte fragments per layer of the BF16 copies
@@ -96,6 +97,9 @@ bool flow_shape_ok(int64_t D, int64_t H, int64_t L);
 bool flow_supported(const DevModel& m, int H, int L);
 // ... and the BF16 form of it (H a multiple of 16, room for its operand buffer)
 bool flow_bf16_supported(int64_t D, int H, int L);
+// ... and BF16 training (H a multiple of 16, room for the BF16 operands of the
+// weight-gradient products)
+bool flow_train_bf16_supported(int64_t D, int H, int L);
 // Sizes of a flow of this shape; the pointers are left null.
 DevFlow flow_shape(int D, int H, int L);
 size_t flow_smem_bytes(int D, int H, int L, int O4);
@@ -109,7 +113,9 @@ cudaError_t launch_traj_flow(const DevModel& m, const DevFlow& f, const TrajArgs
                              cudaStream_t s);
 // Gradient of the weighted NLL of the particles (theta gathered through src,
 // weights 1/n after resampling, else W) into f.grad, using `partials`
-// (n_blocks x n_params floats) for a fixed-order reduction.
+// (n_blocks x n_params floats) for a fixed-order reduction; with f.train_bf16
+// the conditioner, transposed and weight-gradient products run on BF16 warp
+// MMAs (f.frag must hold the fragments of the current params).
 int64_t flow_partials_floats(const DevFlow& f, int64_t N);
 // gate.rs / gate.rp describe the single run of the handle (nullptr: weights W
 // as given, always open).

@@ -1453,8 +1453,13 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
         return reject("precision must be SMC_PREC_FP32 or SMC_PREC_BF16");
     if (fc->precision == SMC_PREC_BF16 && !flow_bf16_supported(h->D, fc->hidden, fc->layers))
         return reject("the BF16 form needs hidden a multiple of 16 in [16, 128]");
+    if (fc->train_precision != SMC_PREC_FP32 && fc->train_precision != SMC_PREC_BF16)
+        return reject("train_precision must be SMC_PREC_FP32 or SMC_PREC_BF16");
+    if (fc->train_precision == SMC_PREC_BF16 && !flow_train_bf16_supported(h->D, fc->hidden, fc->layers))
+        return reject("BF16 training needs hidden a multiple of 16 in [16, 128]");
     DevFlow f = flow_shape((int)h->D, fc->hidden, fc->layers);
     f.bf16 = fc->precision == SMC_PREC_BF16 ? 1 : 0;
+    f.train_bf16 = fc->train_precision == SMC_PREC_BF16 ? 1 : 0;
     std::vector<float> p32((size_t)f.n_params);
     for (int64_t i = 0; i < f.n_params; ++i) {
         if (!std::isfinite(params[i])) return reject("non-finite parameter");
@@ -1466,7 +1471,7 @@ smc_status smc_flow_enable(smc_handle* h, const smc_flow_config* fc, const doubl
     f.adam_v = A.get<float>((size_t)f.n_params);
     f.grad = A.get<float>((size_t)f.n_params);
     f.work = A.get<float>((size_t)(f.L * f.layer_work));
-    if (f.bf16) f.frag = A.get<uint4>((size_t)(f.L * f.layer_frag));
+    if (f.bf16 || f.train_bf16) f.frag = A.get<uint4>((size_t)(f.L * f.layer_frag));
     f.adam_t = A.get<int32_t>(1);
     float* partials = A.get<float>((size_t)flow_partials_floats(f, h->N));
     float* z0 = A.get<float>((size_t)(h->D * h->ld));
@@ -1534,15 +1539,20 @@ struct TmpFlow {
 
 smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, const float* params,
                                 const float* theta, const double* W, int64_t N, int64_t ld, float* grad,
-                                void* stream) {
+                                int32_t precision, void* stream) {
     if (!flow_shape_ok(dim, hidden, layers) || !params || !grad || N < 0 || ld < N) return SMC_E_INVAL;
     if (N > 0 && (!theta || !W)) return SMC_E_INVAL;
+    if (precision != SMC_PREC_FP32 && precision != SMC_PREC_BF16) return SMC_E_INVAL;
+    const bool bf16 = precision == SMC_PREC_BF16;
+    if (bf16 && !flow_train_bf16_supported(dim, hidden, layers)) return SMC_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TmpFlow t;
-    if (!t.make(dim, hidden, layers, params, std::max<int64_t>(N, 1), s)) {
+    if (!t.make(dim, hidden, layers, params, std::max<int64_t>(N, 1), s, bf16)) {
         t.mem.release();
         return SMC_E_NOMEM;
     }
+    t.f.bf16 = 0;
+    t.f.train_bf16 = bf16 ? 1 : 0;
     t.f.grad = grad;
     cudaError_t e = flow_refresh(t.f, s);
     if (e == cudaSuccess && N == 0) e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)t.f.n_params, s);

@@ -66,7 +66,7 @@ def test_loss_gradient_matches_oracle(D, H, L):
     th_d[:, :N] = dev(th.T, torch.float32)
     grad = torch.empty(p.size, dtype=torch.float32, device="cuda")
     p_d, W_d = dev(p, torch.float32), dev(W)          # kept alive across the asynchronous calls
-    st = B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad), stream())
+    st = B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad), 0, stream())
     assert st == 0
     torch.cuda.synchronize()
     g_gpu = grad.cpu().numpy().astype(np.float64)
@@ -83,9 +83,89 @@ def test_loss_gradient_matches_oracle(D, H, L):
             o += sz
     # identical inputs give identical bits (fixed-order reduction)
     grad2 = torch.empty_like(grad)
-    assert B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad2), stream()) == 0
+    assert B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad2), 0,
+                                        stream()) == 0
     torch.cuda.synchronize()
     assert torch.equal(grad, grad2)
+
+
+def _gpu_loss_grad(D, H, L, p, th, W, precision, reps=1):
+    """smc_k_flow_loss_grad on N particles (theta padded to a 32-multiple
+    leading dimension); returns `reps` gradients of identical calls."""
+    N = th.shape[0]
+    ld = ((N + 31) // 32) * 32 + 32
+    th_d = torch.zeros((D, ld), dtype=torch.float32, device="cuda")
+    th_d[:, :N] = dev(th.T, torch.float32)
+    p_d, W_d = dev(p, torch.float32), dev(W)
+    out = []
+    for _ in range(reps):
+        grad = torch.empty(p.size, dtype=torch.float32, device="cuda")
+        st = B.lib().smc_k_flow_loss_grad(D, H, L, ptr(p_d), ptr(th_d), ptr(W_d), N, ld, ptr(grad), precision,
+                                          stream())
+        assert st == 0
+        out.append(grad)
+    torch.cuda.synchronize()
+    return [x.cpu().numpy().astype(np.float64) for x in out]
+
+
+@pytest.mark.parametrize("D,H,L", [(10, 32, 4), (50, 128, 4), (100, 128, 4), (4, 16, 2)])
+def test_bf16_loss_gradient_near_oracle(D, H, L):
+    """The training gradient with its products on BF16 warp MMAs against the
+    FP64 oracle.  A product of two operands rounded to BF16 (unit roundoff
+    u = 2^-8) is off by at most 2u relative to its terms, and the gradient of
+    a layer-l parameter sits at the end of a chain of at most 6 L such
+    products (3 L in the inverse pass, 3 per backward layer up to l, the
+    weight-gradient product last).  First order, a block's norm-wise error and
+    an element's error relative to |g| + rms(g) are below 12 L u (0.19 at
+    L = 4), and with independent roundings the typical block below
+    sqrt(6 L) u (1.9e-2 at L = 4); measured, the block medians are 3.5e-3 to
+    4.5e-3 (about u), the worst block 7.5e-3 and the worst element 4e-2.  A
+    wrong fragment, operand layout or row map gives order one (a lost row:
+    about 0.5).  Identical inputs give identical bits."""
+    N = 300
+    rng = np.random.default_rng(D + H)
+    p = _params(D, H, L, seed=D, scale=0.3)
+    th = f32r(rng.standard_normal((N, D)) * 1.3)
+    W = rng.uniform(0.0, 1.0, N)
+    W /= W.sum()
+    _, g_o = oracle.flow_loss_grad(oracle.FlowSpec(D, H, L, p), th, W)
+    g_gpu, g_again = _gpu_loss_grad(D, H, L, p, th, W, 2, reps=2)
+    np.testing.assert_array_equal(g_gpu, g_again)
+    Dh = D // 2
+    sizes = [H * Dh, H, H * H, H, D * H, D]
+    u = 2.0**-8
+    bound = 12 * L * u
+    o, worst = 0, []
+    for l in range(L):
+        for sz in sizes:
+            go, gg = g_o[o:o + sz], g_gpu[o:o + sz]
+            nrm = np.linalg.norm(gg - go) / (np.linalg.norm(go) + 1e-30)
+            rel = np.abs(gg - go) / (np.abs(go) + np.sqrt(np.mean(go**2)) + 1e-30)
+            worst.append(nrm)
+            assert nrm < bound and rel.max() < bound, (l, sz, nrm, rel.max(), bound)
+            o += sz
+    # the typical block is near the independent-rounding estimate, not the bound
+    assert np.median(worst) < 2 * np.sqrt(6 * L) * u, (np.median(worst), max(worst))
+
+
+def test_bf16_training_from_the_identity_map():
+    """From a zero last layer the transposed product W3^T c_o is exactly zero
+    in BF16 too, so one BF16-trained Adam step moves only W3 and b3, each by
+    lr * sign(gradient) up to Adam's eps, as the FP64 oracle's step; a
+    gradient below the BF16 noise may take the other sign."""
+    D, H, L, lr = 10, 32, 4, 1e-3
+    p_init = f32r(workloads.flow_init(D, H, L, seed=5))
+    p_gpu, p_o = _train_case(p_init, 1, lr, train_precision=2)
+    Dh = D // 2
+    lsz = H * Dh + H + H * H + H + D * H + D
+    for l in range(L):
+        o = l * lsz
+        hid = slice(o, o + H * Dh + 2 * H + H * H)
+        np.testing.assert_array_equal(p_gpu[hid], p_init[hid])
+        last = slice(o + H * Dh + 2 * H + H * H, o + lsz)
+        d = np.abs(p_gpu[last] - p_o[last])
+        assert np.all(d <= 2 * lr + 1e-7)
+        assert np.mean(d <= 1e-3 * lr) > 0.95, np.mean(d <= 1e-3 * lr)
 
 
 def oracle_flow_move(f, t, theta, p0, eps, S):
@@ -248,15 +328,16 @@ def test_flow_iterations_match_oracle_stage_by_stage(name):
     smp.close()
 
 
-def _train_case(p_init, E, lr, seed=9):
-    """GPU iteration 1 with training on; returns the GPU parameters after it
-    and the oracle's parameters after E Adam steps on the same particles."""
+def _train_case(p_init, E, lr, seed=9, train_precision=0):
+    """GPU iteration 1 with training on (its products in FP32 or BF16);
+    returns the GPU parameters after it and the oracle's parameters after E
+    Adam steps on the same particles."""
     w = rounded_workload(workloads.gauss10())
     run = dict(n_particles=512, n_iters=6, n_warmup=4, step_size=0.05, traj_len0=0.3, max_steps=20,
                init_scale=2.0)
     D, H, L = 10, 32, 4
     smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=seed, **run), stream())
-    smp.enable_flow(p_init, H, L, train_every=1, epochs=E, lr=lr, min_ess_frac=0.0)
+    smp.enable_flow(p_init, H, L, train_every=1, epochs=E, lr=lr, min_ess_frac=0.0, train_precision=train_precision)
     th0 = smp.buffer(B.BUF_THETA).T.astype(np.float64)
     logw0 = smp.buffer(B.BUF_LOGW)
     st = smp.step()[0]
@@ -347,12 +428,12 @@ def test_identity_map_gives_the_plain_sampler(precision):
     flow.close()
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_trained_map_raises_acceptance_and_ess(precision):
+@pytest.mark.parametrize("precision,train_precision", [(0, 0), (2, 0), (2, 2)])
+def test_trained_map_raises_acceptance_and_ess(precision, train_precision):
     """Ill-conditioned 4-d Gaussian (variances 0.01 .. 4) at a step size the
     stiff direction barely tolerates (the oracle's pin of the same claim):
     training the map on the particles whitens the target (with the map's
-    products in FP32 or BF16; training is FP32 in both)."""
+    products in FP32 or BF16, and its training products in FP32 or BF16)."""
     tgt = workloads._gauss_from_spectrum(np.array([0.01, 0.1, 1.0, 4.0]), 11)
     w = rounded_workload(tgt)
     run = dict(n_particles=512, n_iters=16, n_warmup=12, step_size=0.18, traj_len0=1.0, max_steps=500,
@@ -361,7 +442,7 @@ def test_trained_map_raises_acceptance_and_ess(precision):
     plain = g.Sampler(md, g.make_config(seed=21, **run), stream())
     flow = g.Sampler(md, g.make_config(seed=21, **run), stream())
     flow.enable_flow(f32r(workloads.flow_init(4, 32, 4, seed=5)), 32, 4, train_every=1, epochs=60, lr=3e-3,
-                     precision=precision)
+                     precision=precision, train_precision=train_precision)
     sp = [plain.step()[0] for _ in range(run["n_iters"])]
     sf = []
     for k in range(run["n_iters"]):
@@ -393,6 +474,10 @@ def test_flow_rejects_unsupported_configurations():
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 30, 4)), 30, 4)     # H not a multiple of 4
     with pytest.raises(RuntimeError):                                                  # BF16: H not a multiple of 16
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 40, 4)), 40, 4, precision=2)
+    with pytest.raises(RuntimeError):                                                  # BF16 training: the same
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 40, 4)), 40, 4, train_precision=2)
+    with pytest.raises(RuntimeError):                                                  # no such training precision
+        smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4, train_precision=1)
     smp.step()
     with pytest.raises(RuntimeError):                                                  # after the first iteration
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4)
@@ -474,7 +559,7 @@ def test_bf16_transport_round_trip_is_exact(name):
 @pytest.mark.parametrize("name,N", [("banana50", 77), ("gauss10", 77), ("gauss100", 77), ("gauss100", 8192)])
 def test_bf16_latent_leapfrog_near_oracle(name, N):
     """One latent leapfrog step with BF16 conditioner products against the FP64
-    oracle map.  BF16 rounds weights and activations (relative 2^-9): the map
+    oracle map.  BF16 rounds weights and activations (unit roundoff 2^-8): the map
     (z0, theta') carries errors of about 2e-3 of its scale (bound 2e-2), and the
     latent gradient, whose vector-Jacobian products pass through the twelve
     BF16 products of the four layers twice, up to 5e-2 of the gradient scale

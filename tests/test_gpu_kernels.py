@@ -338,10 +338,11 @@ def test_resampling_one_hot_and_degenerate():
 
 # ------------------------------------------------------------- tensor-core path
 # Gradient error bounds of the split-BF16 products, relative to the sum of
-# absolute summands: each operand x = hi + lo with |x - hi| <= 2^-9 |x| and
-# |x - hi - lo| <= 2^-17 |x|, so the x3 form (hi*hi + lo*hi + hi*lo, lo*lo
-# dropped) errs by about 2^-16 per product plus FP32 accumulation, and plain
-# BF16 by about 2^-8; the bounds below allow a few times that.  The end-point
+# absolute summands: BF16 keeps 8 significant bits, so each operand
+# x = hi + lo with |x - hi| <= 2^-8 |x| and |x - hi - lo| <= 2^-16 |x|; the
+# x3 form (hi*hi + lo*hi + hi*lo, lo*lo dropped) errs by at most about
+# 3 x 2^-16 (4.6e-5) per product plus FP32 accumulation, and plain BF16 by
+# at most 2 x 2^-8 (7.8e-3); the bounds below sit above these.  The end-point
 # log pi is FP32 in every mode.
 TC_GRAD_TOL = {1: 6e-5, 2: 2e-2}
 
