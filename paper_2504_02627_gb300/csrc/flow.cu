@@ -714,6 +714,23 @@ __device__ __forceinline__ float rot_dot(const float* A, const float* B, int lan
     return acc;
 }
 
+// out[r] = sum over the CTA's 32 particles of X[row(r)][p] for r < R (the
+// bias gradients): a warp per row, its lanes over the particles (one
+// conflict-free load each), summed by shuffles in a fixed order.  CMAP: row
+// r < Dh is X's row r, the others X's row Dh4 + (r - Dh) (the padded
+// conditioner output).
+template <bool CMAP>
+__device__ __forceinline__ void row_sums(const float* X, int R, float* out, int Dh, int Dh4) {
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < R; r += FT / 32) {
+        const int rp = CMAP ? (r < Dh ? r : Dh4 + (r - Dh)) : r;
+        float v = X[rp * FG + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) out[r] = v;
+    }
+}
+
 __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* theta, int64_t ld,
                                                       const int32_t* src, const double* W, FlowGate gate, int64_t N,
                                                       float* partials) {
@@ -790,12 +807,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
             const int rp = r < Dh ? r : Dh4 + (r - Dh);
             gW3[(int64_t)r * H + h] = rot_dot(s.o + rp * FG, s.h2 + h * FG, lane);
         }
-        for (int r = t; r < D; r += FT) {
-            const int rp = r < Dh ? r : Dh4 + (r - Dh);
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.o[rp * FG + q];
-            gb3[r] = acc;
-        }
+        row_sums<true>(s.o, D, gb3, Dh, Dh4);
         cta_mm<false, false>(w + off.W3, f.O4, H, s.o, s.ch, nullptr);
         __syncthreads();
         for (int e = t; e < H * FG; e += FT) s.ch[e] *= 1.0f - s.h2[e] * s.h2[e];   // c_h2
@@ -804,11 +816,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
             const int r = e / H, h = e % H;
             gW2[(int64_t)r * H + h] = rot_dot(s.ch + r * FG, s.h1 + h * FG, lane);
         }
-        for (int r = t; r < H; r += FT) {
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.ch[r * FG + q];
-            gb2[r] = acc;
-        }
+        row_sums<false>(s.ch, H, gb2, Dh, Dh4);
         cta_mm<false, false>(w + off.W2, H, H, s.ch, s.h2, nullptr);   // h2 no longer needed
         __syncthreads();
         for (int e = t; e < H * FG; e += FT) s.h2[e] *= 1.0f - s.h1[e] * s.h1[e];   // c_h1
@@ -817,11 +825,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train(DevFlow f, const float* th
             const int h = e / Dh, k = e % Dh;
             gW1[(int64_t)h * Dh + k] = rot_dot(s.h2 + h * FG, in + (aoff + k) * FG, lane);
         }
-        for (int r = t; r < H; r += FT) {
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.h2[r * FG + q];
-            gb1[r] = acc;
-        }
+        row_sums<false>(s.h2, H, gb1, Dh, Dh4);
         cta_mm<false, false>(w + off.W1, H, Dh4, s.h2, s.ch, nullptr);
         __syncthreads();
         for (int e = t; e < Dh * FG; e += FT) s.c[aoff * FG + e] += s.ch[e];
@@ -1015,12 +1019,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train_mma(DevFlow f, const float
         to_pm(s.o, f.O4, f.o4p, s.pm, f.o4p + 8);
         __syncthreads();
         cta_wgrad<true>(A16, f.o4p / 16, B16, H / 16, gW3, H, 0, H, Dh, Dh4);
-        for (int r = t; r < D; r += FT) {
-            const int rp = r < Dh ? r : Dh4 + (r - Dh);
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.o[rp * FG + q];
-            gb3[r] = acc;
-        }
+        row_sums<true>(s.o, D, gb3, Dh, Dh4);
         cta_mma<false, false>(fr + fo.W3t, H / 16, f.o4p / 16, s.pm, f.o4p + 8, s.ch, nullptr, H);
         __syncthreads();
         for (int e = t; e < H * FG; e += FT) s.ch[e] *= 1.0f - s.h2[e] * s.h2[e];
@@ -1031,11 +1030,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train_mma(DevFlow f, const float
         to_pm(s.ch, H, H, s.pm, H + 8);
         __syncthreads();
         cta_wgrad<false>(A16, H / 16, B16, H / 16, gW2, H, H, H, Dh, Dh4);
-        for (int r = t; r < H; r += FT) {
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.ch[r * FG + q];
-            gb2[r] = acc;
-        }
+        row_sums<false>(s.ch, H, gb2, Dh, Dh4);
         cta_mma<false, false>(fr + fo.W2t, H / 16, H / 16, s.pm, H + 8, s.h2, nullptr, H);   // h2 no longer needed
         __syncthreads();
         for (int e = t; e < H * FG; e += FT) s.h2[e] *= 1.0f - s.h1[e] * s.h1[e];
@@ -1046,11 +1041,7 @@ __global__ void __launch_bounds__(FT, 1) k_flow_train_mma(DevFlow f, const float
         to_pm(s.h2, H, H, s.pm, H + 8);
         __syncthreads();
         cta_wgrad<false>(A16, H / 16, B16, f.kp1 / 16, gW1, Dh, H, Dh, Dh, Dh4);
-        for (int r = t; r < H; r += FT) {
-            float acc = 0.0f;
-            for (int q = 0; q < FG; ++q) acc += s.h2[r * FG + q];
-            gb1[r] = acc;
-        }
+        row_sums<false>(s.h2, H, gb1, Dh, Dh4);
         cta_mma<false, false>(fr + fo.W1t, f.kp1 / 16, H / 16, s.pm, H + 8, s.ch, nullptr, Dh4);
         __syncthreads();
         for (int e = t; e < Dh * FG; e += FT) s.c[aoff * FG + e] += s.ch[e];
