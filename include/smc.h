@@ -247,7 +247,11 @@ typedef enum {
     SMC_BUF_RUNSTATE = 11,  /* f64 [n_runs x 9] log_z, log_L, adam_m, adam_v, Lbar, adam_t, L of the last iteration, its ESS,
                                the step size of the next iteration */
     SMC_BUF_Z0 = 12,        /* f32 [dim x ld]   latent start points z0 = T^-1(theta) of the last move (transport map on) */
-    SMC_BUF_Z1 = 13         /* f32 [dim x ld]   latent end points z' of the last move (transport map on) */
+    SMC_BUF_Z1 = 13,        /* f32 [dim x ld]   latent end points z' of the last move (transport map on) */
+    SMC_BUF_ORDER = 14      /* i32 [N]          launch order of the last move: slot t holds particle
+                               perm[t] (handle-wide), step counts non-increasing
+                               along the slots; particles with equal counts in
+                               any order (a counting sort with atomic slots)   */
 } smc_buffer;
 smc_status smc_get_buffer(const smc_handle* h, int32_t which, void* dst, int64_t bytes,
                           int32_t device_ptrs);

@@ -23,7 +23,7 @@ PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_BF16X2, PREC_BF16C = 0, 1, 2, 3, 4
  JITTER_PRIMES_INV, JITTER_GOLDEN, JITTER_EQUIDISTANT, JITTER_EQUIDISTANT_OFFSET, JITTER_SOBOL1,
  JITTER_HALTON1_ITER) = range(12)
 (BUF_THETA, BUF_GRAD, BUF_LOGPI, BUF_LOGW, BUF_W, BUF_ANCESTORS, BUF_STEPS, BUF_P_FINAL,
- BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1) = range(14)
+ BUF_DH, BUF_ALPHA, BUF_THETA_PREV, BUF_RUNSTATE, BUF_Z0, BUF_Z1, BUF_ORDER) = range(15)
 
 _DP = C.POINTER(C.c_double)
 
@@ -307,7 +307,7 @@ class Sampler:
                   BUF_W: ((N,), np.float64), BUF_DH: ((N,), np.float64),
                   BUF_ALPHA: ((N,), np.float64), BUF_ANCESTORS: ((N,), np.int32),
                   BUF_STEPS: ((N,), np.int32), BUF_RUNSTATE: ((self.n_runs, 9), np.float64),
-                  BUF_Z0: ((D, ld), np.float32), BUF_Z1: ((D, ld), np.float32)}
+                  BUF_Z0: ((D, ld), np.float32), BUF_Z1: ((D, ld), np.float32), BUF_ORDER: ((N,), np.int32)}
         shape, dt = shapes[which]
         out = np.empty(shape, dtype=dt)
         check(lib().smc_get_buffer(self.h, which, out.ctypes.data, out.nbytes, 0), "smc_get_buffer",

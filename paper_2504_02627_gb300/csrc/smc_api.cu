@@ -1109,6 +1109,7 @@ smc_status smc_get_buffer(const smc_handle* hc, int32_t which, void* dst, int64_
         case SMC_BUF_THETA_PREV: srcp = h->theta[1 - h->cur]; avail = nd * 4; break;
         case SMC_BUF_Z0: srcp = h->z0; avail = h->flow_on ? nd * 4 : 0; break;
         case SMC_BUF_Z1: srcp = h->z1; avail = h->flow_on ? nd * 4 : 0; break;
+        case SMC_BUF_ORDER: srcp = h->perm; avail = h->N * 4; break;
         case SMC_BUF_RUNSTATE: {
             std::vector<RunState> st((size_t)h->n_runs);
             cudaError_t e = cudaMemcpyAsync(st.data(), h->d_rstate, sizeof(RunState) * (size_t)h->n_runs,

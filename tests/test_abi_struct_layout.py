@@ -61,3 +61,31 @@ def test_oracle_struct_layouts_match_its_header(tmp_path):
         assert got[(cname, "sizeof")] == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_enum_values_match_the_header(tmp_path):
+    """The binding's status codes, model kinds, precisions and buffer ids are
+    the values of the header's enums."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = {"SMC_OK": B.SMC_OK, "SMC_E_INVAL": B.SMC_E_INVAL, "SMC_E_NOMEM": B.SMC_E_NOMEM,
+             "SMC_E_CUDA": B.SMC_E_CUDA, "SMC_E_DEGENERATE": B.SMC_E_DEGENERATE, "SMC_E_TIMEOUT": B.SMC_E_TIMEOUT,
+             "SMC_E_STATE": B.SMC_E_STATE}
+    for k in ("GAUSS_DENSE", "LOGISTIC", "HIER_NORMAL", "BANANA", "LINEAR_GAUSS"):
+        names["SMC_MODEL_" + k] = getattr(B, k)
+    for k in ("FP32", "BF16X3", "BF16", "BF16X2", "BF16C"):
+        names["SMC_PREC_" + k] = getattr(B, "PREC_" + k)
+    for k in ("THETA", "GRAD", "LOGPI", "LOGW", "W", "ANCESTORS", "STEPS", "P_FINAL", "DH", "ALPHA", "THETA_PREV",
+              "RUNSTATE", "Z0", "Z1", "ORDER"):
+        names["SMC_BUF_" + k] = getattr(B, "BUF_" + k)
+    lines = ['#include <stdio.h>', '#include "smc.h"', "int main(void) {"]
+    lines += [f'    printf("{n} %d\\n", (int){n});' for n in names]
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "enums"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {ln.split()[0]: int(ln.split()[1]) for ln in out if ln.strip()}
+    assert got == names

@@ -197,6 +197,31 @@ def test_batched_runs_equal_single_runs_bit_for_bit(name):
     batch.close()
 
 
+@pytest.mark.parametrize("name,precision", [("gauss10", 0), ("hier", 0), ("logistic", 4)])
+def test_step_count_order_is_a_descending_permutation(name, precision):
+    """Every move launches the particles of the whole handle ordered by step
+    count, longest first (a counting sort over S_j): the order of the last
+    move is a permutation of all particles of all runs with non-increasing
+    step counts; particles with equal counts may come in any order, so only
+    that is compared.  A batch of uneven runs and a single run; the centred
+    form also partitions the order by run, from this same order."""
+    w = _cases()[name]
+    run = dict(w["run"])
+    for sizes in ([300, 37, 1025], [777]):
+        cfgs = [_cfg(dict(run, n_particles=n, precision=precision), 900 + i) for i, n in enumerate(sizes)]
+        smp = g.Sampler(g.ModelData.from_workload(w), cfgs if len(cfgs) > 1 else cfgs[0], stream())
+        for _ in range(3):
+            smp.step(with_stats=False)
+            order = smp.buffer(B.BUF_ORDER)
+            steps = smp.buffer(B.BUF_STEPS)
+            N = sum(sizes)
+            np.testing.assert_array_equal(np.sort(order), np.arange(N))
+            s = steps[order]
+            assert np.all(s[:-1] >= s[1:]), (sizes, s[:20])
+            assert s.min() >= 1 and s.max() <= run["max_steps"]
+        smp.close()
+
+
 def test_degenerate_target_reports_status():
     w = {"kind": "gauss_dense", "D": 2, "mu": np.zeros(2), "P": np.eye(2), "c": float("nan")}
     smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(64, 3, 1, 0.1), stream())
