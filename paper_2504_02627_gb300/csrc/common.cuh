@@ -350,6 +350,30 @@ __device__ __forceinline__ T block_reduce(T v, T* buf, Op op) {
     return r;
 }
 
+// N block reductions in one pass: every value goes through the same
+// shuffle tree and the same warp-by-warp combination as block_reduce, so each
+// result has the bits block_reduce would give it, while the N dependency
+// chains overlap and share two barriers.  `buf` needs N * 32 entries.
+template <int N, typename T, typename Op>
+__device__ __forceinline__ void block_reduce_n(T (&v)[N], T* buf, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = op(v[i], __shfl_xor_sync(0xffffffffu, v[i], o));
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) buf[i * 32 + wid] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T r = buf[i * 32];
+        for (int w = 1; w < nw; ++w) r = op(r, buf[i * 32 + w]);
+        v[i] = r;
+    }
+}
+
 struct OpSum { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
 struct OpMax { template <typename T> __device__ T operator()(T a, T b) const { return a > b ? a : b; } };
 struct OpMin { template <typename T> __device__ T operator()(T a, T b) const { return a < b ? a : b; } };

@@ -450,9 +450,9 @@ __device__ __forceinline__ void block_lse(double a, double* buf, double& M, doub
 }
 
 __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
-    __shared__ double buf[32];
+    __shared__ double buf[5 * 32];
     __shared__ long long lbuf[32];
-    __shared__ int ibuf[32];
+    __shared__ int ibuf[2 * 32];
     const SliceIdx x = slice_idx(b);
     const RunParams& rp = b.runs[x.r];
     const RunState& st = b.rstate[x.r];
@@ -473,18 +473,30 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
         S = b.steps[x.j];
         smin = smax = (int)S;
     }
+    // the slice's reductions, each with block_reduce's tree, in three passes:
+    // the two maxima, then the five sums that need them; the integer parts
     SlicePart part;
-    block_lse(za, buf, part.za_m, part.za_s);
-    part.w_m = block_reduce(lw, buf, OpMax());
+    double mx[2] = {za, lw};
+    block_reduce_n(mx, buf, OpMax());
+    part.za_m = mx[0];
+    part.w_m = mx[1];
     const double e = (x.valid && part.w_m > -CUDART_INF) ? exp(lw - part.w_m) : 0.0;
-    part.w_e1 = block_reduce(e, buf, OpSum());
-    part.w_e2 = block_reduce(e * e, buf, OpSum());
-    part.alpha_sum = block_reduce(al, buf, OpSum());
     const bool step_rule = rp.step_rate > 0.0 && st.k < rp.n_warmup;
-    part.inv_alpha_sum = step_rule ? block_reduce(x.valid ? 1.0 / al : 0.0, buf, OpSum()) : 0.0;
-    part.steps_sum = block_reduce(S, lbuf, OpSum());
-    part.smin = block_reduce(smin, ibuf, OpMin());
-    part.smax = block_reduce(smax, ibuf, OpMax());
+    double sm[5] = {part.za_m > -CUDART_INF ? exp(za - part.za_m) : 0.0, e, e * e, al,
+                    step_rule ? (x.valid ? 1.0 / al : 0.0) : 0.0};
+    block_reduce_n(sm, buf, OpSum());
+    part.za_s = sm[0];
+    part.w_e1 = sm[1];
+    part.w_e2 = sm[2];
+    part.alpha_sum = sm[3];
+    part.inv_alpha_sum = step_rule ? sm[4] : 0.0;
+    long long ls[1] = {S};
+    block_reduce_n(ls, lbuf, OpSum());
+    part.steps_sum = ls[0];
+    int mm[2] = {-smin, smax};   // min S as -max(-S)
+    block_reduce_n(mm, ibuf, OpMax());
+    part.smin = -mm[0];
+    part.smax = mm[1];
     part.g_num = 0.0;
     part.g_den = 0.0;
     if (threadIdx.x == 0) b.parts[c] = part;
@@ -547,7 +559,9 @@ __global__ void __launch_bounds__(SLICE) k_move_stats(StepBufs b) {
 // evidence, log-weights' ESS, Adam ascent on log L, Lbar, the freeze at
 // M_warmup, statistics, and the weight decision of the next iteration.
 __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
-    __shared__ double buf[32];
+    __shared__ double buf[7 * 32];
+    __shared__ long long lbuf[32];
+    __shared__ int ibuf[2 * 32];
     __shared__ float mean_s[4 * MAX_CHEES_DIM];   // negated means as FP32 pairs: hi [2D], lo [2D]
     __shared__ bool last_s;
     const SliceIdx x = slice_idx(b);
@@ -614,11 +628,11 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
             num = a * ((h * st.L_used) * (f2_to_double(sq1) - f2_to_double(sq0)) * f2_to_double(proj));
             den = a;
         }
-        num = block_reduce(num, buf, OpSum());
-        den = block_reduce(den, buf, OpSum());
+        double nd[2] = {num, den};
+        block_reduce_n(nd, buf, OpSum());
         if (threadIdx.x == 0) {
-            b.parts[c].g_num = num;
-            b.parts[c].g_den = den;
+            b.parts[c].g_num = nd[0];
+            b.parts[c].g_den = nd[1];
         }
     }
     // Metropolis variant (Eqs. for alpha and the select rule): keep the
@@ -654,8 +668,10 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
         za_m = fmax(za_m, __ldcg(&p->za_m));
         w_m = fmax(w_m, __ldcg(&p->w_m));
     }
-    za_m = block_reduce(za_m, buf, OpMax());
-    w_m = block_reduce(w_m, buf, OpMax());
+    double mx[2] = {za_m, w_m};
+    block_reduce_n(mx, buf, OpMax());
+    za_m = mx[0];
+    w_m = mx[1];
     double za_s = 0.0, w_e1 = 0.0, w_e2 = 0.0, asum = 0.0, gnum = 0.0, gden = 0.0, iasum = 0.0;
     long long ssum = 0;
     int smin = 0x7fffffff, smax = 0;
@@ -688,16 +704,23 @@ __global__ void __launch_bounds__(SLICE) k_chees_finish(StepBufs b) {
         smin = min(smin, p.smin);
         smax = max(smax, p.smax);
     }
-    za_s = block_reduce(za_s, buf, OpSum());
-    w_e1 = block_reduce(w_e1, buf, OpSum());
-    w_e2 = block_reduce(w_e2, buf, OpSum());
-    asum = block_reduce(asum, buf, OpSum());
-    iasum = block_reduce(iasum, buf, OpSum());
-    gnum = block_reduce(gnum, buf, OpSum());
-    gden = block_reduce(gden, buf, OpSum());
-    ssum = block_reduce(ssum, reinterpret_cast<long long*>(buf), OpSum());
-    smin = block_reduce(smin, reinterpret_cast<int*>(buf), OpMin());
-    smax = block_reduce(smax, reinterpret_cast<int*>(buf), OpMax());
+    // the run's sums, each with block_reduce's tree, in one pass per type
+    double sm[7] = {za_s, w_e1, w_e2, asum, iasum, gnum, gden};
+    block_reduce_n(sm, buf, OpSum());
+    za_s = sm[0];
+    w_e1 = sm[1];
+    w_e2 = sm[2];
+    asum = sm[3];
+    iasum = sm[4];
+    gnum = sm[5];
+    gden = sm[6];
+    long long ls[1] = {ssum};
+    block_reduce_n(ls, lbuf, OpSum());
+    ssum = ls[0];
+    int mm[2] = {-smin, smax};   // min S as -max(-S)
+    block_reduce_n(mm, ibuf, OpMax());
+    smin = -mm[0];
+    smax = mm[1];
     if (threadIdx.x != 0) return;
     const int64_t k = st.k;
     if (adapting) {
