@@ -4,6 +4,7 @@ micro-benchmark and the profiling driver for one trajectory kernel at a time).
     python kernel_bench.py stream --n 20000 --particles 16384 --steps 40
     python kernel_bench.py flow --particles 8192 --steps 8
     python kernel_bench.py flow_train --particles 8192 --precision 2
+    python kernel_bench.py latency --iters 20
     python kernel_bench.py glm --particles 4096 --steps 20
     python kernel_bench.py gauss --particles 8192 --steps 20 --eps 0.005 --precision 1
 
@@ -168,6 +169,31 @@ def run_flow_train(args):
             "tflops_algorithmic": flops / (ms / 1e3) / 1e12}
 
 
+def run_latency(args):
+    """One SMC run of the 10-d Gaussian workload (256 particles, FP32 thread
+    kernel): smc_reset and --iters iterations by graph replay between two
+    events, after one untimed run; the time per iteration, best of --reps."""
+    torch, workloads, B = _setup()
+    import paper_2504_02627_gb300 as g
+    s = torch.cuda.current_stream().cuda_stream
+    w = workloads.gauss10()
+    run = dict(w["run"])
+    smp = g.Sampler(g.ModelData.from_workload(w), g.make_config(seed=31, **run), s)
+    smp.run(run["n_iters"])
+    best = float("inf")
+    for r in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        smp.reset(32 + r)
+        smp.run(args.iters)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e3 / args.iters)
+    smp.close()
+    return {"kernel": "SMC iteration latency", "D": w["D"], "particles": run["n_particles"], "iters": args.iters,
+            "reps": args.reps, "us_per_iteration": best}
+
+
 def run_sampler(args):
     """SMC iterations of the centred sampler on a handle (the path the bench
     runs: slot-ordered state, and with --runs > 1 the run-uniform tiles):
@@ -197,7 +223,7 @@ def run_sampler(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["stream", "flow", "flow_train", "glm", "gauss", "sampler"])
+    ap.add_argument("which", choices=["stream", "flow", "flow_train", "glm", "gauss", "sampler", "latency"])
     ap.add_argument("--n", type=int, default=20000, help="observations (stream)")
     ap.add_argument("--dim", type=int, default=100, help="coefficients of the streamed regression")
     ap.add_argument("--particles", type=int, default=16384)
@@ -210,10 +236,13 @@ def main(argv=None):
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--runs", type=int, default=1, help="sampler: runs in the handle")
-    ap.add_argument("--iters", type=int, default=3, help="sampler: timed SMC iterations")
+    ap.add_argument("--iters", type=int, default=3, help="sampler, latency: timed SMC iterations")
+    ap.add_argument("--reps", type=int, default=5, help="latency: timed runs (the best is reported)")
     args = ap.parse_args(argv)
     if args.which == "sampler":
         out = run_sampler(args)
+    elif args.which == "latency":
+        out = run_latency(args)
     elif args.which == "flow":
         out = run_flow(args)
     elif args.which == "flow_train":
