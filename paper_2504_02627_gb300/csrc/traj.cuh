@@ -78,7 +78,8 @@ struct TrajArgs {
     // run (written by the launcher before the trajectory kernel)
     float* c_centre;        // [c_runs][dk] reference points theta_ref
     float* c_gref;          // [c_runs][dk] reference gradients X'(y - s)
-    float2* c_refs;         // [n_tiles128][c_runs][CENTRED_CHUNK] (-log2(e) eta_ref, sigmoid(eta_ref))
+    float2* c_refs;         // [n_tiles128][c_runs][CENTRED_CHUNK / 2] observation pairs, each as the floats
+                            // (c0, c1, s0, s1): c = -log2(e) eta_ref, s = sigmoid(eta_ref)
     double* c_part;         // [n_tiles128][c_runs][dk] per-tile parts of c_gref
     int32_t c_runs;         // runs in these arrays (1 when runs == nullptr)
     int32_t c_split;        // CTAs per particle tile (observation split), set by the launcher

@@ -49,7 +49,8 @@
 // so one shared-memory load of an observation pair's reference values serves
 // two particles.  The sigmoid's exponential is the SFU's base-2
 // exponential; one SFU reciprocal of the product (1 + 2^x0)(1 + 2^x1) serves
-// a pair of observations.
+// a pair of observations, and the pair's FMAs and adds run as packed FP32x2
+// instructions.
 //
 // Clusters.  A tile's observations may be split over a cluster of k CTAs
 // (k = 1, 2, 4 or 8, fixed by the tile count and the SM count, so that the
@@ -470,18 +471,28 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     // One SFU reciprocal serves both observations of a pair:
                     // 1 / q0 = q1 / (q0 q1), 1 / q1 = q0 / (q0 q1), with the
                     // exponents clamped so that q0 q1 < 2^121 (a sigmoid below
-                    // 2^-60 is then taken as 2^-60, i.e. zero here).
+                    // 2^-60 is then taken as 2^-60, i.e. zero here).  cs holds
+                    // the pair's (c0, c1, s0, s1); the exponents, 1 + 2^x and
+                    // the residuals are packed pair operations (each lane
+                    // rounded as its scalar form), the sum taken as (q1, q0)
+                    // so that it multiplies -1 / (q0 q1) into (r0, r1) as is.
                     auto res_pair = [&](uint32_t e0, uint32_t e1, const float4& cs) -> uint32_t {
                         const float v0f = __uint_as_float(e0), v1f = __uint_as_float(e1);
                         float r0, r1;
                         if (LOGIT) {
-                            const float x0 = fminf(fmaf(kneg, v0f, cs.x), C_X_MAX);
-                            const float x1 = fminf(fmaf(kneg, v1f, cs.z), C_X_MAX);
-                            const float q0 = 1.0f + tc::ex2_approx(x0);
-                            const float q1 = 1.0f + tc::ex2_approx(x1);
+                            float x0, x1;
+                            tc::f32x2_unpack(tc::f32x2_fma(tc::f32x2_pack(kneg, kneg), tc::f32x2_pack(v0f, v1f),
+                                                           tc::f32x2_pack(cs.x, cs.y)),
+                                             x0, x1);
+                            x0 = fminf(x0, C_X_MAX);
+                            x1 = fminf(x1, C_X_MAX);
+                            const uint64_t q10 = tc::f32x2_add(
+                                tc::f32x2_pack(tc::ex2_approx(x1), tc::ex2_approx(x0)), tc::f32x2_pack(1.0f, 1.0f));
+                            float q1, q0;
+                            tc::f32x2_unpack(q10, q1, q0);
                             const float rp = tc::rcp_approx(q0 * q1);
-                            r0 = fmaf(-q1, rp, cs.y);
-                            r1 = fmaf(-q0, rp, cs.w);
+                            tc::f32x2_unpack(tc::f32x2_fma(q10, tc::f32x2_pack(-rp, -rp), tc::f32x2_pack(cs.z, cs.w)),
+                                             r0, r1);
                         } else {
                             r0 = -inv_s2 * v0f;
                             r1 = -inv_s2 * v1f;
@@ -491,8 +502,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) traj_centred_kernel(DevModel m, 
                     // this thread forms the residuals of the quarter's lanes
                     // g4, g4 + 8 (first group) and g4 + 16, g4 + 24 (second)
                     // for the observation pairs 8 mm + 2 tig (+1), mm = 0..7,
-                    // of the half: one (c, s) load serves two observations of
-                    // two particles.  Each observation pair's packed residuals
+                    // of the half: one (c0, c1, s0, s1) load serves two
+                    // observations of two particles.  Each observation pair's packed residuals
                     // overwrite already consumed registers: v[2 mm] (lane g4 or
                     // g4 + 16) and v[2 mm + 1] (lane + 8), the order of the
                     // 16x128b store.
@@ -897,7 +908,13 @@ __global__ void __launch_bounds__(128) k_centre_obs(DevModel m, TrajArgs a) {
                 res = ((double)m.y[i] - eta) / (m.h0 * m.h0);
             }
         }
-        if (LOGIT) a.c_refs[((int64_t)c * R + r) * CC + t] = cs;
+        if (LOGIT) {
+            // an observation pair's values as (c0, c1, s0, s1): the
+            // epilogue's packed FMAs take each pair from adjacent registers
+            float* fr = reinterpret_cast<float*>(a.c_refs + ((int64_t)c * R + r) * CC);
+            fr[4 * (t >> 1) + (t & 1)] = cs.x;
+            fr[4 * (t >> 1) + 2 + (t & 1)] = cs.y;
+        }
         rr[t] = res;
         __syncthreads();
         if (t < dk) {
