@@ -478,6 +478,10 @@ def test_flow_rejects_unsupported_configurations():
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 40, 4)), 40, 4, train_precision=2)
     with pytest.raises(RuntimeError):                                                  # no such training precision
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4, train_precision=1)
+    # the kernel-level training gradient: precision FP32 or BF16 only, BF16 with hidden a multiple of 16
+    g_d = torch.empty(B.lib().smc_flow_num_params(10, 40, 4), dtype=torch.float32, device="cuda")
+    assert B.lib().smc_k_flow_loss_grad(10, 40, 4, ptr(g_d), None, None, 0, 0, ptr(g_d), 1, stream()) == B.SMC_E_INVAL
+    assert B.lib().smc_k_flow_loss_grad(10, 40, 4, ptr(g_d), None, None, 0, 0, ptr(g_d), 2, stream()) == B.SMC_E_INVAL
     smp.step()
     with pytest.raises(RuntimeError):                                                  # after the first iteration
         smp.enable_flow(np.zeros(B.lib().smc_flow_num_params(10, 32, 4)), 32, 4)
