@@ -148,6 +148,34 @@ def test_bf16_loss_gradient_near_oracle(D, H, L):
     assert np.median(worst) < 2 * np.sqrt(6 * L) * u, (np.median(worst), max(worst))
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_loss_gradient_at_the_benchmark_size(precision):
+    """The training gradient at the benchmark's shape (the 100-d Gaussian's
+    map: D = 100, H = 128, L = 4, 8192 particles, 256 CTAs and their
+    fixed-order reduction) against the FP64 oracle's full gradient: FP32
+    within 2e-4 of the block scale as at 300 particles (the per-CTA partials
+    add 256 FP32 terms per parameter), BF16 within the chain-length bound of
+    test_bf16_loss_gradient_near_oracle."""
+    D, H, L, N = 100, 128, 4, 8192
+    rng = np.random.default_rng(77)
+    p = _params(D, H, L, seed=3, scale=0.3)
+    th = f32r(rng.standard_normal((N, D)))
+    W = np.full(N, 1.0 / N)
+    _, g_o = oracle.flow_loss_grad(oracle.FlowSpec(D, H, L, p), th, W)
+    g_gpu = _gpu_loss_grad(D, H, L, p, th, W, precision)[0]
+    Dh = D // 2
+    sizes = [H * Dh, H, H * H, H, D * H, D]
+    bound = 2e-4 if precision == 0 else 12 * L * 2.0**-8
+    o = 0
+    for l in range(L):
+        for sz in sizes:
+            go, gg = g_o[o:o + sz], g_gpu[o:o + sz]
+            rel = np.abs(gg - go) / (np.abs(go) + np.sqrt(np.mean(go**2)) + 1e-30)
+            nrm = np.linalg.norm(gg - go) / (np.linalg.norm(go) + 1e-30)
+            assert rel.max() < bound and nrm < bound, (l, sz, rel.max(), nrm, bound)
+            o += sz
+
+
 def test_bf16_training_from_the_identity_map():
     """From a zero last layer the transposed product W3^T c_o is exactly zero
     in BF16 too, so one BF16-trained Adam step moves only W3 and b3, each by
