@@ -296,6 +296,62 @@ def test_centred_iterations_keep_exact_weights():
     smp.close()
 
 
+def test_centred_ten_run_batch_at_full_size_on_sampled_particles():
+    """The batched configuration at full size, in the launch the benchmark
+    times: ten runs of 4096 particles of the n = 1000, D = 25 regression in
+    one centred handle (320 run-uniform tiles).  Per iteration and run the
+    resampling decision, the ancestors and every step count are bit-exact
+    against the oracle; on 24 sampled particles the momenta are the oracle's
+    Philox normals, Delta H equals the oracle's FP64 energy difference at the
+    GPU's own end points to FP32 accuracy (exact weights), and the end points
+    stay close to the oracle's exact-gradient trajectories."""
+    w = rounded_workload(workloads.logistic())
+    run = dict(w["run"])
+    t = oracle_target(w)
+    R, N, D, K = 10, run["n_particles"], w["D"], run["n_iters"]
+    seeds = [5000 + r for r in range(R)]
+    smp = g.Sampler(g.ModelData.from_workload(w), [g.make_config(seed=sd, precision=PREC, **run) for sd in seeds],
+                    stream())
+    pick = np.sort(np.random.default_rng(2).choice(R * N, 24, replace=False))
+    for k in range(1, 4):
+        th_pre = smp.buffer(B.BUF_THETA).T.astype(np.float64)
+        lw_pre = smp.buffer(B.BUF_LOGW)
+        lp_pre_s = smp.buffer(B.BUF_LOGPI)
+        stats = smp.step()
+        W = smp.buffer(B.BUF_W)
+        anc = smp.buffer(B.BUF_ANCESTORS)
+        steps = smp.buffer(B.BUF_STEPS)
+        rs = smp.runstate()
+        src = np.arange(R * N)
+        for r in range(R):
+            sl = slice(r * N, (r + 1) * N)
+            _, ess, _ = oracle.normalise(lw_pre[sl])
+            assert stats[r]["resampled"] == int(ess < 0.5 * N), (k, r)
+            if stats[r]["resampled"]:
+                _, q = oracle.quantise(W[sl])
+                _, a_o = oracle.systematic(q, oracle.resample_r64(seeds[r], k))
+                np.testing.assert_array_equal(anc[sl], a_o)
+                src[sl] = r * N + a_o
+            L = rs[r]["L_last"]
+            S_o = np.array([oracle.step_count(oracle.halton2(j * K + k), L, run["step_size"], run["max_steps"])
+                            for j in range(N)])
+            np.testing.assert_array_equal(steps[sl], S_o)
+        th1 = smp.buffer(B.BUF_THETA).T.astype(np.float64)[pick]
+        p1 = smp.buffer(B.BUF_P_FINAL).T.astype(np.float64)[pick]
+        dH = smp.buffer(B.BUF_DH)[pick]
+        p0 = f32r(np.stack([oracle.normals(seeds[i // N], oracle.TAG_MOM, k, i % N, D) for i in pick]))
+        lp0, _ = oracle.logpi(t, th_pre[src[pick]])
+        np.testing.assert_allclose(lp_pre_s[src[pick]], lp0, rtol=1e-6, atol=1e-6 * np.abs(lp0).max())
+        lp1, _ = oracle.logpi(t, th1)
+        dH_o = (0.5 * (p1**2).sum(1) - lp1) - (0.5 * (p0**2).sum(1) - lp0)
+        tol = 1e-5 * (np.abs(lp1) + np.abs(lp0) + (p1**2).sum(1) + 1.0)
+        assert np.all(np.abs(dH - dH_o) <= tol), (k, np.max(np.abs(dH - dH_o) / tol))
+        th1_o, _, _, _ = oracle.leapfrog(t, th_pre[src[pick]], p0, run["step_size"], steps[pick])
+        rel = np.abs(th1 - th1_o) / (np.abs(th1_o) + np.sqrt(np.mean(th1_o**2)))
+        assert np.median(rel) < 1e-3, (k, np.median(rel))
+    smp.close()
+
+
 def test_centred_batched_runs_equal_single_runs_bit_for_bit():
     """Each run of a batch has its own reference point, so a run gives the
     same bits in a batch as alone."""
