@@ -1552,7 +1552,7 @@ smc_status smc_k_flow_loss_grad(int64_t dim, int32_t hidden, int32_t layers, con
         t.mem.release();
         return SMC_E_NOMEM;
     }
-    t.f.bf16 = 0;
+    t.f.bf16 = 0;   // the fragments serve the training products only
     t.f.train_bf16 = bf16 ? 1 : 0;
     t.f.grad = grad;
     cudaError_t e = flow_refresh(t.f, s);
